@@ -1,0 +1,168 @@
+"""Seeded synthetic inputs for the kinetic Monte Carlo hard-sphere gas.
+
+This module only draws initial particle states and states the physical set-up of
+each workload (box, boundaries, collision diameter, time step).  It holds none of
+the collision-step arithmetic, and both the CUDA library and the CPU oracle
+consume exactly the arrays it returns.
+
+Workloads (all with m = 1 and kT/m = 1 unless stated):
+
+* ``equilibrium_box``: uniform positions in a periodic cube, velocity components
+  i.i.d. N(0, 1).
+* ``piston_tube``: uniform positions in an 8 x 1 x 1 box, periodic in y and z, a
+  reflecting wall at x = 0 and a piston at x = 8 moving inward at u_p.
+* ``spherical_blast``: periodic unit cube with a central sphere of radius 0.1 at 8x
+  the background number density and 100x its temperature.
+
+The hard-sphere mean free path is lambda = 1/(sqrt(2) n sigma) with
+sigma = pi d0^2, so d0 = sqrt(1/(sqrt(2) pi n lambda)).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+PERIODIC = 0
+REFLECT = 1
+
+
+@dataclass
+class Setup:
+    """Physical set-up of one simulation (shared by both implementations)."""
+
+    n: int
+    box: tuple = (1.0, 1.0, 1.0)
+    bc: tuple = (PERIODIC, PERIODIC, PERIODIC)
+    piston_x0: float = 0.0
+    piston_u: float = 0.0
+    d0: float = 0.02
+    dt: float = 0.01
+    seed: int = 1
+    max_rounds: int = 4
+    profile_bins: int = 0
+    profile_every: int = 0
+    profile_range: float = 1.0
+    steps: int = 1
+    name: str = ""
+    extra: dict = field(default_factory=dict)
+
+    def with_(self, **kw) -> "Setup":
+        return replace(self, **kw)
+
+
+def d0_for_mean_free_path(number_density: float, lam: float) -> float:
+    """Collision diameter giving hard-sphere mean free path ``lam``."""
+    sigma = 1.0 / (math.sqrt(2.0) * number_density * lam)
+    return math.sqrt(sigma / math.pi)
+
+
+def _uniform(rng: np.random.Generator, n: int, hi: float) -> np.ndarray:
+    x = rng.random(n) * hi
+    # keep the half-open interval [0, hi) even if the product rounds up
+    return np.minimum(x, np.nextafter(hi, 0.0))
+
+
+def equilibrium_state(n: int, seed: int, L: float = 1.0, sigma_v: float = 1.0):
+    rng = np.random.default_rng(seed)
+    pos = [_uniform(rng, n, L) for _ in range(3)]
+    vel = [rng.standard_normal(n) * sigma_v for _ in range(3)]
+    return pos + vel
+
+
+def tube_state(n: int, seed: int, box=(8.0, 1.0, 1.0)):
+    rng = np.random.default_rng(seed)
+    pos = [_uniform(rng, n, float(box[k])) for k in range(3)]
+    vel = [rng.standard_normal(n) for _ in range(3)]
+    return pos + vel
+
+
+def blast_state(n: int, seed: int, radius: float = 0.1, density_ratio: float = 8.0,
+                temperature_ratio: float = 100.0):
+    """Hot dense sphere at the centre of a periodic unit cube."""
+    rng = np.random.default_rng(seed)
+    vs = 4.0 * math.pi / 3.0 * radius ** 3
+    n_hot = int(math.floor(n * density_ratio * vs / (1.0 + (density_ratio - 1.0) * vs) + 0.5))
+    out = np.empty((3, n))
+
+    def sample(count, inside):
+        got = np.empty((0, 3))
+        while got.shape[0] < count:
+            m = max(1024, int((count - got.shape[0]) * 1.3))
+            p = rng.random((m, 3))
+            p = np.minimum(p, np.nextafter(1.0, 0.0))
+            r2 = ((p - 0.5) ** 2).sum(axis=1)
+            keep = p[(r2 < radius * radius) if inside else (r2 >= radius * radius)]
+            got = np.concatenate([got, keep])
+        return got[:count]
+
+    out[:, :n_hot] = sample(n_hot, True).T
+    out[:, n_hot:] = sample(n - n_hot, False).T
+    sig = np.ones(n)
+    sig[:n_hot] = math.sqrt(temperature_ratio)
+    vel = [rng.standard_normal(n) * sig for _ in range(3)]
+    return [out[0].copy(), out[1].copy(), out[2].copy()] + vel, n_hot
+
+
+# --------------------------------------------------------------------------- #
+# Named workloads
+
+def equilibrium_setup(n: int = 4096, seed: int = 1, L: float = 1.0, d0: float = 0.02,
+                      dt: float = 0.01, steps: int = 200) -> Setup:
+    return Setup(n=n, box=(L, L, L), bc=(PERIODIC,) * 3, d0=d0, dt=dt, seed=seed,
+                 steps=steps, name=f"equilibrium_box_n{n}")
+
+
+def piston_setup(n: int = 1 << 20, seed: int = 2, u_p: float = 2.0, lam: float = 0.02,
+                 steps: int = 2000, box=(8.0, 1.0, 1.0), profile_bins: int = 256,
+                 profile_every: int = 100) -> Setup:
+    vol = box[0] * box[1] * box[2]
+    d0 = d0_for_mean_free_path(n / vol, lam)
+    dt = 0.1 * lam / math.sqrt(3.0)
+    return Setup(n=n, box=tuple(float(b) for b in box), bc=(REFLECT, PERIODIC, PERIODIC),
+                 piston_x0=float(box[0]), piston_u=u_p, d0=d0, dt=dt, seed=seed,
+                 profile_bins=profile_bins, profile_every=profile_every,
+                 profile_range=float(box[0]), steps=steps, name=f"piston_tube_n{n}",
+                 extra={"lambda": lam})
+
+
+def blast_setup(n: int = 1 << 27, seed: int = 3, lam_bg: float = 0.005,
+                steps: int = 500, radius: float = 0.1) -> Setup:
+    vs = 4.0 * math.pi / 3.0 * radius ** 3
+    n_hot = int(math.floor(n * 8.0 * vs / (1.0 + 7.0 * vs) + 0.5))
+    n_bg = (n - n_hot) / (1.0 - vs)
+    d0 = d0_for_mean_free_path(n_bg, lam_bg)
+    dt = 0.05 * lam_bg / 1.0  # v_th of the background read as sqrt(kT/m) = 1
+    return Setup(n=n, box=(1.0, 1.0, 1.0), bc=(PERIODIC,) * 3, d0=d0, dt=dt, seed=seed,
+                 steps=steps, name=f"spherical_blast_n{n}", extra={"n_hot": n_hot})
+
+
+def initial_state(setup: Setup):
+    """Six float64 arrays (x, y, z, vx, vy, vz) in particle-id order."""
+    if setup.name.startswith("equilibrium"):
+        return equilibrium_state(setup.n, setup.seed, setup.box[0])
+    if setup.name.startswith("piston"):
+        return tube_state(setup.n, setup.seed, setup.box)
+    if setup.name.startswith("spherical_blast"):
+        return blast_state(setup.n, setup.seed)[0]
+    raise ValueError(f"unknown workload {setup.name!r}")
+
+
+def ensemble_setups(count: int = 256, seed0: int = 1000, lo: int = 1 << 12, hi: int = 1 << 18,
+                    steps: int = 500):
+    """Batched ensemble: N log-uniform in [lo, hi]; even index an equilibrium box
+    (d0 scaled so that n*sigma stays that of the 4096-particle box), odd index a
+    piston tube with u_p uniform in [1, 3]."""
+    out = []
+    for k in range(count):
+        rng = np.random.default_rng(seed0 + k)
+        n = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+        if k % 2 == 0:
+            s = equilibrium_setup(n=n, seed=seed0 + k, d0=0.02 * math.sqrt(4096.0 / n),
+                                  steps=steps)
+        else:
+            s = piston_setup(n=n, seed=seed0 + k, u_p=float(rng.uniform(1.0, 3.0)),
+                             steps=steps, profile_bins=0, profile_every=0)
+        out.append(s)
+    return out
