@@ -1,0 +1,175 @@
+/*
+ * kmc.h -- C ABI of libkmc, a GB300 (sm_103a) library for the per-time-step
+ * collision step of the kinetic Monte Carlo hard-sphere gas described in
+ * Howell et al., "Parallelization of Kinetic Theory Simulations" (arXiv:1310.3437).
+ *
+ * One time step (Sec. 2 "Initial Simulation Setup" and Sec. 3):
+ *   1. particles are binned into cells (Sec. 2, grid of bins);
+ *   2. every particle finds its closest collision partner by distance of closest
+ *      approach among the particles of its own and the neighbouring cells
+ *      (Sec. 2, the three criteria and the "closer partner replaces" rule);
+ *   3. particles that chose each other collide (Sec. 2, mutual choice), repeated
+ *      over the still-unmatched particles for up to max_rounds rounds;
+ *   4. colliding pairs scatter isotropically in their centre-of-mass frame;
+ *   5. all particles free-stream and the box boundaries are applied (Sec. 2,
+ *      reflective or periodic walls; here also a moving piston).
+ *
+ * Conventions for every entry point:
+ *   - Status: 0 (KMC_OK) or a negative KMC_E* code.  No C++ exception crosses
+ *     this interface.  sim_last_error() gives a message for the last failure.
+ *   - Asynchrony: work is enqueued on the CUDA stream given at creation and the
+ *     call returns before it finishes.  sim_sync() waits and reports device-side
+ *     errors (a buffer that overflowed, an exhausted random draw).
+ *   - Pointers: arrays passed in or out may be device memory or host memory
+ *     (pinned or pageable); the library copies with cudaMemcpyDefault.  The caller
+ *     keeps ownership of everything it passes.  The library owns and frees its
+ *     own buffers in sim_destroy / sim_group_destroy.
+ *   - Layout: particle arrays are structure-of-arrays, indexed by particle id
+ *     0..n-1.  Positions and velocities are IEEE-754 binary64.
+ */
+#ifndef KMC_H
+#define KMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define KMC_OK 0
+#define KMC_EINVAL (-1)    /* bad argument or parameter */
+#define KMC_ENOMEM (-2)    /* device allocation failed */
+#define KMC_ECUDA (-3)     /* a CUDA runtime call failed */
+#define KMC_ETIMEOUT (-4)  /* a bounded device-side wait ran out */
+#define KMC_EOVERFLOW (-5) /* a buffer capacity was exceeded and could not grow */
+#define KMC_ESTATE (-6)    /* call not allowed in the current state */
+#define KMC_ERANDOM (-7)   /* 128 rejected sphere-point draws (probability ~1e-43) */
+
+/* ---- boundary kinds per axis (Sec. 2: reflective or periodic box) -------- */
+#define KMC_PERIODIC 0
+#define KMC_REFLECT 1  /* walls at 0 and at the box end; on x the end wall may move */
+
+/* ---- precision of the pair tests --------------------------------------- */
+#define KMC_FP64 0          /* every pair test in binary64 */
+#define KMC_GUARDED_FP32 1  /* binary32 pre-tests with proven guard bands, binary64
+                               re-check of the survivors: identical pair lists */
+
+/* ---- observables (sim_observe) ------------------------------------------ */
+#define KMC_OBS_STATE 1    /* 6 x n binary64 (x,y,z,vx,vy,vz) then n uint32 last
+                              partner id (KMC_NONE if none): 52 n bytes */
+#define KMC_OBS_PARTNERS 2 /* n uint32: partner id of each particle in the last
+                              completed step, KMC_NONE if it did not collide */
+#define KMC_OBS_COUNTS 3   /* kmc_step_counts records of the steps completed since
+                              the previous COUNTS call (oldest first) */
+#define KMC_OBS_PROFILES 4 /* profile snapshots taken since the previous PROFILES
+                              call: per snapshot, profile_bins x 7 binary64 */
+#define KMC_OBS_EDGES 5    /* candidate pairs of the last completed step as uint32
+                              (id_lo, id_hi) pairs, unordered list */
+#define KMC_OBS_STEP 6     /* one uint64: absolute index of the next step */
+
+#define KMC_NONE 0xFFFFFFFFu
+
+/* Parameters of one simulation.  Zero-initialise, then set the fields. */
+typedef struct kmc_params {
+  uint32_t n;              /* particles, >= 1 */
+  uint32_t flags;          /* reserved, must be 0 */
+  double box[3];           /* box extents L_x, L_y, L_z; particles live in [0, L) */
+  int32_t bc[3];           /* KMC_PERIODIC or KMC_REFLECT per axis */
+  int32_t max_rounds;      /* mutual-choice rounds per step, 1..4 (0 means 4) */
+  double piston_x0;        /* reflecting x axis: upper wall at piston_x0 - piston_u*t */
+  double piston_u;         /*   (set piston_x0 = box[0], piston_u = 0 for a fixed wall) */
+  double d0;               /* collision diameter (effective radius sum), > 0 */
+  double dt;               /* time step, > 0 */
+  uint64_t seed;           /* Philox4x32-10 key of the scatter directions */
+  uint64_t step0;          /* absolute index of the first step (resume) */
+  int32_t precision;       /* KMC_FP64 or KMC_GUARDED_FP32 */
+  int32_t profile_bins;    /* x-profile bins (0 = no profiles) */
+  int32_t profile_every;   /* profile after every step s with (s+1) % every == 0 */
+  int32_t stencil;         /* cells per search radius: 1 (27-cell search) or 2
+                              (125 half-size cells); 0 means 1.  Never changes results. */
+  double profile_range;    /* profiles cover x in [0, profile_range) */
+  double cell_scale;       /* >= 1: cell size multiplier (occupancy knob); 0 means 1.
+                              Never changes results. */
+  uint32_t edge_cap;       /* initial candidate-pair capacity (0: automatic); grows on
+                              demand at sim_sync */
+  uint32_t history_cap;    /* step records kept for KMC_OBS_COUNTS (0: 4096) */
+  uint32_t profile_cap;    /* profile snapshots kept for KMC_OBS_PROFILES (0: 64) */
+  uint32_t reserved;
+} kmc_params;
+
+/* One record per completed step (KMC_OBS_COUNTS). */
+typedef struct kmc_step_counts {
+  uint64_t step;            /* absolute step index */
+  uint32_t collisions;      /* colliding pairs */
+  uint32_t edges;           /* candidate pairs (before matching) */
+  uint32_t round_pairs[4];  /* pairs matched in rounds 1..4 */
+  uint32_t survivors;       /* pairs that passed the search pre-tests */
+  uint32_t cells;           /* cells of the search grid */
+  uint64_t pair_tests;      /* pair tests done by the search */
+} kmc_step_counts;
+
+typedef struct kmc_sim kmc_sim;
+typedef struct kmc_group kmc_group;
+
+/* Create a simulation from an initial state (Sec. 2: particles initialised in a
+ * box).  x..vz: n binary64 each, id order, host or device.  last: n uint32 last
+ * collision partner ids or NULL (none).  stream: a cudaStream_t (NULL = the
+ * legacy default stream).  The arrays are copied; the caller keeps them.
+ * Errors: KMC_EINVAL (bad parameter, particle outside the box), KMC_ENOMEM,
+ * KMC_ECUDA.  On error *out is NULL. */
+int sim_create(const kmc_params* p, const double* x, const double* y, const double* z,
+               const double* vx, const double* vy, const double* vz, const uint32_t* last,
+               void* stream, kmc_sim** out);
+
+/* Enqueue nsteps time steps (Sec. 2: sort, detect, collide, stream, boundaries).
+ * Errors: KMC_ESTATE if the simulation belongs to a group, KMC_ECUDA. */
+int sim_step(kmc_sim* s, uint32_t nsteps);
+
+/* Wait for the enqueued steps.  If a candidate-pair buffer overflowed, it is grown
+ * and the unfinished steps are re-run from the last completed step (results do not
+ * change).  Errors: KMC_ERANDOM, KMC_EOVERFLOW, KMC_ENOMEM, KMC_ECUDA. */
+int sim_sync(kmc_sim* s);
+
+/* Copy an observable (KMC_OBS_*) into dst (host or device, dst_bytes long).  The
+ * copy is ordered after the enqueued steps; for a host dst the call waits.
+ * Returns the number of items written (records, snapshots, pairs, or 1) or a
+ * negative status: KMC_EINVAL (unknown observable, dst too small). */
+int64_t sim_observe(kmc_sim* s, int what, void* dst, size_t dst_bytes);
+
+/* Free the simulation (waits for its stream).  NULL is accepted. */
+int sim_destroy(kmc_sim* s);
+
+/* Message of the last failure on s (or of the last failed sim_create if s is
+ * NULL).  Never NULL. */
+const char* sim_last_error(const kmc_sim* s);
+
+/* Device bytes sim_create would allocate for these parameters (admission control). */
+size_t sim_bytes_required(const kmc_params* p);
+
+/* ---- batching ------------------------------------------------------------ */
+/* A group steps many simulations of uneven size with one launch per kernel for
+ * all of them; the per-step launch sequence is captured in a CUDA graph.  All
+ * members must share precision and stencil.  Members keep their own state and can
+ * still be observed; sim_step on a member returns KMC_ESTATE.
+ * Errors: KMC_EINVAL (empty, mixed precision, member already grouped). */
+int sim_group_create(kmc_sim* const* sims, uint32_t count, void* stream, kmc_group** out);
+/* Add or remove a member between steps (continuous batching). */
+int sim_group_add(kmc_group* g, kmc_sim* s);
+int sim_group_remove(kmc_group* g, kmc_sim* s);
+/* Give member s a budget of nsteps more steps; a member with no steps left is
+ * skipped by the group's launches. */
+int sim_group_budget(kmc_group* g, kmc_sim* s, uint32_t nsteps);
+/* Enqueue nsteps group steps (each member advances while its budget lasts). */
+int sim_group_step(kmc_group* g, uint32_t nsteps);
+/* Steps left in member s's budget (waits for the group's stream). */
+int64_t sim_group_steps_left(kmc_group* g, kmc_sim* s);
+int sim_group_sync(kmc_group* g);
+int sim_group_destroy(kmc_group* g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KMC_H */

@@ -1,0 +1,809 @@
+// kmc_api.cu -- host side of the C ABI declared in include/kmc.h.
+//
+// A simulation owns its device buffers and a device descriptor (SimDev).  Stepping
+// goes through a LaunchPlan: a device table of descriptors plus tile prefixes,
+// built for one simulation (sim_step) or for a group (sim_group_step).  The kernel
+// sequence of one step is captured once in a CUDA graph and replayed per step; the
+// step index, cell grid and counters live on the device, so replays need no host
+// work.  Device-side failures set status bits that every later kernel of the
+// simulation checks; sim_sync reads them, grows an overflowed pair buffer and
+// re-runs the steps that were skipped (the state of the last completed step is
+// untouched because the sort writes the other buffer).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kmc_internal.cuh"
+
+using namespace kmc;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Plan {
+  LaunchPlan L{};
+  SimDev** d_table = nullptr;
+  uint32_t* d_pre = nullptr;  // one allocation for the four prefix arrays + scratch
+  cudaGraphExec_t graph = nullptr;
+  bool graph_tried = false;
+  int precision = 0, K = 1, max_rounds = 4;
+  bool has_profiles = false;
+};
+
+int g_num_sms = 0;
+
+int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      g_num_sms = v;
+    else
+      g_num_sms = 152;
+  }
+  return g_num_sms;
+}
+
+}  // namespace
+
+struct kmc_group;
+
+struct kmc_sim {
+  kmc_params p{};
+  SimDev h{};            // host mirror of the descriptor (parameters and pointers)
+  SimDev* d = nullptr;   // device descriptor
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  kmc_group* group = nullptr;
+  Plan solo;
+  bool solo_built = false;
+  std::vector<void*> allocs;
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  uint64_t hist_read = 0, prof_read = 0;
+  std::string err;
+};
+
+struct kmc_group {
+  std::vector<kmc_sim*> members;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Plan plan;
+  bool built = false;
+  std::string err;
+};
+
+namespace {
+
+#define KCHECK(call, who)                                                        \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      (who) = std::string(#call) + ": " + cudaGetErrorString(e_);                \
+      return KMC_ECUDA;                                                          \
+    }                                                                            \
+  } while (0)
+
+uint32_t ceil_div(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); }
+
+uint32_t default_edge_cap(uint32_t n) { return std::max<uint32_t>(4096u, n / 4u + 1024u); }
+uint32_t default_cell_cap(uint32_t n) { return 2u * n + 4096u; }
+
+struct Sizes {
+  uint32_t n, cell_cap, edge_cap, hist_cap, prof_cap, bins;
+  bool fp32;
+};
+
+Sizes sizes_of(const kmc_params& p) {
+  Sizes z;
+  z.n = p.n;
+  z.cell_cap = default_cell_cap(p.n);
+  z.edge_cap = p.edge_cap ? p.edge_cap : default_edge_cap(p.n);
+  z.hist_cap = p.history_cap ? p.history_cap : 4096u;
+  z.prof_cap = p.profile_cap ? p.profile_cap : 64u;
+  z.bins = p.profile_bins > 0 ? (uint32_t)p.profile_bins : 0u;
+  z.fp32 = p.precision == KMC_GUARDED_FP32;
+  return z;
+}
+
+size_t edge_bytes(uint32_t cap) {
+  return (size_t)cap * (sizeof(uint2) + 2 * sizeof(double) + sizeof(uint2)) +
+         (size_t)2 * cap * 3 * sizeof(uint32_t);
+}
+
+size_t bytes_for(const Sizes& z) {
+  size_t n = z.n;
+  size_t b = 0;
+  b += 2 * 6 * n * sizeof(double) + 2 * 2 * n * sizeof(uint32_t);  // state, double-buffered
+  if (z.fp32) b += n * (sizeof(float4) + sizeof(float2));
+  b += 3 * n * sizeof(uint32_t);                                      // key, rank, skey
+  b += 2 * ((size_t)z.cell_cap + 1) * sizeof(uint32_t);               // cell count / start
+  b += n * sizeof(uint32_t) + (n + 1) * sizeof(uint32_t);             // deg, off
+  b += 4 * n * sizeof(uint32_t);                                      // best, best_e, partner, medge
+  b += edge_bytes(z.edge_cap);
+  b += (size_t)z.hist_cap * sizeof(kmc_step_counts);
+  if (z.bins) b += (size_t)z.prof_cap * z.bins * kProfQ * sizeof(long long) + z.prof_cap * sizeof(uint64_t);
+  b += sizeof(SimDev);
+  return b;
+}
+
+int validate(const kmc_params* p, std::string& err) {
+  if (!p) { err = "params is NULL"; return KMC_EINVAL; }
+  if (p->n == 0) { err = "n must be >= 1"; return KMC_EINVAL; }
+  if (p->flags != 0) { err = "flags must be 0"; return KMC_EINVAL; }
+  for (int a = 0; a < 3; ++a) {
+    if (!(p->box[a] > 0.0)) { err = "box extents must be > 0"; return KMC_EINVAL; }
+    if (p->bc[a] != KMC_PERIODIC && p->bc[a] != KMC_REFLECT) { err = "bad boundary kind"; return KMC_EINVAL; }
+  }
+  if (!(p->d0 > 0.0) || !(p->dt > 0.0)) { err = "d0 and dt must be > 0"; return KMC_EINVAL; }
+  if (p->max_rounds < 0 || p->max_rounds > 4) { err = "max_rounds must be in 0..4"; return KMC_EINVAL; }
+  if (p->precision != KMC_FP64 && p->precision != KMC_GUARDED_FP32) { err = "bad precision"; return KMC_EINVAL; }
+  if (p->stencil < 0 || p->stencil > 2) { err = "stencil must be 0, 1 or 2"; return KMC_EINVAL; }
+  if (p->profile_bins < 0 || p->profile_bins > 256) { err = "profile_bins must be in 0..256"; return KMC_EINVAL; }
+  if (p->profile_every < 0) { err = "profile_every must be >= 0"; return KMC_EINVAL; }
+  if (p->profile_bins > 0 && !(p->profile_range > 0.0)) { err = "profile_range must be > 0"; return KMC_EINVAL; }
+  if (p->cell_scale != 0.0 && !(p->cell_scale >= 1.0)) { err = "cell_scale must be 0 or >= 1"; return KMC_EINVAL; }
+  if (p->bc[0] == KMC_REFLECT && !(p->piston_x0 > 0.0)) { err = "reflecting x axis needs piston_x0 > 0"; return KMC_EINVAL; }
+  if (p->n > 0x7FFFFFFFu) { err = "n too large"; return KMC_EINVAL; }
+  return KMC_OK;
+}
+
+bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+int dalloc(kmc_sim* s, T** out, size_t count) {
+  void* ptr = nullptr;
+  size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+  cudaError_t e = cudaMalloc(&ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    s->err = std::string("cudaMalloc failed: ") + cudaGetErrorString(e);
+    return KMC_ENOMEM;
+  }
+  s->allocs.push_back(ptr);
+  *out = (T*)ptr;
+  return KMC_OK;
+}
+
+void dfree(kmc_sim* s, void* ptr) {
+  if (!ptr) return;
+  auto it = std::find(s->allocs.begin(), s->allocs.end(), ptr);
+  if (it != s->allocs.end()) s->allocs.erase(it);
+  cudaFree(ptr);
+}
+
+int alloc_edges(kmc_sim* s, uint32_t cap) {
+  int rc;
+  SimDev& h = s->h;
+  if ((rc = dalloc(s, &h.edge, cap))) return rc;
+  if ((rc = dalloc(s, &h.e_d2, cap))) return rc;
+  if ((rc = dalloc(s, &h.e_t, cap))) return rc;
+  if ((rc = dalloc(s, &h.e_slot, cap))) return rc;
+  if ((rc = dalloc(s, &h.adj_owner, 2 * (size_t)cap))) return rc;
+  if ((rc = dalloc(s, &h.adj_other, 2 * (size_t)cap))) return rc;
+  if ((rc = dalloc(s, &h.adj_edge, 2 * (size_t)cap))) return rc;
+  h.edge_cap = cap;
+  return KMC_OK;
+}
+
+void free_edges(kmc_sim* s) {
+  SimDev& h = s->h;
+  void* ptrs[] = {h.edge, h.e_d2, h.e_t, h.e_slot, h.adj_owner, h.adj_other, h.adj_edge};
+  for (void* q : ptrs) dfree(s, q);
+  h.edge = nullptr; h.e_d2 = nullptr; h.e_t = nullptr; h.e_slot = nullptr;
+  h.adj_owner = h.adj_other = h.adj_edge = nullptr;
+}
+
+// ---- plans ----------------------------------------------------------------- //
+void free_plan(Plan& P) {
+  if (P.graph) cudaGraphExecDestroy(P.graph);
+  if (P.d_table) cudaFree(P.d_table);
+  if (P.d_pre) cudaFree(P.d_pre);
+  P = Plan();
+}
+
+int build_plan(Plan& P, const std::vector<kmc_sim*>& sims, cudaStream_t st, std::string& err) {
+  free_plan(P);
+  int m = (int)sims.size();
+  std::vector<uint32_t> pt(m + 1), sn(m + 1), sc(m + 1), pr(m + 1);
+  std::vector<SimDev*> table(m);
+  pt[0] = sn[0] = sc[0] = pr[0] = 0;
+  P.precision = sims[0]->h.precision;
+  P.K = sims[0]->h.K;
+  P.max_rounds = 0;
+  for (int k = 0; k < m; ++k) {
+    const SimDev& h = sims[k]->h;
+    table[k] = sims[k]->d;
+    pt[k + 1] = pt[k] + ceil_div(h.n, kTile);
+    sn[k + 1] = sn[k] + ceil_div((uint64_t)h.n + 1, kScanTile);
+    sc[k + 1] = sc[k] + ceil_div((uint64_t)h.cell_cap + 1, kScanTile);
+    pr[k + 1] = pr[k] + ceil_div(h.n, kProfTile);
+    P.max_rounds = std::max(P.max_rounds, h.max_rounds);
+    if (h.profile_bins > 0) P.has_profiles = true;
+  }
+  size_t scratch = std::max(sn[m], sc[m]) + 1;
+  size_t words = 4 * (size_t)(m + 1) + scratch;
+  if (cudaMalloc(&P.d_table, sizeof(SimDev*) * m) != cudaSuccess ||
+      cudaMalloc(&P.d_pre, words * sizeof(uint32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    err = "cudaMalloc failed for the launch plan";
+    free_plan(P);
+    return KMC_ENOMEM;
+  }
+  std::vector<uint32_t> host(4 * (m + 1));
+  std::copy(pt.begin(), pt.end(), host.begin());
+  std::copy(sn.begin(), sn.end(), host.begin() + (m + 1));
+  std::copy(sc.begin(), sc.end(), host.begin() + 2 * (m + 1));
+  std::copy(pr.begin(), pr.end(), host.begin() + 3 * (m + 1));
+  KCHECK(cudaMemcpyAsync(P.d_table, table.data(), sizeof(SimDev*) * m, cudaMemcpyHostToDevice, st), err);
+  KCHECK(cudaMemcpyAsync(P.d_pre, host.data(), host.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st), err);
+  KCHECK(cudaStreamSynchronize(st), err);
+  LaunchPlan& L = P.L;
+  L.b.sims = P.d_table;
+  L.b.nsims = m;
+  L.b.ptile = P.d_pre;
+  L.b.stile_n = P.d_pre + (m + 1);
+  L.b.stile_c = P.d_pre + 2 * (m + 1);
+  L.b.prtile = P.d_pre + 3 * (m + 1);
+  L.b.tile_sums = P.d_pre + 4 * (m + 1);
+  L.ptiles = pt[m];
+  L.stiles_n = sn[m];
+  L.stiles_c = sc[m];
+  L.prtiles = pr[m];
+  L.edge_blocks = 2 * num_sms();
+  return KMC_OK;
+}
+
+void enqueue_step(const Plan& P, cudaStream_t st) {
+  launch_sort(P.L, st);
+  launch_search(P.L, P.precision, P.K, st);
+  launch_match(P.L, P.max_rounds, st);
+  launch_push(P.L, st);
+}
+
+// Replay the captured step nsteps times (capture on first use; plain launches if
+// the stream cannot be captured).
+int run_steps(Plan& P, cudaStream_t st, uint64_t nsteps, std::string& err) {
+  if (!P.graph_tried) {
+    P.graph_tried = true;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      enqueue_step(P, st);
+      cudaError_t e = cudaStreamEndCapture(st, &graph);
+      if (e == cudaSuccess && graph) {
+        if (cudaGraphInstantiate(&P.graph, graph, 0) != cudaSuccess) P.graph = nullptr;
+        cudaGraphDestroy(graph);
+      }
+    }
+    cudaGetLastError();
+  }
+  for (uint64_t i = 0; i < nsteps; ++i) {
+    if (P.graph) {
+      KCHECK(cudaGraphLaunch(P.graph, st), err);
+    } else {
+      enqueue_step(P, st);
+    }
+  }
+  KCHECK(cudaGetLastError(), err);
+  return KMC_OK;
+}
+
+int ensure_solo(kmc_sim* s) {
+  if (s->solo_built) return KMC_OK;
+  std::vector<kmc_sim*> one{s};
+  int rc = build_plan(s->solo, one, s->stream, s->err);
+  if (rc) return rc;
+  s->solo_built = true;
+  return KMC_OK;
+}
+
+int read_dyn(kmc_sim* s, Dyn* out, cudaStream_t st) {
+  KCHECK(cudaMemcpyAsync(out, &s->d->d, sizeof(Dyn), cudaMemcpyDeviceToHost, st), s->err);
+  KCHECK(cudaStreamSynchronize(st), s->err);
+  return KMC_OK;
+}
+
+int write_dyn(kmc_sim* s, const Dyn* in, cudaStream_t st) {
+  KCHECK(cudaMemcpyAsync(&s->d->d, in, sizeof(Dyn), cudaMemcpyHostToDevice, st), s->err);
+  KCHECK(cudaStreamSynchronize(st), s->err);
+  return KMC_OK;
+}
+
+// Grow the pair buffer of a simulation whose step overflowed it and clear the
+// error; the step is re-run later from the unchanged state.
+int recover_overflow(kmc_sim* s, Dyn& dy, cudaStream_t st) {
+  uint64_t need = (uint64_t)dy.n_raw + dy.n_raw / 4 + 1024;
+  uint64_t cap = std::max<uint64_t>(2ull * s->h.edge_cap, need);
+  if (cap > 0x7FFFFFFFull) cap = 0x7FFFFFFFull;
+  if (cap <= s->h.edge_cap) {
+    s->err = "candidate-pair buffer cannot grow further";
+    return KMC_EOVERFLOW;
+  }
+  KCHECK(cudaStreamSynchronize(st), s->err);
+  free_edges(s);
+  int rc = alloc_edges(s, (uint32_t)cap);
+  if (rc) return rc;
+  KCHECK(cudaMemcpyAsync(s->d, &s->h, offsetof(SimDev, d), cudaMemcpyHostToDevice, st), s->err);
+  dy.status = 0;
+  dy.n_raw = 0;
+  dy.n_edges = 0;
+  for (int r = 0; r < 4; ++r) dy.round_pairs[r] = 0;
+  dy.pair_tests = 0;
+  // the push of the failed step never ran: keep the bound of the previous step
+  dy.vmax2_acc = 0;
+  return write_dyn(s, &dy, st);
+}
+
+int status_code(uint32_t status, std::string& err) {
+  if (status & ST_RANDOM) { err = "128 rejected sphere-point draws"; return KMC_ERANDOM; }
+  if (status & ST_CELL_OVERFLOW) { err = "cell grid exceeds capacity"; return KMC_EOVERFLOW; }
+  if (status & ST_EDGE_OVERFLOW) { err = "candidate-pair buffer overflow"; return KMC_EOVERFLOW; }
+  return KMC_OK;
+}
+
+int stage_reserve(kmc_sim* s, size_t bytes) {
+  if (s->stage_bytes >= bytes) return KMC_OK;
+  if (s->stage) {
+    cudaStreamSynchronize(s->stream);
+    dfree(s, s->stage);
+    s->stage = nullptr;
+    s->stage_bytes = 0;
+  }
+  void* p = nullptr;
+  int rc = dalloc(s, (char**)&p, bytes);
+  if (rc) return rc;
+  s->stage = p;
+  s->stage_bytes = bytes;
+  return KMC_OK;
+}
+
+cudaStream_t sim_work_stream(kmc_sim* s) { return s->group ? s->group->stream : s->stream; }
+
+}  // namespace
+
+// =========================================================================== //
+extern "C" {
+
+size_t sim_bytes_required(const kmc_params* p) {
+  std::string e;
+  if (validate(p, e)) return 0;
+  return bytes_for(sizes_of(*p));
+}
+
+const char* sim_last_error(const kmc_sim* s) {
+  if (!s) return g_create_error.c_str();
+  return s->err.c_str();
+}
+
+int sim_destroy(kmc_sim* s) {
+  if (!s) return KMC_OK;
+  if (s->group) sim_group_remove(s->group, s);
+  cudaStreamSynchronize(s->stream);
+  free_plan(s->solo);
+  for (void* q : s->allocs) cudaFree(q);
+  s->allocs.clear();
+  if (s->d) cudaFree(s->d);
+  if (s->own_stream) cudaStreamDestroy(s->stream);
+  delete s;
+  return KMC_OK;
+}
+
+int sim_create(const kmc_params* p, const double* x, const double* y, const double* z,
+               const double* vx, const double* vy, const double* vz, const uint32_t* last,
+               void* stream, kmc_sim** out) {
+  if (out) *out = nullptr;
+  g_create_error.clear();
+  int rc = validate(p, g_create_error);
+  if (rc) return rc;
+  if (!out || !x || !y || !z || !vx || !vy || !vz) {
+    g_create_error = "NULL array or output pointer";
+    return KMC_EINVAL;
+  }
+  kmc_sim* s = new (std::nothrow) kmc_sim();
+  if (!s) { g_create_error = "out of host memory"; return KMC_ENOMEM; }
+  s->p = *p;
+  if (stream) {
+    s->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      g_create_error = "cudaStreamCreate failed";
+      delete s;
+      return KMC_ECUDA;
+    }
+    s->own_stream = true;
+  }
+  Sizes zs = sizes_of(*p);
+  SimDev& h = s->h;
+  h.n = p->n;
+  for (int a = 0; a < 3; ++a) { h.bc[a] = p->bc[a]; h.box[a] = p->box[a]; }
+  h.max_rounds = p->max_rounds ? p->max_rounds : 4;
+  h.precision = p->precision;
+  h.profile_bins = (int32_t)zs.bins;
+  h.profile_every = p->profile_every;
+  h.K = p->stencil ? p->stencil : 1;
+  h.piston_x0 = p->bc[0] == KMC_REFLECT ? p->piston_x0 : p->box[0];
+  h.piston_u = p->bc[0] == KMC_REFLECT ? p->piston_u : 0.0;
+  h.d0 = p->d0;
+  h.dt = p->dt;
+  h.d0sq = p->d0 * p->d0;
+  h.profile_range = p->profile_range;
+  h.cell_scale = p->cell_scale >= 1.0 ? p->cell_scale : 1.0;
+  h.seed = p->seed;
+  h.cell_cap = zs.cell_cap;
+  h.hist_cap = zs.hist_cap;
+  h.prof_cap = zs.prof_cap;
+  size_t n = p->n;
+  auto fail = [&](int code) {
+    g_create_error = s->err;
+    sim_destroy(s);
+    return code;
+  };
+  if (cudaMalloc(&s->d, sizeof(SimDev)) != cudaSuccess) {
+    cudaGetLastError();
+    s->err = "cudaMalloc failed for the descriptor";
+    return fail(KMC_ENOMEM);
+  }
+  for (int b = 0; b < 2; ++b) {
+    for (int a = 0; a < 3; ++a) {
+      if ((rc = dalloc(s, &h.x[b][a], n))) return fail(rc);
+      if ((rc = dalloc(s, &h.v[b][a], n))) return fail(rc);
+    }
+    if ((rc = dalloc(s, &h.id[b], n))) return fail(rc);
+    if ((rc = dalloc(s, &h.last[b], n))) return fail(rc);
+  }
+  if (zs.fp32) {
+    if ((rc = dalloc(s, &h.mir_a, n))) return fail(rc);
+    if ((rc = dalloc(s, &h.mir_b, n))) return fail(rc);
+  }
+  if ((rc = dalloc(s, &h.key, n))) return fail(rc);
+  if ((rc = dalloc(s, &h.rank, n))) return fail(rc);
+  if ((rc = dalloc(s, &h.skey, n))) return fail(rc);
+  if ((rc = dalloc(s, &h.cell_count, (size_t)zs.cell_cap + 1))) return fail(rc);
+  if ((rc = dalloc(s, &h.cell_start, (size_t)zs.cell_cap + 1))) return fail(rc);
+  if ((rc = dalloc(s, &h.deg, n))) return fail(rc);
+  if ((rc = dalloc(s, &h.off, n + 1))) return fail(rc);
+  if ((rc = dalloc(s, &h.best, n))) return fail(rc);
+  if ((rc = dalloc(s, &h.best_e, n))) return fail(rc);
+  if ((rc = dalloc(s, &h.partner, n))) return fail(rc);
+  if ((rc = dalloc(s, &h.medge, n))) return fail(rc);
+  if ((rc = alloc_edges(s, zs.edge_cap))) return fail(rc);
+  if ((rc = dalloc(s, &h.hist, zs.hist_cap))) return fail(rc);
+  if (zs.bins) {
+    if ((rc = dalloc(s, &h.prof_acc, (size_t)zs.prof_cap * zs.bins * kProfQ))) return fail(rc);
+    if ((rc = dalloc(s, &h.prof_step, zs.prof_cap))) return fail(rc);
+  }
+  cudaStream_t st = s->stream;
+  auto ck = [&](cudaError_t e) {
+    if (e != cudaSuccess) {
+      s->err = std::string("CUDA error during creation: ") + cudaGetErrorString(e);
+      return false;
+    }
+    return true;
+  };
+  bool ok = true;
+  const double* src[6] = {x, y, z, vx, vy, vz};
+  for (int a = 0; a < 3 && ok; ++a) {
+    ok = ck(cudaMemcpyAsync(h.x[0][a], src[a], n * sizeof(double), cudaMemcpyDefault, st)) &&
+         ck(cudaMemcpyAsync(h.v[0][a], src[3 + a], n * sizeof(double), cudaMemcpyDefault, st));
+  }
+  std::vector<uint32_t> ids(n);
+  for (size_t i = 0; i < n; ++i) ids[i] = (uint32_t)i;
+  ok = ok && ck(cudaMemcpyAsync(h.id[0], ids.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+  if (last) ok = ok && ck(cudaMemcpyAsync(h.last[0], last, n * sizeof(uint32_t), cudaMemcpyDefault, st));
+  else ok = ok && ck(cudaMemsetAsync(h.last[0], 0xFF, n * sizeof(uint32_t), st));
+  ok = ok && ck(cudaMemsetAsync(h.cell_count, 0, ((size_t)zs.cell_cap + 1) * sizeof(uint32_t), st));
+  ok = ok && ck(cudaMemsetAsync(h.partner, 0xFF, n * sizeof(uint32_t), st));
+  ok = ok && ck(cudaMemsetAsync(h.e_slot, 0xFF, (size_t)h.edge_cap * sizeof(uint2), st));
+  if (zs.bins) ok = ok && ck(cudaMemsetAsync(h.prof_acc, 0, (size_t)zs.prof_cap * zs.bins * kProfQ * sizeof(long long), st));
+  if (!ok) return fail(KMC_ECUDA);
+  Dyn dy;
+  std::memset(&dy, 0, sizeof(dy));
+  dy.step = p->step0;
+  dy.steps_left = 0;
+  dy.parity = 0;
+  if (!ck(cudaMemcpyAsync(s->d, &h, sizeof(SimDev), cudaMemcpyHostToDevice, st))) return fail(KMC_ECUDA);
+  if (!ck(cudaMemcpyAsync(&s->d->d, &dy, sizeof(Dyn), cudaMemcpyHostToDevice, st))) return fail(KMC_ECUDA);
+  // positions must lie in the box, velocities must be finite
+  uint32_t* bad = nullptr;
+  if ((rc = dalloc(s, &bad, 1))) return fail(rc);
+  uint32_t nbad = 0;
+  if (!ck(cudaMemsetAsync(bad, 0, sizeof(uint32_t), st))) return fail(KMC_ECUDA);
+  launch_validate(s->d, p->n, bad, st);
+  if (!ck(cudaMemcpyAsync(&nbad, bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) ||
+      !ck(cudaStreamSynchronize(st)))
+    return fail(KMC_ECUDA);
+  dfree(s, bad);
+  if (nbad) {
+    s->err = std::to_string(nbad) + " particle(s) outside the box or with non-finite velocity";
+    return fail(KMC_EINVAL);
+  }
+  if ((rc = ensure_solo(s))) return fail(rc);
+  launch_init_grid(s->solo.L, st);
+  if (!ck(cudaGetLastError()) || !ck(cudaStreamSynchronize(st))) return fail(KMC_ECUDA);
+  *out = s;
+  return KMC_OK;
+}
+
+int sim_step(kmc_sim* s, uint32_t nsteps) {
+  if (!s) return KMC_EINVAL;
+  if (s->group) { s->err = "simulation belongs to a group"; return KMC_ESTATE; }
+  if (nsteps == 0) return KMC_OK;
+  int rc = ensure_solo(s);
+  if (rc) return rc;
+  launch_add_steps(s->d, nsteps, s->stream);
+  return run_steps(s->solo, s->stream, nsteps, s->err);
+}
+
+int sim_sync(kmc_sim* s) {
+  if (!s) return KMC_EINVAL;
+  cudaStream_t st = sim_work_stream(s);
+  for (int attempt = 0; attempt < 64; ++attempt) {
+    KCHECK(cudaStreamSynchronize(st), s->err);
+    Dyn dy;
+    int rc = read_dyn(s, &dy, st);
+    if (rc) return rc;
+    if (dy.status == 0) return KMC_OK;
+    if (dy.status == ST_EDGE_OVERFLOW) {
+      if ((rc = recover_overflow(s, dy, st))) return rc;
+      if (s->group) return KMC_OK;  // the group's next steps run the rest of the budget
+      if (dy.steps_left) {
+        if ((rc = run_steps(s->solo, st, dy.steps_left, s->err))) return rc;
+      }
+      continue;
+    }
+    return status_code(dy.status, s->err);
+  }
+  s->err = "overflow recovery did not converge";
+  return KMC_EOVERFLOW;
+}
+
+int64_t sim_observe(kmc_sim* s, int what, void* dst, size_t dst_bytes) {
+  if (!s) return KMC_EINVAL;
+  if (!dst) { s->err = "dst is NULL"; return KMC_EINVAL; }
+  cudaStream_t st = sim_work_stream(s);
+  uint32_t n = s->h.n;
+  bool dev = is_device_ptr(dst);
+  int rc;
+  switch (what) {
+    case KMC_OBS_STATE: {
+      size_t need = (size_t)n * (6 * sizeof(double) + sizeof(uint32_t));
+      if (dst_bytes < need) { s->err = "dst too small for STATE"; return KMC_EINVAL; }
+      void* target = dst;
+      if (!dev) {
+        if ((rc = stage_reserve(s, need))) return rc;
+        target = s->stage;
+      }
+      launch_gather_state(s->d, n, target, st);
+      KCHECK(cudaGetLastError(), s->err);
+      if (!dev) {
+        KCHECK(cudaMemcpyAsync(dst, target, need, cudaMemcpyDeviceToHost, st), s->err);
+        KCHECK(cudaStreamSynchronize(st), s->err);
+      }
+      return 1;
+    }
+    case KMC_OBS_PARTNERS: {
+      size_t need = (size_t)n * sizeof(uint32_t);
+      if (dst_bytes < need) { s->err = "dst too small for PARTNERS"; return KMC_EINVAL; }
+      void* target = dst;
+      if (!dev) {
+        if ((rc = stage_reserve(s, need))) return rc;
+        target = s->stage;
+      }
+      launch_gather_partners(s->d, n, (uint32_t*)target, st);
+      KCHECK(cudaGetLastError(), s->err);
+      if (!dev) {
+        KCHECK(cudaMemcpyAsync(dst, target, need, cudaMemcpyDeviceToHost, st), s->err);
+        KCHECK(cudaStreamSynchronize(st), s->err);
+      }
+      return n;
+    }
+    case KMC_OBS_EDGES: {
+      uint32_t cap = (uint32_t)std::min<size_t>(dst_bytes / sizeof(uint2), 0xFFFFFFFFu);
+      size_t need = (size_t)cap * sizeof(uint2) + 16;
+      if ((rc = stage_reserve(s, need))) return rc;
+      uint32_t* cnt = (uint32_t*)s->stage;
+      uint2* buf = (uint2*)((char*)s->stage + 16);
+      KCHECK(cudaMemsetAsync(cnt, 0, sizeof(uint32_t), st), s->err);
+      launch_gather_edges(s->d, cap, buf, cnt, st);
+      KCHECK(cudaGetLastError(), s->err);
+      uint32_t count = 0;
+      KCHECK(cudaMemcpyAsync(&count, cnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), s->err);
+      KCHECK(cudaStreamSynchronize(st), s->err);
+      if (count > cap) { s->err = "dst too small for EDGES"; return KMC_EINVAL; }
+      KCHECK(cudaMemcpyAsync(dst, buf, (size_t)count * sizeof(uint2), cudaMemcpyDefault, st), s->err);
+      KCHECK(cudaStreamSynchronize(st), s->err);
+      return count;
+    }
+    case KMC_OBS_COUNTS: {
+      Dyn dy;
+      if ((rc = read_dyn(s, &dy, st))) return rc;
+      uint64_t avail = dy.hist_count - s->hist_read;
+      uint64_t first = s->hist_read;
+      if (avail > s->h.hist_cap) {
+        first = dy.hist_count - s->h.hist_cap;
+        avail = s->h.hist_cap;
+      }
+      uint64_t fit = dst_bytes / sizeof(kmc_step_counts);
+      if (avail > fit) { s->err = "dst too small for COUNTS"; return KMC_EINVAL; }
+      kmc_step_counts* o = (kmc_step_counts*)dst;
+      for (uint64_t i = 0; i < avail;) {
+        uint64_t slot = (first + i) % s->h.hist_cap;
+        uint64_t run = std::min<uint64_t>(avail - i, s->h.hist_cap - slot);
+        KCHECK(cudaMemcpyAsync(o + i, s->h.hist + slot, run * sizeof(kmc_step_counts), cudaMemcpyDefault, st), s->err);
+        i += run;
+      }
+      KCHECK(cudaStreamSynchronize(st), s->err);
+      s->hist_read = dy.hist_count;
+      return (int64_t)avail;
+    }
+    case KMC_OBS_PROFILES: {
+      if (s->h.profile_bins == 0) return 0;
+      Dyn dy;
+      if ((rc = read_dyn(s, &dy, st))) return rc;
+      uint64_t avail = dy.prof_count - s->prof_read;
+      uint64_t first = s->prof_read;
+      if (avail > s->h.prof_cap) {
+        first = dy.prof_count - s->h.prof_cap;
+        avail = s->h.prof_cap;
+      }
+      size_t per = (size_t)s->h.profile_bins * 7 * sizeof(double);
+      if (avail * per > dst_bytes) { s->err = "dst too small for PROFILES"; return KMC_EINVAL; }
+      if (avail == 0) return 0;
+      if ((rc = stage_reserve(s, avail * per))) return rc;
+      launch_profile_convert(s->d, (uint32_t)(first % s->h.prof_cap), (uint32_t)avail,
+                             (uint32_t)s->h.profile_bins, (double*)s->stage, st);
+      KCHECK(cudaGetLastError(), s->err);
+      KCHECK(cudaMemcpyAsync(dst, s->stage, avail * per, cudaMemcpyDefault, st), s->err);
+      KCHECK(cudaStreamSynchronize(st), s->err);
+      s->prof_read = dy.prof_count;
+      return (int64_t)avail;
+    }
+    case KMC_OBS_STEP: {
+      if (dst_bytes < sizeof(uint64_t)) { s->err = "dst too small for STEP"; return KMC_EINVAL; }
+      Dyn dy;
+      if ((rc = read_dyn(s, &dy, st))) return rc;
+      KCHECK(cudaMemcpyAsync(dst, &dy.step, sizeof(uint64_t), cudaMemcpyDefault, st), s->err);
+      KCHECK(cudaStreamSynchronize(st), s->err);
+      return 1;
+    }
+    default:
+      s->err = "unknown observable";
+      return KMC_EINVAL;
+  }
+}
+
+// ---- groups ------------------------------------------------------------------ //
+int sim_group_create(kmc_sim* const* sims, uint32_t count, void* stream, kmc_group** out) {
+  if (out) *out = nullptr;
+  if (!sims || count == 0 || !out || count > (uint32_t)kMaxGroup) {
+    g_create_error = "bad group arguments";
+    return KMC_EINVAL;
+  }
+  for (uint32_t i = 0; i < count; ++i) {
+    if (!sims[i] || sims[i]->group) { g_create_error = "member NULL or already grouped"; return KMC_EINVAL; }
+    if (sims[i]->h.precision != sims[0]->h.precision || sims[i]->h.K != sims[0]->h.K) {
+      g_create_error = "members must share precision and stencil";
+      return KMC_EINVAL;
+    }
+    for (uint32_t j = 0; j < i; ++j)
+      if (sims[j] == sims[i]) { g_create_error = "duplicate member"; return KMC_EINVAL; }
+  }
+  kmc_group* g = new (std::nothrow) kmc_group();
+  if (!g) return KMC_ENOMEM;
+  if (stream) {
+    g->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete g;
+      g_create_error = "cudaStreamCreate failed";
+      return KMC_ECUDA;
+    }
+    g->own_stream = true;
+  }
+  for (uint32_t i = 0; i < count; ++i) {
+    cudaStreamSynchronize(sims[i]->stream);
+    sims[i]->group = g;
+    g->members.push_back(sims[i]);
+  }
+  *out = g;
+  return KMC_OK;
+}
+
+int sim_group_add(kmc_group* g, kmc_sim* s) {
+  if (!g || !s) return KMC_EINVAL;
+  if (s->group) { g->err = "simulation already grouped"; return KMC_EINVAL; }
+  if (g->members.size() >= (size_t)kMaxGroup) { g->err = "group full"; return KMC_EINVAL; }
+  if (!g->members.empty() && (s->h.precision != g->members[0]->h.precision || s->h.K != g->members[0]->h.K)) {
+    g->err = "members must share precision and stencil";
+    return KMC_EINVAL;
+  }
+  cudaStreamSynchronize(s->stream);
+  s->group = g;
+  g->members.push_back(s);
+  g->built = false;
+  return KMC_OK;
+}
+
+int sim_group_remove(kmc_group* g, kmc_sim* s) {
+  if (!g || !s || s->group != g) return KMC_EINVAL;
+  cudaStreamSynchronize(g->stream);
+  g->members.erase(std::remove(g->members.begin(), g->members.end(), s), g->members.end());
+  s->group = nullptr;
+  g->built = false;
+  return KMC_OK;
+}
+
+int sim_group_budget(kmc_group* g, kmc_sim* s, uint32_t nsteps) {
+  if (!g || !s || s->group != g) return KMC_EINVAL;
+  launch_add_steps(s->d, nsteps, g->stream);
+  KCHECK(cudaGetLastError(), g->err);
+  return KMC_OK;
+}
+
+int sim_group_step(kmc_group* g, uint32_t nsteps) {
+  if (!g) return KMC_EINVAL;
+  if (g->members.empty() || nsteps == 0) return KMC_OK;
+  if (!g->built) {
+    cudaStreamSynchronize(g->stream);
+    int rc = build_plan(g->plan, g->members, g->stream, g->err);
+    if (rc) return rc;
+    g->built = true;
+  }
+  return run_steps(g->plan, g->stream, nsteps, g->err);
+}
+
+int64_t sim_group_steps_left(kmc_group* g, kmc_sim* s) {
+  if (!g || !s || s->group != g) return KMC_EINVAL;
+  Dyn dy;
+  int rc = read_dyn(s, &dy, g->stream);
+  if (rc) return rc;
+  return (int64_t)dy.steps_left;
+}
+
+int sim_group_sync(kmc_group* g) {
+  if (!g) return KMC_EINVAL;
+  KCHECK(cudaStreamSynchronize(g->stream), g->err);
+  int worst = KMC_OK;
+  for (kmc_sim* s : g->members) {
+    Dyn dy;
+    int rc = read_dyn(s, &dy, g->stream);
+    if (rc) return rc;
+    if (dy.status == 0) continue;
+    if (dy.status == ST_EDGE_OVERFLOW) {
+      rc = recover_overflow(s, dy, g->stream);
+    } else {
+      rc = status_code(dy.status, s->err);
+    }
+    if (rc) {
+      g->err = s->err;
+      worst = rc;
+    }
+  }
+  return worst;
+}
+
+int sim_group_destroy(kmc_group* g) {
+  if (!g) return KMC_OK;
+  cudaStreamSynchronize(g->stream);
+  for (kmc_sim* s : g->members) s->group = nullptr;
+  free_plan(g->plan);
+  if (g->own_stream) cudaStreamDestroy(g->stream);
+  delete g;
+  return KMC_OK;
+}
+
+}  // extern "C"

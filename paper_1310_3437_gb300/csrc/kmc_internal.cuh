@@ -1,0 +1,215 @@
+// kmc_internal.cuh -- device data layout and helpers shared by the libkmc kernels.
+//
+// Every kernel is written for a *batch* of simulations: it receives a device table
+// of SimDev pointers and a prefix array that maps its tiles (blocks) onto the
+// simulations.  A lone simulation is a batch of one.  Per-step quantities that the
+// host never needs (cell grid, counters, step index) live in device memory, so the
+// launch sequence of a step is fixed and can be captured once in a CUDA graph.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kmc.h"
+
+namespace kmc {
+
+constexpr int kTile = 256;          // particles per block in particle kernels
+constexpr int kScanTile = 2048;     // elements per block in the segmented scans
+constexpr int kProfTile = 8192;     // particles per block in the profile kernel
+constexpr int kEdgeBlock = 256;     // threads per block in edge / adjacency kernels
+constexpr int kSearchBuf = 512;     // per-block shared-memory staging of emitted pairs
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr int kProfQ = 19;          // int64 counters per profile bin (see kmc_push.cu)
+constexpr int kMaxGroup = 4096;     // simulations per batch
+
+enum : uint32_t {
+  ST_EDGE_OVERFLOW = 1u << 0,  // candidate-pair buffer too small (host grows it)
+  ST_RANDOM = 1u << 1,         // 128 rejected sphere-point draws
+  ST_CELL_OVERFLOW = 1u << 2,  // grid key space above capacity (cannot happen: coarsened)
+};
+
+// Search grid of the current step.  Cells are keyed column-major along x inside
+// a Z-order (Morton) walk over the (y, z) columns: key = col(cy, cz) * nc[0] + cx.
+struct Grid {
+  int32_t nc[3];      // cells per axis; 1 means the axis is one cell (no stencil on it)
+  int32_t K;          // stencil radius in cells
+  uint32_t nkeys;     // size of the key space (padded Morton columns x nc[0])
+  uint32_t col_shift; // log2 of the Morton block edge P (P = next pow2 of the smaller axis)
+  uint32_t y_major;   // 1 if nc[1] >= nc[2] (y carries the high, non-interleaved bits)
+  uint32_t pad0;
+  double w[3];        // cell widths
+  float wf[3];        // cell widths (binary32)
+  float inv_wf[3];    // cells per unit length (binary32, cell assignment)
+  // guarded binary32 pre-tests (kmc_search.cu derives them; kmc_push.cu sets them)
+  float s_c0, s_c1;   // sphere test: drop if R > s_c0 + s_c1 * B
+  float a_g;          // approach test: drop if A < -a_g
+  float t_g, dtf;     // time test: drop if A - dtf * B > t_g
+  float d0up, b_rel, b_abs, w_e, w_rel;  // distance test (see kmc_search.cu)
+  float Lf[3], halfLf[3], tief[3];        // one-cell periodic axes: minimum image
+  // binary64 sphere pre-test: drop if R > c0 + c1 * B (B >= 2^-900)
+  double c0, c1;
+};
+
+struct Dyn {
+  uint64_t step;        // absolute index of the next step
+  uint64_t steps_left;  // step budget; kernels skip the simulation when 0
+  uint32_t parity;      // state buffer holding the state at the start of the step
+  uint32_t status;      // ST_* bits; kernels skip the simulation when non-zero
+  uint32_t vmax2_acc;   // binary32 bits of an upper bound of max |v|^2 (atomicMax)
+  float vmax2;          // bound the current grid was built from
+  Grid grid;
+  uint32_t n_raw;       // pairs emitted by the search (may exceed edge_cap)
+  uint32_t n_edges;     // candidate pairs after the exact test
+  uint32_t round_pairs[4];
+  unsigned long long pair_tests;
+  uint32_t last_raw;    // n_raw of the last completed step (its pair buffer is kept)
+  uint32_t prof_due;    // the step being run ends with a profile
+  uint32_t prof_count;  // snapshots written
+  uint64_t hist_count;  // step records written
+};
+
+struct SimDev {
+  // ---- parameters ----
+  uint32_t n;
+  int32_t bc[3];
+  int32_t max_rounds, precision, profile_bins, profile_every, K;
+  double box[3];
+  double piston_x0, piston_u, d0, dt, d0sq;
+  double profile_range, cell_scale;
+  uint64_t seed;
+  uint32_t cell_cap, edge_cap, hist_cap, prof_cap;
+  // ---- state, double-buffered by the sort ----
+  double* x[2][3];
+  double* v[2][3];
+  uint32_t* id[2];
+  uint32_t* last[2];
+  // ---- per-step work arrays ----
+  float4* mir_a;        // (ox, oy, oz, vx): binary32 offsets from the cell corner
+  float2* mir_b;        // (vy, vz)
+  uint32_t* key;        // cell key per particle (pre-sort order)
+  uint32_t* rank;       // rank inside the cell (pre-sort order)
+  uint32_t* skey;       // cell key per particle (sorted order)
+  uint32_t* cell_count; // nkeys counters, all zero between steps
+  uint32_t* cell_start; // nkeys + 1
+  uint32_t* deg;        // candidate pairs per particle
+  uint32_t* off;        // n + 1, exclusive scan of deg
+  uint2* edge;          // emitted pairs (sorted indices, owner first)
+  double* e_d2;         // binary64 key of each pair
+  double* e_t;
+  uint2* e_slot;        // slot of the pair in each endpoint's list, x = kNone if rejected
+  uint32_t* adj_owner;  // adjacency (CSR by owner): owner, other end, pair index
+  uint32_t* adj_other;
+  uint32_t* adj_edge;
+  uint32_t* best;       // best unmatched candidate (sorted index) in the current round
+  uint32_t* best_e;
+  uint32_t* partner;    // partner (sorted index) this step, kNone if none
+  uint32_t* medge;      // pair index of the collision
+  kmc_step_counts* hist;
+  long long* prof_acc;  // prof_cap x bins x kProfQ fixed-point counters
+  uint64_t* prof_step;
+  Dyn d;
+};
+
+// ---- batch mapping ------------------------------------------------------- //
+struct Batch {
+  SimDev* const* sims;     // device table
+  int nsims;
+  const uint32_t* ptile;   // prefix of ceil(n / kTile) per simulation
+  const uint32_t* stile_n; // prefix of ceil((n + 1) / kScanTile)
+  const uint32_t* stile_c; // prefix of ceil((cell_cap + 1) / kScanTile)
+  const uint32_t* prtile;  // prefix of ceil(n / kProfTile)
+  uint32_t* tile_sums;      // scratch for the segmented scans
+};
+
+__device__ __forceinline__ int find_sim(const uint32_t* prefix, int nsims, uint32_t tile) {
+  int lo = 0, hi = nsims;  // prefix[lo] <= tile < prefix[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(prefix + mid) <= tile) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ bool sim_active(const SimDev& s) {
+  return s.d.status == 0 && s.d.steps_left > 0;
+}
+
+// ---- exact binary64 arithmetic (never contracted into FMA) --------------- //
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double dsqrt(double a) { return __dsqrt_rn(a); }
+
+// ---- Morton column code --------------------------------------------------- //
+__device__ __forceinline__ uint32_t dilate16(uint32_t x) {
+  x &= 0xFFFFu;
+  x = (x | (x << 8)) & 0x00FF00FFu;
+  x = (x | (x << 4)) & 0x0F0F0F0Fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x;
+}
+__device__ __forceinline__ uint32_t compact16(uint32_t x) {
+  x &= 0x55555555u;
+  x = (x | (x >> 1)) & 0x33333333u;
+  x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+  x = (x | (x >> 4)) & 0x00FF00FFu;
+  x = (x | (x >> 8)) & 0x0000FFFFu;
+  return x;
+}
+__device__ __forceinline__ uint32_t col_code(const Grid& g, uint32_t cy, uint32_t cz) {
+  uint32_t a = g.y_major ? cy : cz;  // longer transverse axis
+  uint32_t b = g.y_major ? cz : cy;  // shorter one, < P
+  uint32_t sh = g.col_shift;
+  uint32_t mask = (1u << sh) - 1u;
+  return ((a >> sh) << (2 * sh)) | dilate16(a & mask) | (dilate16(b) << 1);
+}
+__device__ __forceinline__ void key_decode(const Grid& g, uint32_t key, int& cx, int& cy, int& cz) {
+  uint32_t nx = (uint32_t)g.nc[0];
+  uint32_t col = key / nx;
+  cx = (int)(key - col * nx);
+  uint32_t sh = g.col_shift;
+  uint32_t hi = col >> (2 * sh);
+  uint32_t lo = col & ((1u << (2 * sh)) - 1u);
+  uint32_t a = (hi << sh) | compact16(lo);
+  uint32_t b = compact16(lo >> 1);
+  cy = (int)(g.y_major ? a : b);
+  cz = (int)(g.y_major ? b : a);
+}
+
+// cell coordinate along one axis, binary32 (only the speed depends on it)
+__device__ __forceinline__ int cell_coord(const Grid& g, int k, double x) {
+  if (g.nc[k] == 1) return 0;
+  float f = floorf((float)x * g.inv_wf[k]);
+  int c = (int)f;
+  c = c < 0 ? 0 : c;
+  c = c >= g.nc[k] ? g.nc[k] - 1 : c;
+  return c;
+}
+
+// ---- launch helpers (host) ----------------------------------------------- //
+struct LaunchPlan {
+  Batch b;
+  uint32_t ptiles, stiles_n, stiles_c, prtiles;
+  int edge_blocks;
+};
+
+void launch_sort(const LaunchPlan& L, cudaStream_t st);
+void launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st);
+void launch_match(const LaunchPlan& L, int max_rounds, cudaStream_t st);
+void launch_push(const LaunchPlan& L, cudaStream_t st);
+void launch_init_grid(const LaunchPlan& L, cudaStream_t st);
+void launch_seg_scan(const LaunchPlan& L, int which, cudaStream_t st);
+
+// observe helpers
+void launch_gather_state(SimDev* d, uint32_t n, void* out, cudaStream_t st);
+void launch_gather_partners(SimDev* d, uint32_t n, uint32_t* out, cudaStream_t st);
+void launch_gather_edges(SimDev* d, uint32_t cap, uint2* out, uint32_t* count, cudaStream_t st);
+void launch_profile_convert(SimDev* d, uint32_t first, uint32_t count, uint32_t bins,
+                            double* out, cudaStream_t st);
+void launch_add_steps(SimDev* d, uint64_t nsteps, cudaStream_t st);
+void launch_validate(SimDev* d, uint32_t n, uint32_t* bad, cudaStream_t st);
+
+}  // namespace kmc

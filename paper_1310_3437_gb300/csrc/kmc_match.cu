@@ -1,0 +1,267 @@
+// kmc_match.cu -- exact candidate test, mutual-choice matching and the collision
+// update (Sec. 2: "a closer partner replaces the one found so far"; "two particles
+// only collide if they have both found each other"; positions and velocities of
+// the colliding pair are then updated).
+//
+// All binary64 arithmetic goes through the __d*_rn intrinsics (never contracted),
+// in the operation order of the definitions below, so every value is bit-identical
+// to the binary64 definition evaluated on any IEEE-754 machine.
+//
+//   k_refine  exact test of every pair emitted by the search:
+//             r = x_j - x_i (minimum image on periodic axes), v = v_j - v_i,
+//             t* = -(r.v)/|v|^2, d_min^2 = |r x v|^2/|v|^2; candidate iff |v| != 0,
+//             0 <= t* < dt, d_min^2 < d0^2, and the pair is not the pair that last
+//             collided for both of its members.  Survivors take a slot in each
+//             endpoint's candidate list.
+//   k_fill    candidate lists in CSR form (owner, other end, pair).
+//   k_best    per round: every unmatched particle picks its unmatched candidate of
+//             least key (d_min^2, t*, partner id) -- a total order, so the choice does
+//             not depend on the order of the list.
+//   k_mutual  per round: pairs that picked each other are matched; the count uses
+//             warp ballots (one atomic per warp).
+//   k_collide isotropic centre-of-mass scatter at the time of closest approach.
+#include "kmc_internal.cuh"
+
+namespace kmc {
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ---------------------- //
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+    uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+    uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+// Point on the unit sphere by Marsaglia's method (Ann. Math. Stat. 43, 1972):
+// u1, u2 uniform in [-1, 1) from 32-bit words, s = u1^2 + u2^2 accepted if
+// 0 < s < 1, n = (2 u1 sqrt(1-s), 2 u2 sqrt(1-s), 1 - 2 s).  Counter (id, step lo,
+// k, step hi), key (seed lo, seed hi); two attempts per Philox call.
+__device__ bool sphere_point(uint64_t seed, uint64_t step, uint32_t id, double nv[3]) {
+  for (uint32_t k = 0; k < 64; ++k) {
+    uint32_t c[4] = {id, (uint32_t)step, k, (uint32_t)(step >> 32)};
+    philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      double u1 = dsub(dmul((double)c[2 * a], 0x1p-31), 1.0);
+      double u2 = dsub(dmul((double)c[2 * a + 1], 0x1p-31), 1.0);
+      double s = dadd(dmul(u1, u1), dmul(u2, u2));
+      if (s > 0.0 && s < 1.0) {
+        double q = dsqrt(dsub(1.0, s));
+        nv[0] = dmul(dadd(u1, u1), q);
+        nv[1] = dmul(dadd(u2, u2), q);
+        nv[2] = dsub(1.0, dadd(s, s));
+        return true;
+      }
+    }
+  }
+  return false;
+}
+
+__device__ __forceinline__ double min_image(double r, double L) {
+  double h = dmul(L, 0.5);
+  if (r > h) return dsub(r, L);
+  if (r < -h) return dadd(r, L);
+  return r;
+}
+
+// ---- k_refine ------------------------------------------------------------ //
+__global__ void __launch_bounds__(kEdgeBlock) k_refine(Batch B) {
+  for (int k = 0; k < B.nsims; ++k) {
+    SimDev& s = *B.sims[k];
+    if (!sim_active(s)) continue;
+    const int cur = s.d.parity ^ 1;
+    uint32_t nraw = s.d.n_raw < s.edge_cap ? s.d.n_raw : s.edge_cap;
+    uint32_t found = 0;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nraw; e += gridDim.x * blockDim.x) {
+      uint2 pr = s.edge[e];
+      uint32_t i = pr.x, j = pr.y;
+      bool cand = false;
+      double d2 = 0.0, t = 0.0;
+      uint32_t idi = s.id[cur][i], idj = s.id[cur][j];
+      if (!(s.last[cur][i] == idj && s.last[cur][j] == idi)) {
+        double r[3], v[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          double dd = dsub(s.x[cur][a][j], s.x[cur][a][i]);
+          r[a] = s.bc[a] == KMC_PERIODIC ? min_image(dd, s.box[a]) : dd;
+          v[a] = dsub(s.v[cur][a][j], s.v[cur][a][i]);
+        }
+        double vv = dadd(dadd(dmul(v[0], v[0]), dmul(v[1], v[1])), dmul(v[2], v[2]));
+        if (vv != 0.0) {
+          double rv = dadd(dadd(dmul(r[0], v[0]), dmul(r[1], v[1])), dmul(r[2], v[2]));
+          t = ddiv(-rv, vv);
+          double wx = dsub(dmul(r[1], v[2]), dmul(r[2], v[1]));
+          double wy = dsub(dmul(r[2], v[0]), dmul(r[0], v[2]));
+          double wz = dsub(dmul(r[0], v[1]), dmul(r[1], v[0]));
+          d2 = ddiv(dadd(dadd(dmul(wx, wx), dmul(wy, wy)), dmul(wz, wz)), vv);
+          cand = t >= 0.0 && t < s.dt && d2 < s.d0sq;
+        }
+      }
+      if (cand) {
+        s.e_d2[e] = d2;
+        s.e_t[e] = t;
+        uint32_t si = atomicAdd(&s.deg[i], 1u);
+        uint32_t sj = atomicAdd(&s.deg[j], 1u);
+        s.e_slot[e] = make_uint2(si, sj);
+        ++found;
+      } else {
+        s.e_slot[e] = make_uint2(kNone, kNone);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) found += __shfl_down_sync(0xFFFFFFFFu, found, o);
+    if ((threadIdx.x & 31) == 0 && found) atomicAdd(&s.d.n_edges, found);
+  }
+}
+
+// ---- k_fill -------------------------------------------------------------- //
+__global__ void __launch_bounds__(kEdgeBlock) k_fill(Batch B) {
+  for (int k = 0; k < B.nsims; ++k) {
+    SimDev& s = *B.sims[k];
+    if (!sim_active(s)) continue;
+    uint32_t nraw = s.d.n_raw < s.edge_cap ? s.d.n_raw : s.edge_cap;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nraw; e += gridDim.x * blockDim.x) {
+      uint2 sl = s.e_slot[e];
+      if (sl.x == kNone) continue;
+      uint2 pr = s.edge[e];
+      uint32_t a = s.off[pr.x] + sl.x, b = s.off[pr.y] + sl.y;
+      s.adj_owner[a] = pr.x; s.adj_other[a] = pr.y; s.adj_edge[a] = e;
+      s.adj_owner[b] = pr.y; s.adj_other[b] = pr.x; s.adj_edge[b] = e;
+    }
+  }
+}
+
+// ---- matching rounds ------------------------------------------------------ //
+__device__ __forceinline__ bool key_less(double d2a, double ta, uint32_t ja, double d2b, double tb,
+                                         uint32_t jb) {
+  if (d2a < d2b) return true;
+  if (d2a > d2b) return false;
+  if (ta < tb) return true;
+  if (ta > tb) return false;
+  return ja < jb;
+}
+
+__global__ void __launch_bounds__(kEdgeBlock) k_best(Batch B) {
+  for (int k = 0; k < B.nsims; ++k) {
+    SimDev& s = *B.sims[k];
+    if (!sim_active(s)) continue;
+    const int cur = s.d.parity ^ 1;
+    const uint32_t total = s.off[s.n];
+    for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < total; a += gridDim.x * blockDim.x) {
+      uint32_t i = s.adj_owner[a];
+      if (a > 0 && s.adj_owner[a - 1] == i) continue;  // not the head of i's list
+      if (s.partner[i] != kNone) continue;
+      uint32_t bj = kNone, be = kNone, bid = kNone;
+      double bd2 = 0.0, bt = 0.0;
+      for (uint32_t q = a; q < total && s.adj_owner[q] == i; ++q) {
+        uint32_t j = s.adj_other[q];
+        if (s.partner[j] != kNone) continue;
+        uint32_t e = s.adj_edge[q];
+        double d2 = s.e_d2[e], t = s.e_t[e];
+        uint32_t idj = s.id[cur][j];
+        if (bj == kNone || key_less(d2, t, idj, bd2, bt, bid)) {
+          bj = j; be = e; bid = idj; bd2 = d2; bt = t;
+        }
+      }
+      s.best[i] = bj;
+      s.best_e[i] = be;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kEdgeBlock) k_mutual(Batch B, int round) {
+  for (int k = 0; k < B.nsims; ++k) {
+    SimDev& s = *B.sims[k];
+    if (!sim_active(s)) continue;
+    if (round >= s.max_rounds) continue;
+    const int cur = s.d.parity ^ 1;
+    const uint32_t total = s.off[s.n];
+    const uint32_t stride = gridDim.x * blockDim.x;
+    // uniform trip count per warp so that the ballot sees every lane
+    const uint32_t span = ((total + stride - 1) / stride) * stride;
+    for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < span; a += stride) {
+      bool pair = false;
+      if (a < total) {
+        uint32_t i = s.adj_owner[a];
+        bool head = a == 0 || s.adj_owner[a - 1] != i;
+        if (head && s.partner[i] == kNone) {
+          uint32_t j = s.best[i];
+          if (j != kNone && s.best[j] == i) {
+            s.partner[i] = j;
+            s.medge[i] = s.best_e[i];
+            pair = s.id[cur][i] < s.id[cur][j];
+          }
+        }
+      }
+      unsigned m = __ballot_sync(0xFFFFFFFFu, pair);
+      if ((threadIdx.x & 31) == 0 && m) atomicAdd(&s.d.round_pairs[round], (uint32_t)__popc(m));
+    }
+  }
+}
+
+// ---- collision update ------------------------------------------------------ //
+// For the pair (a, b) with a the smaller id: stream both to t*, scatter
+//   g = v_a - v_b, V = (v_a + v_b) * 0.5, G = |g|,  v_a' = V + (G/2) n,  v_b' = V - (G/2) n,
+// then stream the rest of the step:  x' = (x + v t*) + v' (dt - t*).
+__global__ void __launch_bounds__(kEdgeBlock) k_collide(Batch B) {
+  for (int k = 0; k < B.nsims; ++k) {
+    SimDev& s = *B.sims[k];
+    if (!sim_active(s)) continue;
+    const int cur = s.d.parity ^ 1;
+    const uint32_t total = s.off[s.n];
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+      uint32_t i = s.adj_owner[q];
+      if (q > 0 && s.adj_owner[q - 1] == i) continue;
+      uint32_t j = s.partner[i];
+      if (j == kNone) continue;
+      uint32_t ida = s.id[cur][i], idb = s.id[cur][j];
+      if (ida > idb) continue;  // the pair is handled by its smaller id
+      double t = s.e_t[s.medge[i]];
+      double nv[3];
+      if (!sphere_point(s.seed, s.d.step, ida, nv)) {
+        atomicOr(&s.d.status, ST_RANDOM);
+        continue;
+      }
+      double va[3], vb[3], g[3], V[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        va[c] = s.v[cur][c][i];
+        vb[c] = s.v[cur][c][j];
+        g[c] = dsub(va[c], vb[c]);
+        V[c] = dmul(dadd(va[c], vb[c]), 0.5);
+      }
+      double G = dsqrt(dadd(dadd(dmul(g[0], g[0]), dmul(g[1], g[1])), dmul(g[2], g[2])));
+      double hG = dmul(0.5, G);
+      double rest = dsub(s.dt, t);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double pc = dmul(hG, nv[c]);
+        double na = dadd(V[c], pc);
+        double nb = dsub(V[c], pc);
+        double xa = s.x[cur][c][i], xb = s.x[cur][c][j];
+        s.x[cur][c][i] = dadd(dadd(xa, dmul(va[c], t)), dmul(na, rest));
+        s.x[cur][c][j] = dadd(dadd(xb, dmul(vb[c], t)), dmul(nb, rest));
+        s.v[cur][c][i] = na;
+        s.v[cur][c][j] = nb;
+      }
+    }
+  }
+}
+
+void launch_match(const LaunchPlan& L, int max_rounds, cudaStream_t st) {
+  int nb = L.edge_blocks;
+  k_refine<<<nb, kEdgeBlock, 0, st>>>(L.b);
+  launch_seg_scan(L, 1, st);
+  k_fill<<<nb, kEdgeBlock, 0, st>>>(L.b);
+  for (int r = 0; r < max_rounds; ++r) {
+    k_best<<<nb, kEdgeBlock, 0, st>>>(L.b);
+    k_mutual<<<nb, kEdgeBlock, 0, st>>>(L.b, r);
+  }
+  k_collide<<<nb, kEdgeBlock, 0, st>>>(L.b);
+}
+
+}  // namespace kmc

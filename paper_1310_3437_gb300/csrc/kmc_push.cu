@@ -1,0 +1,354 @@
+// kmc_push.cu -- free streaming, boundaries, observables and the end-of-step
+// bookkeeping (Sec. 2: positions updated, boundary conditions applied to particles
+// that reach the walls; output at fixed intervals).
+//
+//   k_push      x += v dt for particles that did not collide (colliders were
+//               streamed by k_collide), then the boundaries per axis:
+//                 periodic   one wrap into [0, L), x == L mapped to 0;
+//                 reflecting lower wall at 0; upper wall at L, or on x at the piston
+//                            X = x0 - u ((step+1) dt): x -> 2X - x, v -> -v - 2u
+//                            (specular reflection in the frame of the moving wall).
+//               It also records the last partner and a binary32 upper bound of
+//               max |v|^2 (directed rounding) for the next step's cell size.
+//   k_profile   every profile_every steps: per x-bin count, sum v and sum v^2, in
+//               exact fixed point (int64 digits), so the sums do not depend on the
+//               order of the particles.
+//   k_finalize  one thread per simulation: step record, step counter, the next
+//               grid (kmc_grid.cuh) and the per-step counters reset.
+#include "kmc_grid.cuh"
+#include "kmc_internal.cuh"
+
+namespace kmc {
+
+__device__ __forceinline__ float vmag2_up(double vx, double vy, double vz) {
+  float ax = __double2float_ru(fabs(vx)), ay = __double2float_ru(fabs(vy)),
+        az = __double2float_ru(fabs(vz));
+  return __fadd_ru(__fadd_ru(__fmul_ru(ax, ax), __fmul_ru(ay, ay)), __fmul_ru(az, az));
+}
+
+__device__ __forceinline__ void block_max_to(uint32_t* dst, float v) {
+  __shared__ float wmax[kTile / 32];
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xFFFFFFFFu, v, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) m = fmaxf(m, wmax[w]);
+    atomicMax(dst, __float_as_uint(m));
+  }
+}
+
+// ---- k_push ---------------------------------------------------------------- //
+__global__ void __launch_bounds__(kTile) k_push(Batch B) {
+  int k = find_sim(B.ptile, B.nsims, blockIdx.x);
+  SimDev& s = *B.sims[k];
+  if (!sim_active(s)) return;
+  const int cur = s.d.parity ^ 1;
+  uint32_t p = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
+  float vm = 0.0f;
+  if (p < s.n) {
+    const uint64_t step = s.d.step;
+    const double dt = s.dt;
+    uint32_t q = s.partner[p];
+    double vv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double x = s.x[cur][a][p];
+      double v = s.v[cur][a][p];
+      if (q == kNone) x = dadd(x, dmul(v, dt));
+      if (s.bc[a] == KMC_PERIODIC) {
+        double L = s.box[a];
+        if (x >= L) x = dsub(x, L);
+        if (x < 0.0) {
+          x = dadd(x, L);
+          if (x == L) x = 0.0;
+        }
+      } else {
+        double X, u;
+        if (a == 0) {
+          u = s.piston_u;
+          X = dsub(s.piston_x0, dmul(u, dmul((double)(step + 1), dt)));
+        } else {
+          u = 0.0;
+          X = s.box[a];
+        }
+        bool vchg = false;
+        if (x < 0.0) {
+          x = -x;
+          v = -v;
+          vchg = true;
+        }
+        if (x > X) {
+          x = dsub(dadd(X, X), x);
+          v = dsub(-v, dadd(u, u));
+          vchg = true;
+        }
+        if (vchg) s.v[cur][a][p] = v;
+      }
+      s.x[cur][a][p] = x;
+      vv[a] = v;
+    }
+    if (q != kNone) s.last[cur][p] = s.id[cur][q];
+    vm = vmag2_up(vv[0], vv[1], vv[2]);
+  }
+  block_max_to(&s.d.vmax2_acc, vm);
+}
+
+// ---- fixed-point digits for the profile sums ------------------------------- //
+// |q| * 2^64, truncated, split into three 32-bit digits (q must satisfy |q| < 2^31).
+__device__ __forceinline__ void fx_digits(double q, long long d[3]) {
+  unsigned long long bits = (unsigned long long)__double_as_longlong(q);
+  bool neg = (bits >> 63) != 0;
+  int ex = (int)((bits >> 52) & 0x7FF);
+  d[0] = d[1] = d[2] = 0;
+  if (ex == 0) return;  // zero or subnormal: below 2^-64
+  unsigned long long man = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+  int sh = ex - 1075 + 64;
+  unsigned __int128 f;
+  if (sh >= 0) f = (unsigned __int128)man << (sh > 42 ? 42 : sh);
+  else if (sh > -64) f = (unsigned __int128)(man >> (-sh));
+  else f = 0;
+  long long d0 = (long long)(uint32_t)f, d1 = (long long)(uint32_t)(f >> 32),
+            d2 = (long long)(uint32_t)(f >> 64);
+  if (neg) { d0 = -d0; d1 = -d1; d2 = -d2; }
+  d[0] = d0; d[1] = d1; d[2] = d2;
+}
+
+__global__ void __launch_bounds__(kTile) k_profile(Batch B) {
+  extern __shared__ long long acc[];
+  int k = find_sim(B.prtile, B.nsims, blockIdx.x);
+  SimDev& s = *B.sims[k];
+  if (!sim_active(s) || !s.d.prof_due) return;
+  const int nb = s.profile_bins;
+  for (int i = threadIdx.x; i < nb * kProfQ; i += blockDim.x) acc[i] = 0;
+  __syncthreads();
+  const int cur = s.d.parity ^ 1;
+  const double scale = ddiv((double)nb, s.profile_range);
+  uint32_t base = (blockIdx.x - B.prtile[k]) * kProfTile;
+  for (uint32_t i = threadIdx.x; i < kProfTile; i += blockDim.x) {
+    uint32_t p = base + i;
+    if (p >= s.n) break;
+    double x = s.x[cur][0][p];
+    if (!(x >= 0.0)) continue;
+    double f = dmul(x, scale);
+    if (f >= (double)nb) continue;
+    int b = (int)f;
+    long long* q = acc + b * kProfQ;
+    atomicAdd((unsigned long long*)&q[0], 1ull);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double v = s.v[cur][a][p];
+      long long d[3];
+      fx_digits(v, d);
+      for (int c = 0; c < 3; ++c) atomicAdd((unsigned long long*)&q[1 + 3 * a + c], (unsigned long long)d[c]);
+      fx_digits(dmul(v, v), d);
+      for (int c = 0; c < 3; ++c) atomicAdd((unsigned long long*)&q[10 + 3 * a + c], (unsigned long long)d[c]);
+    }
+  }
+  __syncthreads();
+  long long* out = s.prof_acc + (size_t)(s.d.prof_count % s.prof_cap) * nb * kProfQ;
+  for (int i = threadIdx.x; i < nb * kProfQ; i += blockDim.x)
+    if (acc[i]) atomicAdd((unsigned long long*)&out[i], (unsigned long long)acc[i]);
+}
+
+// ---- end of step ------------------------------------------------------------ //
+__device__ void reset_step_counters(SimDev& s) {
+  s.d.n_raw = 0;
+  s.d.n_edges = 0;
+  for (int r = 0; r < 4; ++r) s.d.round_pairs[r] = 0;
+  s.d.pair_tests = 0;
+  s.d.vmax2_acc = 0;
+}
+
+__device__ void set_prof_due(SimDev& s) {
+  s.d.prof_due = (s.profile_bins > 0 && s.profile_every > 0 &&
+                  (s.d.step + 1) % (uint64_t)s.profile_every == 0) ? 1u : 0u;
+}
+
+__global__ void k_finalize(Batch B) {
+  for (int k = threadIdx.x; k < B.nsims; k += blockDim.x) {
+    SimDev& s = *B.sims[k];
+    if (!sim_active(s)) continue;
+    kmc_step_counts rec;
+    rec.step = s.d.step;
+    uint32_t coll = 0;
+    for (int r = 0; r < 4; ++r) {
+      rec.round_pairs[r] = s.d.round_pairs[r];
+      coll += s.d.round_pairs[r];
+    }
+    rec.collisions = coll;
+    rec.edges = s.d.n_edges;
+    rec.survivors = s.d.n_raw;
+    rec.cells = s.d.grid.nkeys;
+    rec.pair_tests = s.d.pair_tests;
+    s.hist[s.d.hist_count % s.hist_cap] = rec;
+    s.d.hist_count += 1;
+    if (s.d.prof_due) {
+      s.prof_step[s.d.prof_count % s.prof_cap] = s.d.step;
+      s.d.prof_count += 1;
+    }
+    s.d.last_raw = s.d.n_raw;
+    s.d.parity ^= 1u;
+    s.d.step += 1;
+    s.d.steps_left -= 1;
+    float vm = __uint_as_float(s.d.vmax2_acc);
+    s.d.vmax2 = vm;
+    compute_grid(s, vm, s.d.step);
+    reset_step_counters(s);
+    set_prof_due(s);
+    if (s.d.prof_due) {
+      long long* out = s.prof_acc + (size_t)(s.d.prof_count % s.prof_cap) * s.profile_bins * kProfQ;
+      for (int i = 0; i < s.profile_bins * kProfQ; ++i) out[i] = 0;
+    }
+  }
+}
+
+// ---- initial grid (creation, resume, after an error is cleared) ------------ //
+__global__ void __launch_bounds__(kTile) k_vmax(Batch B) {
+  int k = find_sim(B.ptile, B.nsims, blockIdx.x);
+  SimDev& s = *B.sims[k];
+  uint32_t p = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
+  float vm = 0.0f;
+  if (p < s.n) {
+    int par = s.d.parity;
+    vm = vmag2_up(s.v[par][0][p], s.v[par][1][p], s.v[par][2][p]);
+  }
+  block_max_to(&s.d.vmax2_acc, vm);
+}
+
+__global__ void k_init_grid(Batch B) {
+  for (int k = threadIdx.x; k < B.nsims; k += blockDim.x) {
+    SimDev& s = *B.sims[k];
+    float vm = __uint_as_float(s.d.vmax2_acc);
+    s.d.vmax2 = vm;
+    compute_grid(s, vm, s.d.step);
+    reset_step_counters(s);
+    set_prof_due(s);
+    if (s.d.prof_due && s.prof_acc) {
+      long long* out = s.prof_acc + (size_t)(s.d.prof_count % s.prof_cap) * s.profile_bins * kProfQ;
+      for (int i = 0; i < s.profile_bins * kProfQ; ++i) out[i] = 0;
+    }
+  }
+}
+
+__global__ void k_zero_vmax(Batch B) {
+  for (int k = threadIdx.x; k < B.nsims; k += blockDim.x) B.sims[k]->d.vmax2_acc = 0;
+}
+
+void launch_init_grid(const LaunchPlan& L, cudaStream_t st) {
+  k_zero_vmax<<<1, 256, 0, st>>>(L.b);
+  k_vmax<<<L.ptiles, kTile, 0, st>>>(L.b);
+  k_init_grid<<<1, 256, 0, st>>>(L.b);
+}
+
+void launch_push(const LaunchPlan& L, cudaStream_t st) {
+  k_push<<<L.ptiles, kTile, 0, st>>>(L.b);
+  k_profile<<<L.prtiles, kTile, 256 * kProfQ * sizeof(long long), st>>>(L.b);
+  k_finalize<<<1, 256, 0, st>>>(L.b);
+}
+
+__global__ void k_add_steps(SimDev* d, uint64_t n) { d->d.steps_left += n; }
+void launch_add_steps(SimDev* d, uint64_t nsteps, cudaStream_t st) {
+  k_add_steps<<<1, 1, 0, st>>>(d, nsteps);
+}
+
+// ---- observables ------------------------------------------------------------ //
+__global__ void k_gather_state(SimDev* d, void* out) {
+  SimDev& s = *d;
+  uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= s.n) return;
+  int par = s.d.parity;
+  uint32_t id = s.id[par][p];
+  double* o = (double*)out;
+  for (int a = 0; a < 3; ++a) {
+    o[(size_t)a * s.n + id] = s.x[par][a][p];
+    o[(size_t)(3 + a) * s.n + id] = s.v[par][a][p];
+  }
+  uint32_t* ol = (uint32_t*)(o + (size_t)6 * s.n);
+  ol[id] = s.last[par][p];
+}
+
+__global__ void k_gather_partners(SimDev* d, uint32_t* out) {
+  SimDev& s = *d;
+  uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= s.n) return;
+  // partners refer to the buffer the last step ran on, which is the current one
+  int par = s.d.parity;
+  uint32_t q = s.partner[p];
+  out[s.id[par][p]] = q == kNone ? kNone : s.id[par][q];
+}
+
+__global__ void k_gather_edges(SimDev* d, uint32_t cap, uint2* out, uint32_t* count) {
+  SimDev& s = *d;
+  int par = s.d.parity;
+  uint32_t nraw = s.d.last_raw < s.edge_cap ? s.d.last_raw : s.edge_cap;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nraw; e += gridDim.x * blockDim.x) {
+    uint2 sl = s.e_slot[e];
+    if (sl.x == kNone) continue;
+    uint2 pr = s.edge[e];
+    uint32_t a = s.id[par][pr.x], b = s.id[par][pr.y];
+    uint32_t pos = atomicAdd(count, 1u);
+    if (pos < cap) out[pos] = a < b ? make_uint2(a, b) : make_uint2(b, a);
+  }
+}
+
+__global__ void k_profile_convert(SimDev* d, uint32_t first, uint32_t count, uint32_t bins, double* out) {
+  SimDev& s = *d;
+  uint32_t total = count * bins * 7;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    uint32_t snap = i / (bins * 7), rem = i % (bins * 7), b = rem / 7, q = rem % 7;
+    const long long* src = s.prof_acc + ((size_t)((first + snap) % s.prof_cap) * bins + b) * kProfQ;
+    double val;
+    if (q == 0) {
+      val = (double)src[0];
+    } else {
+      const long long* dg = src + 1 + 3 * (q - 1);
+      // value = (d2 * 2^64 + d1 * 2^32 + d0) * 2^-64 with signed 128-bit accumulation
+      __int128 tot = ((__int128)dg[2] << 64) + ((__int128)dg[1] << 32) + (__int128)dg[0];
+      bool neg = tot < 0;
+      unsigned __int128 mag = neg ? (unsigned __int128)(-tot) : (unsigned __int128)tot;
+      double hi = (double)(unsigned long long)(mag >> 64);
+      double lo = (double)(unsigned long long)mag;
+      val = dadd(dmul(hi, 1.0), dmul(lo, 0x1p-64));
+      val = neg ? -val : val;
+    }
+    out[i] = val;
+  }
+}
+
+// particles outside the box at creation: count them (host reports KMC_EINVAL)
+__global__ void k_validate(SimDev* d, uint32_t* bad) {
+  SimDev& s = *d;
+  uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= s.n) return;
+  bool out = false;
+  for (int a = 0; a < 3; ++a) {
+    double q = s.x[s.d.parity][a][p];
+    double hi = (a == 0 && s.bc[0] == KMC_REFLECT) ? s.piston_x0 : s.box[a];
+    bool periodic = s.bc[a] == KMC_PERIODIC;
+    if (!(q >= 0.0) || (periodic ? !(q < hi) : !(q <= hi))) out = true;
+    if (!(fabs(s.v[s.d.parity][a][p]) < 1e15)) out = true;
+  }
+  if (out) atomicAdd(bad, 1u);
+}
+
+void launch_validate(SimDev* d, uint32_t n, uint32_t* bad, cudaStream_t st) {
+  k_validate<<<(n + 255) / 256, 256, 0, st>>>(d, bad);
+}
+
+void launch_gather_state(SimDev* d, uint32_t n, void* out, cudaStream_t st) {
+  k_gather_state<<<(n + 255) / 256, 256, 0, st>>>(d, out);
+}
+void launch_gather_partners(SimDev* d, uint32_t n, uint32_t* out, cudaStream_t st) {
+  k_gather_partners<<<(n + 255) / 256, 256, 0, st>>>(d, out);
+}
+void launch_gather_edges(SimDev* d, uint32_t cap, uint2* out, uint32_t* count, cudaStream_t st) {
+  k_gather_edges<<<304, 256, 0, st>>>(d, cap, out, count);
+}
+void launch_profile_convert(SimDev* d, uint32_t first, uint32_t count, uint32_t bins, double* out,
+                            cudaStream_t st) {
+  if (count == 0) return;
+  k_profile_convert<<<152, 256, 0, st>>>(d, first, count, bins, out);
+}
+
+}  // namespace kmc

@@ -1,0 +1,249 @@
+// kmc_sort.cu -- binning of the particles into cells (Sec. 2: every particle is
+// appended to the list of its bin; the grid is rebuilt every step).
+//
+// GB300 form: a counting sort into a column-Morton cell order.
+//   k_count   cell key per particle; rank inside the cell by a warp-aggregated
+//             atomic increment (lanes with equal keys share one atomic).
+//   scan      segmented exclusive scan of the counts -> cell_start (three launches,
+//             no inter-block waiting); clears the counts for the next step.
+//   k_scatter permutes the binary64 state into the other buffer, writes the
+//             binary32 cell-local mirror for the guarded search and resets the
+//             per-particle step arrays.
+// The order inside a cell depends on atomic timing; nothing downstream depends on
+// it (argmin over a total order, integer counters, order-free profile sums).
+#include "kmc_internal.cuh"
+
+namespace kmc {
+
+// --------------------------------------------------------------------------- //
+__global__ void __launch_bounds__(kTile) k_count(Batch B) {
+  int k = find_sim(B.ptile, B.nsims, blockIdx.x);
+  SimDev& s = *B.sims[k];
+  if (!sim_active(s)) return;
+  const Grid& g = s.d.grid;
+  uint32_t p = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
+  bool valid = p < s.n;
+  uint32_t key = 0;
+  if (valid) {
+    int par = s.d.parity;
+    int cx = cell_coord(g, 0, s.x[par][0][p]);
+    int cy = cell_coord(g, 1, s.x[par][1][p]);
+    int cz = cell_coord(g, 2, s.x[par][2][p]);
+    key = col_code(g, (uint32_t)cy, (uint32_t)cz) * (uint32_t)g.nc[0] + (uint32_t)cx;
+  }
+  // warp aggregation: one atomic per distinct key in the warp
+  unsigned active = __ballot_sync(0xFFFFFFFFu, valid);
+  if (valid) {
+    unsigned peers = __match_any_sync(active, key);
+    int leader = __ffs(peers) - 1;
+    unsigned lane = threadIdx.x & 31u;
+    uint32_t base = 0;
+    if ((int)lane == leader) base = atomicAdd(&s.cell_count[key], (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    uint32_t below = __popc(peers & ((1u << lane) - 1u));
+    s.key[p] = key;
+    s.rank[p] = base + below;
+  }
+}
+
+// --------------------------------------------------------------------------- //
+// Segmented exclusive scan.  which = 0: cell counts -> cell_start (and clear the
+// counts); which = 1: degrees -> CSR offsets.  Element `len` is a virtual zero, so
+// out[len] receives the total.
+struct ScanView {
+  const uint32_t* in;
+  uint32_t* out;
+  uint32_t* clear;
+  uint32_t len;
+};
+
+__device__ __forceinline__ ScanView scan_view(SimDev& s, int which) {
+  ScanView v;
+  if (which == 0) {
+    v.in = s.cell_count; v.out = s.cell_start; v.clear = s.cell_count; v.len = s.d.grid.nkeys;
+  } else {
+    v.in = s.deg; v.out = s.off; v.clear = nullptr; v.len = s.n;
+  }
+  return v;
+}
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* total) {
+  __shared__ uint32_t warp_sums[kTile / 32 + 1];
+  unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+  uint32_t incl = x;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= (unsigned)o) incl += y;
+  }
+  if (lane == 31) warp_sums[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = lane < kTile / 32 ? warp_sums[lane] : 0;
+    uint32_t wi = w;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+      if (lane >= (unsigned)o) wi += y;
+    }
+    if (lane < kTile / 32) warp_sums[lane] = wi - w;  // exclusive
+    if (lane == kTile / 32 - 1) warp_sums[kTile / 32] = wi;
+  }
+  __syncthreads();
+  uint32_t r = warp_sums[wid] + incl - x;
+  if (total) *total = warp_sums[kTile / 32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kTile) k_scan_reduce(Batch B, int which) {
+  const uint32_t* pre = which == 0 ? B.stile_c : B.stile_n;
+  int k = find_sim(pre, B.nsims, blockIdx.x);
+  SimDev& s = *B.sims[k];
+  uint32_t sum = 0;
+  if (sim_active(s)) {
+    ScanView v = scan_view(s, which);
+    uint32_t base = (blockIdx.x - pre[k]) * kScanTile;
+    for (int i = threadIdx.x; i < kScanTile; i += kTile) {
+      uint32_t e = base + i;
+      if (e < v.len) sum += v.in[e];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
+  __shared__ uint32_t ws[kTile / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < kTile / 32; ++w) t += ws[w];
+    B.tile_sums[blockIdx.x] = t;
+  }
+}
+
+// one block: exclusive scan of the tile sums inside each simulation's segment
+__global__ void __launch_bounds__(1024) k_scan_tiles(Batch B, int which, uint32_t ntiles) {
+  const uint32_t* pre = which == 0 ? B.stile_c : B.stile_n;
+  __shared__ uint32_t warp_sums[32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+  for (uint32_t base = 0; base < ntiles; base += 1024) {
+    uint32_t i = base + threadIdx.x;
+    uint32_t x = i < ntiles ? B.tile_sums[i] : 0;
+    uint32_t incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= (unsigned)o) incl += y;
+    }
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t w = warp_sums[lane];
+      uint32_t wi = w;
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+        if (lane >= (unsigned)o) wi += y;
+      }
+      warp_sums[lane] = wi - w;
+    }
+    __syncthreads();
+    uint32_t excl = carry + warp_sums[wid] + incl - x;
+    __syncthreads();
+    if (i < ntiles) B.tile_sums[i] = excl;
+    if (threadIdx.x == 1023) carry = excl + x;
+    __syncthreads();
+  }
+  // make each segment start at zero
+  __shared__ uint32_t seg_base[kMaxGroup];
+  for (int k = threadIdx.x; k < B.nsims; k += 1024) {
+    uint32_t t0 = pre[k];
+    seg_base[k] = t0 < ntiles ? B.tile_sums[t0] : 0;
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < ntiles; i += 1024) {
+    int k = find_sim(pre, B.nsims, i);
+    B.tile_sums[i] -= seg_base[k];
+  }
+}
+
+__global__ void __launch_bounds__(kTile) k_scan_apply(Batch B, int which) {
+  const uint32_t* pre = which == 0 ? B.stile_c : B.stile_n;
+  int k = find_sim(pre, B.nsims, blockIdx.x);
+  SimDev& s = *B.sims[k];
+  if (!sim_active(s)) return;
+  ScanView v = scan_view(s, which);
+  uint32_t base = (blockIdx.x - pre[k]) * kScanTile;
+  if (base > v.len) return;
+  constexpr int PER = kScanTile / kTile;
+  uint32_t vals[PER];
+  uint32_t e0 = base + threadIdx.x * PER;
+  uint32_t local = 0;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    uint32_t e = e0 + i;
+    vals[i] = e < v.len ? v.in[e] : 0;
+    local += vals[i];
+  }
+  uint32_t off = block_exclusive_scan(local, nullptr) + B.tile_sums[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    uint32_t e = e0 + i;
+    if (e <= v.len) v.out[e] = off;
+    if (v.clear && e < v.len && vals[i]) v.clear[e] = 0;
+    off += vals[i];
+  }
+}
+
+// --------------------------------------------------------------------------- //
+__global__ void __launch_bounds__(kTile) k_scatter(Batch B) {
+  int k = find_sim(B.ptile, B.nsims, blockIdx.x);
+  SimDev& s = *B.sims[k];
+  if (!sim_active(s)) return;
+  uint32_t p = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
+  if (p >= s.n) return;
+  const Grid& g = s.d.grid;
+  int src = s.d.parity, dstb = src ^ 1;
+  uint32_t key = s.key[p];
+  uint32_t dst = s.cell_start[key] + s.rank[p];
+  double xs[3], vs[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    xs[a] = s.x[src][a][p];
+    vs[a] = s.v[src][a][p];
+    s.x[dstb][a][dst] = xs[a];
+    s.v[dstb][a][dst] = vs[a];
+  }
+  s.id[dstb][dst] = s.id[src][p];
+  s.last[dstb][dst] = s.last[src][p];
+  s.skey[dst] = key;
+  s.deg[dst] = 0;
+  s.partner[dst] = kNone;
+  if (s.precision == KMC_GUARDED_FP32) {
+    int c[3];
+    key_decode(g, key, c[0], c[1], c[2]);
+    float o[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      // offset from the cell's lower corner, subtracted in binary64, rounded once
+      double corner = g.nc[a] == 1 ? 0.0 : dmul((double)c[a], g.w[a]);
+      o[a] = __double2float_rn(dsub(xs[a], corner));
+    }
+    s.mir_a[dst] = make_float4(o[0], o[1], o[2], __double2float_rn(vs[0]));
+    s.mir_b[dst] = make_float2(__double2float_rn(vs[1]), __double2float_rn(vs[2]));
+  }
+}
+
+// --------------------------------------------------------------------------- //
+void launch_seg_scan(const LaunchPlan& L, int which, cudaStream_t st) {
+  uint32_t nt = which == 0 ? L.stiles_c : L.stiles_n;
+  k_scan_reduce<<<nt, kTile, 0, st>>>(L.b, which);
+  k_scan_tiles<<<1, 1024, 0, st>>>(L.b, which, nt);
+  k_scan_apply<<<nt, kTile, 0, st>>>(L.b, which);
+}
+
+void launch_sort(const LaunchPlan& L, cudaStream_t st) {
+  k_count<<<L.ptiles, kTile, 0, st>>>(L.b);
+  launch_seg_scan(L, 0, st);
+  k_scatter<<<L.ptiles, kTile, 0, st>>>(L.b);
+}
+
+}  // namespace kmc

@@ -1,0 +1,245 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Trajectories, candidate-pair lists, partners and per-step counts must be
+bit-identical; profiles (order-free fixed-point sums on the GPU, id-order binary64
+sums in the oracle) agree within the rounding bound of the oracle's summation.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import kmc_inputs as ki
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1310_3437_gb300 as kmc  # noqa: E402
+
+FP64 = kmc.KMC_FP64
+FP32 = kmc.KMC_GUARDED_FP32
+
+
+def gpu_sim(setup, arrays, precision=FP64, stencil=1, cell_scale=1.0, last=None, step0=0,
+            edge_cap=0):
+    p = kmc.params_from_setup(setup, precision=precision, stencil=stencil, cell_scale=cell_scale,
+                              step0=step0, edge_cap=edge_cap)
+    return kmc.Simulation(p, arrays, last=last)
+
+
+def assert_same_state(sim, st: oracle.State):
+    arrays, last = sim.state()
+    for k in range(6):
+        a, b = arrays[k], st.a[k]
+        if not np.array_equal(a.view(np.uint64), b.view(np.uint64)):
+            bad = np.nonzero(a.view(np.uint64) != b.view(np.uint64))[0]
+            raise AssertionError(f"component {k}: {len(bad)} particles differ, first {bad[:5]}: "
+                                 f"{a[bad[:3]]} vs {b[bad[:3]]}")
+    assert np.array_equal(last, st.last)
+
+
+def assert_same_counts(gpu_counts, or_counts):
+    assert len(gpu_counts) == len(or_counts)
+    for g, o in zip(gpu_counts, or_counts):
+        assert g["step"] == o["step"]
+        assert (g["collisions"], g["edges"], g["round_pairs"]) == \
+               (o["collisions"], o["edges"], o["round_pairs"]), (g, o)
+
+
+def run_both(setup, steps, precision=FP64, arrays=None, **kw):
+    arrays = arrays if arrays is not None else ki.initial_state(setup)
+    st = oracle.State(arrays)
+    oc, oprof = oracle.run(setup, st, 0, steps)
+    sim = gpu_sim(setup, arrays, precision=precision, **kw)
+    sim.step(steps).sync()
+    return sim, st, oc, oprof
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_equilibrium_box_4096_200_steps_bit_exact(precision):
+    s = ki.equilibrium_setup(n=4096, seed=1)
+    sim, st, oc, _ = run_both(s, 200, precision)
+    assert_same_counts(sim.counts(), oc)
+    assert_same_state(sim, st)
+    assert sum(c["collisions"] for c in oc) > 20000
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_piston_tube_pair_lists_every_step(precision):
+    s = ki.piston_setup(n=1 << 15, seed=2, box=(8.0, 0.25, 0.25), profile_bins=0, profile_every=0)
+    arrays = ki.initial_state(s)
+    st = oracle.State(arrays)
+    sim = gpu_sim(s, arrays, precision=precision)
+    for step in range(6):
+        pi, pj, _, _ = oracle.candidate_pairs(s, st)
+        counts, partner, _ = oracle.step(s, st, step)
+        sim.step(1).sync()
+        e = sim.edges()
+        want = np.stack([pi, pj], axis=1)
+        assert e.shape == want.shape and np.array_equal(e, want), f"step {step}"
+        assert np.array_equal(sim.partners(), partner), f"step {step}"
+    assert_same_state(sim, st)
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_piston_tube_trajectory_bit_exact(precision):
+    s = ki.piston_setup(n=1 << 14, seed=3, box=(8.0, 0.125, 0.125), profile_bins=0,
+                        profile_every=0)
+    sim, st, oc, _ = run_both(s, 300, precision)
+    assert_same_counts(sim.counts(), oc)
+    assert_same_state(sim, st)
+
+
+@pytest.mark.parametrize("stencil,cell_scale", [(2, 1.0), (1, 1.7), (2, 2.3)])
+def test_results_do_not_depend_on_grid_tuning(stencil, cell_scale):
+    s = ki.equilibrium_setup(n=6000, seed=4)
+    arrays = ki.initial_state(s)
+    ref = gpu_sim(s, arrays, FP32).step(40).sync()
+    alt = gpu_sim(s, arrays, FP32, stencil=stencil, cell_scale=cell_scale).step(40).sync()
+    a, la = ref.state()
+    b, lb = alt.state()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    assert np.array_equal(la, lb)
+    assert [c["collisions"] for c in ref.counts()] == [c["collisions"] for c in alt.counts()]
+
+
+def test_fp32_and_fp64_pair_lists_identical_with_many_near_threshold_pairs():
+    """Velocities and positions on coarse lattices make many pairs sit exactly on or
+    within a few ulps of the t* = 0, t* = dt and d_min = d0 thresholds."""
+    rng = np.random.default_rng(5)
+    n = 5000
+    L = 1.0
+    pos = [np.minimum(np.round(rng.random(n) * 64) / 64, np.nextafter(L, 0)) for _ in range(3)]
+    vel = [np.round(rng.normal(0, 1, n) * 8) / 8 for _ in range(3)]
+    s = ki.Setup(n=n, box=(L, L, L), bc=(0, 0, 0), d0=1 / 32, dt=1 / 16, seed=5,
+                 name="equilibrium_lattice")
+    st = oracle.State(pos + vel)
+    pi, pj, _, _ = oracle.candidate_pairs(s, st)
+    for prec in (FP64, FP32):
+        sim = gpu_sim(s, pos + vel, prec).step(1).sync()
+        e = sim.edges()
+        assert np.array_equal(e, np.stack([pi, pj], axis=1))
+
+
+def test_edge_cases():
+    # one particle
+    s = ki.equilibrium_setup(n=1, seed=1)
+    sim, st, oc, _ = run_both(s, 5)
+    assert_same_state(sim, st)
+    # a head-on pair
+    s = ki.Setup(n=2, box=(1.0, 1.0, 1.0), bc=(0, 0, 0), d0=0.05, dt=0.1, seed=9,
+                 name="equilibrium_pair")
+    arrays = [np.array([0.40, 0.45]), np.array([0.5, 0.51]), np.array([0.5, 0.5]),
+              np.array([0.3, -0.3]), np.array([0.0, 0.0]), np.array([0.0, 0.0])]
+    for prec in (FP64, FP32):
+        sim, st, oc, _ = run_both(s, 3, prec, arrays=arrays)
+        assert oc[0]["collisions"] == 1
+        assert_same_counts(sim.counts(), oc)
+        assert_same_state(sim, st)
+    # thin periodic slab (y and z collapse to one cell), particles on the faces
+    rng = np.random.default_rng(6)
+    n = 3000
+    pos = [rng.random(n), rng.random(n) * 0.05, rng.random(n) * 0.05]
+    pos[0][:50] = 0.0
+    pos[0][50:100] = np.nextafter(1.0, 0)
+    vel = [rng.normal(0, 1, n) for _ in range(3)]
+    vel[0][100:200] = vel[0][99]
+    s = ki.Setup(n=n, box=(1.0, 0.05, 0.05), bc=(0, 0, 0), d0=0.01, dt=0.01, seed=7,
+                 name="equilibrium_slab")
+    for prec in (FP64, FP32):
+        sim, st, oc, _ = run_both(s, 20, prec, arrays=pos + vel)
+        assert_same_counts(sim.counts(), oc)
+        assert_same_state(sim, st)
+    # reflecting box on all axes with a static upper wall
+    s = ki.Setup(n=2000, box=(1.0, 0.5, 0.7), bc=(1, 1, 1), piston_x0=1.0, piston_u=0.0,
+                 d0=0.02, dt=0.02, seed=8, name="walls")
+    rng = np.random.default_rng(8)
+    arrays = [rng.random(2000) * b for b in (1.0, 0.5, 0.7)] + [rng.normal(0, 2, 2000) for _ in range(3)]
+    for prec in (FP64, FP32):
+        sim, st, oc, _ = run_both(s, 30, prec, arrays=arrays)
+        assert_same_counts(sim.counts(), oc)
+        assert_same_state(sim, st)
+
+
+def test_overflowing_pair_buffer_grows_and_results_are_unchanged():
+    s = ki.equilibrium_setup(n=4096, seed=10)
+    arrays = ki.initial_state(s)
+    st = oracle.State(arrays)
+    oc, _ = oracle.run(s, st, 0, 30)
+    sim = gpu_sim(s, arrays, FP64, edge_cap=8)
+    sim.step(30).sync()
+    assert_same_counts(sim.counts(), oc)
+    assert_same_state(sim, st)
+
+
+def test_resume_from_observed_state_is_bit_exact():
+    s = ki.piston_setup(n=6000, seed=11, box=(2.0, 0.5, 0.5), profile_bins=0, profile_every=0)
+    arrays = ki.initial_state(s)
+    full = gpu_sim(s, arrays, FP32).step(30).sync()
+    half = gpu_sim(s, arrays, FP32).step(12).sync()
+    mid, last = half.state()
+    rest = gpu_sim(s, mid, FP32, last=last, step0=12).step(18).sync()
+    a, la = full.state()
+    b, lb = rest.state()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    assert np.array_equal(la, lb)
+    assert rest.step_index() == 30
+
+
+def test_profiles_match_oracle_within_summation_bound():
+    s = ki.piston_setup(n=1 << 14, seed=12, box=(8.0, 0.125, 0.125), profile_bins=256,
+                        profile_every=50)
+    sim, st, oc, oprof = run_both(s, 150)
+    gprof = sim.profiles()
+    assert gprof.shape == oprof.shape == (3, 256, 7)
+    assert np.array_equal(gprof[:, :, 0], oprof[:, :, 0])  # counts are integers
+    # the oracle sums in id order in binary64: |error| <= (n-1) u sum|terms|; the GPU
+    # sum is exact to 2^-64 per term and rounded once
+    u = 2.0 ** -53
+    _, _ = sim.state()
+    cnt = oprof[:, :, 0]
+    for q in range(1, 7):
+        mag_bound = np.abs(oprof[:, :, q]) + 1e-300
+        # sum |terms| <= count * max|term|: bound with the per-bin second moments
+        sq = oprof[:, :, 4 + (q - 1) % 3]
+        abs_sum = np.sqrt(np.maximum(cnt * sq, 0)) if q <= 3 else sq
+        tol = (cnt + 2) * u * abs_sum + cnt * 2.0 ** -64 + 2 * u * mag_bound
+        assert np.all(np.abs(gprof[:, :, q] - oprof[:, :, q]) <= tol), q
+
+
+def test_full_size_piston_tube_two_steps_bit_exact():
+    """The 2^20-particle piston tube at full size: two steps against the oracle."""
+    s = ki.piston_setup(n=1 << 20, seed=2)
+    arrays = ki.initial_state(s)
+    st = oracle.State(arrays)
+    oc, _ = oracle.run(s, st, 0, 2)
+    for prec in (FP64, FP32):
+        sim = gpu_sim(s, arrays, prec).step(2).sync()
+        assert_same_counts(sim.counts(), oc)
+        assert_same_state(sim, st)
+
+
+def test_group_of_uneven_runs_equals_each_run_alone():
+    setups = ki.ensemble_setups(count=6, lo=1 << 10, hi=1 << 14, steps=25)
+    arrays = [ki.initial_state(s) for s in setups]
+    sims = [gpu_sim(s, a, FP32) for s, a in zip(setups, arrays)]
+    g = kmc.Group(sims)
+    budgets = [25, 10, 25, 17, 3, 25]
+    for sim, b in zip(sims, budgets):
+        g.budget(sim, b)
+    g.step(25)
+    g.sync()
+    for sim, b in zip(sims, budgets):
+        assert g.steps_left(sim) == 0
+    for s, a, sim, b in zip(setups, arrays, sims, budgets):
+        st = oracle.State(a)
+        oc, _ = oracle.run(s, st, 0, b)
+        assert_same_counts(sim.counts(), oc)
+        assert_same_state(sim, st)
+    g.close()
