@@ -1,0 +1,420 @@
+"""Benchmark: particle-steps/s of the collision step at 2^24 particles on GB300.
+
+Workload: the piston-shock tube (box 8 x 1 x 1, periodic in y and z, reflecting wall
+at x = 0, piston from x = 8 inward at u_p = 2), N = 2^24, mean free path 0.02
+(d0 from lambda = 1/(sqrt(2) n sigma)), dt = 0.1 lambda / sqrt(3), seed 2; synthetic
+uniform positions and Maxwellian velocities (kT/m = 1).  The headline value is the
+guarded-binary32 path; the binary64 GPU path is timed on the same workload beside it.
+
+One JSON line on rank 0.  Under torchrun each rank runs an independent replica on
+its own GPU (the method has no exchange step in this form); value = all ranks'
+particle-steps / max over ranks of the timed region.
+
+--impl reference times the CPU oracle (the plain binary64 definition) on a bounded
+sample of the same workload: the 8 x 0.25 x 0.25 cross-section of the tube at the
+same density (2^20 particles), one oracle step per benchmark step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import kmc_inputs as ki  # noqa: E402
+
+METRIC = "particle-steps/s at 2^24, guarded-FP32 vs FP64 GPU; serve p50/p99 latency"
+UNIT = "particle-steps/s"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# binary32 lanes x 2 flop per FMA x SM count x maximum SM clock (unit counts and
+# clocks of the part: 152 SMs, 128 FP32 lanes per SM, 2070 MHz)
+ALU_FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# flops of one binary32 pair pre-test: r (3), v (3), |r|^2 (5), |v|^2 (5), bound (2)
+FLOPS_PER_PAIR_TEST = 18
+# algorithmic bytes of the sort per particle: read the binary64 state and id/last
+# (56), write it permuted (56), write the cell-local binary32 mirror (24) and the key (4)
+SORT_BYTES_PER_PARTICLE = 140
+
+
+def headline_setup(n: int):
+    return ki.piston_setup(n=n, seed=2, profile_bins=256, profile_every=100)
+
+
+def sample_setup():
+    """Cross-section sample of the headline tube: same density, 1/16 of the particles."""
+    n_full = 1 << 24
+    full = headline_setup(n_full)
+    s = ki.piston_setup(n=n_full // 16, seed=2, box=(8.0, 0.25, 0.25), profile_bins=0,
+                        profile_every=0)
+    return s.with_(d0=full.d0, dt=full.dt, name="piston_tube_cross_section")
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def wait_first_sample(self, timeout: float = 3.0):
+        t0 = time.time()
+        while self.proc and time.time() - t0 < timeout:
+            try:
+                if os.path.getsize(self.path) > 0:
+                    return
+            except OSError:
+                pass
+            time.sleep(0.02)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def source_sha(path):
+    h = hashlib.sha256()
+    with open(path, "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_file: str):
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, or None if
+    the kernel source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        rec = json.load(open(p)).get(kernel_file)
+        src = os.path.join(ROOT, "paper_1310_3437_gb300", "csrc", kernel_file)
+        if rec and rec.get("source_sha") == source_sha(src):
+            return rec
+    except Exception:
+        pass
+    return None
+
+
+# --------------------------------------------------------------------------- #
+def oracle_sample_rate(max_seconds: float, warmup: int = 0, steps_cap: int = 50):
+    """Time the oracle on the cross-section sample; returns (rate, steps, seconds, threads)."""
+    import oracle
+
+    s = sample_setup()
+    st = oracle.State(ki.initial_state(s))
+    for k in range(warmup):
+        oracle.step(s, st, k)
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps_cap:
+        oracle.step(s, st, warmup + done)
+        done += 1
+        if time.perf_counter() - t0 >= max_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return s.n * done / dt, done, dt, oracle.max_threads(), s
+
+
+def run_reference(args):
+    world, rank, local = dist_info()
+    if rank != 0:
+        return
+    import oracle
+
+    s = sample_setup()
+    st = oracle.State(ki.initial_state(s))
+    for k in range(args.warmup):
+        oracle.step(s, st, k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.step(s, st, args.warmup + k)
+    dt = time.perf_counter() - t0
+    rate = s.n * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"piston_tube_n{1 << 24}", "sample": "8x0.25x0.25 cross-section",
+                   "n_sample": s.n},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": oracle.max_threads(),
+                         "kind": "oracle",
+                         "sample": f"{s.n} particles (8x0.25x0.25 cross-section at the same "
+                                   f"density), {args.steps} steps after {args.warmup}"},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- #
+def run_gpu(args):
+    import torch
+
+    import paper_1310_3437_gb300 as kmc
+
+    world, rank, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    if args.workload == "sample":
+        setup = sample_setup()
+        n = setup.n
+    else:
+        n = args.n
+        setup = headline_setup(n)
+    if world > 1:
+        setup = setup.with_(seed=setup.seed + rank)
+    arrays = ki.initial_state(setup)
+    dev_arrays = [torch.from_numpy(a).to(dev) for a in arrays]
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # a dedicated stream: the library launches on it and the events are recorded on it
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+
+    def timed_run(precision, warm, steps, sample_clocks=False):
+        params = kmc.params_from_setup(setup, precision=precision)
+        sim = kmc.Simulation(params, dev_arrays, stream=stream.cuda_stream)
+        sim.step(warm).sync()
+        sim.counts()
+        l0 = sim.launches()
+        sampler = ClockSampler(dev.index or 0) if sample_clocks else None
+        barrier()
+        if sampler:
+            sampler.start()
+            sampler.wait_first_sample()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        sim.sync()
+        launches = sim.launches() - l0
+        counts = sim.counts()
+        return sim, ms, counts, launches, clocks
+
+    # ---- guarded binary32 (headline) ----
+    sim32, ms32, counts32, launches32, clocks = timed_run(kmc.KMC_GUARDED_FP32, args.warmup,
+                                                          args.steps, sample_clocks=True)
+    value = world * n * args.steps / (ms32 / 1e3)
+    # per-phase times of the next steps, CUDA events on the simulation's stream
+    tsteps = max(3, min(args.steps, 10))
+    sim32.set_timing(True)
+    sim32.step(tsteps).sync()
+    ph = sim32.phase_ms()
+    tcounts = sim32.counts()
+    sim32.set_timing(False)
+    tests = np.mean([c["pair_tests"] for c in tcounts]) if tcounts else 0.0
+    search_ms = ph["search"] / max(1, ph["steps"])
+    sort_ms = ph["sort"] / max(1, ph["steps"])
+    edges_mean = float(np.mean([c["edges"] for c in counts32])) if counts32 else 0.0
+    coll_mean = float(np.mean([c["collisions"] for c in counts32])) if counts32 else 0.0
+    sim32.close()
+
+    # ---- binary64 path on the same workload (fewer steps: ~70x slower arithmetic) ----
+    fp64 = None
+    if not args.skip_fp64:
+        k64 = max(1, min(args.steps, args.fp64_steps))
+        sim64, ms64, counts64, _, _ = timed_run(kmc.KMC_FP64, args.warmup, k64)
+        v64 = world * n * k64 / (ms64 / 1e3)
+        same = [(c["collisions"], c["edges"]) for c in counts64] == \
+               [(c["collisions"], c["edges"]) for c in counts32[:k64]]
+        fp64 = {"value": v64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
+                "same_counts_as_fp32": bool(same)}
+        sim64.close()
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.skip_e2e:
+        pinned = [torch.from_numpy(a).pin_memory() for a in arrays]
+        out = torch.empty(52 * n, dtype=torch.uint8).pin_memory()
+        ke = args.steps
+        barrier()
+        t0 = time.perf_counter()
+        params = kmc.params_from_setup(setup, precision=kmc.KMC_GUARDED_FP32)
+        sim = kmc.Simulation(params, pinned, stream=stream.cuda_stream)
+        sim.step(ke)
+        kmc.sim_observe(sim.handle, kmc.KMC_OBS_STATE, out.data_ptr(), out.numel())
+        torch.cuda.synchronize(dev)
+        te = max_over_ranks(time.perf_counter() - t0)
+        sim.close()
+        e2e = {"value": world * n * ke / te, "unit": UNIT,
+               "h2d_bytes_per_step": 48 * n / ke, "d2h_bytes_per_step": 52 * n / ke,
+               "job": f"create from pinned host arrays, {ke} steps, state read back"}
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    pk, pk_kind = peaks()
+    achieved_tflops = tests * FLOPS_PER_PAIR_TEST / (search_ms / 1e3) / 1e12 if search_ms > 0 else 0.0
+    traffic = ncu_traffic("kmc_search.cu")
+    roofline = {
+        "kernel": "k_search<guarded fp32>",
+        "bound": "alu",
+        "achieved": achieved_tflops,
+        "peak": ALU_FP32_PEAK_TFLOPS,
+        "unit": "TFLOP/s",
+        "frac": achieved_tflops / ALU_FP32_PEAK_TFLOPS,
+        "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz",
+        "traffic": (traffic["dram_bytes_per_particle"] * n) if traffic else None,
+        "flops_per_pair_test": FLOPS_PER_PAIR_TEST,
+        "pair_tests_per_launch": float(tests),
+        "launch_ms": search_ms,
+    }
+    sort_gbs = SORT_BYTES_PER_PARTICLE * n / (sort_ms / 1e3) / 1e9 if sort_ms > 0 else 0.0
+    roofline_sort = {
+        "kernel": "sort phase (k_count, scan, k_scatter)",
+        "bound": "hbm", "achieved": sort_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+        "frac": sort_gbs / pk["hbm_gbs"], "peak_source": f"{pk_kind} hbm_gbs",
+        "bytes_per_particle": SORT_BYTES_PER_PARTICLE, "launch_ms": sort_ms,
+    }
+
+    cpu = None
+    if not args.skip_cpu and world >= 1:
+        rate, done, secs, threads, s = oracle_sample_rate(args.cpu_seconds, warmup=0)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{s.n} particles (8x0.25x0.25 cross-section of the tube, same "
+                         f"density), {done} oracle steps from t=0, {secs:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair tests + f64 state",
+        "data": "synthetic",
+        "config": {"workload": f"piston_tube_n{n}" if args.workload == "tube" else
+                   f"piston_tube_cross_section_n{n}", "n": n, "box": list(setup.box),
+                   "lambda": 0.02, "d0": setup.d0, "dt": setup.dt, "u_p": setup.piston_u,
+                   "precision": "guarded-fp32", "l2": "inputs larger than L2 (state ~1.9 GB)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "fp64": fp64,
+        "speedup_fp32_over_fp64": (value / fp64["value"]) if fp64 else None,
+        "roofline": roofline,
+        "roofline_sort": roofline_sort,
+        "phase_ms_per_step": {k: ph[k] / max(1, ph["steps"]) for k in ("sort", "search", "match", "push")},
+        "pair_tests_per_s": tests / (search_ms / 1e3) if search_ms > 0 else None,
+        "candidate_pairs_per_step": edges_mean, "collisions_per_step": coll_mean,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches32),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1 << 24)
+    ap.add_argument("--workload", default="tube", choices=["tube", "sample"],
+                    help="tube: the 2^24 piston tube; sample: its 8x0.25x0.25 cross-section "
+                         "(2^20 particles, same density), for profiling")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -68,6 +68,11 @@ extern "C" {
 #define KMC_OBS_EDGES 5    /* candidate pairs of the last completed step as uint32
                               (id_lo, id_hi) pairs, unordered list */
 #define KMC_OBS_STEP 6     /* one uint64: absolute index of the next step */
+#define KMC_OBS_LAUNCHES 7 /* one uint64: kernel launches enqueued for this simulation
+                              (steps of its group included) */
+#define KMC_OBS_PHASE_MS 8 /* 5 binary64: milliseconds spent in the sort, search,
+                              matching (exact test, lists, rounds, scatter) and push
+                              phases while timing was on, then the number of timed steps */
 
 #define KMC_NONE 0xFFFFFFFFu
 
@@ -115,8 +120,8 @@ typedef struct kmc_group kmc_group;
 
 /* Create a simulation from an initial state (Sec. 2: particles initialised in a
  * box).  x..vz: n binary64 each, id order, host or device.  last: n uint32 last
- * collision partner ids or NULL (none).  stream: a cudaStream_t (NULL = the
- * legacy default stream).  The arrays are copied; the caller keeps them.
+ * collision partner ids or NULL (none).  stream: a cudaStream_t (NULL: the library
+ * creates a stream of its own).  The arrays are copied; the caller keeps them.
  * Errors: KMC_EINVAL (bad parameter, particle outside the box), KMC_ENOMEM,
  * KMC_ECUDA.  On error *out is NULL. */
 int sim_create(const kmc_params* p, const double* x, const double* y, const double* z,
@@ -137,6 +142,12 @@ int sim_sync(kmc_sim* s);
  * Returns the number of items written (records, snapshots, pairs, or 1) or a
  * negative status: KMC_EINVAL (unknown observable, dst too small). */
 int64_t sim_observe(kmc_sim* s, int what, void* dst, size_t dst_bytes);
+
+/* Diagnostics: with enable != 0, later sim_step calls launch the kernels one by one
+ * (no CUDA graph) with CUDA events around each phase on the simulation's stream, and
+ * wait for each step; KMC_OBS_PHASE_MS returns the accumulated times.  enable = 0
+ * restores graph replay.  Results do not change. */
+int sim_set_timing(kmc_sim* s, int enable);
 
 /* Free the simulation (waits for its stream).  NULL is accepted. */
 int sim_destroy(kmc_sim* s);

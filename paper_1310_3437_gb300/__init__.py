@@ -38,6 +38,8 @@ KMC_OBS_COUNTS = 3
 KMC_OBS_PROFILES = 4
 KMC_OBS_EDGES = 5
 KMC_OBS_STEP = 6
+KMC_OBS_LAUNCHES = 7
+KMC_OBS_PHASE_MS = 8
 
 KMC_NONE = 0xFFFFFFFF
 
@@ -95,6 +97,8 @@ def lib():
             L.sim_sync.restype = C.c_int
             L.sim_observe.argtypes = [_P, C.c_int, _P, C.c_size_t]
             L.sim_observe.restype = C.c_int64
+            L.sim_set_timing.argtypes = [_P, C.c_int]
+            L.sim_set_timing.restype = C.c_int
             L.sim_destroy.argtypes = [_P]
             L.sim_destroy.restype = C.c_int
             L.sim_last_error.argtypes = [_P]
@@ -150,6 +154,10 @@ def sim_sync(sim):
 
 def sim_observe(sim, what: int, dst, dst_bytes: int):
     return _check(lib().sim_observe(sim, what, dst, dst_bytes), sim)
+
+
+def sim_set_timing(sim, enable: bool):
+    return _check(lib().sim_set_timing(sim, 1 if enable else 0), sim)
 
 
 def sim_destroy(sim):

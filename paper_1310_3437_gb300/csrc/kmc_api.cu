@@ -34,6 +34,7 @@ struct Plan {
   cudaGraphExec_t graph = nullptr;
   bool graph_tried = false;
   int precision = 0, K = 1, max_rounds = 4;
+  int launches_per_step = 0;
   bool has_profiles = false;
 };
 
@@ -68,6 +69,10 @@ struct kmc_sim {
   void* stage = nullptr;
   size_t stage_bytes = 0;
   uint64_t hist_read = 0, prof_read = 0;
+  uint64_t launches = 0;     // kernel launches enqueued for this simulation
+  bool timing = false;       // per-phase CUDA-event timing (no graph)
+  double phase_ms[4] = {0, 0, 0, 0};
+  uint64_t timed_steps = 0;
   std::string err;
 };
 
@@ -268,21 +273,57 @@ int build_plan(Plan& P, const std::vector<kmc_sim*>& sims, cudaStream_t st, std:
   return KMC_OK;
 }
 
-void enqueue_step(const Plan& P, cudaStream_t st) {
-  launch_sort(P.L, st);
-  launch_search(P.L, P.precision, P.K, st);
-  launch_match(P.L, P.max_rounds, st);
-  launch_push(P.L, st);
+int enqueue_step(const Plan& P, cudaStream_t st) {
+  int n = launch_sort(P.L, st);
+  n += launch_search(P.L, P.precision, P.K, st);
+  n += launch_match(P.L, P.max_rounds, st);
+  n += launch_push(P.L, st);
+  return n;
+}
+
+// Diagnostic stepping: phases launched one by one between CUDA events on the
+// stream, waiting for each step.
+int run_steps_timed(Plan& P, cudaStream_t st, uint64_t nsteps, kmc_sim* s) {
+  cudaEvent_t ev[5];
+  for (int i = 0; i < 5; ++i) KCHECK(cudaEventCreate(&ev[i]), s->err);
+  int rc = KMC_OK;
+  for (uint64_t k = 0; k < nsteps && rc == KMC_OK; ++k) {
+    int n = 0;
+    cudaEventRecord(ev[0], st);
+    n += launch_sort(P.L, st);
+    cudaEventRecord(ev[1], st);
+    n += launch_search(P.L, P.precision, P.K, st);
+    cudaEventRecord(ev[2], st);
+    n += launch_match(P.L, P.max_rounds, st);
+    cudaEventRecord(ev[3], st);
+    n += launch_push(P.L, st);
+    cudaEventRecord(ev[4], st);
+    cudaError_t e = cudaEventSynchronize(ev[4]);
+    if (e != cudaSuccess) {
+      s->err = std::string("timed step: ") + cudaGetErrorString(e);
+      rc = KMC_ECUDA;
+      break;
+    }
+    for (int i = 0; i < 4; ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      s->phase_ms[i] += ms;
+    }
+    s->timed_steps += 1;
+    s->launches += n;
+  }
+  for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+  return rc;
 }
 
 // Replay the captured step nsteps times (capture on first use; plain launches if
-// the stream cannot be captured).
-int run_steps(Plan& P, cudaStream_t st, uint64_t nsteps, std::string& err) {
+// the stream cannot be captured).  Returns launches through *launched.
+int run_steps(Plan& P, cudaStream_t st, uint64_t nsteps, std::string& err, uint64_t* launched) {
   if (!P.graph_tried) {
     P.graph_tried = true;
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      enqueue_step(P, st);
+      P.launches_per_step = enqueue_step(P, st);
       cudaError_t e = cudaStreamEndCapture(st, &graph);
       if (e == cudaSuccess && graph) {
         if (cudaGraphInstantiate(&P.graph, graph, 0) != cudaSuccess) P.graph = nullptr;
@@ -294,8 +335,9 @@ int run_steps(Plan& P, cudaStream_t st, uint64_t nsteps, std::string& err) {
   for (uint64_t i = 0; i < nsteps; ++i) {
     if (P.graph) {
       KCHECK(cudaGraphLaunch(P.graph, st), err);
+      *launched += P.launches_per_step;
     } else {
-      enqueue_step(P, st);
+      *launched += enqueue_step(P, st);
     }
   }
   KCHECK(cudaGetLastError(), err);
@@ -545,7 +587,15 @@ int sim_step(kmc_sim* s, uint32_t nsteps) {
   int rc = ensure_solo(s);
   if (rc) return rc;
   launch_add_steps(s->d, nsteps, s->stream);
-  return run_steps(s->solo, s->stream, nsteps, s->err);
+  s->launches += 1;
+  if (s->timing) return run_steps_timed(s->solo, s->stream, nsteps, s);
+  return run_steps(s->solo, s->stream, nsteps, s->err, &s->launches);
+}
+
+int sim_set_timing(kmc_sim* s, int enable) {
+  if (!s) return KMC_EINVAL;
+  s->timing = enable != 0;
+  return KMC_OK;
 }
 
 int sim_sync(kmc_sim* s) {
@@ -561,7 +611,7 @@ int sim_sync(kmc_sim* s) {
       if ((rc = recover_overflow(s, dy, st))) return rc;
       if (s->group) return KMC_OK;  // the group's next steps run the rest of the budget
       if (dy.steps_left) {
-        if ((rc = run_steps(s->solo, st, dy.steps_left, s->err))) return rc;
+        if ((rc = run_steps(s->solo, st, dy.steps_left, s->err, &s->launches))) return rc;
       }
       continue;
     }
@@ -672,6 +722,17 @@ int64_t sim_observe(kmc_sim* s, int what, void* dst, size_t dst_bytes) {
       s->prof_read = dy.prof_count;
       return (int64_t)avail;
     }
+    case KMC_OBS_LAUNCHES: {
+      if (dst_bytes < sizeof(uint64_t)) { s->err = "dst too small for LAUNCHES"; return KMC_EINVAL; }
+      KCHECK(cudaMemcpy(dst, &s->launches, sizeof(uint64_t), cudaMemcpyDefault), s->err);
+      return 1;
+    }
+    case KMC_OBS_PHASE_MS: {
+      if (dst_bytes < 5 * sizeof(double)) { s->err = "dst too small for PHASE_MS"; return KMC_EINVAL; }
+      double v[5] = {s->phase_ms[0], s->phase_ms[1], s->phase_ms[2], s->phase_ms[3], (double)s->timed_steps};
+      KCHECK(cudaMemcpy(dst, v, sizeof(v), cudaMemcpyDefault), s->err);
+      return 5;
+    }
     case KMC_OBS_STEP: {
       if (dst_bytes < sizeof(uint64_t)) { s->err = "dst too small for STEP"; return KMC_EINVAL; }
       Dyn dy;
@@ -750,6 +811,7 @@ int sim_group_remove(kmc_group* g, kmc_sim* s) {
 int sim_group_budget(kmc_group* g, kmc_sim* s, uint32_t nsteps) {
   if (!g || !s || s->group != g) return KMC_EINVAL;
   launch_add_steps(s->d, nsteps, g->stream);
+  s->launches += 1;
   KCHECK(cudaGetLastError(), g->err);
   return KMC_OK;
 }
@@ -763,7 +825,10 @@ int sim_group_step(kmc_group* g, uint32_t nsteps) {
     if (rc) return rc;
     g->built = true;
   }
-  return run_steps(g->plan, g->stream, nsteps, g->err);
+  uint64_t launched = 0;
+  int rc = run_steps(g->plan, g->stream, nsteps, g->err, &launched);
+  for (kmc_sim* s : g->members) s->launches += launched;
+  return rc;
 }
 
 int64_t sim_group_steps_left(kmc_group* g, kmc_sim* s) {

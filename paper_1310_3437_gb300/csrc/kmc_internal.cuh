@@ -196,12 +196,13 @@ struct LaunchPlan {
   int edge_blocks;
 };
 
-void launch_sort(const LaunchPlan& L, cudaStream_t st);
-void launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st);
-void launch_match(const LaunchPlan& L, int max_rounds, cudaStream_t st);
-void launch_push(const LaunchPlan& L, cudaStream_t st);
-void launch_init_grid(const LaunchPlan& L, cudaStream_t st);
-void launch_seg_scan(const LaunchPlan& L, int which, cudaStream_t st);
+// each returns the number of kernels it launched
+int launch_sort(const LaunchPlan& L, cudaStream_t st);
+int launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st);
+int launch_match(const LaunchPlan& L, int max_rounds, cudaStream_t st);
+int launch_push(const LaunchPlan& L, cudaStream_t st);
+int launch_init_grid(const LaunchPlan& L, cudaStream_t st);
+int launch_seg_scan(const LaunchPlan& L, int which, cudaStream_t st);
 
 // observe helpers
 void launch_gather_state(SimDev* d, uint32_t n, void* out, cudaStream_t st);

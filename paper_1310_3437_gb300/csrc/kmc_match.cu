@@ -252,16 +252,17 @@ __global__ void __launch_bounds__(kEdgeBlock) k_collide(Batch B) {
   }
 }
 
-void launch_match(const LaunchPlan& L, int max_rounds, cudaStream_t st) {
+int launch_match(const LaunchPlan& L, int max_rounds, cudaStream_t st) {
   int nb = L.edge_blocks;
   k_refine<<<nb, kEdgeBlock, 0, st>>>(L.b);
-  launch_seg_scan(L, 1, st);
+  int n = launch_seg_scan(L, 1, st);
   k_fill<<<nb, kEdgeBlock, 0, st>>>(L.b);
   for (int r = 0; r < max_rounds; ++r) {
     k_best<<<nb, kEdgeBlock, 0, st>>>(L.b);
     k_mutual<<<nb, kEdgeBlock, 0, st>>>(L.b, r);
   }
   k_collide<<<nb, kEdgeBlock, 0, st>>>(L.b);
+  return n + 3 + 2 * max_rounds;
 }
 
 }  // namespace kmc

@@ -235,16 +235,18 @@ __global__ void k_zero_vmax(Batch B) {
   for (int k = threadIdx.x; k < B.nsims; k += blockDim.x) B.sims[k]->d.vmax2_acc = 0;
 }
 
-void launch_init_grid(const LaunchPlan& L, cudaStream_t st) {
+int launch_init_grid(const LaunchPlan& L, cudaStream_t st) {
   k_zero_vmax<<<1, 256, 0, st>>>(L.b);
   k_vmax<<<L.ptiles, kTile, 0, st>>>(L.b);
   k_init_grid<<<1, 256, 0, st>>>(L.b);
+  return 3;
 }
 
-void launch_push(const LaunchPlan& L, cudaStream_t st) {
+int launch_push(const LaunchPlan& L, cudaStream_t st) {
   k_push<<<L.ptiles, kTile, 0, st>>>(L.b);
   k_profile<<<L.prtiles, kTile, 256 * kProfQ * sizeof(long long), st>>>(L.b);
   k_finalize<<<1, 256, 0, st>>>(L.b);
+  return 3;
 }
 
 __global__ void k_add_steps(SimDev* d, uint64_t n) { d->d.steps_left += n; }

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kTile) k_search(Batch B) {
   }
 }
 
-void launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st) {
+int launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st) {
   if (precision == KMC_FP64) {
     if (K == 2) k_search<KMC_FP64, 2><<<L.ptiles, kTile, 0, st>>>(L.b);
     else k_search<KMC_FP64, 1><<<L.ptiles, kTile, 0, st>>>(L.b);
@@ -210,6 +210,7 @@ void launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st) {
     if (K == 2) k_search<KMC_GUARDED_FP32, 2><<<L.ptiles, kTile, 0, st>>>(L.b);
     else k_search<KMC_GUARDED_FP32, 1><<<L.ptiles, kTile, 0, st>>>(L.b);
   }
+  return 1;
 }
 
 }  // namespace kmc

@@ -233,17 +233,19 @@ __global__ void __launch_bounds__(kTile) k_scatter(Batch B) {
 }
 
 // --------------------------------------------------------------------------- //
-void launch_seg_scan(const LaunchPlan& L, int which, cudaStream_t st) {
+int launch_seg_scan(const LaunchPlan& L, int which, cudaStream_t st) {
   uint32_t nt = which == 0 ? L.stiles_c : L.stiles_n;
   k_scan_reduce<<<nt, kTile, 0, st>>>(L.b, which);
   k_scan_tiles<<<1, 1024, 0, st>>>(L.b, which, nt);
   k_scan_apply<<<nt, kTile, 0, st>>>(L.b, which);
+  return 3;
 }
 
-void launch_sort(const LaunchPlan& L, cudaStream_t st) {
+int launch_sort(const LaunchPlan& L, cudaStream_t st) {
   k_count<<<L.ptiles, kTile, 0, st>>>(L.b);
-  launch_seg_scan(L, 0, st);
+  int n = launch_seg_scan(L, 0, st);
   k_scatter<<<L.ptiles, kTile, 0, st>>>(L.b);
+  return n + 2;
 }
 
 }  // namespace kmc

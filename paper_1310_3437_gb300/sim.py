@@ -10,7 +10,8 @@ import ctypes as C
 import numpy as np
 
 from . import (KMC_FP64, KMC_GUARDED_FP32, KMC_NONE, KMC_OBS_COUNTS, KMC_OBS_EDGES,
-               KMC_OBS_PARTNERS, KMC_OBS_PROFILES, KMC_OBS_STATE, KMC_OBS_STEP, kmc_params,
+               KMC_OBS_LAUNCHES, KMC_OBS_PARTNERS, KMC_OBS_PHASE_MS, KMC_OBS_PROFILES,
+               KMC_OBS_STATE, KMC_OBS_STEP, kmc_params, sim_set_timing,
                kmc_step_counts, sim_create, sim_destroy, sim_group_add, sim_group_budget,
                sim_group_create, sim_group_destroy, sim_group_remove, sim_group_step,
                sim_group_steps_left, sim_group_sync, sim_observe, sim_step, sim_sync)
@@ -149,6 +150,22 @@ class Simulation:
         out = np.empty((cap, bins, 7))
         cnt = sim_observe(self.handle, KMC_OBS_PROFILES, out.ctypes.data, out.nbytes)
         return out[:cnt].copy()
+
+    def launches(self) -> int:
+        out = np.zeros(1, dtype=np.uint64)
+        sim_observe(self.handle, KMC_OBS_LAUNCHES, out.ctypes.data, out.nbytes)
+        return int(out[0])
+
+    def set_timing(self, enable: bool):
+        sim_set_timing(self.handle, enable)
+
+    def phase_ms(self):
+        """Accumulated ms of the sort, search, matching and push phases, and the number
+        of steps timed (after set_timing(True))."""
+        out = np.zeros(5)
+        sim_observe(self.handle, KMC_OBS_PHASE_MS, out.ctypes.data, out.nbytes)
+        return {"sort": out[0], "search": out[1], "match": out[2], "push": out[3],
+                "steps": int(out[4])}
 
     def step_index(self) -> int:
         out = np.zeros(1, dtype=np.uint64)
