@@ -76,6 +76,12 @@ extern "C" {
 
 #define KMC_NONE 0xFFFFFFFFu
 
+/* ---- search kernels (kmc_params.search_kernel) ----------------------------- */
+#define KMC_SEARCH_AUTO 0      /* per step: warp-per-cell search when cells are well
+                                  filled, thread-per-particle search otherwise */
+#define KMC_SEARCH_PARTICLE 1  /* one thread per particle */
+#define KMC_SEARCH_CELL 2      /* one warp per cell, partners in lanes */
+
 /* Parameters of one simulation.  Zero-initialise, then set the fields. */
 typedef struct kmc_params {
   uint32_t n;              /* particles, >= 1 */
@@ -101,7 +107,8 @@ typedef struct kmc_params {
                               demand at sim_sync */
   uint32_t history_cap;    /* step records kept for KMC_OBS_COUNTS (0: 4096) */
   uint32_t profile_cap;    /* profile snapshots kept for KMC_OBS_PROFILES (0: 64) */
-  uint32_t reserved;
+  int32_t search_kernel;   /* KMC_SEARCH_AUTO (0), KMC_SEARCH_PARTICLE (1) or
+                              KMC_SEARCH_CELL (2).  Never changes results. */
 } kmc_params;
 
 /* One record per completed step (KMC_OBS_COUNTS). */

@@ -43,6 +43,10 @@ KMC_OBS_PHASE_MS = 8
 
 KMC_NONE = 0xFFFFFFFF
 
+KMC_SEARCH_AUTO = 0
+KMC_SEARCH_PARTICLE = 1
+KMC_SEARCH_CELL = 2
+
 
 class kmc_params(C.Structure):
     _fields_ = [
@@ -57,7 +61,7 @@ class kmc_params(C.Structure):
         ("profile_every", C.c_int32), ("stencil", C.c_int32),
         ("profile_range", C.c_double), ("cell_scale", C.c_double),
         ("edge_cap", C.c_uint32), ("history_cap", C.c_uint32),
-        ("profile_cap", C.c_uint32), ("reserved", C.c_uint32),
+        ("profile_cap", C.c_uint32), ("search_kernel", C.c_int32),
     ]
 
 

@@ -157,6 +157,7 @@ int validate(const kmc_params* p, std::string& err) {
   if (p->cell_scale != 0.0 && !(p->cell_scale >= 1.0)) { err = "cell_scale must be 0 or >= 1"; return KMC_EINVAL; }
   if (p->bc[0] == KMC_REFLECT && !(p->piston_x0 > 0.0)) { err = "reflecting x axis needs piston_x0 > 0"; return KMC_EINVAL; }
   if (p->n > 0x7FFFFFFFu) { err = "n too large"; return KMC_EINVAL; }
+  if (p->search_kernel < 0 || p->search_kernel > 2) { err = "bad search_kernel"; return KMC_EINVAL; }
   return KMC_OK;
 }
 
@@ -270,6 +271,7 @@ int build_plan(Plan& P, const std::vector<kmc_sim*>& sims, cudaStream_t st, std:
   L.stiles_c = sc[m];
   L.prtiles = pr[m];
   L.edge_blocks = 2 * num_sms();
+  L.cell_blocks = cell_search_blocks(P.precision, P.K, num_sms());
   return KMC_OK;
 }
 
@@ -477,6 +479,7 @@ int sim_create(const kmc_params* p, const double* x, const double* y, const doub
   h.profile_bins = (int32_t)zs.bins;
   h.profile_every = p->profile_every;
   h.K = p->stencil ? p->stencil : 1;
+  h.search_kernel = p->search_kernel;
   h.piston_x0 = p->bc[0] == KMC_REFLECT ? p->piston_x0 : p->box[0];
   h.piston_u = p->bc[0] == KMC_REFLECT ? p->piston_u : 0.0;
   h.d0 = p->d0;

@@ -69,6 +69,19 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
     if (attempt == 63) s.d.status |= ST_CELL_OVERFLOW;
   }
   g.K = K;
+  {
+    // search kernel: warp per cell when cells hold enough particles to fill a warp's
+    // lanes with partners; the binary32 warp-per-cell search handles no one-cell
+    // periodic axis (those need the minimum image per pair)
+    double cells = (double)nc[0] * nc[1] * nc[2];
+    double occ = (double)s.n / cells;
+    bool cp = false;
+    for (int a = 0; a < 3; ++a) cp = cp || (nc[a] == 1 && s.bc[a] == KMC_PERIODIC);
+    int mode = s.search_kernel;
+    if (mode == 0) mode = occ >= 4.0 ? KMC_SEARCH_CELL : KMC_SEARCH_PARTICLE;
+    if (mode == KMC_SEARCH_CELL && cp && s.precision == KMC_GUARDED_FP32) mode = KMC_SEARCH_PARTICLE;
+    g.mode = mode;
+  }
   double wmax = 0.0;
   for (int a = 0; a < 3; ++a) {
     g.nc[a] = nc[a];

@@ -34,6 +34,7 @@ enum : uint32_t {
 struct Grid {
   int32_t nc[3];      // cells per axis; 1 means the axis is one cell (no stencil on it)
   int32_t K;          // stencil radius in cells
+  int32_t mode;       // search kernel of this step: KMC_SEARCH_PARTICLE or KMC_SEARCH_CELL
   uint32_t nkeys;     // size of the key space (padded Morton columns x nc[0])
   uint32_t col_shift; // log2 of the Morton block edge P (P = next pow2 of the smaller axis)
   uint32_t y_major;   // 1 if nc[1] >= nc[2] (y carries the high, non-interleaved bits)
@@ -73,7 +74,7 @@ struct SimDev {
   // ---- parameters ----
   uint32_t n;
   int32_t bc[3];
-  int32_t max_rounds, precision, profile_bins, profile_every, K;
+  int32_t max_rounds, precision, profile_bins, profile_every, K, search_kernel;
   double box[3];
   double piston_x0, piston_u, d0, dt, d0sq;
   double profile_range, cell_scale;
@@ -194,11 +195,13 @@ struct LaunchPlan {
   Batch b;
   uint32_t ptiles, stiles_n, stiles_c, prtiles;
   int edge_blocks;
+  int cell_blocks;  // persistent grid of the warp-per-cell search
 };
 
 // each returns the number of kernels it launched
 int launch_sort(const LaunchPlan& L, cudaStream_t st);
 int launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st);
+int cell_search_blocks(int precision, int K, int num_sms);
 int launch_match(const LaunchPlan& L, int max_rounds, cudaStream_t st);
 int launch_push(const LaunchPlan& L, cudaStream_t st);
 int launch_init_grid(const LaunchPlan& L, cudaStream_t st);

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kTile) k_search(Batch B) {
   __shared__ unsigned long long stests;
   int k = find_sim(B.ptile, B.nsims, blockIdx.x);
   SimDev& s = *B.sims[k];
-  if (!sim_active(s)) return;
+  if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_PARTICLE) return;
   if (threadIdx.x == 0) { scnt = 0; stests = 0; }
   __syncthreads();
 
@@ -202,15 +202,275 @@ __global__ void __launch_bounds__(kTile) k_search(Batch B) {
   }
 }
 
-int launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st) {
-  if (precision == KMC_FP64) {
-    if (K == 2) k_search<KMC_FP64, 2><<<L.ptiles, kTile, 0, st>>>(L.b);
-    else k_search<KMC_FP64, 1><<<L.ptiles, kTile, 0, st>>>(L.b);
-  } else {
-    if (K == 2) k_search<KMC_GUARDED_FP32, 2><<<L.ptiles, kTile, 0, st>>>(L.b);
-    else k_search<KMC_GUARDED_FP32, 1><<<L.ptiles, kTile, 0, st>>>(L.b);
+// --------------------------------------------------------------------------- //
+// Warp-per-cell search.  A warp owns one cell A.  For every forward column run of
+// the stencil, the run's particles (contiguous in cell order) are loaded 32 at a
+// time, one partner j per lane, with coalesced loads; the particles i of A are
+// staged in shared memory and read by broadcast in a warp-uniform loop.  Each lane
+// thus tests its j against every i of A with no divergence and no per-pair address
+// arithmetic.  Emitted pairs go through a per-warp shared-memory buffer (one global
+// atomic per flush).
+constexpr int kCellWarps = 8;
+constexpr int kWarpBuf = 64;
+
+struct WarpEmit {
+  uint2* buf;        // this warp's staging buffer in shared memory
+  uint32_t count;    // warp-uniform fill level
+};
+
+__device__ __forceinline__ void warp_flush(WarpEmit& w, SimDev& s, uint32_t lane) {
+  __syncwarp();
+  if (w.count) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&s.d.n_raw, w.count);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    for (uint32_t k = lane; k < w.count; k += 32) {
+      uint32_t g = base + k;
+      if (g < s.edge_cap) s.edge[g] = w.buf[k];
+      else atomicOr(&s.d.status, ST_EDGE_OVERFLOW);
+    }
+    w.count = 0;
   }
-  return 1;
+  __syncwarp();
+}
+
+__device__ __forceinline__ void warp_emit(WarpEmit& w, SimDev& s, uint32_t lane, bool emit,
+                                          uint32_t i, uint32_t j) {
+  unsigned m = __ballot_sync(0xFFFFFFFFu, emit);
+  if (!m) return;
+  uint32_t c = (uint32_t)__popc(m);
+  if (w.count + c > (uint32_t)kWarpBuf) warp_flush(w, s, lane);
+  if (emit) w.buf[w.count + __popc(m & ((1u << lane) - 1u))] = make_uint2(i, j);
+  w.count += c;
+  __syncwarp();
+}
+
+template <int PREC, int K>
+__global__ void __launch_bounds__(kCellWarps * 32) k_search_cell(Batch B) {
+  constexpr int ICAP = PREC == KMC_FP64 ? 32 : 64;
+  constexpr int NF = PREC == KMC_FP64 ? 1 : kCellWarps;
+  constexpr int ND = PREC == KMC_FP64 ? kCellWarps : 1;
+  __shared__ float4 sa[NF][PREC == KMC_FP64 ? 1 : ICAP];
+  __shared__ float2 sb[NF][PREC == KMC_FP64 ? 1 : ICAP];
+  __shared__ double sd[ND][6][PREC == KMC_FP64 ? ICAP : 1];
+  __shared__ uint2 wbuf[kCellWarps][kWarpBuf];
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t gwarp = blockIdx.x * kCellWarps + warp, nwarps = gridDim.x * kCellWarps;
+
+  for (int k = 0; k < B.nsims; ++k) {
+    SimDev& s = *B.sims[k];
+    if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_CELL) continue;
+    const Grid& G = s.d.grid;
+    const int nx = G.nc[0], ny = G.nc[1], nz = G.nc[2];
+    const int Kx = nx == 1 ? 0 : K, Ky = ny == 1 ? 0 : K, Kz = nz == 1 ? 0 : K;
+    const bool px = s.bc[0] == KMC_PERIODIC, py = s.bc[1] == KMC_PERIODIC,
+               pz = s.bc[2] == KMC_PERIODIC;
+    const uint32_t nkeys = G.nkeys;
+    const uint32_t* __restrict__ cs = s.cell_start;
+    const int cur = s.d.parity ^ 1;
+    const float wx = G.wf[0], wy = G.wf[1], wz = G.wf[2];
+    const float c0 = G.s_c0, c1 = G.s_c1, ag = G.a_g, tg = G.t_g, dtf = G.dtf;
+    const float d0up = G.d0up, brel = G.b_rel, babs = G.b_abs, we = G.w_e, wrel = G.w_rel;
+    const double C0 = G.c0, C1 = G.c1;
+    const double L0 = s.box[0], L1 = s.box[1], L2 = s.box[2];
+    const float4* __restrict__ MA = s.mir_a;
+    const float2* __restrict__ MB = s.mir_b;
+    const double* __restrict__ X0 = s.x[cur][0];
+    const double* __restrict__ X1 = s.x[cur][1];
+    const double* __restrict__ X2 = s.x[cur][2];
+    const double* __restrict__ V0 = s.v[cur][0];
+    const double* __restrict__ V1 = s.v[cur][1];
+    const double* __restrict__ V2 = s.v[cur][2];
+    WarpEmit we_ = {wbuf[warp], 0u};
+    unsigned long long tests = 0;
+
+    for (uint32_t key = gwarp; key < nkeys; key += nwarps) {
+      const uint32_t startA = __ldg(cs + key), endA = __ldg(cs + key + 1);
+      if (startA == endA) continue;
+      int cx, cy, cz;
+      key_decode(G, key, cx, cy, cz);
+      for (uint32_t i0 = startA; i0 < endA; i0 += ICAP) {
+        const uint32_t nI = endA - i0 < (uint32_t)ICAP ? endA - i0 : (uint32_t)ICAP;
+        __syncwarp();
+        for (uint32_t t = lane; t < nI; t += 32) {
+          if (PREC == KMC_FP64) {
+            sd[warp][0][t] = X0[i0 + t]; sd[warp][1][t] = X1[i0 + t]; sd[warp][2][t] = X2[i0 + t];
+            sd[warp][3][t] = V0[i0 + t]; sd[warp][4][t] = V1[i0 + t]; sd[warp][5][t] = V2[i0 + t];
+          } else {
+            sa[warp][t] = MA[i0 + t];
+            sb[warp][t] = MB[i0 + t];
+          }
+        }
+        __syncwarp();
+        for (int dz = 0; dz <= Kz; ++dz) {
+          int qz = cz + dz;
+          if (qz >= nz) {
+            if (!pz) break;
+            qz -= nz;
+          }
+          for (int dy = (dz == 0 ? 0 : -Ky); dy <= Ky; ++dy) {
+            int qy = cy + dy;
+            if (qy < 0) {
+              if (!py) continue;
+              qy += ny;
+            } else if (qy >= ny) {
+              if (!py) continue;
+              qy -= ny;
+            }
+            const uint32_t colbase = col_code(G, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx;
+            const bool own_col = dz == 0 && dy == 0;
+            const float shy = (float)dy * wy, shz = (float)dz * wz;
+            // split the x run into pieces of consecutive cells (periodic wrap)
+            int dx = own_col ? 0 : -Kx;
+            while (dx <= Kx) {
+              const int q0 = cx + dx;  // unwrapped cell index
+              const int region = q0 < 0 ? -1 : (q0 >= nx ? 1 : 0);
+              if (region != 0 && !px) { ++dx; continue; }
+              const int qx = q0 - region * nx;
+              // extend the piece while the next cell lies in the same wrap region, so
+              // that its cells are consecutive keys of the column
+              int m = 1;
+              while (dx + m <= Kx) {
+                const int q2 = cx + dx + m;
+                const int r2 = q2 < 0 ? -1 : (q2 >= nx ? 1 : 0);
+                if (r2 != region) break;
+                ++m;
+              }
+              const int dxa = dx;
+              dx += m;
+              const uint32_t jbeg = __ldg(cs + colbase + qx), jend = __ldg(cs + colbase + qx + m);
+              if (jbeg == jend) continue;
+              uint32_t bnd[2 * K];
+#pragma unroll
+              for (int t = 0; t < 2 * K; ++t) bnd[t] = (t + 1 < m) ? __ldg(cs + colbase + qx + t + 1) : jend;
+              const bool has_own = own_col && dxa <= 0 && dxa + m > 0;
+              // analytic count of the pair tests of this piece
+              if (lane == 0) {
+                uint64_t len = jend - jbeg;
+                if (has_own) {
+                  uint64_t nA = endA - startA;
+                  uint64_t inc = (uint64_t)nI * (endA - i0 - 1) - (uint64_t)nI * (nI - 1) / 2;
+                  tests += (uint64_t)nI * (len - nA) + inc;
+                } else {
+                  tests += (uint64_t)nI * len;
+                }
+              }
+              for (uint32_t cb = jbeg; cb < jend; cb += 32) {
+                const uint32_t j = cb + lane;
+                const bool jv = j < jend;
+                const bool jown = has_own && j >= startA && j < endA;
+                if (PREC == KMC_FP64) {
+                  double xj0 = 0, xj1 = 0, xj2 = 0, vj0 = 0, vj1 = 0, vj2 = 0;
+                  if (jv) {
+                    xj0 = X0[j]; xj1 = X1[j]; xj2 = X2[j];
+                    vj0 = V0[j]; vj1 = V1[j]; vj2 = V2[j];
+                  }
+                  for (uint32_t ii = 0; ii < nI; ++ii) {
+                    const uint32_t i = i0 + ii;
+                    bool valid = jv && (!jown || j > i);
+                    double r0 = dsub(xj0, sd[warp][0][ii]);
+                    double r1 = dsub(xj1, sd[warp][1][ii]);
+                    double r2 = dsub(xj2, sd[warp][2][ii]);
+                    if (px) { if (r0 > 0.5 * L0) r0 = dsub(r0, L0); else if (r0 < -0.5 * L0) r0 = dadd(r0, L0); }
+                    if (py) { if (r1 > 0.5 * L1) r1 = dsub(r1, L1); else if (r1 < -0.5 * L1) r1 = dadd(r1, L1); }
+                    if (pz) { if (r2 > 0.5 * L2) r2 = dsub(r2, L2); else if (r2 < -0.5 * L2) r2 = dadd(r2, L2); }
+                    double g0 = dsub(vj0, sd[warp][3][ii]);
+                    double g1 = dsub(vj1, sd[warp][4][ii]);
+                    double g2 = dsub(vj2, sd[warp][5][ii]);
+                    double R = dadd(dadd(dmul(r0, r0), dmul(r1, r1)), dmul(r2, r2));
+                    double Bv = dadd(dadd(dmul(g0, g0), dmul(g1, g1)), dmul(g2, g2));
+                    bool emit = valid && !(Bv >= 0x1p-900 && R > dadd(C0, dmul(C1, Bv)));
+                    warp_emit(we_, s, lane, emit, i, j);
+                  }
+                } else {
+                  float jx = 0.f, jy = 0.f, jz = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+                  if (jv) {
+                    float4 a = __ldg(MA + j);
+                    float2 b = __ldg(MB + j);
+                    int t = 0;
+#pragma unroll
+                    for (int q = 0; q < 2 * K; ++q) t += j >= bnd[q] ? 1 : 0;
+                    // partner coordinates moved into the frame of cell A's corner
+                    jx = a.x + (float)(dxa + t) * wx;
+                    jy = a.y + shy;
+                    jz = a.z + shz;
+                    gx = a.w; gy = b.x; gz = b.y;
+                  }
+                  for (uint32_t ii = 0; ii < nI; ++ii) {
+                    const uint32_t i = i0 + ii;
+                    const float4 ia = sa[warp][ii];
+                    const float2 ib = sb[warp][ii];
+                    const bool valid = jv && (!jown || j > i);
+                    const float rx = jx - ia.x, ry = jy - ia.y, rz = jz - ia.z;
+                    const float vx = gx - ia.w, vy = gy - ib.x, vz = gz - ib.y;
+                    const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+                    const float Bv = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
+                    bool cand = valid && !(R > fmaf(c1, Bv, c0));
+                    if (__any_sync(0xFFFFFFFFu, cand)) {
+                      if (cand) {
+                        // full guarded test on the sphere survivors
+                        const float A = -fmaf(rz, vz, fmaf(ry, vy, rx * vx));
+                        if (A < -ag) cand = false;
+                        if (fmaf(-dtf, Bv, A) > tg) cand = false;
+                        const float w0 = fmaf(ry, vz, -(rz * vy));
+                        const float w1 = fmaf(rz, vx, -(rx * vz));
+                        const float w2 = fmaf(rx, vy, -(ry * vx));
+                        const float W = fmaf(w2, w2, fmaf(w1, w1, w0 * w0));
+                        const float thr = fmaf(d0up, sqrtf(fmaf(Bv, brel, babs)), we);
+                        if (W > thr * thr * wrel) cand = false;
+                      }
+                      warp_emit(we_, s, lane, cand, i, j);
+                    }
+                  }
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+    warp_flush(we_, s, lane);
+    if (lane == 0 && tests) atomicAdd(&s.d.pair_tests, tests);
+  }
+}
+
+int cell_search_blocks(int precision, int K, int num_sms) {
+  int per_sm = 0;
+  cudaError_t e;
+  if (precision == KMC_FP64)
+    e = K == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_cell<KMC_FP64, 2>, kCellWarps * 32, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_cell<KMC_FP64, 1>, kCellWarps * 32, 0);
+  else
+    e = K == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_cell<KMC_GUARDED_FP32, 2>, kCellWarps * 32, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_cell<KMC_GUARDED_FP32, 1>, kCellWarps * 32, 0);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 2;
+  }
+  return per_sm * num_sms;
+}
+
+int launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st) {
+  // both kernels are launched; each simulation runs in the one its grid selected
+  const int cb = L.cell_blocks;
+  if (precision == KMC_FP64) {
+    if (K == 2) {
+      k_search<KMC_FP64, 2><<<L.ptiles, kTile, 0, st>>>(L.b);
+      k_search_cell<KMC_FP64, 2><<<cb, kCellWarps * 32, 0, st>>>(L.b);
+    } else {
+      k_search<KMC_FP64, 1><<<L.ptiles, kTile, 0, st>>>(L.b);
+      k_search_cell<KMC_FP64, 1><<<cb, kCellWarps * 32, 0, st>>>(L.b);
+    }
+  } else {
+    if (K == 2) {
+      k_search<KMC_GUARDED_FP32, 2><<<L.ptiles, kTile, 0, st>>>(L.b);
+      k_search_cell<KMC_GUARDED_FP32, 2><<<cb, kCellWarps * 32, 0, st>>>(L.b);
+    } else {
+      k_search<KMC_GUARDED_FP32, 1><<<L.ptiles, kTile, 0, st>>>(L.b);
+      k_search_cell<KMC_GUARDED_FP32, 1><<<cb, kCellWarps * 32, 0, st>>>(L.b);
+    }
+  }
+  return 2;
 }
 
 }  // namespace kmc

@@ -25,9 +25,9 @@ FP32 = kmc.KMC_GUARDED_FP32
 
 
 def gpu_sim(setup, arrays, precision=FP64, stencil=1, cell_scale=1.0, last=None, step0=0,
-            edge_cap=0):
+            edge_cap=0, search_kernel=0):
     p = kmc.params_from_setup(setup, precision=precision, stencil=stencil, cell_scale=cell_scale,
-                              step0=step0, edge_cap=edge_cap)
+                              step0=step0, edge_cap=edge_cap, search_kernel=search_kernel)
     return kmc.Simulation(p, arrays, last=last)
 
 
@@ -86,20 +86,30 @@ def test_piston_tube_pair_lists_every_step(precision):
 
 
 @pytest.mark.parametrize("precision", [FP64, FP32])
-def test_piston_tube_trajectory_bit_exact(precision):
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_piston_tube_trajectory_bit_exact(precision, kernel):
     s = ki.piston_setup(n=1 << 14, seed=3, box=(8.0, 0.125, 0.125), profile_bins=0,
                         profile_every=0)
-    sim, st, oc, _ = run_both(s, 300, precision)
+    sim, st, oc, _ = run_both(s, 300, precision, search_kernel=kernel)
     assert_same_counts(sim.counts(), oc)
     assert_same_state(sim, st)
 
 
-@pytest.mark.parametrize("stencil,cell_scale", [(2, 1.0), (1, 1.7), (2, 2.3)])
-def test_results_do_not_depend_on_grid_tuning(stencil, cell_scale):
+@pytest.mark.parametrize("precision", [FP64, FP32])
+@pytest.mark.parametrize("stencil,cell_scale,kernel", [
+    (2, 1.0, 0), (1, 1.7, 0), (2, 2.3, 0), (1, 1.0, 1), (1, 1.0, 2), (2, 1.0, 1), (2, 1.0, 2),
+    (1, 3.0, 2), (2, 4.0, 2), (1, 2.5, 1)])
+def test_results_do_not_depend_on_grid_tuning(precision, stencil, cell_scale, kernel):
+    """Cell size, stencil and search kernel (incl. cells above the per-warp staging
+    capacity at cell_scale 3-4) change the work, never the result."""
     s = ki.equilibrium_setup(n=6000, seed=4)
     arrays = ki.initial_state(s)
-    ref = gpu_sim(s, arrays, FP32).step(40).sync()
-    alt = gpu_sim(s, arrays, FP32, stencil=stencil, cell_scale=cell_scale).step(40).sync()
+    st = oracle.State(arrays)
+    oracle.run(s, st, 0, 40)
+    ref = gpu_sim(s, arrays, precision).step(40).sync()
+    assert_same_state(ref, st)
+    alt = gpu_sim(s, arrays, precision, stencil=stencil, cell_scale=cell_scale,
+                  search_kernel=kernel).step(40).sync()
     a, la = ref.state()
     b, lb = alt.state()
     for x, y in zip(a, b):
@@ -121,9 +131,10 @@ def test_fp32_and_fp64_pair_lists_identical_with_many_near_threshold_pairs():
     st = oracle.State(pos + vel)
     pi, pj, _, _ = oracle.candidate_pairs(s, st)
     for prec in (FP64, FP32):
-        sim = gpu_sim(s, pos + vel, prec).step(1).sync()
-        e = sim.edges()
-        assert np.array_equal(e, np.stack([pi, pj], axis=1))
+        for kern in (1, 2):
+            sim = gpu_sim(s, pos + vel, prec, search_kernel=kern).step(1).sync()
+            e = sim.edges()
+            assert np.array_equal(e, np.stack([pi, pj], axis=1))
 
 
 def test_edge_cases():
@@ -151,8 +162,8 @@ def test_edge_cases():
     vel[0][100:200] = vel[0][99]
     s = ki.Setup(n=n, box=(1.0, 0.05, 0.05), bc=(0, 0, 0), d0=0.01, dt=0.01, seed=7,
                  name="equilibrium_slab")
-    for prec in (FP64, FP32):
-        sim, st, oc, _ = run_both(s, 20, prec, arrays=pos + vel)
+    for prec, kern in ((FP64, 0), (FP32, 0), (FP64, 2), (FP32, 2), (FP64, 1)):
+        sim, st, oc, _ = run_both(s, 20, prec, arrays=pos + vel, search_kernel=kern)
         assert_same_counts(sim.counts(), oc)
         assert_same_state(sim, st)
     # reflecting box on all axes with a static upper wall
