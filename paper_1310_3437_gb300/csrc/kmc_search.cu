@@ -434,6 +434,211 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_cell(Batch B) {
   }
 }
 
+// --------------------------------------------------------------------------- //
+// Binary32 warp-per-cell search, unrolled.  The particles i of cell A are staged as
+// structure-of-arrays in shared memory, padded to a multiple of 4 with a sentinel
+// position (-1e30) that every sphere test rejects; lanes past the end of a partner
+// chunk carry the opposite sentinel (+1e30).  Four pairs per lane are tested per
+// iteration with one warp vote, so the loop body is pure arithmetic plus four
+// 16-byte shared-memory broadcasts.
+struct Guard32 {
+  float c0, c1, ag, tg, dtf, d0up, brel, babs, we, wrel;
+};
+
+// exact guarded test of one pair on the sphere survivors (rare path)
+__device__ __forceinline__ bool full_test32(const Guard32& q, float rx, float ry, float rz,
+                                            float vx, float vy, float vz, float Bv) {
+  const float A = -fmaf(rz, vz, fmaf(ry, vy, rx * vx));
+  if (A < -q.ag) return false;
+  if (fmaf(-q.dtf, Bv, A) > q.tg) return false;
+  const float w0 = fmaf(ry, vz, -(rz * vy));
+  const float w1 = fmaf(rz, vx, -(rx * vz));
+  const float w2 = fmaf(rx, vy, -(ry * vx));
+  const float W = fmaf(w2, w2, fmaf(w1, w1, w0 * w0));
+  const float thr = fmaf(q.d0up, sqrtf(fmaf(Bv, q.brel, q.babs)), q.we);
+  return !(W > thr * thr * q.wrel);
+}
+
+template <bool OWN>
+__device__ __forceinline__ void cell32_sweep(const float* __restrict__ si, uint32_t nI4, uint32_t i0,
+                                             float jx, float jy, float jz, float gx, float gy,
+                                             float gz, uint32_t j, bool jown, const Guard32& q,
+                                             WarpEmit& w, SimDev& s, uint32_t lane) {
+  const float* sx = si;
+  const float* sy = si + 1 * 64;
+  const float* sz = si + 2 * 64;
+  const float* su = si + 3 * 64;
+  const float* sv = si + 4 * 64;
+  const float* sw = si + 5 * 64;
+  for (uint32_t ii = 0; ii < nI4; ii += 4) {
+    const float4 X = *reinterpret_cast<const float4*>(sx + ii);
+    const float4 Y = *reinterpret_cast<const float4*>(sy + ii);
+    const float4 Z = *reinterpret_cast<const float4*>(sz + ii);
+    const float4 U = *reinterpret_cast<const float4*>(su + ii);
+    const float4 V = *reinterpret_cast<const float4*>(sv + ii);
+    const float4 W = *reinterpret_cast<const float4*>(sw + ii);
+    bool c[4];
+    {
+      const float xs[4] = {X.x, X.y, X.z, X.w}, ys[4] = {Y.x, Y.y, Y.z, Y.w},
+                  zs[4] = {Z.x, Z.y, Z.z, Z.w}, us[4] = {U.x, U.y, U.z, U.w},
+                  vs[4] = {V.x, V.y, V.z, V.w}, ws[4] = {W.x, W.y, W.z, W.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float rx = jx - xs[u], ry = jy - ys[u], rz = jz - zs[u];
+        const float vx = gx - us[u], vy = gy - vs[u], vz = gz - ws[u];
+        const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+        const float Bv = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
+        c[u] = R <= fmaf(q.c1, Bv, q.c0);
+        if (OWN) c[u] = c[u] && (!jown || j > i0 + ii + (uint32_t)u);
+      }
+    }
+    if (__any_sync(0xFFFFFFFFu, c[0] || c[1] || c[2] || c[3])) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        bool cand = false;
+        if (c[u]) {
+          const uint32_t t = ii + (uint32_t)u;
+          const float rx = jx - sx[t], ry = jy - sy[t], rz = jz - sz[t];
+          const float vx = gx - su[t], vy = gy - sv[t], vz = gz - sw[t];
+          const float Bv = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
+          cand = full_test32(q, rx, ry, rz, vx, vy, vz, Bv);
+        }
+        warp_emit(w, s, lane, cand, i0 + ii + (uint32_t)u, j);
+      }
+    }
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kCellWarps * 32, 2) k_search_cell32(Batch B) {
+  constexpr int ICAP = 64;
+  __shared__ __align__(16) float si[kCellWarps][6 * ICAP];
+  __shared__ uint2 wbuf[kCellWarps][kWarpBuf];
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t gwarp = blockIdx.x * kCellWarps + warp, nwarps = gridDim.x * kCellWarps;
+
+  for (int k = 0; k < B.nsims; ++k) {
+    SimDev& s = *B.sims[k];
+    if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_CELL) continue;
+    const Grid& G = s.d.grid;
+    const int nx = G.nc[0], ny = G.nc[1], nz = G.nc[2];
+    const int Kx = nx == 1 ? 0 : K, Ky = ny == 1 ? 0 : K, Kz = nz == 1 ? 0 : K;
+    const bool px = s.bc[0] == KMC_PERIODIC, py = s.bc[1] == KMC_PERIODIC,
+               pz = s.bc[2] == KMC_PERIODIC;
+    const uint32_t nkeys = G.nkeys;
+    const uint32_t* __restrict__ cs = s.cell_start;
+    const float wx = G.wf[0], wy = G.wf[1], wz = G.wf[2];
+    Guard32 q;
+    q.c0 = G.s_c0; q.c1 = G.s_c1; q.ag = G.a_g; q.tg = G.t_g; q.dtf = G.dtf;
+    q.d0up = G.d0up; q.brel = G.b_rel; q.babs = G.b_abs; q.we = G.w_e; q.wrel = G.w_rel;
+    const float4* __restrict__ MA = s.mir_a;
+    const float2* __restrict__ MB = s.mir_b;
+    float* my = si[warp];
+    WarpEmit we_ = {wbuf[warp], 0u};
+    unsigned long long tests = 0;
+
+    for (uint32_t key = gwarp; key < nkeys; key += nwarps) {
+      const uint32_t startA = __ldg(cs + key), endA = __ldg(cs + key + 1);
+      if (startA == endA) continue;
+      int cx, cy, cz;
+      key_decode(G, key, cx, cy, cz);
+      for (uint32_t i0 = startA; i0 < endA; i0 += ICAP) {
+        const uint32_t nI = endA - i0 < (uint32_t)ICAP ? endA - i0 : (uint32_t)ICAP;
+        const uint32_t nI4 = (nI + 3u) & ~3u;
+        __syncwarp();
+        for (uint32_t t = lane; t < nI4; t += 32) {
+          if (t < nI) {
+            const float4 a = MA[i0 + t];
+            const float2 b = MB[i0 + t];
+            my[t] = a.x; my[ICAP + t] = a.y; my[2 * ICAP + t] = a.z;
+            my[3 * ICAP + t] = a.w; my[4 * ICAP + t] = b.x; my[5 * ICAP + t] = b.y;
+          } else {
+            my[t] = -1e30f; my[ICAP + t] = 0.f; my[2 * ICAP + t] = 0.f;
+            my[3 * ICAP + t] = 0.f; my[4 * ICAP + t] = 0.f; my[5 * ICAP + t] = 0.f;
+          }
+        }
+        __syncwarp();
+        for (int dz = 0; dz <= Kz; ++dz) {
+          int qz = cz + dz;
+          if (qz >= nz) {
+            if (!pz) break;
+            qz -= nz;
+          }
+          for (int dy = (dz == 0 ? 0 : -Ky); dy <= Ky; ++dy) {
+            int qy = cy + dy;
+            if (qy < 0) {
+              if (!py) continue;
+              qy += ny;
+            } else if (qy >= ny) {
+              if (!py) continue;
+              qy -= ny;
+            }
+            const uint32_t colbase = col_code(G, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx;
+            const bool own_col = dz == 0 && dy == 0;
+            const float shy = (float)dy * wy, shz = (float)dz * wz;
+            int dx = own_col ? 0 : -Kx;
+            while (dx <= Kx) {
+              const int q0 = cx + dx;
+              const int region = q0 < 0 ? -1 : (q0 >= nx ? 1 : 0);
+              if (region != 0 && !px) { ++dx; continue; }
+              const int qx = q0 - region * nx;
+              int m = 1;
+              while (dx + m <= Kx) {
+                const int q2 = cx + dx + m;
+                const int r2 = q2 < 0 ? -1 : (q2 >= nx ? 1 : 0);
+                if (r2 != region) break;
+                ++m;
+              }
+              const int dxa = dx;
+              dx += m;
+              const uint32_t jbeg = __ldg(cs + colbase + qx), jend = __ldg(cs + colbase + qx + m);
+              if (jbeg == jend) continue;
+              uint32_t bnd[2 * K];
+#pragma unroll
+              for (int t = 0; t < 2 * K; ++t) bnd[t] = (t + 1 < m) ? __ldg(cs + colbase + qx + t + 1) : jend;
+              const bool has_own = own_col && dxa <= 0 && dxa + m > 0;
+              if (lane == 0) {
+                uint64_t len = jend - jbeg;
+                if (has_own) {
+                  uint64_t nA = endA - startA;
+                  uint64_t inc = (uint64_t)nI * (endA - i0 - 1) - (uint64_t)nI * (nI - 1) / 2;
+                  tests += (uint64_t)nI * (len - nA) + inc;
+                } else {
+                  tests += (uint64_t)nI * len;
+                }
+              }
+              for (uint32_t cb = jbeg; cb < jend; cb += 32) {
+                const uint32_t j = cb + lane;
+                float jx = 1e30f, jy = 0.f, jz = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+                if (j < jend) {
+                  const float4 a = __ldg(MA + j);
+                  const float2 b = __ldg(MB + j);
+                  int t = 0;
+#pragma unroll
+                  for (int qq = 0; qq < 2 * K; ++qq) t += j >= bnd[qq] ? 1 : 0;
+                  // partner moved into the frame of cell A's corner
+                  jx = a.x + (float)(dxa + t) * wx;
+                  jy = a.y + shy;
+                  jz = a.z + shz;
+                  gx = a.w; gy = b.x; gz = b.y;
+                }
+                if (has_own) {
+                  const bool jown = j >= startA && j < endA;
+                  cell32_sweep<true>(my, nI4, i0, jx, jy, jz, gx, gy, gz, j, jown, q, we_, s, lane);
+                } else {
+                  cell32_sweep<false>(my, nI4, i0, jx, jy, jz, gx, gy, gz, j, false, q, we_, s, lane);
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+    warp_flush(we_, s, lane);
+    if (lane == 0 && tests) atomicAdd(&s.d.pair_tests, tests);
+  }
+}
+
 int cell_search_blocks(int precision, int K, int num_sms) {
   int per_sm = 0;
   cudaError_t e;
@@ -441,8 +646,8 @@ int cell_search_blocks(int precision, int K, int num_sms) {
     e = K == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_cell<KMC_FP64, 2>, kCellWarps * 32, 0)
                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_cell<KMC_FP64, 1>, kCellWarps * 32, 0);
   else
-    e = K == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_cell<KMC_GUARDED_FP32, 2>, kCellWarps * 32, 0)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_cell<KMC_GUARDED_FP32, 1>, kCellWarps * 32, 0);
+    e = K == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_cell32<2>, kCellWarps * 32, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_cell32<1>, kCellWarps * 32, 0);
   if (e != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     per_sm = 2;
@@ -464,10 +669,10 @@ int launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st) {
   } else {
     if (K == 2) {
       k_search<KMC_GUARDED_FP32, 2><<<L.ptiles, kTile, 0, st>>>(L.b);
-      k_search_cell<KMC_GUARDED_FP32, 2><<<cb, kCellWarps * 32, 0, st>>>(L.b);
+      k_search_cell32<2><<<cb, kCellWarps * 32, 0, st>>>(L.b);
     } else {
       k_search<KMC_GUARDED_FP32, 1><<<L.ptiles, kTile, 0, st>>>(L.b);
-      k_search_cell<KMC_GUARDED_FP32, 1><<<cb, kCellWarps * 32, 0, st>>>(L.b);
+      k_search_cell32<1><<<cb, kCellWarps * 32, 0, st>>>(L.b);
     }
   }
   return 2;
