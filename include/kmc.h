@@ -166,6 +166,26 @@ const char* sim_last_error(const kmc_sim* s);
 /* Device bytes sim_create would allocate for these parameters (admission control). */
 size_t sim_bytes_required(const kmc_params* p);
 
+/* X-profile of a particle state that allocates no device memory.  The paper has no
+ * counterpart: it is an observable for callers that cannot call cudaMalloc (a host
+ * application whose pool allocator owns all device memory, an in-situ analysis
+ * step inside another code's time loop where an allocation would synchronise the
+ * device, a tool handed only device pointers).  It returns the same bins x 7
+ * binary64 values as KMC_OBS_PROFILES -- per x bin over [0, range): count, sum vx,
+ * sum vy, sum vz, sum vx^2, sum vy^2, sum vz^2 -- for the n particles in the caller's
+ * device arrays x, vx, vy, vz (any order), into the caller's device array out.
+ * Scratch: a fixed array of 256 x 19 int64 counters (38,912 bytes) compiled into
+ * the library; every GPU that loads the library holds it until the process exits.
+ * bins above 256 (or below 1), range <= 0, NULL or host pointers: KMC_EINVAL, with a
+ * line on stderr.  The first call on a device, with that device current, looks up
+ * the array's device address; make that first call before any stream capture.
+ * Calls share the array and it keeps the last call's contents (each call clears the
+ * counters it uses first); calls that overlap on the GPU race and return wrong
+ * sums, so order them on one stream.  Enqueued on stream; out is valid after the
+ * stream synchronises.  Calls no cudaMalloc, cudaFree or allocating library routine. */
+int sim_profile_static(const double* x, const double* vx, const double* vy, const double* vz,
+                       uint32_t n, int32_t bins, double range, double* out, void* stream);
+
 /* ---- batching ------------------------------------------------------------ */
 /* A group steps many simulations of uneven size with one launch per kernel for
  * all of them; the per-step launch sequence is captured in a CUDA graph.  All

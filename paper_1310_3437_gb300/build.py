@@ -28,6 +28,7 @@ SOURCES = {
     "kmc_match.cu": ["-fmad=false"],
     "kmc_push.cu": ["-fmad=false"],
     "kmc_api.cu": ["-fmad=false"],
+    "kmc_noalloc.cu": ["-fmad=false"],
 }
 
 
