@@ -179,6 +179,89 @@ def oracle_sample_rate(max_seconds: float, warmup: int = 0, steps_cap: int = 50)
     return s.n * done / dt, done, dt, oracle.max_threads(), s
 
 
+def run_serving(args, stream, dev):
+    """Serving stream at ~70% load: calibrate the aggregate throughput S on a batch of
+    requests, then send Poisson arrivals at rate 0.7 S / W (W = mean particle-steps of
+    a request) and report latency percentiles and aggregate throughput."""
+    import torch
+
+    import paper_1310_3437_gb300 as kmc
+    from paper_1310_3437_gb300.serve import Request, Server, summarize
+
+    n_lo, n_hi = 1 << 14, args.serve_n_hi
+    st_lo, st_hi = args.serve_steps_lo, args.serve_steps_hi
+    setups = ki.serving_requests(args.serve_requests + 16, master_seed=7, n_lo=n_lo, n_hi=n_hi,
+                                 steps_lo=st_lo, steps_hi=st_hi)
+    cal, rest = setups[:16], setups[16:]
+    # calibration: 16 requests admitted at once
+    reqs = [Request(rid=k, setup=q, steps=q.steps, arrival=0.0, arrays=ki.initial_state(q))
+            for k, q in enumerate(cal)]
+    server = Server(budget_bytes=args.serve_budget_gb * 1e9, keep_state=False,
+                    stream=stream.cuda_stream)
+    done, wall = server.run(reqs)
+    S = summarize(done, wall)["particle_steps_per_s"]
+    W = ki.mean_loguniform(n_lo, n_hi) * 0.5 * (st_lo + st_hi)
+    rate = 0.7 * S / W
+    rng = np.random.default_rng(7)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=len(rest)))
+    reqs = [Request(rid=k, setup=q, steps=q.steps, arrival=float(t[k]),
+                    arrays=(lambda q=q: ki.initial_state(q))) for k, q in enumerate(rest)]
+    server = Server(budget_bytes=args.serve_budget_gb * 1e9, keep_state=True,
+                    stream=stream.cuda_stream)
+    done, wall = server.run(reqs)
+    sm = summarize(done, wall)
+    return {
+        "p50_latency_ms": sm["p50_latency_s"] * 1e3, "p99_latency_ms": sm["p99_latency_s"] * 1e3,
+        "mean_latency_ms": sm["mean_latency_s"] * 1e3,
+        "particle_steps_per_s": sm["particle_steps_per_s"], "requests": sm["requests"],
+        "wall_s": sm["wall_s"], "load": 0.7, "arrival_rate_per_s": rate,
+        "calibration_particle_steps_per_s": S, "budget_gb": args.serve_budget_gb,
+        "mix": f"equilibrium boxes and piston tubes, N log-uniform [{n_lo}, {n_hi}], steps "
+               f"U[{st_lo}, {st_hi}], guarded FP32, SplitMix64 seeds from master seed 7",
+        "latency": "arrival -> final state and step counts on the host",
+    }
+
+
+def run_ensemble(args, stream):
+    """Batched ensemble: 256 independent runs of uneven size (N log-uniform in
+    [2^12, 2^18], equilibrium boxes and piston tubes) stepped as one group: one launch
+    per kernel per step for all runs, the step captured in a CUDA graph."""
+    import torch
+
+    import paper_1310_3437_gb300 as kmc
+
+    setups = ki.ensemble_setups(count=256, steps=args.ensemble_steps)
+    sims = [kmc.Simulation(kmc.params_from_setup(q, precision=kmc.KMC_GUARDED_FP32),
+                           ki.initial_state(q), stream=stream.cuda_stream) for q in setups]
+    g = kmc.Group(sims, stream=stream.cuda_stream)
+    warm = 3
+    for q in sims:
+        g.budget(q, warm + args.ensemble_steps)
+    g.step(warm)
+    g.sync()
+    l0 = sims[0].launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(args.ensemble_steps)
+    e1.record(stream)
+    e1.synchronize()
+    g.sync()
+    ms = e0.elapsed_time(e1)
+    launches = sims[0].launches() - l0
+    total_n = sum(q.n for q in setups)
+    out = {"runs": len(setups), "particles": total_n, "steps": args.ensemble_steps,
+           "particle_steps_per_s": total_n * args.ensemble_steps / (ms / 1e3),
+           "ms_per_group_step": ms / args.ensemble_steps,
+           "kernel_launches_per_group_step": launches / args.ensemble_steps,
+           "mix": "seeds 1000-1255, N log-uniform [2^12, 2^18], even: equilibrium box, "
+                  "odd: piston tube with u_p in [1, 3]; guarded FP32; one CUDA graph per step"}
+    g.close()
+    for q in sims:
+        q.close()
+    return out
+
+
 def run_reference(args):
     world, rank, local = dist_info()
     if rank != 0:
@@ -253,8 +336,17 @@ def run_gpu(args):
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
 
+    knobs = {"search_kernel": 0, "stencil": 1, "cell_scale": 1.0}
+    tuning = None
+    if not args.no_tune:
+        from paper_1310_3437_gb300.tune import Autotuner
+        tuner = Autotuner(steps=3, warmup=max(2, args.warmup))
+        best = tuner.choose(setup, dev_arrays, kmc.KMC_GUARDED_FP32, stream=stream)
+        knobs = {k: best[k] for k in knobs}
+        tuning = {"chosen": best, "trials": next(iter(tuner.trials.values()))}
+
     def timed_run(precision, warm, steps, sample_clocks=False):
-        params = kmc.params_from_setup(setup, precision=precision)
+        params = kmc.params_from_setup(setup, precision=precision, **knobs)
         sim = kmc.Simulation(params, dev_arrays, stream=stream.cuda_stream)
         sim.step(warm).sync()
         sim.counts()
@@ -316,7 +408,7 @@ def run_gpu(args):
         ke = args.steps
         barrier()
         t0 = time.perf_counter()
-        params = kmc.params_from_setup(setup, precision=kmc.KMC_GUARDED_FP32)
+        params = kmc.params_from_setup(setup, precision=kmc.KMC_GUARDED_FP32, **knobs)
         sim = kmc.Simulation(params, pinned, stream=stream.cuda_stream)
         sim.step(ke)
         kmc.sim_observe(sim.handle, kmc.KMC_OBS_STATE, out.data_ptr(), out.numel())
@@ -326,6 +418,13 @@ def run_gpu(args):
         e2e = {"value": world * n * ke / te, "unit": UNIT,
                "h2d_bytes_per_step": 48 * n / ke, "d2h_bytes_per_step": 52 * n / ke,
                "job": f"create from pinned host arrays, {ke} steps, state read back"}
+
+    serve = None
+    if not args.skip_serve and rank == 0:
+        serve = run_serving(args, stream, dev)
+    ensemble = None
+    if not args.skip_ensemble and rank == 0:
+        ensemble = run_ensemble(args, stream)
 
     if rank != 0:
         if world > 1:
@@ -383,6 +482,9 @@ def run_gpu(args):
         "candidate_pairs_per_step": edges_mean, "collisions_per_step": coll_mean,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "serve": serve,
+        "ensemble": ensemble,
+        "tuning": tuning,
         "gpu_launches": int(launches32),
         "clocks": clocks,
     }
@@ -407,6 +509,18 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--skip-ensemble", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--ensemble-steps", type=int, default=100)
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests of the serving stream (the full stream is 10000)")
+    ap.add_argument("--serve-n-hi", type=int, default=1 << 18,
+                    help="largest request size (the full stream uses 2^22)")
+    ap.add_argument("--serve-steps-lo", type=int, default=20)
+    ap.add_argument("--serve-steps-hi", type=int, default=200,
+                    help="the full stream uses steps in [100, 2000]")
+    ap.add_argument("--serve-budget-gb", type=float, default=160.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -166,3 +166,44 @@ def ensemble_setups(count: int = 256, seed0: int = 1000, lo: int = 1 << 12, hi: 
                              steps=steps, profile_bins=0, profile_every=0)
         out.append(s)
     return out
+
+
+# --------------------------------------------------------------------------- #
+# Serving stream
+
+def splitmix64(state: int):
+    """One step of the SplitMix64 generator (Steele, Lea, Flood, OOPSLA 2014):
+    returns (new_state, output)."""
+    mask = (1 << 64) - 1
+    state = (state + 0x9E3779B97F4A7C15) & mask
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+    return state, z ^ (z >> 31)
+
+
+def serving_requests(count: int = 10000, master_seed: int = 7, n_lo: int = 1 << 14,
+                     n_hi: int = 1 << 22, steps_lo: int = 100, steps_hi: int = 2000):
+    """Request mix of the serving stream: each request is an equilibrium box (the
+    4096-particle box's density and d0, box edge (N/4096)^(1/3)) or a piston tube
+    (8 x 1 x 1, lambda = 0.02), N log-uniform in [n_lo, n_hi], steps uniform in
+    [steps_lo, steps_hi]; per-request seeds from a SplitMix64 chain."""
+    state = master_seed
+    out = []
+    for k in range(count):
+        state, seed = splitmix64(state)
+        rng = np.random.default_rng(seed)
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        steps = int(rng.integers(steps_lo, steps_hi + 1))
+        seed32 = int(seed & 0x7FFFFFFF)
+        if rng.random() < 0.5:
+            L = (n / 4096.0) ** (1.0 / 3.0)
+            s = equilibrium_setup(n=n, seed=seed32, L=L, steps=steps)
+        else:
+            s = piston_setup(n=n, seed=seed32, steps=steps, profile_bins=0, profile_every=0)
+        out.append(s)
+    return out
+
+
+def mean_loguniform(lo: float, hi: float) -> float:
+    return (hi - lo) / math.log(hi / lo)

@@ -459,11 +459,46 @@ __device__ __forceinline__ bool full_test32(const Guard32& q, float rx, float ry
   return !(W > thr * thr * q.wrel);
 }
 
+// Emission from divergent lanes: a shared-memory counter per warp; entries that do
+// not fit in the warp's buffer go straight to the global list.
+__device__ __forceinline__ void emit_lane(uint2* buf, uint32_t* count, SimDev& s, uint32_t i,
+                                          uint32_t j) {
+  uint32_t pos = atomicAdd(count, 1u);
+  if (pos < (uint32_t)kWarpBuf) {
+    buf[pos] = make_uint2(i, j);
+  } else {
+    uint32_t g = atomicAdd(&s.d.n_raw, 1u);
+    if (g < s.edge_cap) s.edge[g] = make_uint2(i, j);
+    else atomicOr(&s.d.status, ST_EDGE_OVERFLOW);
+  }
+}
+
+// warp-uniform: move the buffered pairs to the global list
+__device__ __forceinline__ void flush_lanes(uint2* buf, uint32_t* count, SimDev& s, uint32_t lane) {
+  __syncwarp();
+  uint32_t c = *count;
+  c = c < (uint32_t)kWarpBuf ? c : (uint32_t)kWarpBuf;
+  if (c) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&s.d.n_raw, c);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    for (uint32_t k = lane; k < c; k += 32) {
+      uint32_t g = base + k;
+      if (g < s.edge_cap) s.edge[g] = buf[k];
+      else atomicOr(&s.d.status, ST_EDGE_OVERFLOW);
+    }
+  }
+  __syncwarp();
+  if (lane == 0) *count = 0;
+  __syncwarp();
+}
+
 template <bool OWN>
 __device__ __forceinline__ void cell32_sweep(const float* __restrict__ si, uint32_t nI4, uint32_t i0,
                                              float jx, float jy, float jz, float gx, float gy,
-                                             float gz, uint32_t j, bool jown, const Guard32& q,
-                                             WarpEmit& w, SimDev& s, uint32_t lane) {
+                                             float gz, uint32_t j, bool jown, float c0, float c1,
+                                             const Guard32& q, uint2* buf, uint32_t* count,
+                                             SimDev& s) {
   const float* sx = si;
   const float* sy = si + 1 * 64;
   const float* sz = si + 2 * 64;
@@ -477,49 +512,56 @@ __device__ __forceinline__ void cell32_sweep(const float* __restrict__ si, uint3
     const float4 U = *reinterpret_cast<const float4*>(su + ii);
     const float4 V = *reinterpret_cast<const float4*>(sv + ii);
     const float4 W = *reinterpret_cast<const float4*>(sw + ii);
-    bool c[4];
-    {
-      const float xs[4] = {X.x, X.y, X.z, X.w}, ys[4] = {Y.x, Y.y, Y.z, Y.w},
-                  zs[4] = {Z.x, Z.y, Z.z, Z.w}, us[4] = {U.x, U.y, U.z, U.w},
-                  vs[4] = {V.x, V.y, V.z, V.w}, ws[4] = {W.x, W.y, W.z, W.w};
+    const float xs[4] = {X.x, X.y, X.z, X.w}, ys[4] = {Y.x, Y.y, Y.z, Y.w},
+                zs[4] = {Z.x, Z.y, Z.z, Z.w}, us[4] = {U.x, U.y, U.z, U.w},
+                vs[4] = {V.x, V.y, V.z, V.w}, ws[4] = {W.x, W.y, W.z, W.w};
+    unsigned mask = 0;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float rx = jx - xs[u], ry = jy - ys[u], rz = jz - zs[u];
-        const float vx = gx - us[u], vy = gy - vs[u], vz = gz - ws[u];
-        const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-        const float Bv = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
-        c[u] = R <= fmaf(q.c1, Bv, q.c0);
-        if (OWN) c[u] = c[u] && (!jown || j > i0 + ii + (uint32_t)u);
-      }
+    for (int u = 0; u < 4; ++u) {
+      const float rx = jx - xs[u], ry = jy - ys[u], rz = jz - zs[u];
+      const float vx = gx - us[u], vy = gy - vs[u], vz = gz - ws[u];
+      const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+      const float Bv = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
+      bool c = R <= fmaf(c1, Bv, c0);
+      if (OWN) c = c && (!jown || j > i0 + ii + (uint32_t)u);
+      mask |= c ? (1u << u) : 0u;
     }
-    if (__any_sync(0xFFFFFFFFu, c[0] || c[1] || c[2] || c[3])) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        bool cand = false;
-        if (c[u]) {
-          const uint32_t t = ii + (uint32_t)u;
-          const float rx = jx - sx[t], ry = jy - sy[t], rz = jz - sz[t];
-          const float vx = gx - su[t], vy = gy - sv[t], vz = gz - sw[t];
-          const float Bv = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
-          cand = full_test32(q, rx, ry, rz, vx, vy, vz, Bv);
-        }
-        warp_emit(w, s, lane, cand, i0 + ii + (uint32_t)u, j);
-      }
+    if (mask) {
+      // rare and divergent: only the lanes with sphere survivors run the full test
+      do {
+        const int u = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const uint32_t t = ii + (uint32_t)u;
+        const float rx = jx - sx[t], ry = jy - sy[t], rz = jz - sz[t];
+        const float vx = gx - su[t], vy = gy - sv[t], vz = gz - sw[t];
+        const float Bv = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
+        if (full_test32(q, rx, ry, rz, vx, vy, vz, Bv)) emit_lane(buf, count, s, i0 + t, j);
+      } while (mask);
     }
   }
 }
 
 template <int K>
-__global__ void __launch_bounds__(kCellWarps * 32, 2) k_search_cell32(Batch B) {
+__global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_cell32(Batch B) {
   constexpr int ICAP = 64;
   __shared__ __align__(16) float si[kCellWarps][6 * ICAP];
   __shared__ uint2 wbuf[kCellWarps][kWarpBuf];
+  __shared__ uint32_t wcount[kCellWarps];
+  __shared__ Guard32 sq;
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const uint32_t gwarp = blockIdx.x * kCellWarps + warp, nwarps = gridDim.x * kCellWarps;
 
   for (int k = 0; k < B.nsims; ++k) {
     SimDev& s = *B.sims[k];
     if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_CELL) continue;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const Grid& G0 = s.d.grid;
+      sq.c0 = G0.s_c0; sq.c1 = G0.s_c1; sq.ag = G0.a_g; sq.tg = G0.t_g; sq.dtf = G0.dtf;
+      sq.d0up = G0.d0up; sq.brel = G0.b_rel; sq.babs = G0.b_abs; sq.we = G0.w_e; sq.wrel = G0.w_rel;
+    }
+    if (lane == 0) wcount[warp] = 0;
+    __syncthreads();
     const Grid& G = s.d.grid;
     const int nx = G.nc[0], ny = G.nc[1], nz = G.nc[2];
     const int Kx = nx == 1 ? 0 : K, Ky = ny == 1 ? 0 : K, Kz = nz == 1 ? 0 : K;
@@ -528,13 +570,12 @@ __global__ void __launch_bounds__(kCellWarps * 32, 2) k_search_cell32(Batch B) {
     const uint32_t nkeys = G.nkeys;
     const uint32_t* __restrict__ cs = s.cell_start;
     const float wx = G.wf[0], wy = G.wf[1], wz = G.wf[2];
-    Guard32 q;
-    q.c0 = G.s_c0; q.c1 = G.s_c1; q.ag = G.a_g; q.tg = G.t_g; q.dtf = G.dtf;
-    q.d0up = G.d0up; q.brel = G.b_rel; q.babs = G.b_abs; q.we = G.w_e; q.wrel = G.w_rel;
+    const float c0 = G.s_c0, c1 = G.s_c1;
     const float4* __restrict__ MA = s.mir_a;
     const float2* __restrict__ MB = s.mir_b;
     float* my = si[warp];
-    WarpEmit we_ = {wbuf[warp], 0u};
+    uint2* buf = wbuf[warp];
+    uint32_t* cnt = &wcount[warp];
     unsigned long long tests = 0;
 
     for (uint32_t key = gwarp; key < nkeys; key += nwarps) {
@@ -624,17 +665,19 @@ __global__ void __launch_bounds__(kCellWarps * 32, 2) k_search_cell32(Batch B) {
                 }
                 if (has_own) {
                   const bool jown = j >= startA && j < endA;
-                  cell32_sweep<true>(my, nI4, i0, jx, jy, jz, gx, gy, gz, j, jown, q, we_, s, lane);
+                  cell32_sweep<true>(my, nI4, i0, jx, jy, jz, gx, gy, gz, j, jown, c0, c1, sq, buf, cnt, s);
                 } else {
-                  cell32_sweep<false>(my, nI4, i0, jx, jy, jz, gx, gy, gz, j, false, q, we_, s, lane);
+                  cell32_sweep<false>(my, nI4, i0, jx, jy, jz, gx, gy, gz, j, false, c0, c1, sq, buf, cnt, s);
                 }
+                __syncwarp();
+                if (*cnt >= (uint32_t)(kWarpBuf / 2)) flush_lanes(buf, cnt, s, lane);
               }
             }
           }
         }
       }
     }
-    warp_flush(we_, s, lane);
+    flush_lanes(buf, cnt, s, lane);
     if (lane == 0 && tests) atomicAdd(&s.d.pair_tests, tests);
   }
 }
