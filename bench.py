@@ -138,6 +138,22 @@ def dist_info():
     return world, rank, local
 
 
+def reduce_max(x: float, world: int, device=None) -> float:
+    """Max over ranks (timing only: no simulation data crosses ranks)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job rate: units all ranks processed / slowest rank's time."""
+    return world * units_per_rank / (max_ms / 1e3)
+
+
 def source_sha(path):
     h = hashlib.sha256()
     with open(path, "rb") as f:
@@ -325,12 +341,7 @@ def run_gpu(args):
             dist.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, world, dev)
 
     # a dedicated stream: the library launches on it and the events are recorded on it
     stream = torch.cuda.Stream(dev)
@@ -373,7 +384,7 @@ def run_gpu(args):
     # ---- guarded binary32 (headline) ----
     sim32, ms32, counts32, launches32, clocks = timed_run(kmc.KMC_GUARDED_FP32, args.warmup,
                                                           args.steps, sample_clocks=True)
-    value = world * n * args.steps / (ms32 / 1e3)
+    value = aggregate_rate(n * args.steps, world, ms32)
     # per-phase times of the next steps, CUDA events on the simulation's stream
     tsteps = max(3, min(args.steps, 10))
     sim32.set_timing(True)
