@@ -76,16 +76,24 @@ extern "C" {
 
 #define KMC_NONE 0xFFFFFFFFu
 
+/* ---- flags (kmc_params.flags) --------------------------------------------- */
+#define KMC_FLAG_NO_SPLIT 1u   /* never split fast particles into a second population
+                                  (the speed split changes the work, never a result) */
+#define KMC_FLAG_FORCE_SPLIT 2u /* split whenever possible, cycling the threshold through
+                                  the trial values step by step (exercises the split) */
+
 /* ---- search kernels (kmc_params.search_kernel) ----------------------------- */
 #define KMC_SEARCH_AUTO 0      /* per step: warp-per-cell search when cells are well
                                   filled, thread-per-particle search otherwise */
 #define KMC_SEARCH_PARTICLE 1  /* one thread per particle */
 #define KMC_SEARCH_CELL 2      /* one warp per cell, partners in lanes */
+#define KMC_SEARCH_SEGMENT 3   /* one warp per run of cells of a column, partners in lanes
+                                  (guarded binary32; binary64 uses KMC_SEARCH_CELL) */
 
 /* Parameters of one simulation.  Zero-initialise, then set the fields. */
 typedef struct kmc_params {
   uint32_t n;              /* particles, >= 1 */
-  uint32_t flags;          /* reserved, must be 0 */
+  uint32_t flags;          /* 0 or KMC_FLAG_* bits */
   double box[3];           /* box extents L_x, L_y, L_z; particles live in [0, L) */
   int32_t bc[3];           /* KMC_PERIODIC or KMC_REFLECT per axis */
   int32_t max_rounds;      /* mutual-choice rounds per step, 1..4 (0 means 4) */
@@ -107,8 +115,9 @@ typedef struct kmc_params {
                               demand at sim_sync */
   uint32_t history_cap;    /* step records kept for KMC_OBS_COUNTS (0: 4096) */
   uint32_t profile_cap;    /* profile snapshots kept for KMC_OBS_PROFILES (0: 64) */
-  int32_t search_kernel;   /* KMC_SEARCH_AUTO (0), KMC_SEARCH_PARTICLE (1) or
-                              KMC_SEARCH_CELL (2).  Never changes results. */
+  int32_t search_kernel;   /* KMC_SEARCH_AUTO (0), KMC_SEARCH_PARTICLE (1),
+                              KMC_SEARCH_CELL (2) or KMC_SEARCH_SEGMENT (3).
+                              Never changes results. */
 } kmc_params;
 
 /* One record per completed step (KMC_OBS_COUNTS). */

@@ -43,9 +43,13 @@ KMC_OBS_PHASE_MS = 8
 
 KMC_NONE = 0xFFFFFFFF
 
+KMC_FLAG_NO_SPLIT = 1
+KMC_FLAG_FORCE_SPLIT = 2
+
 KMC_SEARCH_AUTO = 0
 KMC_SEARCH_PARTICLE = 1
 KMC_SEARCH_CELL = 2
+KMC_SEARCH_SEGMENT = 3
 
 
 class kmc_params(C.Structure):

@@ -142,7 +142,8 @@ size_t bytes_for(const Sizes& z) {
 int validate(const kmc_params* p, std::string& err) {
   if (!p) { err = "params is NULL"; return KMC_EINVAL; }
   if (p->n == 0) { err = "n must be >= 1"; return KMC_EINVAL; }
-  if (p->flags != 0) { err = "flags must be 0"; return KMC_EINVAL; }
+  if (p->flags & ~(uint32_t)(KMC_FLAG_NO_SPLIT | KMC_FLAG_FORCE_SPLIT)) { err = "unknown flags"; return KMC_EINVAL; }
+  if ((p->flags & KMC_FLAG_NO_SPLIT) && (p->flags & KMC_FLAG_FORCE_SPLIT)) { err = "conflicting split flags"; return KMC_EINVAL; }
   for (int a = 0; a < 3; ++a) {
     if (!(p->box[a] > 0.0)) { err = "box extents must be > 0"; return KMC_EINVAL; }
     if (p->bc[a] != KMC_PERIODIC && p->bc[a] != KMC_REFLECT) { err = "bad boundary kind"; return KMC_EINVAL; }
@@ -157,7 +158,7 @@ int validate(const kmc_params* p, std::string& err) {
   if (p->cell_scale != 0.0 && !(p->cell_scale >= 1.0)) { err = "cell_scale must be 0 or >= 1"; return KMC_EINVAL; }
   if (p->bc[0] == KMC_REFLECT && !(p->piston_x0 > 0.0)) { err = "reflecting x axis needs piston_x0 > 0"; return KMC_EINVAL; }
   if (p->n > 0x7FFFFFFFu) { err = "n too large"; return KMC_EINVAL; }
-  if (p->search_kernel < 0 || p->search_kernel > 2) { err = "bad search_kernel"; return KMC_EINVAL; }
+  if (p->search_kernel < 0 || p->search_kernel > 3) { err = "bad search_kernel"; return KMC_EINVAL; }
   return KMC_OK;
 }
 
@@ -480,6 +481,7 @@ int sim_create(const kmc_params* p, const double* x, const double* y, const doub
   h.profile_every = p->profile_every;
   h.K = p->stencil ? p->stencil : 1;
   h.search_kernel = p->search_kernel;
+  h.split_ok = (p->flags & KMC_FLAG_NO_SPLIT) ? 0 : ((p->flags & KMC_FLAG_FORCE_SPLIT) ? 2 : 1);
   h.piston_x0 = p->bc[0] == KMC_REFLECT ? p->piston_x0 : p->box[0];
   h.piston_u = p->bc[0] == KMC_REFLECT ? p->piston_u : 0.0;
   h.d0 = p->d0;

@@ -1,14 +1,24 @@
 // kmc_grid.cuh -- per-step search grid and the guard bands of the binary32
 // pre-tests, computed on the device by one thread per simulation.
 //
-// Cell size.  A candidate pair has |r| <= d_min + |v| t* < d0 + 2 vmax dt (the
-// relative speed is at most 2 vmax), so with cells at least h = d0 + 2 vmax dt wide
-// the partner lies in the same or a neighbouring cell (Sec. 2: 26 neighbours in 3D).
-// With stencil K the cell is h/K wide and K cells are searched on each side.  The
-// cell width gets a relative margin m that covers the binary32 rounding of the
-// cell assignment, and cell_scale >= 1 only enlarges it: none of this can change a
-// result, only the amount of work.  An axis with fewer than 2K+1 cells becomes a
-// single cell (searched once, no duplicate neighbours).
+// Cell size.  A candidate pair has |r| <= d_min + |v| t* < d0 + |v_i - v_j| dt
+// <= d0 + (s_i + s_j) dt with s = |v| (Sec. 2: the partner must reach its distance
+// of closest approach within the next time step).  With every particle at most S
+// fast, cells at least d0 + 2 S dt wide hold each partner in the same or a
+// neighbouring cell (Sec. 2: 26 neighbours in 3D).  With stencil K the cell is 1/K of
+// that and K cells are searched on each side.  The width gets a relative margin m
+// for the binary32 cell assignment, and cell_scale >= 1 only enlarges it.
+//
+// Speed split.  The fastest particle sets S = vmax, although nearly all particles
+// are much slower.  The grid may instead be sized for a threshold S1 < vmax: the
+// particles faster than S1 ("fast") are sorted into a second population.  Slow-slow
+// pairs are searched on the S1 grid as above; every fast particle searches c cells
+// on each side, c = ceil((d0 + 2 vmax dt) / w), over both populations (fast-fast
+// pairs once, by the lower index).  Each candidate pair is still tested exactly
+// once.  S1 is chosen per step from the number of particles above a few trial
+// thresholds (counted by the push of the previous step) with a cost estimate.
+// None of this can change a result, only the amount of work.  An axis with fewer
+// than 2K+1 cells becomes a single cell (searched once, no duplicate neighbours).
 #pragma once
 
 #include "kmc_internal.cuh"
@@ -17,12 +27,74 @@ namespace kmc {
 
 __device__ __forceinline__ float f_up(double x) { return __double2float_ru(x); }
 
+struct CellPlan {
+  int nc[3];
+  double m;
+  uint32_t col_shift, y_major, nkeys;
+  bool ok;
+};
+
+// cells for search radius h (before the stencil split); key space capped by max_keys
+__device__ inline CellPlan plan_cells(const double ext[3], double h, int K, uint64_t max_keys) {
+  const double u32 = 0x1p-24;
+  CellPlan p;
+  p.ok = false;
+  p.m = 0.0;
+  p.col_shift = 0;
+  p.y_major = 1;
+  p.nkeys = 1;
+  p.nc[0] = p.nc[1] = p.nc[2] = 1;
+  for (int attempt = 0; attempt < 64; ++attempt) {
+    // margin for binary32 cell assignment: index error <= 4 u32 n per particle
+    double nmax = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      double q = ext[a] * K / h;
+      nmax = q > nmax ? q : nmax;
+    }
+    if (nmax > 65535.0) nmax = 65535.0;
+    p.m = 1e-4 + 16.0 * u32 * nmax;
+    double wt = h * (1.0 + p.m) / K;  // target cell width
+    for (int a = 0; a < 3; ++a) {
+      double q = floor(ext[a] / wt);
+      int c = q > 65535.0 ? 65535 : (int)q;
+      if (c < 2 * K + 1) c = 1;
+      p.nc[a] = c;
+    }
+    // key space of the column-Morton order
+    uint32_t ny = (uint32_t)p.nc[1], nz = (uint32_t)p.nc[2];
+    uint32_t small = ny < nz ? ny : nz, large = ny < nz ? nz : ny;
+    uint32_t sh = 0;
+    while ((1u << sh) < small) ++sh;
+    uint64_t P = 1ull << sh;
+    uint64_t cols = ((large + P - 1) / P) * P * P;
+    uint64_t nkeys = cols * (uint64_t)p.nc[0];
+    if (nkeys <= max_keys && sh <= 15) {
+      p.col_shift = sh;
+      p.y_major = ny >= nz ? 1u : 0u;
+      p.nkeys = (uint32_t)nkeys;
+      p.ok = true;
+      return p;
+    }
+    h *= 1.25;  // coarsen until the key space fits
+  }
+  return p;
+}
+
+__device__ inline double search_cost(double n, double rho, int K) {
+  // pair tests of the half stencil, inflated when cells hold fewer particles than a
+  // warp's lanes can use
+  double st = (2 * K + 1.0) * (2 * K + 1.0) * (2 * K + 1.0) * 0.5;
+  double eff = rho < 16.0 ? sqrt(16.0 / (rho > 0.25 ? rho : 0.25)) : 1.0;
+  return n * st * rho * eff;
+}
+
 __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step) {
   Grid& g = s.d.grid;
   const double u32 = 0x1p-24, u64 = 0x1p-53;
   const int K = s.K;
-  double V = sqrt((double)vmax2_bound) * (1.0 + 0x1p-20);  // upper bound of max |v|
-  double hmin = s.d0 + 2.0 * V * s.dt;
+  const double scale = s.cell_scale > 1.0 ? s.cell_scale : 1.0;
+  const double V = sqrt((double)vmax2_bound) * (1.0 + 0x1p-20);  // upper bound of max |v|
+  const double Rfull = s.d0 + 2.0 * V * s.dt;
   double ext[3];
   for (int a = 0; a < 3; ++a) {
     ext[a] = s.box[a];
@@ -32,63 +104,121 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
       ext[0] = X > 0.0 ? X : s.box[0];
     }
   }
-  double h = hmin * (s.cell_scale > 1.0 ? s.cell_scale : 1.0);
-  int nc[3];
-  double m = 0.0;
-  for (int attempt = 0; attempt < 64; ++attempt) {
-    // margin for binary32 cell assignment: index error <= 4 u32 n per particle
-    double nmax = 0.0;
+
+  // ---- split threshold: estimated pair-test cost of each trial ----------------
+  bool feasible[kSplitTrials];
+  double cost[kSplitTrials];
+  const bool can_split = s.split_ok && s.d.have_counts;
+  for (int t = 0; t < kSplitTrials; ++t) {
+    feasible[t] = false;
+    cost[t] = 0.0;
+    if (t > 0 && !can_split) continue;
+    // trial thresholds were set from the previous step's bound; the slow cell must
+    // cover the threshold actually used for classification (a binary32 square)
+    const float sq = t == 0 ? 0.0f : s.d.split_thr[t];
+    const double S1 = t == 0 ? V : sqrt((double)sq);
+    if (t > 0 && !(S1 < V)) continue;
+    const double hs = (s.d0 + 2.0 * S1 * s.dt) * scale;
+    CellPlan p = plan_cells(ext, hs, K, (uint64_t)s.cell_cap / (t == 0 ? 1 : 2));
+    if (!p.ok) continue;
+    const double cells = (double)p.nc[0] * p.nc[1] * p.nc[2];
+    const double rho = (double)s.n / cells;
+    if (t == 0) {
+      cost[t] = search_cost((double)s.n, rho, K);
+      feasible[t] = true;
+      continue;
+    }
+    // fast stencil: c cells on each side per split axis; periodic axes must hold it,
+    // and no axis may be a one-cell periodic axis (no minimum-image test there)
+    const double nfast = (double)s.d.split_cnt[t];
+    double fast_cells = 1.0;
+    bool fits = true;
     for (int a = 0; a < 3; ++a) {
-      double q = ext[a] * K / h;
-      nmax = q > nmax ? q : nmax;
+      if (p.nc[a] == 1) {
+        if (s.bc[a] == KMC_PERIODIC) fits = false;
+        continue;
+      }
+      const double w = ext[a] / p.nc[a];
+      int c = (int)ceil(Rfull * (1.0 + p.m) / w);
+      if (c < K) c = K;
+      if (s.bc[a] == KMC_PERIODIC && p.nc[a] < 2 * c + 2) fits = false;
+      fast_cells *= (2.0 * c + 1.0);
     }
-    if (nmax > 65535.0) nmax = 65535.0;
-    m = 1e-4 + 16.0 * u32 * nmax;
-    double wt = h * (1.0 + m) / K;  // target cell width
-    for (int a = 0; a < 3; ++a) {
-      double q = floor(ext[a] / wt);
-      int c = q > 65535.0 ? 65535 : (int)q;
-      if (c < 2 * K + 1) c = 1;
-      nc[a] = c;
-    }
-    // key space of the column-Morton order
-    uint32_t ny = (uint32_t)nc[1], nz = (uint32_t)nc[2];
-    uint32_t small = ny < nz ? ny : nz, large = ny < nz ? nz : ny;
-    uint32_t sh = 0;
-    while ((1u << sh) < small) ++sh;
-    uint64_t P = 1ull << sh;
-    uint64_t cols = ((large + P - 1) / P) * P * P;
-    uint64_t nkeys = cols * (uint64_t)nc[0];
-    if (nkeys <= (uint64_t)s.cell_cap && sh <= 15) {
-      g.col_shift = sh;
-      g.y_major = ny >= nz ? 1u : 0u;
-      g.nkeys = (uint32_t)nkeys;
-      break;
-    }
-    h *= 1.25;  // coarsen until the key space fits
-    if (attempt == 63) s.d.status |= ST_CELL_OVERFLOW;
+    if (!fits) continue;
+    cost[t] = search_cost((double)s.n - nfast, rho, K) + nfast * fast_cells * rho * 3.0;
+    feasible[t] = true;
   }
+  int best = 0;
+  if (s.split_ok == 2) {
+    // forced: cycle through the feasible trial thresholds step by step
+    const int want = (int)(step % (uint64_t)(kSplitTrials - 1));
+    for (int d = 0; d < kSplitTrials - 1; ++d) {
+      const int t = 1 + (want + d) % (kSplitTrials - 1);
+      if (feasible[t]) { best = t; break; }
+    }
+  } else {
+    for (int t = 1; t < kSplitTrials; ++t)
+      if (feasible[t] && cost[t] < 0.9 * cost[best]) best = t;
+  }
+  const float s1sq = best > 0 ? s.d.split_thr[best] : 0.0f;
+  const bool split = best > 0;
+  const double S1 = split ? sqrt((double)s1sq) : V;
+  g.split = split ? 1u : 0u;
+  g.s1sq = s1sq;
+  // trial thresholds for the next step (counted by the push of this step)
+  for (int t = 0; t < kSplitTrials; ++t) {
+    const double f = (double)split_frac(t);
+    s.d.split_thr[t] = __double2float_rd(f * V * f * V);
+    s.d.split_cnt[t] = 0;
+  }
+
+  const CellPlan p = plan_cells(ext, (s.d0 + 2.0 * S1 * s.dt) * scale, K,
+                                (uint64_t)s.cell_cap / (split ? 2 : 1));
+  if (!p.ok) s.d.status |= ST_CELL_OVERFLOW;
+  const int* nc = p.nc;
+  const double m = p.m;
+  g.col_shift = p.col_shift;
+  g.y_major = p.y_major;
+  g.nkeys = p.nkeys;
   g.K = K;
+  int cfast[3] = {0, 0, 0};
+  for (int a = 0; a < 3; ++a) {
+    if (!split || nc[a] == 1) continue;
+    const double w = ext[a] / nc[a];
+    int c = (int)ceil(Rfull * (1.0 + m) / w);
+    if (c < K) c = K;
+    cfast[a] = c;
+  }
+  for (int a = 0; a < 3; ++a) g.cfast[a] = cfast[a];
   {
-    // search kernel: warp per cell when cells hold enough particles to fill a warp's
-    // lanes with partners; the binary32 warp-per-cell search handles no one-cell
-    // periodic axis (those need the minimum image per pair)
-    double cells = (double)nc[0] * nc[1] * nc[2];
-    double occ = (double)s.n / cells;
+    // search kernel for the slow population: warp per cell when cells are well
+    // filled; the binary32 warp-level searches handle no one-cell periodic axis
+    const double cells = (double)nc[0] * nc[1] * nc[2];
+    const double occ = (double)s.n / cells;
     bool cp = false;
     for (int a = 0; a < 3; ++a) cp = cp || (nc[a] == 1 && s.bc[a] == KMC_PERIODIC);
     int mode = s.search_kernel;
-    if (mode == 0) mode = occ >= 4.0 ? KMC_SEARCH_CELL : KMC_SEARCH_PARTICLE;
-    if (mode == KMC_SEARCH_CELL && cp && s.precision == KMC_GUARDED_FP32) mode = KMC_SEARCH_PARTICLE;
+    const bool fp32 = s.precision == KMC_GUARDED_FP32;
+    if (mode == 0) {
+      if (fp32) mode = occ >= 16.0 ? KMC_SEARCH_CELL : KMC_SEARCH_SEGMENT;
+      else mode = occ >= 4.0 ? KMC_SEARCH_CELL : KMC_SEARCH_PARTICLE;
+    }
+    if (mode == KMC_SEARCH_SEGMENT && !fp32) mode = KMC_SEARCH_CELL;
+    if ((mode == KMC_SEARCH_CELL || mode == KMC_SEARCH_SEGMENT) && cp && fp32) mode = KMC_SEARCH_PARTICLE;
     g.mode = mode;
+    // segment length: about 32 particles per warp, and a run of S + 2K cells must
+    // not wrap onto itself
+    int S = (int)floor(32.0 / (occ > 0.05 ? occ : 0.05) + 0.5);
+    S = S < 1 ? 1 : (S > 32 ? 32 : S);
+    if (nc[0] > 1 && S > nc[0] - 2 * K) S = nc[0] - 2 * K;
+    if (nc[0] == 1 || S < 1) S = 1;
+    g.seg = S;
   }
-  double wmax = 0.0;
   for (int a = 0; a < 3; ++a) {
     g.nc[a] = nc[a];
     g.w[a] = nc[a] == 1 ? ext[a] : ext[a] / nc[a];
     g.wf[a] = (float)g.w[a];
     g.inv_wf[a] = nc[a] == 1 ? 0.0f : (float)((double)nc[a] / ext[a]);
-    wmax = g.w[a] > wmax ? g.w[a] : wmax;
   }
 
   // ---- binary64 sphere pre-test: R > c0 + c1 B  =>  not a candidate ----------
@@ -101,20 +231,23 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
   // ---- binary32 pre-tests ------------------------------------------------------
   // Error of the binary32 separation against the binary64 one, per component:
   //   split axis: offsets from the cell corner (binary64 difference rounded once)
-  //     plus the stencil shift: u32 w (3K + 5) + 8 u64 L;
+  //     plus the stencil shift of up to Ke = max(K, fast reach) cells, or for x in
+  //     the segment kernel coordinates measured from the segment start:
+  //     u32 w (4 seg + 4 Ke + 4) + 8 u64 L;
   //   one-cell axis: u32 * 6.1 * extent + 8 u64 L.
   // Velocity difference: 4.1 u32 V.  Component bounds: |r_k| <= rb_k, |v_k| <= 2V.
-  double Lmax = 0.0, er = 0.0, rn2 = 0.0, rbmax = 0.0;
+  double er = 0.0, rn2 = 0.0, rbmax = 0.0;
   for (int a = 0; a < 3; ++a) {
-    double L = s.box[a] > ext[a] ? s.box[a] : ext[a];
-    Lmax = L > Lmax ? L : Lmax;
+    const double L = s.box[a] > ext[a] ? s.box[a] : ext[a];
+    const int Ke = cfast[a] > K ? cfast[a] : K;
     double e, rb;
     if (nc[a] == 1) {
       e = 6.1 * u32 * L + 8.0 * u64 * L;
       rb = s.bc[a] == KMC_PERIODIC ? 0.5 * L * (1.0 + 8.0 * u32) + 2.0 * e : L;
     } else {
-      e = u32 * g.w[a] * (3.0 * K + 5.0) * (1.0 + 1e-3) + 8.0 * u64 * L;
-      rb = (K + 1.0 + 2.0 * m) * g.w[a];
+      const double span = a == 0 ? (4.0 * g.seg + 4.0 * Ke + 4.0) : (4.0 * Ke + 5.0);
+      e = u32 * g.w[a] * span * (1.0 + 1e-3) + 8.0 * u64 * L;
+      rb = (Ke + 1.0 + 2.0 * m) * g.w[a];
     }
     er = e > er ? e : er;
     rbmax = rb > rbmax ? rb : rbmax;
@@ -123,39 +256,38 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
     g.halfLf[a] = (float)(0.5 * s.box[a]);
     g.tief[a] = f_up(4.0 * e);
   }
-  double rn = sqrt(rn2) * (1.0 + 1e-6);
-  double ev = 4.1 * u32 * V;
-  double g3 = 3.0 * u32 / (1.0 - 3.0 * u32);
-  double g3d = 3.0 * u64 / (1.0 - 3.0 * u64);
-  double g2 = 2.0 * u32 / (1.0 - 2.0 * u32);
-  double up2 = 1.0 + 2.0 * u32, up4 = 1.0 + 4.0 * u32;
-  double rel40 = 1.0 + 0x1p-40;
-  double s3 = 1.7320508075688772 * (1.0 + 1e-15);
-  double bslack = 7.0 * ev * V + 3.0 * ev * ev;  // |v|^2 - |v~|^2 slack, absolute
-  double dt = s.dt, d0sq = s.d0sq;
+  const double rn = sqrt(rn2) * (1.0 + 1e-6);
+  const double ev = 4.1 * u32 * V;
+  const double g3 = 3.0 * u32 / (1.0 - 3.0 * u32);
+  const double g3d = 3.0 * u64 / (1.0 - 3.0 * u64);
+  const double g2 = 2.0 * u32 / (1.0 - 2.0 * u32);
+  const double up2 = 1.0 + 2.0 * u32, up4 = 1.0 + 4.0 * u32;
+  const double rel40 = 1.0 + 0x1p-40;
+  const double s3 = 1.7320508075688772 * (1.0 + 1e-15);
+  const double bslack = 7.0 * ev * V + 3.0 * ev * ev;  // |v|^2 - |v~|^2 slack, absolute
+  const double dt = s.dt, d0sq = s.d0sq;
   // sphere test
-  double c0 = (rel40 * (d0sq + dt * dt * bslack) + 2.0 * s3 * er * rn) * (1.0 + g3);
-  double c1 = dt * dt * rel40 * (1.0 + g3) / (1.0 - g3);
+  const double c0 = (rel40 * (d0sq + dt * dt * bslack) + 2.0 * s3 * er * rn) * (1.0 + g3);
+  const double c1 = dt * dt * rel40 * (1.0 + g3) / (1.0 - g3);
   g.s_c0 = f_up(c0 * up2);
   g.s_c1 = f_up(c1 * up2);
   // approach test (t* >= 0): |A~ - A64| <= a_g
-  double Ga = (s3 * (ev * rn + 2.0 * V * er) + g3 * rn * 2.0 * V * 1.01 + g3d * rn * 2.0 * V) *
-              (1.0 + 1e-3);
+  const double Ga = (s3 * (ev * rn + 2.0 * V * er) + g3 * rn * 2.0 * V * 1.01 + g3d * rn * 2.0 * V) *
+                    (1.0 + 1e-3);
   g.a_g = f_up(Ga);
   // time test (t* < dt): X~ = A~ - dt B~ > t_g  =>  A64 >= dt B64
-  double Ex = u32 * (rn * 2.0 * V * 1.01 + 2.0 * dt * 4.0 * V * V * 1.02);
-  double Gt = (Ex + Ga + dt * (8.1 * V * V * g3 + bslack)) * (1.0 + 1e-3);
+  const double Ex = u32 * (rn * 2.0 * V * 1.01 + 2.0 * dt * 4.0 * V * V * 1.02);
+  const double Gt = (Ex + Ga + dt * (8.1 * V * V * g3 + bslack)) * (1.0 + 1e-3);
   g.t_g = f_up(Gt);
   g.dtf = (float)dt;
   // distance test (d_min < d0): |w~| >= w_e + d0 sqrt(B_up)  =>  W64 >= d0^2 B64
-  double ew = (2.0 * (rbmax * ev + 2.0 * V * er) * 1.001 + g2 * 2.0 * rbmax * 2.0 * V * 1.01) +
-              2.0 * (2.0 * u64) * rbmax * 2.0 * V;
+  const double ew = (2.0 * (rbmax * ev + 2.0 * V * er) * 1.001 + g2 * 2.0 * rbmax * 2.0 * V * 1.01) +
+                    2.0 * (2.0 * u64) * rbmax * 2.0 * V;
   g.w_e = f_up(s3 * ew * up4);
   g.b_rel = f_up((1.0 / (1.0 - g3)) * (1.0 + g3d) * up2);
   g.b_abs = f_up(bslack * (1.0 + g3d) * up2);
   g.d0up = f_up(s.d0 * rel40 / sqrt(1.0 - g3d) * up4 * (1.0 + 4.0 * u32));
   g.w_rel = f_up((1.0 + g3) * up4);
-  (void)Lmax;
 }
 
 }  // namespace kmc

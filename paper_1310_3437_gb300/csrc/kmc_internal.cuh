@@ -22,6 +22,13 @@ constexpr int kSearchBuf = 512;     // per-block shared-memory staging of emitte
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr int kProfQ = 19;          // int64 counters per profile bin (see kmc_push.cu)
 constexpr int kMaxGroup = 4096;     // simulations per batch
+constexpr int kSplitTrials = 7;     // trial thresholds of the speed split (index 0: none)
+
+// trial thresholds of the speed split as fractions of vmax (index 0: no split)
+__device__ __forceinline__ float split_frac(int t) {
+  return t == 0 ? 1.0f : t == 1 ? 0.85f : t == 2 ? 0.72f : t == 3 ? 0.6f : t == 4 ? 0.5f
+                 : t == 5 ? 0.42f : 0.35f;
+}
 
 enum : uint32_t {
   ST_EDGE_OVERFLOW = 1u << 0,  // candidate-pair buffer too small (host grows it)
@@ -34,7 +41,11 @@ enum : uint32_t {
 struct Grid {
   int32_t nc[3];      // cells per axis; 1 means the axis is one cell (no stencil on it)
   int32_t K;          // stencil radius in cells
-  int32_t mode;       // search kernel of this step: KMC_SEARCH_PARTICLE or KMC_SEARCH_CELL
+  int32_t mode;       // search kernel of this step: KMC_SEARCH_PARTICLE, _CELL or _SEGMENT
+  int32_t seg;        // cells per segment (KMC_SEARCH_SEGMENT) along x
+  uint32_t split;     // 1: particles with |v|^2 above s1sq form a second population
+  float s1sq;         // binary32 split threshold on the upper bound of |v|^2
+  int32_t cfast[3];   // fast particles search cfast cells on each side (split axes)
   uint32_t nkeys;     // size of the key space (padded Morton columns x nc[0])
   uint32_t col_shift; // log2 of the Morton block edge P (P = next pow2 of the smaller axis)
   uint32_t y_major;   // 1 if nc[1] >= nc[2] (y carries the high, non-interleaved bits)
@@ -65,6 +76,9 @@ struct Dyn {
   uint32_t round_pairs[4];
   unsigned long long pair_tests;
   uint32_t last_raw;    // n_raw of the last completed step (its pair buffer is kept)
+  uint32_t have_counts; // split_cnt holds counts of the current state
+  float split_thr[kSplitTrials];     // trial thresholds on |v|^2 (set with the grid)
+  uint32_t split_cnt[kSplitTrials];  // particles above each trial threshold
   uint32_t prof_due;    // the step being run ends with a profile
   uint32_t prof_count;  // snapshots written
   uint64_t hist_count;  // step records written
@@ -75,6 +89,7 @@ struct SimDev {
   uint32_t n;
   int32_t bc[3];
   int32_t max_rounds, precision, profile_bins, profile_every, K, search_kernel;
+  int32_t split_ok;     // 0: never split, 1: split when cheaper, 2: split whenever possible
   double box[3];
   double piston_x0, piston_u, d0, dt, d0sq;
   double profile_range, cell_scale;
@@ -178,6 +193,14 @@ __device__ __forceinline__ void key_decode(const Grid& g, uint32_t key, int& cx,
   uint32_t b = compact16(lo >> 1);
   cy = (int)(g.y_major ? a : b);
   cz = (int)(g.y_major ? b : a);
+}
+
+// upper bound of |v|^2 in binary32 (directed rounding; used to size cells and to
+// split fast from slow particles, never in a result)
+__device__ __forceinline__ float vmag2_up(double vx, double vy, double vz) {
+  float ax = __double2float_ru(fabs(vx)), ay = __double2float_ru(fabs(vy)),
+        az = __double2float_ru(fabs(vz));
+  return __fadd_ru(__fadd_ru(__fmul_ru(ax, ax), __fmul_ru(ay, ay)), __fmul_ru(az, az));
 }
 
 // cell coordinate along one axis, binary32 (only the speed depends on it)

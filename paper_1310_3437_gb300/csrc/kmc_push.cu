@@ -20,12 +20,6 @@
 
 namespace kmc {
 
-__device__ __forceinline__ float vmag2_up(double vx, double vy, double vz) {
-  float ax = __double2float_ru(fabs(vx)), ay = __double2float_ru(fabs(vy)),
-        az = __double2float_ru(fabs(vz));
-  return __fadd_ru(__fadd_ru(__fmul_ru(ax, ax), __fmul_ru(ay, ay)), __fmul_ru(az, az));
-}
-
 __device__ __forceinline__ void block_max_to(uint32_t* dst, float v) {
   __shared__ float wmax[kTile / 32];
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xFFFFFFFFu, v, o));
@@ -90,6 +84,15 @@ __global__ void __launch_bounds__(kTile) k_push(Batch B) {
     }
     if (q != kNone) s.last[cur][p] = s.id[cur][q];
     vm = vmag2_up(vv[0], vv[1], vv[2]);
+  }
+  if (s.split_ok) {
+    // particles above each trial split threshold (warp ballots, one atomic per warp)
+    const bool valid = p < s.n;
+#pragma unroll
+    for (int t = 1; t < kSplitTrials; ++t) {
+      unsigned m = __ballot_sync(0xFFFFFFFFu, valid && vm > s.d.split_thr[t]);
+      if ((threadIdx.x & 31) == 0 && m) atomicAdd(&s.d.split_cnt[t], (uint32_t)__popc(m));
+    }
   }
   block_max_to(&s.d.vmax2_acc, vm);
 }
@@ -188,6 +191,7 @@ __global__ void k_finalize(Batch B) {
       s.d.prof_count += 1;
     }
     s.d.last_raw = s.d.n_raw;
+    s.d.have_counts = s.split_ok ? 1u : 0u;
     s.d.parity ^= 1u;
     s.d.step += 1;
     s.d.steps_left -= 1;
@@ -221,6 +225,7 @@ __global__ void k_init_grid(Batch B) {
     SimDev& s = *B.sims[k];
     float vm = __uint_as_float(s.d.vmax2_acc);
     s.d.vmax2 = vm;
+    s.d.have_counts = 0;
     compute_grid(s, vm, s.d.step);
     reset_step_counters(s);
     set_prof_due(s);

@@ -55,7 +55,9 @@ __global__ void __launch_bounds__(kTile) k_search(Batch B) {
   unsigned long long tests = 0;
 
   uint32_t p = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
-  if (p < n) {
+  // with the speed split only the slow population (keys below nkeys) is searched here
+  const uint32_t nslow = g.split ? __ldg(cs + g.nkeys) : n;
+  if (p < nslow) {
     int cx, cy, cz;
     key_decode(g, s.skey[p], cx, cy, cz);
 
@@ -682,6 +684,329 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_cell32(Batch B) {
   }
 }
 
+// --------------------------------------------------------------------------- //
+// Binary32 warp-per-segment search, for sparsely filled cells.  A warp owns a run of
+// S consecutive cells of one column (S from the occupancy, about 32 particles), whose
+// particles i are staged in shared memory with x measured from the segment start.
+// For every forward column of the stencil the partner run (S + 2K cells, contiguous
+// in cell order) is loaded 32 at a time, one partner j per lane; each lane then
+// loops over exactly the i's of the segment that lie in its stencil -- a contiguous
+// index range, because cells are ordered along x -- with a warp-uniform trip count
+// (the warp maximum of the range lengths).
+template <int K>
+__global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_seg32(Batch B) {
+  constexpr int ICAP = 64;
+  __shared__ __align__(16) float si[kCellWarps][6 * ICAP];
+  __shared__ uint2 wbuf[kCellWarps][kWarpBuf];
+  __shared__ uint32_t wcount[kCellWarps];
+  __shared__ Guard32 sq;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t gwarp = blockIdx.x * kCellWarps + warp, nwarps = gridDim.x * kCellWarps;
+
+  for (int k = 0; k < B.nsims; ++k) {
+    SimDev& s = *B.sims[k];
+    if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_SEGMENT) continue;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const Grid& G0 = s.d.grid;
+      sq.c0 = G0.s_c0; sq.c1 = G0.s_c1; sq.ag = G0.a_g; sq.tg = G0.t_g; sq.dtf = G0.dtf;
+      sq.d0up = G0.d0up; sq.brel = G0.b_rel; sq.babs = G0.b_abs; sq.we = G0.w_e; sq.wrel = G0.w_rel;
+    }
+    if (lane == 0) wcount[warp] = 0;
+    __syncthreads();
+    const Grid& G = s.d.grid;
+    const int nx = G.nc[0], ny = G.nc[1], nz = G.nc[2];
+    const int Kx = nx == 1 ? 0 : K, Ky = ny == 1 ? 0 : K, Kz = nz == 1 ? 0 : K;
+    const bool px = s.bc[0] == KMC_PERIODIC, py = s.bc[1] == KMC_PERIODIC,
+               pz = s.bc[2] == KMC_PERIODIC;
+    const int S = G.seg;
+    const uint32_t nseg = (uint32_t)((nx + S - 1) / S);
+    const uint32_t ncols = G.nkeys / (uint32_t)nx;
+    const uint32_t items = ncols * nseg;
+    const uint32_t* __restrict__ cs = s.cell_start;
+    const float wx = G.wf[0], wy = G.wf[1], wz = G.wf[2];
+    const float c0 = G.s_c0, c1 = G.s_c1;
+    const float4* __restrict__ MA = s.mir_a;
+    const float2* __restrict__ MB = s.mir_b;
+    float* my = si[warp];
+    const float* sxx = my;
+    const float* syy = my + ICAP;
+    const float* szz = my + 2 * ICAP;
+    const float* suu = my + 3 * ICAP;
+    const float* svv = my + 4 * ICAP;
+    const float* sww = my + 5 * ICAP;
+    uint2* buf = wbuf[warp];
+    uint32_t* cnt = &wcount[warp];
+    unsigned long long tests = 0;
+
+    for (uint32_t item = gwarp; item < items; item += nwarps) {
+      const uint32_t col = item / nseg, sidx = item - col * nseg;
+      const uint32_t colA = col * (uint32_t)nx;
+      const int cx0 = (int)sidx * S;
+      const int cx1 = (cx0 + S < nx ? cx0 + S : nx) - 1;
+      const uint32_t segA = __ldg(cs + colA + cx0), segB = __ldg(cs + colA + cx1 + 1);
+      if (segA == segB) continue;
+      int tx, cy, cz;
+      key_decode(G, colA, tx, cy, cz);
+      for (uint32_t i0 = segA; i0 < segB; i0 += ICAP) {
+        const uint32_t nI = segB - i0 < (uint32_t)ICAP ? segB - i0 : (uint32_t)ICAP;
+        __syncwarp();
+        for (uint32_t t = lane; t < nI; t += 32) {
+          const uint32_t i = i0 + t;
+          // cell of i inside the segment (largest c with start(c) <= i)
+          int lo = cx0, hi = cx1;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(cs + colA + mid) <= i) lo = mid; else hi = mid - 1;
+          }
+          const float4 a = MA[i];
+          const float2 b = MB[i];
+          my[t] = fmaf((float)(lo - cx0), wx, a.x);
+          my[ICAP + t] = a.y; my[2 * ICAP + t] = a.z;
+          my[3 * ICAP + t] = a.w; my[4 * ICAP + t] = b.x; my[5 * ICAP + t] = b.y;
+        }
+        __syncwarp();
+        for (int dz = 0; dz <= Kz; ++dz) {
+          int qz = cz + dz;
+          if (qz >= nz) {
+            if (!pz) break;
+            qz -= nz;
+          }
+          for (int dy = (dz == 0 ? 0 : -Ky); dy <= Ky; ++dy) {
+            int qy = cy + dy;
+            if (qy < 0) {
+              if (!py) continue;
+              qy += ny;
+            } else if (qy >= ny) {
+              if (!py) continue;
+              qy -= ny;
+            }
+            const uint32_t colB = col_code(G, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx;
+            const bool own_col = dz == 0 && dy == 0;
+            const float shy = (float)dy * wy, shz = (float)dz * wz;
+            // partner run in unwrapped cell coordinates [ua, ub]
+            const int ua = own_col ? cx0 : cx0 - Kx;
+            const int ub = cx1 + Kx;
+            int u = ua;
+            while (u <= ub) {
+              const int region = u < 0 ? -1 : (u >= nx ? 1 : 0);
+              if (region != 0 && !px) { ++u; continue; }
+              int m = 1;
+              while (u + m <= ub) {
+                const int u2 = u + m;
+                const int r2 = u2 < 0 ? -1 : (u2 >= nx ? 1 : 0);
+                if (r2 != region) break;
+                ++m;
+              }
+              const int qa = u - region * nx;  // first cell of the piece in the column
+              const int ua_piece = u;
+              u += m;
+              const uint32_t jbeg = __ldg(cs + colB + qa), jend = __ldg(cs + colB + qa + m);
+              if (jbeg == jend) continue;
+              for (uint32_t cb = jbeg; cb < jend; cb += 32) {
+                const uint32_t j = cb + lane;
+                uint32_t lo_i = 0, hi_i = 0;
+                float jx = 0.f, jy = 0.f, jz = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+                if (j < jend) {
+                  // cell of j in the piece
+                  int lo = 0, hi = m - 1;
+                  while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (__ldg(cs + colB + qa + mid) <= j) lo = mid; else hi = mid - 1;
+                  }
+                  const int uj = ua_piece + lo;  // unwrapped cell of j
+                  const float4 a = __ldg(MA + j);
+                  const float2 b = __ldg(MB + j);
+                  jx = fmaf((float)(uj - cx0), wx, a.x);
+                  jy = a.y + shy;
+                  jz = a.z + shz;
+                  gx = a.w; gy = b.x; gz = b.y;
+                  // i's of the segment inside j's stencil: cells [uj-K, uj+K] (other
+                  // columns) or [uj-K, uj] with i < j in j's own cell (own column)
+                  int ca = uj - Kx > cx0 ? uj - Kx : cx0;
+                  int cbnd = own_col ? (region == 0 ? uj : uj - 1) : uj + Kx;
+                  cbnd = cbnd < cx1 ? cbnd : cx1;
+                  if (ca <= cbnd) {
+                    lo_i = __ldg(cs + colA + ca);
+                    hi_i = __ldg(cs + colA + cbnd + 1);
+                    if (own_col && region == 0 && hi_i > j) hi_i = j;
+                    if (lo_i < i0) lo_i = i0;
+                    if (hi_i > i0 + nI) hi_i = i0 + nI;
+                    if (hi_i < lo_i) hi_i = lo_i;
+                  }
+                }
+                const uint32_t len = hi_i - lo_i;
+                tests += len;
+                const uint32_t T = __reduce_max_sync(0xFFFFFFFFu, len);
+                for (uint32_t t = 0; t < T; ++t) {
+                  if (t < len) {
+                    const uint32_t ti = lo_i + t - i0;
+                    const float rx = jx - sxx[ti], ry = jy - syy[ti], rz = jz - szz[ti];
+                    const float vx = gx - suu[ti], vy = gy - svv[ti], vz = gz - sww[ti];
+                    const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+                    const float Bv = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
+                    if (R <= fmaf(c1, Bv, c0) && full_test32(sq, rx, ry, rz, vx, vy, vz, Bv))
+                      emit_lane(buf, cnt, s, lo_i + t, j);
+                  }
+                }
+                __syncwarp();
+                if (*cnt >= (uint32_t)(kWarpBuf / 2)) flush_lanes(buf, cnt, s, lane);
+              }
+            }
+          }
+        }
+      }
+    }
+    flush_lanes(buf, cnt, s, lane);
+    for (int o = 16; o > 0; o >>= 1) tests += __shfl_down_sync(0xFFFFFFFFu, tests, o);
+    if (lane == 0 && tests) atomicAdd(&s.d.pair_tests, tests);
+  }
+}
+
+// --------------------------------------------------------------------------- //
+// Fast particles of the speed split: one thread per fast particle p, searching
+// cfast cells on each side over both populations -- every slow particle, and the
+// fast particles j > p (each fast-fast pair once).  The pair tests are those of the
+// thread-per-particle search.
+template <int PREC>
+__global__ void __launch_bounds__(kTile) k_search_fast(Batch B) {
+  __shared__ uint2 sbuf[kSearchBuf];
+  __shared__ uint32_t scnt, sbase;
+  __shared__ unsigned long long stests;
+  int k = find_sim(B.ptile, B.nsims, blockIdx.x);
+  SimDev& s = *B.sims[k];
+  if (!sim_active(s) || !s.d.grid.split) return;
+  const Grid g = s.d.grid;
+  const uint32_t* __restrict__ cs = s.cell_start;
+  const uint32_t nk = g.nkeys;
+  const uint32_t nslow = __ldg(cs + nk);
+  const uint32_t p = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
+  // blocks entirely below the fast population have nothing to do
+  if ((blockIdx.x - B.ptile[k]) * kTile + kTile <= nslow) return;
+  if (threadIdx.x == 0) { scnt = 0; stests = 0; }
+  __syncthreads();
+  const uint32_t n = s.n;
+  const int cur = s.d.parity ^ 1;
+  const uint32_t edge_cap = s.edge_cap;
+  uint2* __restrict__ edges = s.edge;
+  const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
+  const int Cx = g.cfast[0], Cy = g.cfast[1], Cz = g.cfast[2];
+  const bool px = s.bc[0] == KMC_PERIODIC, py = s.bc[1] == KMC_PERIODIC,
+             pz = s.bc[2] == KMC_PERIODIC;
+  unsigned long long tests = 0;
+  if (p >= nslow && p < n) {
+    int cx, cy, cz;
+    key_decode(g, s.skey[p] - nk, cx, cy, cz);
+    const double* __restrict__ X0 = s.x[cur][0];
+    const double* __restrict__ X1 = s.x[cur][1];
+    const double* __restrict__ X2 = s.x[cur][2];
+    const double* __restrict__ V0 = s.v[cur][0];
+    const double* __restrict__ V1 = s.v[cur][1];
+    const double* __restrict__ V2 = s.v[cur][2];
+    const float4* __restrict__ MA = s.mir_a;
+    const float2* __restrict__ MB = s.mir_b;
+    double xo[3] = {0, 0, 0}, vo[3] = {0, 0, 0};
+    Own32 o32 = {0, 0, 0, 0, 0, 0};
+    if (PREC == KMC_FP64) {
+      xo[0] = X0[p]; xo[1] = X1[p]; xo[2] = X2[p];
+      vo[0] = V0[p]; vo[1] = V1[p]; vo[2] = V2[p];
+    } else {
+      const float4 a = MA[p];
+      const float2 b = MB[p];
+      o32 = {a.x, a.y, a.z, a.w, b.x, b.y};
+    }
+    const double L0 = s.box[0], L1 = s.box[1], L2 = s.box[2];
+    for (int dz = -Cz; dz <= Cz; ++dz) {
+      int qz = cz + dz;
+      if (qz < 0 || qz >= nz) {
+        if (!pz) continue;
+        qz = qz < 0 ? qz + nz : qz - nz;
+      }
+      for (int dy = -Cy; dy <= Cy; ++dy) {
+        int qy = cy + dy;
+        if (qy < 0 || qy >= ny) {
+          if (!py) continue;
+          qy = qy < 0 ? qy + ny : qy - ny;
+        }
+        const uint32_t colbase = col_code(g, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx;
+        for (int dx = -Cx; dx <= Cx; ++dx) {
+          int qx = cx + dx;
+          if (qx < 0 || qx >= nx) {
+            if (!px) continue;
+            qx = qx < 0 ? qx + nx : qx - nx;
+          }
+          const uint32_t key = colbase + (uint32_t)qx;
+          const float sx = o32.ox - (float)dx * g.wf[0];
+          const float sy = o32.oy - (float)dy * g.wf[1];
+          const float sz = o32.oz - (float)dz * g.wf[2];
+          // slow particles of the cell, then its fast particles above p
+          for (int pop = 0; pop < 2; ++pop) {
+            uint32_t beg = __ldg(cs + pop * nk + key), end = __ldg(cs + pop * nk + key + 1);
+            if (pop == 1 && beg <= p) beg = p + 1;
+            if (beg >= end) continue;
+            tests += end - beg;
+            for (uint32_t j = beg; j < end; ++j) {
+              bool emit;
+              if (PREC == KMC_FP64) {
+                double r0 = dsub(__ldg(X0 + j), xo[0]);
+                double r1 = dsub(__ldg(X1 + j), xo[1]);
+                double r2 = dsub(__ldg(X2 + j), xo[2]);
+                if (px) { if (r0 > 0.5 * L0) r0 = dsub(r0, L0); else if (r0 < -0.5 * L0) r0 = dadd(r0, L0); }
+                if (py) { if (r1 > 0.5 * L1) r1 = dsub(r1, L1); else if (r1 < -0.5 * L1) r1 = dadd(r1, L1); }
+                if (pz) { if (r2 > 0.5 * L2) r2 = dsub(r2, L2); else if (r2 < -0.5 * L2) r2 = dadd(r2, L2); }
+                double g0 = dsub(__ldg(V0 + j), vo[0]);
+                double g1 = dsub(__ldg(V1 + j), vo[1]);
+                double g2 = dsub(__ldg(V2 + j), vo[2]);
+                double R = dadd(dadd(dmul(r0, r0), dmul(r1, r1)), dmul(r2, r2));
+                double Bv = dadd(dadd(dmul(g0, g0), dmul(g1, g1)), dmul(g2, g2));
+                emit = !(Bv >= 0x1p-900 && R > dadd(g.c0, dmul(g.c1, Bv)));
+              } else {
+                const float4 a = __ldg(MA + j);
+                const float2 b = __ldg(MB + j);
+                const float rx = a.x - sx, ry = a.y - sy, rz = a.z - sz;
+                const float gx = a.w - o32.vx, gy = b.x - o32.vy, gz = b.y - o32.vz;
+                const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+                const float Bv = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
+                emit = false;
+                if (R <= fmaf(g.s_c1, Bv, g.s_c0)) {
+                  Guard32 q;
+                  q.c0 = g.s_c0; q.c1 = g.s_c1; q.ag = g.a_g; q.tg = g.t_g; q.dtf = g.dtf;
+                  q.d0up = g.d0up; q.brel = g.b_rel; q.babs = g.b_abs; q.we = g.w_e; q.wrel = g.w_rel;
+                  emit = full_test32(q, rx, ry, rz, gx, gy, gz, Bv);
+                }
+              }
+              if (emit) {
+                uint32_t pos = atomicAdd(&scnt, 1u);
+                if (pos < (uint32_t)kSearchBuf) {
+                  sbuf[pos] = make_uint2(p, j);
+                } else {
+                  uint32_t gpos = atomicAdd(&s.d.n_raw, 1u);
+                  if (gpos < edge_cap) edges[gpos] = make_uint2(p, j);
+                  else atomicOr(&s.d.status, ST_EDGE_OVERFLOW);
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) tests += __shfl_down_sync(0xFFFFFFFFu, tests, o);
+  if ((threadIdx.x & 31) == 0 && tests) atomicAdd(&stests, tests);
+  __syncthreads();
+  uint32_t cnt = scnt < (uint32_t)kSearchBuf ? scnt : (uint32_t)kSearchBuf;
+  if (threadIdx.x == 0) {
+    if (stests) atomicAdd(&s.d.pair_tests, stests);
+    sbase = cnt ? atomicAdd(&s.d.n_raw, cnt) : 0u;
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < cnt; i += kTile) {
+    uint32_t gpos = sbase + i;
+    if (gpos < edge_cap) edges[gpos] = sbuf[i];
+    else atomicOr(&s.d.status, ST_EDGE_OVERFLOW);
+  }
+}
+
 int cell_search_blocks(int precision, int K, int num_sms) {
   int per_sm = 0;
   cudaError_t e;
@@ -713,12 +1038,16 @@ int launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st) {
     if (K == 2) {
       k_search<KMC_GUARDED_FP32, 2><<<L.ptiles, kTile, 0, st>>>(L.b);
       k_search_cell32<2><<<cb, kCellWarps * 32, 0, st>>>(L.b);
+      k_search_seg32<2><<<cb, kCellWarps * 32, 0, st>>>(L.b);
     } else {
       k_search<KMC_GUARDED_FP32, 1><<<L.ptiles, kTile, 0, st>>>(L.b);
       k_search_cell32<1><<<cb, kCellWarps * 32, 0, st>>>(L.b);
+      k_search_seg32<1><<<cb, kCellWarps * 32, 0, st>>>(L.b);
     }
   }
-  return 2;
+  if (precision == KMC_FP64) k_search_fast<KMC_FP64><<<L.ptiles, kTile, 0, st>>>(L.b);
+  else k_search_fast<KMC_GUARDED_FP32><<<L.ptiles, kTile, 0, st>>>(L.b);
+  return precision == KMC_FP64 ? 3 : 4;
 }
 
 }  // namespace kmc

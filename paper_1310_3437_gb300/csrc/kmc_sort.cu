@@ -30,6 +30,8 @@ __global__ void __launch_bounds__(kTile) k_count(Batch B) {
     int cy = cell_coord(g, 1, s.x[par][1][p]);
     int cz = cell_coord(g, 2, s.x[par][2][p]);
     key = col_code(g, (uint32_t)cy, (uint32_t)cz) * (uint32_t)g.nc[0] + (uint32_t)cx;
+    // fast particles (speed bound above the split threshold) form the second population
+    if (g.split && vmag2_up(s.v[par][0][p], s.v[par][1][p], s.v[par][2][p]) > g.s1sq) key += g.nkeys;
   }
   // warp aggregation: one atomic per distinct key in the warp
   unsigned active = __ballot_sync(0xFFFFFFFFu, valid);
@@ -60,7 +62,8 @@ struct ScanView {
 __device__ __forceinline__ ScanView scan_view(SimDev& s, int which) {
   ScanView v;
   if (which == 0) {
-    v.in = s.cell_count; v.out = s.cell_start; v.clear = s.cell_count; v.len = s.d.grid.nkeys;
+    v.in = s.cell_count; v.out = s.cell_start; v.clear = s.cell_count;
+    v.len = s.d.grid.nkeys * (s.d.grid.split ? 2u : 1u);
   } else {
     v.in = s.deg; v.out = s.off; v.clear = nullptr; v.len = s.n;
   }
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(kTile) k_scatter(Batch B) {
   s.partner[dst] = kNone;
   if (s.precision == KMC_GUARDED_FP32) {
     int c[3];
-    key_decode(g, key, c[0], c[1], c[2]);
+    key_decode(g, key >= g.nkeys ? key - g.nkeys : key, c[0], c[1], c[2]);
     float o[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {

@@ -17,10 +17,10 @@ import os
 from .sim import Simulation, params_from_setup
 
 DEFAULT_CANDIDATES = [
-    # (search_kernel, stencil, cell_scale)
-    (0, 1, 1.0), (2, 1, 1.0), (1, 1, 1.0),
-    (0, 2, 1.0), (2, 2, 1.0), (1, 2, 1.0),
-    (0, 1, 1.3), (2, 1, 1.3), (1, 1, 1.6), (2, 2, 1.3),
+    # (search_kernel, stencil, cell_scale): 0 auto, 1 particle, 2 cell, 3 segment
+    (0, 1, 1.0), (2, 1, 1.0), (3, 1, 1.0), (1, 1, 1.0),
+    (0, 2, 1.0), (2, 2, 1.0), (3, 2, 1.0), (1, 2, 1.0),
+    (3, 2, 1.3), (2, 1, 1.3), (3, 1, 1.3),
 ]
 
 

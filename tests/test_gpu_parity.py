@@ -25,9 +25,10 @@ FP32 = kmc.KMC_GUARDED_FP32
 
 
 def gpu_sim(setup, arrays, precision=FP64, stencil=1, cell_scale=1.0, last=None, step0=0,
-            edge_cap=0, search_kernel=0):
+            edge_cap=0, search_kernel=0, flags=0):
     p = kmc.params_from_setup(setup, precision=precision, stencil=stencil, cell_scale=cell_scale,
                               step0=step0, edge_cap=edge_cap, search_kernel=search_kernel)
+    p.flags = flags
     return kmc.Simulation(p, arrays, last=last)
 
 
@@ -86,7 +87,7 @@ def test_piston_tube_pair_lists_every_step(precision):
 
 
 @pytest.mark.parametrize("precision", [FP64, FP32])
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 def test_piston_tube_trajectory_bit_exact(precision, kernel):
     s = ki.piston_setup(n=1 << 14, seed=3, box=(8.0, 0.125, 0.125), profile_bins=0,
                         profile_every=0)
@@ -98,7 +99,7 @@ def test_piston_tube_trajectory_bit_exact(precision, kernel):
 @pytest.mark.parametrize("precision", [FP64, FP32])
 @pytest.mark.parametrize("stencil,cell_scale,kernel", [
     (2, 1.0, 0), (1, 1.7, 0), (2, 2.3, 0), (1, 1.0, 1), (1, 1.0, 2), (2, 1.0, 1), (2, 1.0, 2),
-    (1, 3.0, 2), (2, 4.0, 2), (1, 2.5, 1)])
+    (1, 3.0, 2), (2, 4.0, 2), (1, 2.5, 1), (1, 1.0, 3), (2, 1.0, 3), (1, 2.0, 3), (2, 3.5, 3)])
 def test_results_do_not_depend_on_grid_tuning(precision, stencil, cell_scale, kernel):
     """Cell size, stencil and search kernel (incl. cells above the per-warp staging
     capacity at cell_scale 3-4) change the work, never the result."""
@@ -131,7 +132,7 @@ def test_fp32_and_fp64_pair_lists_identical_with_many_near_threshold_pairs():
     st = oracle.State(pos + vel)
     pi, pj, _, _ = oracle.candidate_pairs(s, st)
     for prec in (FP64, FP32):
-        for kern in (1, 2):
+        for kern in (1, 2, 3):
             sim = gpu_sim(s, pos + vel, prec, search_kernel=kern).step(1).sync()
             e = sim.edges()
             assert np.array_equal(e, np.stack([pi, pj], axis=1))
@@ -162,7 +163,7 @@ def test_edge_cases():
     vel[0][100:200] = vel[0][99]
     s = ki.Setup(n=n, box=(1.0, 0.05, 0.05), bc=(0, 0, 0), d0=0.01, dt=0.01, seed=7,
                  name="equilibrium_slab")
-    for prec, kern in ((FP64, 0), (FP32, 0), (FP64, 2), (FP32, 2), (FP64, 1)):
+    for prec, kern in ((FP64, 0), (FP32, 0), (FP64, 2), (FP32, 2), (FP64, 1), (FP32, 3)):
         sim, st, oc, _ = run_both(s, 20, prec, arrays=pos + vel, search_kernel=kern)
         assert_same_counts(sim.counts(), oc)
         assert_same_state(sim, st)
@@ -254,3 +255,41 @@ def test_group_of_uneven_runs_equals_each_run_alone():
         assert_same_counts(sim.counts(), oc)
         assert_same_state(sim, st)
     g.close()
+
+
+@pytest.mark.parametrize("stencil", [1, 2])
+def test_segment_search_periodic_x_wrap(stencil):
+    """Short periodic x axis (few cells) with sparse cells: segments reach both column
+    ends, so partner runs wrap."""
+    rng = np.random.default_rng(31)
+    n = 3000
+    box = (0.3, 1.0, 1.0)
+    pos = [np.minimum(rng.random(n) * b, np.nextafter(b, 0)) for b in box]
+    vel = [rng.normal(0, 1, n) for _ in range(3)]
+    s = ki.Setup(n=n, box=box, bc=(0, 0, 0), d0=0.01, dt=0.01, seed=31, name="equilibrium_short")
+    for prec in (FP32,):
+        sim, st, oc, _ = run_both(s, 15, prec, arrays=pos + vel, search_kernel=3, stencil=stencil)
+        assert_same_counts(sim.counts(), oc)
+        assert_same_state(sim, st)
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+@pytest.mark.parametrize("kernel,stencil", [(0, 1), (1, 1), (2, 1), (3, 1), (3, 2)])
+def test_speed_split_forced_is_bit_exact(precision, kernel, stencil):
+    """Fast particles in a second population (threshold cycling through all trial
+    values step by step), searched by the fast-particle kernel: same trajectory."""
+    s = ki.piston_setup(n=1 << 15, seed=41, box=(8.0, 0.25, 0.25), profile_bins=0,
+                        profile_every=0)
+    flags = kmc.KMC_FLAG_FORCE_SPLIT
+    sim, st, oc, _ = run_both(s, 40, precision, search_kernel=kernel, stencil=stencil, flags=flags)
+    assert_same_counts(sim.counts(), oc)
+    assert_same_state(sim, st)
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_speed_split_forced_equilibrium_and_no_split(precision):
+    s = ki.equilibrium_setup(n=8192, seed=42, L=1.3, dt=0.005)
+    for flags in (kmc.KMC_FLAG_FORCE_SPLIT, kmc.KMC_FLAG_NO_SPLIT):
+        sim, st, oc, _ = run_both(s, 30, precision, flags=flags)
+        assert_same_counts(sim.counts(), oc)
+        assert_same_state(sim, st)
