@@ -347,7 +347,7 @@ def run_gpu(args):
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
 
-    knobs = {"search_kernel": 0, "stencil": 1, "cell_scale": 1.0}
+    knobs = {"search_kernel": 0, "stencil": 1, "cell_scale": 1.0, "split_min_occ": 0.0}
     tuning = None
     if not args.no_tune:
         from paper_1310_3437_gb300.tune import Autotuner

@@ -118,6 +118,9 @@ typedef struct kmc_params {
   int32_t search_kernel;   /* KMC_SEARCH_AUTO (0), KMC_SEARCH_PARTICLE (1),
                               KMC_SEARCH_CELL (2) or KMC_SEARCH_SEGMENT (3).
                               Never changes results. */
+  double split_min_occ;    /* speed split only if the slow grid keeps at least this
+                              many particles per cell on average (0: no floor).
+                              Never changes results. */
 } kmc_params;
 
 /* One record per completed step (KMC_OBS_COUNTS). */

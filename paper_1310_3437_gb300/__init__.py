@@ -66,6 +66,7 @@ class kmc_params(C.Structure):
         ("profile_range", C.c_double), ("cell_scale", C.c_double),
         ("edge_cap", C.c_uint32), ("history_cap", C.c_uint32),
         ("profile_cap", C.c_uint32), ("search_kernel", C.c_int32),
+        ("split_min_occ", C.c_double),
     ]
 
 

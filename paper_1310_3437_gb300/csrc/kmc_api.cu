@@ -159,6 +159,7 @@ int validate(const kmc_params* p, std::string& err) {
   if (p->bc[0] == KMC_REFLECT && !(p->piston_x0 > 0.0)) { err = "reflecting x axis needs piston_x0 > 0"; return KMC_EINVAL; }
   if (p->n > 0x7FFFFFFFu) { err = "n too large"; return KMC_EINVAL; }
   if (p->search_kernel < 0 || p->search_kernel > 3) { err = "bad search_kernel"; return KMC_EINVAL; }
+  if (p->split_min_occ < 0.0) { err = "split_min_occ must be >= 0"; return KMC_EINVAL; }
   return KMC_OK;
 }
 
@@ -271,7 +272,7 @@ int build_plan(Plan& P, const std::vector<kmc_sim*>& sims, cudaStream_t st, std:
   L.stiles_n = sn[m];
   L.stiles_c = sc[m];
   L.prtiles = pr[m];
-  L.edge_blocks = 2 * num_sms();
+  L.edge_blocks = 8 * num_sms();
   L.cell_blocks = cell_search_blocks(P.precision, P.K, num_sms());
   return KMC_OK;
 }
@@ -482,6 +483,7 @@ int sim_create(const kmc_params* p, const double* x, const double* y, const doub
   h.K = p->stencil ? p->stencil : 1;
   h.search_kernel = p->search_kernel;
   h.split_ok = (p->flags & KMC_FLAG_NO_SPLIT) ? 0 : ((p->flags & KMC_FLAG_FORCE_SPLIT) ? 2 : 1);
+  h.split_min_occ = p->split_min_occ;
   h.piston_x0 = p->bc[0] == KMC_REFLECT ? p->piston_x0 : p->box[0];
   h.piston_u = p->bc[0] == KMC_REFLECT ? p->piston_u : 0.0;
   h.d0 = p->d0;

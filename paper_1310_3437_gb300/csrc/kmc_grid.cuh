@@ -128,6 +128,7 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
       feasible[t] = true;
       continue;
     }
+    if (s.split_ok == 1 && rho < s.split_min_occ) continue;
     // fast stencil: c cells on each side per split axis; periodic axes must hold it,
     // and no axis may be a one-cell periodic axis (no minimum-image test there)
     const double nfast = (double)s.d.split_cnt[t];
@@ -206,9 +207,9 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
     if (mode == KMC_SEARCH_SEGMENT && !fp32) mode = KMC_SEARCH_CELL;
     if ((mode == KMC_SEARCH_CELL || mode == KMC_SEARCH_SEGMENT) && cp && fp32) mode = KMC_SEARCH_PARTICLE;
     g.mode = mode;
-    // segment length: about 32 particles per warp, and a run of S + 2K cells must
-    // not wrap onto itself
-    int S = (int)floor(32.0 / (occ > 0.05 ? occ : 0.05) + 0.5);
+    // segment length: about 48 particles per warp (the staging holds 64), and a run
+    // of S + 2K cells must not wrap onto itself
+    int S = (int)floor(48.0 / (occ > 0.05 ? occ : 0.05) + 0.5);
     S = S < 1 ? 1 : (S > 32 ? 32 : S);
     if (nc[0] > 1 && S > nc[0] - 2 * K) S = nc[0] - 2 * K;
     if (nc[0] == 1 || S < 1) S = 1;

@@ -90,6 +90,7 @@ struct SimDev {
   int32_t bc[3];
   int32_t max_rounds, precision, profile_bins, profile_every, K, search_kernel;
   int32_t split_ok;     // 0: never split, 1: split when cheaper, 2: split whenever possible
+  double split_min_occ; // smallest mean occupancy of the slow grid under a split
   double box[3];
   double piston_x0, piston_u, d0, dt, d0sq;
   double profile_range, cell_scale;
@@ -195,18 +196,43 @@ __device__ __forceinline__ void key_decode(const Grid& g, uint32_t key, int& cx,
   cz = (int)(g.y_major ? b : a);
 }
 
+// binary64 -> binary32 conversions on the integer pipes (on this part the hardware
+// conversion issues on the binary64 pipe, which runs at 1/72 of the binary32 rate).
+// Round to nearest even for normal results, identical to the hardware conversion;
+// zero, subnormal and out-of-range inputs take the hardware path.
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  const int fe = e - 1023 + 127;
+  if (e == 0 || fe <= 0 || fe >= 255) return __double2float_rn(x);
+  const uint32_t top = (uint32_t)((b >> 29) & 0x7FFFFFu);
+  const uint32_t rest = (uint32_t)(b & 0x1FFFFFFFu);
+  const uint32_t up = (rest > 0x10000000u || (rest == 0x10000000u && (top & 1u))) ? 1u : 0u;
+  const uint32_t bits = (uint32_t)((b >> 63) << 31) | (((uint32_t)fe << 23) + top + up);
+  return __uint_as_float(bits);
+}
+// |x| rounded up to binary32
+__device__ __forceinline__ float d2f_abs_ru(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+  const int e = (int)(b >> 52);
+  const int fe = e - 1023 + 127;
+  if (e == 0 || fe <= 0 || fe >= 255) return __double2float_ru(__longlong_as_double((long long)b));
+  const uint32_t top = (uint32_t)((b >> 29) & 0x7FFFFFu);
+  const uint32_t up = (b & 0x1FFFFFFFull) ? 1u : 0u;
+  return __uint_as_float(((uint32_t)fe << 23) + top + up);
+}
+
 // upper bound of |v|^2 in binary32 (directed rounding; used to size cells and to
 // split fast from slow particles, never in a result)
 __device__ __forceinline__ float vmag2_up(double vx, double vy, double vz) {
-  float ax = __double2float_ru(fabs(vx)), ay = __double2float_ru(fabs(vy)),
-        az = __double2float_ru(fabs(vz));
+  float ax = d2f_abs_ru(vx), ay = d2f_abs_ru(vy), az = d2f_abs_ru(vz);
   return __fadd_ru(__fadd_ru(__fmul_ru(ax, ax), __fmul_ru(ay, ay)), __fmul_ru(az, az));
 }
 
 // cell coordinate along one axis, binary32 (only the speed depends on it)
 __device__ __forceinline__ int cell_coord(const Grid& g, int k, double x) {
   if (g.nc[k] == 1) return 0;
-  float f = floorf((float)x * g.inv_wf[k]);
+  float f = floorf(d2f_rn(x) * g.inv_wf[k]);
   int c = (int)f;
   c = c < 0 ? 0 : c;
   c = c >= g.nc[k] ? g.nc[k] - 1 : c;

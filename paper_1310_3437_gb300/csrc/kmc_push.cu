@@ -32,6 +32,15 @@ __device__ __forceinline__ void block_max_to(uint32_t* dst, float v) {
   }
 }
 
+// Comparisons of finite doubles on the integer pipes (the binary64 pipe is the
+// scarce one on this part).  For a finite x and a positive finite bound y the order
+// of the values is the order of the bit patterns read as signed integers; negative
+// x (including -0.0) compare below every positive y.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ bool lt_zero(double x) {  // x < 0.0 (false for -0.0)
+  return (unsigned long long)dbits(x) > 0x8000000000000000ull;
+}
+
 // ---- k_push ---------------------------------------------------------------- //
 __global__ void __launch_bounds__(kTile) k_push(Batch B) {
   int k = find_sim(B.ptile, B.nsims, blockIdx.x);
@@ -51,11 +60,11 @@ __global__ void __launch_bounds__(kTile) k_push(Batch B) {
       double v = s.v[cur][a][p];
       if (q == kNone) x = dadd(x, dmul(v, dt));
       if (s.bc[a] == KMC_PERIODIC) {
-        double L = s.box[a];
-        if (x >= L) x = dsub(x, L);
-        if (x < 0.0) {
+        double L = s.box[a];  // > 0
+        if (dbits(x) >= dbits(L)) x = dsub(x, L);
+        if (lt_zero(x)) {
           x = dadd(x, L);
-          if (x == L) x = 0.0;
+          if (dbits(x) == dbits(L)) x = 0.0;
         }
       } else {
         double X, u;
@@ -67,12 +76,12 @@ __global__ void __launch_bounds__(kTile) k_push(Batch B) {
           X = s.box[a];
         }
         bool vchg = false;
-        if (x < 0.0) {
+        if (lt_zero(x)) {
           x = -x;
           v = -v;
           vchg = true;
         }
-        if (x > X) {
+        if (dbits(X) > 0 ? dbits(x) > dbits(X) : x > X) {
           x = dsub(dadd(X, X), x);
           v = dsub(-v, dadd(u, u));
           vchg = true;

@@ -838,6 +838,7 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_seg32(Batch B) {
                 const uint32_t len = hi_i - lo_i;
                 tests += len;
                 const uint32_t T = __reduce_max_sync(0xFFFFFFFFu, len);
+#pragma unroll 2
                 for (uint32_t t = 0; t < T; ++t) {
                   if (t < len) {
                     const uint32_t ti = lo_i + t - i0;

@@ -228,10 +228,10 @@ __global__ void __launch_bounds__(kTile) k_scatter(Batch B) {
     for (int a = 0; a < 3; ++a) {
       // offset from the cell's lower corner, subtracted in binary64, rounded once
       double corner = g.nc[a] == 1 ? 0.0 : dmul((double)c[a], g.w[a]);
-      o[a] = __double2float_rn(dsub(xs[a], corner));
+      o[a] = d2f_rn(dsub(xs[a], corner));
     }
-    s.mir_a[dst] = make_float4(o[0], o[1], o[2], __double2float_rn(vs[0]));
-    s.mir_b[dst] = make_float2(__double2float_rn(vs[1]), __double2float_rn(vs[2]));
+    s.mir_a[dst] = make_float4(o[0], o[1], o[2], d2f_rn(vs[0]));
+    s.mir_b[dst] = make_float2(d2f_rn(vs[1]), d2f_rn(vs[2]));
   }
 }
 

@@ -18,7 +18,8 @@ from . import (KMC_FP64, KMC_GUARDED_FP32, KMC_NONE, KMC_OBS_COUNTS, KMC_OBS_EDG
 
 
 def params_from_setup(setup, precision=KMC_FP64, stencil=1, cell_scale=1.0, step0=0,
-                      edge_cap=0, history_cap=0, profile_cap=0, search_kernel=0) -> kmc_params:
+                      edge_cap=0, history_cap=0, profile_cap=0, search_kernel=0,
+                      split_min_occ=0.0, flags=0) -> kmc_params:
     """kmc_params from any object with the fields n, box, bc, piston_x0, piston_u, d0,
     dt, seed, max_rounds, profile_bins, profile_every, profile_range."""
     p = kmc_params()
@@ -43,6 +44,8 @@ def params_from_setup(setup, precision=KMC_FP64, stencil=1, cell_scale=1.0, step
     p.history_cap = int(history_cap)
     p.profile_cap = int(profile_cap)
     p.search_kernel = int(search_kernel)
+    p.split_min_occ = float(split_min_occ)
+    p.flags = int(flags)
     return p
 
 

@@ -1,8 +1,9 @@
 """Autotuner for the knobs that change the work of a step but never its result.
 
-Knobs: the search kernel (one warp per cell, one thread per particle, or the
-per-step automatic switch), the stencil (27 cells of width h, or 125 cells of width
-h/2) and the cell-size multiplier (>= 1: larger cells hold more particles).  Every
+Knobs: the search kernel (one warp per cell, one warp per run of cells, one thread
+per particle, or the per-step automatic switch), the stencil (27 cells of width h, or
+125 cells of width h/2), the cell-size multiplier (>= 1: larger cells hold more
+particles) and how far the speed split may thin out the slow grid.  Every
 combination yields bit-identical trajectories (the tests check this), so the tuner
 only has to time them: it runs a few steps of each candidate from the same initial
 state, times them with CUDA events on the simulation's stream and keeps the
@@ -17,10 +18,12 @@ import os
 from .sim import Simulation, params_from_setup
 
 DEFAULT_CANDIDATES = [
-    # (search_kernel, stencil, cell_scale): 0 auto, 1 particle, 2 cell, 3 segment
-    (0, 1, 1.0), (2, 1, 1.0), (3, 1, 1.0), (1, 1, 1.0),
-    (0, 2, 1.0), (2, 2, 1.0), (3, 2, 1.0), (1, 2, 1.0),
-    (3, 2, 1.3), (2, 1, 1.3), (3, 1, 1.3),
+    # (search_kernel, stencil, cell_scale, split_min_occ): kernels 0 auto, 1 particle,
+    # 2 cell, 3 segment; split_min_occ = smallest mean slow-cell occupancy a speed split
+    # may leave (0: no floor, 1e9: no split)
+    (0, 1, 1.0, 0.0), (0, 1, 1.0, 2.0), (0, 1, 1.0, 4.0), (0, 1, 1.0, 8.0),
+    (0, 1, 1.0, 16.0), (0, 1, 1.0, 1e9), (2, 1, 1.0, 1e9), (2, 1, 1.0, 16.0),
+    (3, 1, 1.0, 0.0), (0, 2, 1.0, 0.0), (1, 1, 1.0, 0.0),
 ]
 
 
@@ -60,9 +63,9 @@ class Autotuner:
 
         st = torch.cuda.Stream() if stream is None else stream
         results = []
-        for kern, stencil, scale in self.candidates:
+        for kern, stencil, scale, occ in self.candidates:
             params = params_from_setup(setup, precision=precision, stencil=stencil,
-                                       cell_scale=scale, search_kernel=kern)
+                                       cell_scale=scale, search_kernel=kern, split_min_occ=occ)
             sim = Simulation(params, arrays, stream=st.cuda_stream)
             sim.step(self.warmup).sync()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -74,13 +77,14 @@ class Autotuner:
             sim.sync()
             ms = e0.elapsed_time(e1) / self.steps
             sim.close()
-            results.append((ms, kern, stencil, scale))
+            results.append((ms, kern, stencil, scale, occ))
         results.sort()
-        ms, kern, stencil, scale = results[0]
-        best = {"search_kernel": kern, "stencil": stencil, "cell_scale": scale, "ms_per_step": ms}
+        ms, kern, stencil, scale, occ = results[0]
+        best = {"search_kernel": kern, "stencil": stencil, "cell_scale": scale,
+                "split_min_occ": occ, "ms_per_step": ms}
         self.cache[key] = best
         self.trials[key] = [{"ms_per_step": r[0], "search_kernel": r[1], "stencil": r[2],
-                             "cell_scale": r[3]} for r in results]
+                             "cell_scale": r[3], "split_min_occ": r[4]} for r in results]
         if self.cache_path:
             with open(self.cache_path, "w") as f:
                 json.dump(self.cache, f, indent=1)
@@ -90,4 +94,5 @@ class Autotuner:
         best = self.choose(setup, arrays, precision, stream)
         return params_from_setup(setup, precision=precision, stencil=best["stencil"],
                                  cell_scale=best["cell_scale"],
-                                 search_kernel=best["search_kernel"], **kw)
+                                 search_kernel=best["search_kernel"],
+                                 split_min_occ=best["split_min_occ"], **kw)
