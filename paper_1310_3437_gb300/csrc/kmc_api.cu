@@ -132,6 +132,7 @@ size_t bytes_for(const Sizes& z) {
   b += 2 * ((size_t)z.cell_cap + 1) * sizeof(uint32_t);               // cell count / start
   b += n * sizeof(uint32_t) + (n + 1) * sizeof(uint32_t);             // deg, off
   b += 4 * n * sizeof(uint32_t);                                      // best, best_e, partner, medge
+  b += (n / 2 + 1) * sizeof(uint32_t);                                // pair list
   b += edge_bytes(z.edge_cap);
   b += (size_t)z.hist_cap * sizeof(kmc_step_counts);
   if (z.bins) b += (size_t)z.prof_cap * z.bins * kProfQ * sizeof(long long) + z.prof_cap * sizeof(uint64_t);
@@ -388,6 +389,7 @@ int recover_overflow(kmc_sim* s, Dyn& dy, cudaStream_t st) {
   dy.n_raw = 0;
   dy.n_edges = 0;
   for (int r = 0; r < 4; ++r) dy.round_pairs[r] = 0;
+  dy.n_pairs = 0;
   dy.pair_tests = 0;
   // the push of the failed step never ran: keep the bound of the previous step
   dy.vmax2_acc = 0;
@@ -529,6 +531,7 @@ int sim_create(const kmc_params* p, const double* x, const double* y, const doub
   if ((rc = dalloc(s, &h.best_e, n))) return fail(rc);
   if ((rc = dalloc(s, &h.partner, n))) return fail(rc);
   if ((rc = dalloc(s, &h.medge, n))) return fail(rc);
+  if ((rc = dalloc(s, &h.pairs, n / 2 + 1))) return fail(rc);
   if ((rc = alloc_edges(s, zs.edge_cap))) return fail(rc);
   if ((rc = dalloc(s, &h.hist, zs.hist_cap))) return fail(rc);
   if (zs.bins) {

@@ -30,7 +30,7 @@ __device__ __forceinline__ float f_up(double x) { return __double2float_ru(x); }
 struct CellPlan {
   int nc[3];
   double m;
-  uint32_t col_shift, y_major, nkeys;
+  uint32_t col_shift, col_tz, nkeys;
   bool ok;
 };
 
@@ -41,7 +41,7 @@ __device__ inline CellPlan plan_cells(const double ext[3], double h, int K, uint
   p.ok = false;
   p.m = 0.0;
   p.col_shift = 0;
-  p.y_major = 1;
+  p.col_tz = 1;
   p.nkeys = 1;
   p.nc[0] = p.nc[1] = p.nc[2] = 1;
   for (int attempt = 0; attempt < 64; ++attempt) {
@@ -60,17 +60,17 @@ __device__ inline CellPlan plan_cells(const double ext[3], double h, int K, uint
       if (c < 2 * K + 1) c = 1;
       p.nc[a] = c;
     }
-    // key space of the column-Morton order
-    uint32_t ny = (uint32_t)p.nc[1], nz = (uint32_t)p.nc[2];
-    uint32_t small = ny < nz ? ny : nz, large = ny < nz ? nz : ny;
-    uint32_t sh = 0;
-    while ((1u << sh) < small) ++sh;
-    uint64_t P = 1ull << sh;
-    uint64_t cols = ((large + P - 1) / P) * P * P;
-    uint64_t nkeys = cols * (uint64_t)p.nc[0];
-    if (nkeys <= max_keys && sh <= 15) {
-      p.col_shift = sh;
-      p.y_major = ny >= nz ? 1u : 0u;
+    // key space of the tiled column order: T x T Morton tiles, T = 2^t <= 8
+    const uint32_t ny = (uint32_t)p.nc[1], nz = (uint32_t)p.nc[2];
+    const uint32_t small = ny < nz ? ny : nz;
+    uint32_t t = 0;
+    while (t < 3 && (1u << (t + 1)) <= small) ++t;
+    const uint64_t T = 1ull << t;
+    const uint64_t ty = (ny + T - 1) / T, tz = (nz + T - 1) / T;
+    const uint64_t nkeys = ty * tz * T * T * (uint64_t)p.nc[0];
+    if (nkeys <= max_keys) {
+      p.col_shift = t;
+      p.col_tz = (uint32_t)tz;
       p.nkeys = (uint32_t)nkeys;
       p.ok = true;
       return p;
@@ -179,7 +179,7 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
   const int* nc = p.nc;
   const double m = p.m;
   g.col_shift = p.col_shift;
-  g.y_major = p.y_major;
+  g.col_tz = p.col_tz;
   g.nkeys = p.nkeys;
   g.K = K;
   int cfast[3] = {0, 0, 0};

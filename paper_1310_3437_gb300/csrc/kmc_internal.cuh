@@ -36,8 +36,8 @@ enum : uint32_t {
   ST_CELL_OVERFLOW = 1u << 2,  // grid key space above capacity (cannot happen: coarsened)
 };
 
-// Search grid of the current step.  Cells are keyed column-major along x inside
-// a Z-order (Morton) walk over the (y, z) columns: key = col(cy, cz) * nc[0] + cx.
+// Search grid of the current step.  Cells are keyed column-major along x inside a
+// tiled Z-order (Morton) walk over the (y, z) columns: key = col(cy, cz) * nc[0] + cx.
 struct Grid {
   int32_t nc[3];      // cells per axis; 1 means the axis is one cell (no stencil on it)
   int32_t K;          // stencil radius in cells
@@ -47,8 +47,8 @@ struct Grid {
   float s1sq;         // binary32 split threshold on the upper bound of |v|^2
   int32_t cfast[3];   // fast particles search cfast cells on each side (split axes)
   uint32_t nkeys;     // size of the key space (padded Morton columns x nc[0])
-  uint32_t col_shift; // log2 of the Morton block edge P (P = next pow2 of the smaller axis)
-  uint32_t y_major;   // 1 if nc[1] >= nc[2] (y carries the high, non-interleaved bits)
+  uint32_t col_shift; // log2 of the Morton tile edge T (T <= 8)
+  uint32_t col_tz;    // tiles along z
   uint32_t pad0;
   double w[3];        // cell widths
   float wf[3];        // cell widths (binary32)
@@ -74,6 +74,7 @@ struct Dyn {
   uint32_t n_raw;       // pairs emitted by the search (may exceed edge_cap)
   uint32_t n_edges;     // candidate pairs after the exact test
   uint32_t round_pairs[4];
+  uint32_t n_pairs;     // entries of the pair list
   unsigned long long pair_tests;
   uint32_t last_raw;    // n_raw of the last completed step (its pair buffer is kept)
   uint32_t have_counts; // split_cnt holds counts of the current state
@@ -122,6 +123,7 @@ struct SimDev {
   uint32_t* best_e;
   uint32_t* partner;    // partner (sorted index) this step, kNone if none
   uint32_t* medge;      // pair index of the collision
+  uint32_t* pairs;      // colliding pairs of the step, by their smaller-id member
   kmc_step_counts* hist;
   long long* prof_acc;  // prof_cap x bins x kProfQ fixed-point counters
   uint64_t* prof_step;
@@ -176,24 +178,24 @@ __device__ __forceinline__ uint32_t compact16(uint32_t x) {
   x = (x | (x >> 8)) & 0x0000FFFFu;
   return x;
 }
+// Column order: the (y, z) plane is cut into T x T tiles (T = 2^col_shift <= 8)
+// walked row by row; inside a tile the columns follow the Z-order (Morton) curve.
+// Padding is below T per axis.
 __device__ __forceinline__ uint32_t col_code(const Grid& g, uint32_t cy, uint32_t cz) {
-  uint32_t a = g.y_major ? cy : cz;  // longer transverse axis
-  uint32_t b = g.y_major ? cz : cy;  // shorter one, < P
-  uint32_t sh = g.col_shift;
-  uint32_t mask = (1u << sh) - 1u;
-  return ((a >> sh) << (2 * sh)) | dilate16(a & mask) | (dilate16(b) << 1);
+  const uint32_t t = g.col_shift, mask = (1u << t) - 1u;
+  const uint32_t tile = (cy >> t) * g.col_tz + (cz >> t);
+  return (tile << (2 * t)) | dilate16(cy & mask) | (dilate16(cz & mask) << 1);
 }
 __device__ __forceinline__ void key_decode(const Grid& g, uint32_t key, int& cx, int& cy, int& cz) {
-  uint32_t nx = (uint32_t)g.nc[0];
-  uint32_t col = key / nx;
+  const uint32_t nx = (uint32_t)g.nc[0];
+  const uint32_t col = key / nx;
   cx = (int)(key - col * nx);
-  uint32_t sh = g.col_shift;
-  uint32_t hi = col >> (2 * sh);
-  uint32_t lo = col & ((1u << (2 * sh)) - 1u);
-  uint32_t a = (hi << sh) | compact16(lo);
-  uint32_t b = compact16(lo >> 1);
-  cy = (int)(g.y_major ? a : b);
-  cz = (int)(g.y_major ? b : a);
+  const uint32_t t = g.col_shift;
+  const uint32_t tile = col >> (2 * t);
+  const uint32_t in = col & ((1u << (2 * t)) - 1u);
+  const uint32_t by = tile / g.col_tz, bz = tile - by * g.col_tz;
+  cy = (int)((by << t) | compact16(in));
+  cz = (int)((bz << t) | compact16(in >> 1));
 }
 
 // binary64 -> binary32 conversions on the integer pipes (on this part the hardware

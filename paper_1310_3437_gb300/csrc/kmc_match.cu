@@ -197,8 +197,18 @@ __global__ void __launch_bounds__(kEdgeBlock) k_mutual(Batch B, int round) {
           }
         }
       }
+      // warp-aggregated append to the pair list (one atomic per warp)
       unsigned m = __ballot_sync(0xFFFFFFFFu, pair);
-      if ((threadIdx.x & 31) == 0 && m) atomicAdd(&s.d.round_pairs[round], (uint32_t)__popc(m));
+      if (m) {
+        const unsigned lane = threadIdx.x & 31u;
+        uint32_t base = 0;
+        if (lane == 0) {
+          base = atomicAdd(&s.d.n_pairs, (uint32_t)__popc(m));
+          atomicAdd(&s.d.round_pairs[round], (uint32_t)__popc(m));
+        }
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (pair) s.pairs[base + __popc(m & ((1u << lane) - 1u))] = s.adj_owner[a];
+      }
     }
   }
 }
@@ -212,14 +222,12 @@ __global__ void __launch_bounds__(kEdgeBlock) k_collide(Batch B) {
     SimDev& s = *B.sims[k];
     if (!sim_active(s)) continue;
     const int cur = s.d.parity ^ 1;
-    const uint32_t total = s.off[s.n];
+    const uint32_t total = s.d.n_pairs;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
-      uint32_t i = s.adj_owner[q];
-      if (q > 0 && s.adj_owner[q - 1] == i) continue;
-      uint32_t j = s.partner[i];
-      if (j == kNone) continue;
-      uint32_t ida = s.id[cur][i], idb = s.id[cur][j];
-      if (ida > idb) continue;  // the pair is handled by its smaller id
+      // the pair list holds each colliding pair once, by its smaller-id member
+      const uint32_t i = s.pairs[q];
+      const uint32_t j = s.partner[i];
+      const uint32_t ida = s.id[cur][i];
       double t = s.e_t[s.medge[i]];
       double nv[3];
       if (!sphere_point(s.seed, s.d.step, ida, nv)) {

@@ -168,6 +168,7 @@ __device__ void reset_step_counters(SimDev& s) {
   s.d.n_raw = 0;
   s.d.n_edges = 0;
   for (int r = 0; r < 4; ++r) s.d.round_pairs[r] = 0;
+  s.d.n_pairs = 0;
   s.d.pair_tests = 0;
   s.d.vmax2_acc = 0;
 }

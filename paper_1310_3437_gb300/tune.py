@@ -22,8 +22,9 @@ DEFAULT_CANDIDATES = [
     # 2 cell, 3 segment; split_min_occ = smallest mean slow-cell occupancy a speed split
     # may leave (0: no floor, 1e9: no split)
     (0, 1, 1.0, 0.0), (0, 1, 1.0, 2.0), (0, 1, 1.0, 4.0), (0, 1, 1.0, 8.0),
-    (0, 1, 1.0, 16.0), (0, 1, 1.0, 1e9), (2, 1, 1.0, 1e9), (2, 1, 1.0, 16.0),
-    (3, 1, 1.0, 0.0), (0, 2, 1.0, 0.0), (1, 1, 1.0, 0.0),
+    (0, 1, 1.0, 1e9), (2, 1, 1.0, 1e9), (2, 1, 1.0, 16.0), (2, 1, 1.0, 8.0),
+    (2, 1, 1.0, 5.0), (2, 1, 1.0, 3.0), (3, 1, 1.0, 0.0), (0, 2, 1.0, 0.0),
+    (1, 1, 1.0, 0.0),
 ]
 
 
