@@ -231,7 +231,8 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
 
   // ---- binary32 pre-tests ------------------------------------------------------
   // Error of the binary32 separation against the binary64 one, per component:
-  //   split axis: offsets from the cell corner (binary64 difference rounded once)
+  //   split axis: offsets from the cell corner (x - c w, one binary64 fused
+  //     multiply-add, rounded once to binary32)
   //     plus the stencil shift of up to Ke = max(K, fast reach) cells, or for x in
   //     the segment kernel coordinates measured from the segment start:
   //     u32 w (4 seg + 4 Ke + 4) + 8 u64 L;

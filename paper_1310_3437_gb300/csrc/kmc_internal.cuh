@@ -213,6 +213,14 @@ __device__ __forceinline__ float d2f_rn(double x) {
   const uint32_t bits = (uint32_t)((b >> 63) << 31) | (((uint32_t)fe << 23) + top + up);
   return __uint_as_float(bits);
 }
+// exact binary64 value of an unsigned 32-bit integer, built with integer operations
+// (the conversion instruction runs on the binary64 pipe)
+__device__ __forceinline__ double u2d_exact(uint32_t c) {
+  if (c == 0u) return 0.0;
+  const int e = 31 - __clz(c);
+  const unsigned long long mant = ((unsigned long long)c << (52 - e)) & 0xFFFFFFFFFFFFFull;
+  return __longlong_as_double((long long)(((unsigned long long)(1023 + e) << 52) | mant));
+}
 // |x| rounded up to binary32
 __device__ __forceinline__ float d2f_abs_ru(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;

@@ -43,15 +43,22 @@ __device__ __forceinline__ bool lt_zero(double x) {  // x < 0.0 (false for -0.0)
 
 // ---- k_push ---------------------------------------------------------------- //
 __global__ void __launch_bounds__(kTile) k_push(Batch B) {
+  __shared__ double sX;                       // piston position at the end of the step
+  __shared__ uint32_t scnt[kSplitTrials];     // particles above each trial threshold
   int k = find_sim(B.ptile, B.nsims, blockIdx.x);
   SimDev& s = *B.sims[k];
   if (!sim_active(s)) return;
   const int cur = s.d.parity ^ 1;
+  const uint64_t step = s.d.step;
+  const double dt = s.dt;
+  if (threadIdx.x == 0)
+    sX = s.bc[0] == KMC_PERIODIC ? 0.0
+                                 : dsub(s.piston_x0, dmul(s.piston_u, dmul((double)(step + 1), dt)));
+  if (threadIdx.x < kSplitTrials) scnt[threadIdx.x] = 0;
+  __syncthreads();
   uint32_t p = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
   float vm = 0.0f;
   if (p < s.n) {
-    const uint64_t step = s.d.step;
-    const double dt = s.dt;
     uint32_t q = s.partner[p];
     double vv[3];
 #pragma unroll
@@ -70,7 +77,7 @@ __global__ void __launch_bounds__(kTile) k_push(Batch B) {
         double X, u;
         if (a == 0) {
           u = s.piston_u;
-          X = dsub(s.piston_x0, dmul(u, dmul((double)(step + 1), dt)));
+          X = sX;
         } else {
           u = 0.0;
           X = s.box[a];
@@ -95,15 +102,18 @@ __global__ void __launch_bounds__(kTile) k_push(Batch B) {
     vm = vmag2_up(vv[0], vv[1], vv[2]);
   }
   if (s.split_ok) {
-    // particles above each trial split threshold (warp ballots, one atomic per warp)
+    // particles above each trial split threshold: warp ballots, shared counters, one
+    // global atomic per block and trial
     const bool valid = p < s.n;
 #pragma unroll
     for (int t = 1; t < kSplitTrials; ++t) {
       unsigned m = __ballot_sync(0xFFFFFFFFu, valid && vm > s.d.split_thr[t]);
-      if ((threadIdx.x & 31) == 0 && m) atomicAdd(&s.d.split_cnt[t], (uint32_t)__popc(m));
+      if ((threadIdx.x & 31) == 0 && m) atomicAdd(&scnt[t], (uint32_t)__popc(m));
     }
   }
-  block_max_to(&s.d.vmax2_acc, vm);
+  block_max_to(&s.d.vmax2_acc, vm);  // its block barrier also orders the shared counters
+  if (s.split_ok && threadIdx.x > 0 && threadIdx.x < kSplitTrials && scnt[threadIdx.x])
+    atomicAdd(&s.d.split_cnt[threadIdx.x], scnt[threadIdx.x]);
 }
 
 // ---- fixed-point digits for the profile sums ------------------------------- //

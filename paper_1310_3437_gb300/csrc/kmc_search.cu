@@ -696,7 +696,13 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_cell32(Batch B) {
 template <int K>
 __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_seg32(Batch B) {
   constexpr int ICAP = 64;
-  __shared__ __align__(16) float si[kCellWarps][6 * ICAP];
+  // staged segment particles (x from the segment start): AoS, 4 + 2 floats
+  __shared__ float4 sia[kCellWarps][ICAP];
+  __shared__ float2 sib[kCellWarps][ICAP];
+  // the chunk's partners and their work: data, first i, range length, group offset
+  __shared__ float sj[kCellWarps][6][32];
+  __shared__ uint32_t sjidx[kCellWarps][32], slo[kCellWarps][32], slen[kCellWarps][32],
+      soff[kCellWarps][32];
   __shared__ uint2 wbuf[kCellWarps][kWarpBuf];
   __shared__ uint32_t wcount[kCellWarps];
   __shared__ Guard32 sq;
@@ -728,13 +734,8 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_seg32(Batch B) {
     const float c0 = G.s_c0, c1 = G.s_c1;
     const float4* __restrict__ MA = s.mir_a;
     const float2* __restrict__ MB = s.mir_b;
-    float* my = si[warp];
-    const float* sxx = my;
-    const float* syy = my + ICAP;
-    const float* szz = my + 2 * ICAP;
-    const float* suu = my + 3 * ICAP;
-    const float* svv = my + 4 * ICAP;
-    const float* sww = my + 5 * ICAP;
+    float4* ia = sia[warp];
+    float2* ib = sib[warp];
     uint2* buf = wbuf[warp];
     uint32_t* cnt = &wcount[warp];
     unsigned long long tests = 0;
@@ -761,9 +762,8 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_seg32(Batch B) {
           }
           const float4 a = MA[i];
           const float2 b = MB[i];
-          my[t] = fmaf((float)(lo - cx0), wx, a.x);
-          my[ICAP + t] = a.y; my[2 * ICAP + t] = a.z;
-          my[3 * ICAP + t] = a.w; my[4 * ICAP + t] = b.x; my[5 * ICAP + t] = b.y;
+          ia[t] = make_float4(fmaf((float)(lo - cx0), wx, a.x), a.y, a.z, a.w);
+          ib[t] = b;
         }
         __syncwarp();
         for (int dz = 0; dz <= Kz; ++dz) {
@@ -806,7 +806,6 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_seg32(Batch B) {
               for (uint32_t cb = jbeg; cb < jend; cb += 32) {
                 const uint32_t j = cb + lane;
                 uint32_t lo_i = 0, hi_i = 0;
-                float jx = 0.f, jy = 0.f, jz = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
                 if (j < jend) {
                   // cell of j in the piece
                   int lo = 0, hi = m - 1;
@@ -817,10 +816,12 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_seg32(Batch B) {
                   const int uj = ua_piece + lo;  // unwrapped cell of j
                   const float4 a = __ldg(MA + j);
                   const float2 b = __ldg(MB + j);
-                  jx = fmaf((float)(uj - cx0), wx, a.x);
-                  jy = a.y + shy;
-                  jz = a.z + shz;
-                  gx = a.w; gy = b.x; gz = b.y;
+                  sj[warp][0][lane] = fmaf((float)(uj - cx0), wx, a.x);
+                  sj[warp][1][lane] = a.y + shy;
+                  sj[warp][2][lane] = a.z + shz;
+                  sj[warp][3][lane] = a.w;
+                  sj[warp][4][lane] = b.x;
+                  sj[warp][5][lane] = b.y;
                   // i's of the segment inside j's stencil: cells [uj-K, uj+K] (other
                   // columns) or [uj-K, uj] with i < j in j's own cell (own column)
                   int ca = uj - Kx > cx0 ? uj - Kx : cx0;
@@ -837,17 +838,50 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_seg32(Batch B) {
                 }
                 const uint32_t len = hi_i - lo_i;
                 tests += len;
-                const uint32_t T = __reduce_max_sync(0xFFFFFFFFu, len);
-#pragma unroll 2
-                for (uint32_t t = 0; t < T; ++t) {
-                  if (t < len) {
-                    const uint32_t ti = lo_i + t - i0;
-                    const float rx = jx - sxx[ti], ry = jy - syy[ti], rz = jz - szz[ti];
-                    const float vx = gx - suu[ti], vy = gy - svv[ti], vz = gz - sww[ti];
-                    const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-                    const float Bv = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
-                    if (R <= fmaf(c1, Bv, c0) && full_test32(sq, rx, ry, rz, vx, vy, vz, Bv))
-                      emit_lane(buf, cnt, s, lo_i + t, j);
+                // balanced work: the ranges are cut into groups of 4 pairs and the
+                // groups are dealt out to all lanes
+                const uint32_t g = (len + 3u) >> 2;
+                uint32_t incl = g;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                  const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                  if (lane >= (uint32_t)o) incl += y;
+                }
+                const uint32_t Gtot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+                sjidx[warp][lane] = j;
+                slo[warp][lane] = lo_i - i0;
+                slen[warp][lane] = len;
+                soff[warp][lane] = incl - g;
+                __syncwarp();
+                for (uint32_t kb = 0; kb < Gtot; kb += 32) {
+                  const uint32_t kq = kb + lane;
+                  if (kq < Gtot) {
+                    // owner: the last lane whose first group is at or before kq
+                    int lo = 0, hi = 31;
+                    while (lo < hi) {
+                      const int mid = (lo + hi + 1) >> 1;
+                      if (soff[warp][mid] <= kq) lo = mid; else hi = mid - 1;
+                    }
+                    const uint32_t grp = kq - soff[warp][lo];
+                    const uint32_t tfirst = slo[warp][lo] + 4u * grp;
+                    const uint32_t left = slen[warp][lo] - 4u * grp;
+                    const uint32_t jj = sjidx[warp][lo];
+                    const float jx = sj[warp][0][lo], jy = sj[warp][1][lo], jz = sj[warp][2][lo];
+                    const float gx = sj[warp][3][lo], gy = sj[warp][4][lo], gz = sj[warp][5][lo];
+#pragma unroll
+                    for (uint32_t uu = 0; uu < 4; ++uu) {
+                      if (uu < left) {
+                        const uint32_t ti = tfirst + uu;
+                        const float4 A = ia[ti];
+                        const float2 Bq = ib[ti];
+                        const float rx = jx - A.x, ry = jy - A.y, rz = jz - A.z;
+                        const float vx = gx - A.w, vy = gy - Bq.x, vz = gz - Bq.y;
+                        const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+                        const float Bv = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
+                        if (R <= fmaf(c1, Bv, c0) && full_test32(sq, rx, ry, rz, vx, vy, vz, Bv))
+                          emit_lane(buf, cnt, s, i0 + ti, jj);
+                      }
+                    }
                   }
                 }
                 __syncwarp();
@@ -865,47 +899,66 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_seg32(Batch B) {
 }
 
 // --------------------------------------------------------------------------- //
-// Fast particles of the speed split: one thread per fast particle p, searching
-// cfast cells on each side over both populations -- every slow particle, and the
-// fast particles j > p (each fast-fast pair once).  The pair tests are those of the
+// Fast particles of the speed split: one warp per fast particle p, searching cfast
+// cells on each side over both populations -- every slow particle, and the fast
+// particles j > p (each fast-fast pair once).  The lanes first take one stencil cell
+// each and read its two candidate ranges; a warp prefix sum over the range lengths
+// then deals the candidates of 32 cells out to the lanes, so every lane tests a pair
+// in every iteration whatever the cell occupancies.  The pair tests are those of the
 // thread-per-particle search.
 template <int PREC>
-__global__ void __launch_bounds__(kTile) k_search_fast(Batch B) {
-  __shared__ uint2 sbuf[kSearchBuf];
-  __shared__ uint32_t scnt, sbase;
-  __shared__ unsigned long long stests;
-  int k = find_sim(B.ptile, B.nsims, blockIdx.x);
+__global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
+  __shared__ uint2 wbuf[kCellWarps][kWarpBuf];
+  __shared__ uint32_t wcount[kCellWarps];
+  // per stencil cell of the current batch: candidate offset, slow begin/length, fast begin,
+  // cell offset (dx, dy, dz) packed in bytes
+  __shared__ uint32_t soff[kCellWarps][32], sb0[kCellWarps][32], sn0[kCellWarps][32],
+      sb1[kCellWarps][32], sd[kCellWarps][32];
+  const int k = find_sim(B.ptile, B.nsims, blockIdx.x);
   SimDev& s = *B.sims[k];
   if (!sim_active(s) || !s.d.grid.split) return;
-  const Grid g = s.d.grid;
+  const Grid& g = s.d.grid;
   const uint32_t* __restrict__ cs = s.cell_start;
   const uint32_t nk = g.nkeys;
-  const uint32_t nslow = __ldg(cs + nk);
-  const uint32_t p = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
-  // blocks entirely below the fast population have nothing to do
-  if ((blockIdx.x - B.ptile[k]) * kTile + kTile <= nslow) return;
-  if (threadIdx.x == 0) { scnt = 0; stests = 0; }
-  __syncthreads();
   const uint32_t n = s.n;
+  const uint32_t nslow = __ldg(cs + nk);
+  const uint32_t nfast = n - nslow;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t blk = blockIdx.x - B.ptile[k];
+  // blocks past the fast population have nothing to do (no block-wide barrier below)
+  if (blk * kCellWarps >= nfast) return;
+  const uint32_t wstride = (B.ptile[k + 1] - B.ptile[k]) * kCellWarps;
+  uint2* buf = wbuf[warp];
+  uint32_t* cnt = &wcount[warp];
+  if (lane == 0) *cnt = 0;
+  __syncwarp();
+
   const int cur = s.d.parity ^ 1;
-  const uint32_t edge_cap = s.edge_cap;
-  uint2* __restrict__ edges = s.edge;
   const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
   const int Cx = g.cfast[0], Cy = g.cfast[1], Cz = g.cfast[2];
+  const int Wx = 2 * Cx + 1, Wxy = Wx * (2 * Cy + 1);
+  const int ncell = Wxy * (2 * Cz + 1);
   const bool px = s.bc[0] == KMC_PERIODIC, py = s.bc[1] == KMC_PERIODIC,
              pz = s.bc[2] == KMC_PERIODIC;
+  const double* __restrict__ X0 = s.x[cur][0];
+  const double* __restrict__ X1 = s.x[cur][1];
+  const double* __restrict__ X2 = s.x[cur][2];
+  const double* __restrict__ V0 = s.v[cur][0];
+  const double* __restrict__ V1 = s.v[cur][1];
+  const double* __restrict__ V2 = s.v[cur][2];
+  const float4* __restrict__ MA = s.mir_a;
+  const float2* __restrict__ MB = s.mir_b;
+  const double L0 = s.box[0], L1 = s.box[1], L2 = s.box[2];
+  Guard32 q;
+  q.c0 = g.s_c0; q.c1 = g.s_c1; q.ag = g.a_g; q.tg = g.t_g; q.dtf = g.dtf;
+  q.d0up = g.d0up; q.brel = g.b_rel; q.babs = g.b_abs; q.we = g.w_e; q.wrel = g.w_rel;
+  const float wf0 = g.wf[0], wf1 = g.wf[1], wf2 = g.wf[2];
   unsigned long long tests = 0;
-  if (p >= nslow && p < n) {
+
+  for (uint32_t f = blk * kCellWarps + warp; f < nfast; f += wstride) {
+    const uint32_t p = nslow + f;
     int cx, cy, cz;
     key_decode(g, s.skey[p] - nk, cx, cy, cz);
-    const double* __restrict__ X0 = s.x[cur][0];
-    const double* __restrict__ X1 = s.x[cur][1];
-    const double* __restrict__ X2 = s.x[cur][2];
-    const double* __restrict__ V0 = s.v[cur][0];
-    const double* __restrict__ V1 = s.v[cur][1];
-    const double* __restrict__ V2 = s.v[cur][2];
-    const float4* __restrict__ MA = s.mir_a;
-    const float2* __restrict__ MB = s.mir_b;
     double xo[3] = {0, 0, 0}, vo[3] = {0, 0, 0};
     Own32 o32 = {0, 0, 0, 0, 0, 0};
     if (PREC == KMC_FP64) {
@@ -916,96 +969,98 @@ __global__ void __launch_bounds__(kTile) k_search_fast(Batch B) {
       const float2 b = MB[p];
       o32 = {a.x, a.y, a.z, a.w, b.x, b.y};
     }
-    const double L0 = s.box[0], L1 = s.box[1], L2 = s.box[2];
-    for (int dz = -Cz; dz <= Cz; ++dz) {
-      int qz = cz + dz;
-      if (qz < 0 || qz >= nz) {
-        if (!pz) continue;
-        qz = qz < 0 ? qz + nz : qz - nz;
-      }
-      for (int dy = -Cy; dy <= Cy; ++dy) {
-        int qy = cy + dy;
-        if (qy < 0 || qy >= ny) {
-          if (!py) continue;
-          qy = qy < 0 ? qy + ny : qy - ny;
+    for (int c0 = 0; c0 < ncell; c0 += 32) {
+      // this lane's stencil cell and its two candidate ranges
+      const int c = c0 + (int)lane;
+      uint32_t b0 = 0, n0 = 0, b1 = 0, n1 = 0, dpack = 0;
+      if (c < ncell) {
+        const int dz = c / Wxy - Cz;
+        const int rem = c - (dz + Cz) * Wxy;
+        const int dy = rem / Wx - Cy;
+        const int dx = rem - (dy + Cy) * Wx - Cx;
+        int qx = cx + dx, qy = cy + dy, qz = cz + dz;
+        bool ok = true;
+        if (qx < 0 || qx >= nx) { ok = ok && px; qx = qx < 0 ? qx + nx : qx - nx; }
+        if (qy < 0 || qy >= ny) { ok = ok && py; qy = qy < 0 ? qy + ny : qy - ny; }
+        if (qz < 0 || qz >= nz) { ok = ok && pz; qz = qz < 0 ? qz + nz : qz - nz; }
+        if (ok) {
+          const uint32_t key = col_code(g, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx + (uint32_t)qx;
+          b0 = __ldg(cs + key);
+          n0 = __ldg(cs + key + 1) - b0;
+          b1 = __ldg(cs + nk + key);
+          const uint32_t e1 = __ldg(cs + nk + key + 1);
+          if (b1 <= p) b1 = p + 1;
+          n1 = e1 > b1 ? e1 - b1 : 0u;
         }
-        const uint32_t colbase = col_code(g, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx;
-        for (int dx = -Cx; dx <= Cx; ++dx) {
-          int qx = cx + dx;
-          if (qx < 0 || qx >= nx) {
-            if (!px) continue;
-            qx = qx < 0 ? qx + nx : qx - nx;
-          }
-          const uint32_t key = colbase + (uint32_t)qx;
-          const float sx = o32.ox - (float)dx * g.wf[0];
-          const float sy = o32.oy - (float)dy * g.wf[1];
-          const float sz = o32.oz - (float)dz * g.wf[2];
-          // slow particles of the cell, then its fast particles above p
-          for (int pop = 0; pop < 2; ++pop) {
-            uint32_t beg = __ldg(cs + pop * nk + key), end = __ldg(cs + pop * nk + key + 1);
-            if (pop == 1 && beg <= p) beg = p + 1;
-            if (beg >= end) continue;
-            tests += end - beg;
-            for (uint32_t j = beg; j < end; ++j) {
-              bool emit;
-              if (PREC == KMC_FP64) {
-                double r0 = dsub(__ldg(X0 + j), xo[0]);
-                double r1 = dsub(__ldg(X1 + j), xo[1]);
-                double r2 = dsub(__ldg(X2 + j), xo[2]);
-                if (px) { if (r0 > 0.5 * L0) r0 = dsub(r0, L0); else if (r0 < -0.5 * L0) r0 = dadd(r0, L0); }
-                if (py) { if (r1 > 0.5 * L1) r1 = dsub(r1, L1); else if (r1 < -0.5 * L1) r1 = dadd(r1, L1); }
-                if (pz) { if (r2 > 0.5 * L2) r2 = dsub(r2, L2); else if (r2 < -0.5 * L2) r2 = dadd(r2, L2); }
-                double g0 = dsub(__ldg(V0 + j), vo[0]);
-                double g1 = dsub(__ldg(V1 + j), vo[1]);
-                double g2 = dsub(__ldg(V2 + j), vo[2]);
-                double R = dadd(dadd(dmul(r0, r0), dmul(r1, r1)), dmul(r2, r2));
-                double Bv = dadd(dadd(dmul(g0, g0), dmul(g1, g1)), dmul(g2, g2));
-                emit = !(Bv >= 0x1p-900 && R > dadd(g.c0, dmul(g.c1, Bv)));
-              } else {
-                const float4 a = __ldg(MA + j);
-                const float2 b = __ldg(MB + j);
-                const float rx = a.x - sx, ry = a.y - sy, rz = a.z - sz;
-                const float gx = a.w - o32.vx, gy = b.x - o32.vy, gz = b.y - o32.vz;
-                const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-                const float Bv = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
-                emit = false;
-                if (R <= fmaf(g.s_c1, Bv, g.s_c0)) {
-                  Guard32 q;
-                  q.c0 = g.s_c0; q.c1 = g.s_c1; q.ag = g.a_g; q.tg = g.t_g; q.dtf = g.dtf;
-                  q.d0up = g.d0up; q.brel = g.b_rel; q.babs = g.b_abs; q.we = g.w_e; q.wrel = g.w_rel;
-                  emit = full_test32(q, rx, ry, rz, gx, gy, gz, Bv);
-                }
-              }
-              if (emit) {
-                uint32_t pos = atomicAdd(&scnt, 1u);
-                if (pos < (uint32_t)kSearchBuf) {
-                  sbuf[pos] = make_uint2(p, j);
-                } else {
-                  uint32_t gpos = atomicAdd(&s.d.n_raw, 1u);
-                  if (gpos < edge_cap) edges[gpos] = make_uint2(p, j);
-                  else atomicOr(&s.d.status, ST_EDGE_OVERFLOW);
-                }
-              }
-            }
-          }
-        }
+        dpack = (uint32_t)(dx & 0xFF) | ((uint32_t)(dy & 0xFF) << 8) | ((uint32_t)(dz & 0xFF) << 16);
       }
+      const uint32_t tot = n0 + n1;
+      uint32_t incl = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+      }
+      const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      tests += tot;
+      soff[warp][lane] = incl - tot;
+      sb0[warp][lane] = b0;
+      sn0[warp][lane] = n0;
+      sb1[warp][lane] = b1;
+      sd[warp][lane] = dpack;
+      __syncwarp();
+      for (uint32_t kb = 0; kb < total; kb += 32) {
+        const uint32_t qi = kb + lane;
+        if (qi < total) {
+          // owner: the last cell whose first candidate is at or before qi
+          int lo = 0, hi = 31;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (soff[warp][mid] <= qi) lo = mid; else hi = mid - 1;
+          }
+          const uint32_t o = qi - soff[warp][lo];
+          const uint32_t m0 = sn0[warp][lo];
+          const uint32_t j = o < m0 ? sb0[warp][lo] + o : sb1[warp][lo] + (o - m0);
+          bool emit;
+          if (PREC == KMC_FP64) {
+            double r0 = dsub(__ldg(X0 + j), xo[0]);
+            double r1 = dsub(__ldg(X1 + j), xo[1]);
+            double r2 = dsub(__ldg(X2 + j), xo[2]);
+            if (px) { if (r0 > 0.5 * L0) r0 = dsub(r0, L0); else if (r0 < -0.5 * L0) r0 = dadd(r0, L0); }
+            if (py) { if (r1 > 0.5 * L1) r1 = dsub(r1, L1); else if (r1 < -0.5 * L1) r1 = dadd(r1, L1); }
+            if (pz) { if (r2 > 0.5 * L2) r2 = dsub(r2, L2); else if (r2 < -0.5 * L2) r2 = dadd(r2, L2); }
+            const double g0 = dsub(__ldg(V0 + j), vo[0]);
+            const double g1 = dsub(__ldg(V1 + j), vo[1]);
+            const double g2 = dsub(__ldg(V2 + j), vo[2]);
+            const double R = dadd(dadd(dmul(r0, r0), dmul(r1, r1)), dmul(r2, r2));
+            const double Bv = dadd(dadd(dmul(g0, g0), dmul(g1, g1)), dmul(g2, g2));
+            emit = !(Bv >= 0x1p-900 && R > dadd(g.c0, dmul(g.c1, Bv)));
+          } else {
+            const uint32_t d = sd[warp][lo];
+            const int dx = (int)(int8_t)(d & 0xFF), dy = (int)(int8_t)((d >> 8) & 0xFF),
+                      dz = (int)(int8_t)((d >> 16) & 0xFF);
+            const float sx = o32.ox - (float)dx * wf0;
+            const float sy = o32.oy - (float)dy * wf1;
+            const float sz = o32.oz - (float)dz * wf2;
+            const float4 a = __ldg(MA + j);
+            const float2 b = __ldg(MB + j);
+            const float rx = a.x - sx, ry = a.y - sy, rz = a.z - sz;
+            const float gx = a.w - o32.vx, gy = b.x - o32.vy, gz = b.y - o32.vz;
+            const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+            const float Bv = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
+            emit = R <= fmaf(q.c1, Bv, q.c0) && full_test32(q, rx, ry, rz, gx, gy, gz, Bv);
+          }
+          if (emit) emit_lane(buf, cnt, s, p, j);
+        }
+        __syncwarp();
+        if (*cnt >= (uint32_t)(kWarpBuf / 2)) flush_lanes(buf, cnt, s, lane);
+      }
+      __syncwarp();
     }
   }
+  flush_lanes(buf, cnt, s, lane);
   for (int o = 16; o > 0; o >>= 1) tests += __shfl_down_sync(0xFFFFFFFFu, tests, o);
-  if ((threadIdx.x & 31) == 0 && tests) atomicAdd(&stests, tests);
-  __syncthreads();
-  uint32_t cnt = scnt < (uint32_t)kSearchBuf ? scnt : (uint32_t)kSearchBuf;
-  if (threadIdx.x == 0) {
-    if (stests) atomicAdd(&s.d.pair_tests, stests);
-    sbase = cnt ? atomicAdd(&s.d.n_raw, cnt) : 0u;
-  }
-  __syncthreads();
-  for (uint32_t i = threadIdx.x; i < cnt; i += kTile) {
-    uint32_t gpos = sbase + i;
-    if (gpos < edge_cap) edges[gpos] = sbuf[i];
-    else atomicOr(&s.d.status, ST_EDGE_OVERFLOW);
-  }
+  if (lane == 0 && tests) atomicAdd(&s.d.pair_tests, tests);
 }
 
 int cell_search_blocks(int precision, int K, int num_sms) {
@@ -1046,8 +1101,8 @@ int launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st) {
       k_search_seg32<1><<<cb, kCellWarps * 32, 0, st>>>(L.b);
     }
   }
-  if (precision == KMC_FP64) k_search_fast<KMC_FP64><<<L.ptiles, kTile, 0, st>>>(L.b);
-  else k_search_fast<KMC_GUARDED_FP32><<<L.ptiles, kTile, 0, st>>>(L.b);
+  if (precision == KMC_FP64) k_search_fast<KMC_FP64><<<L.ptiles, kCellWarps * 32, 0, st>>>(L.b);
+  else k_search_fast<KMC_GUARDED_FP32><<<L.ptiles, kCellWarps * 32, 0, st>>>(L.b);
   return precision == KMC_FP64 ? 3 : 4;
 }
 

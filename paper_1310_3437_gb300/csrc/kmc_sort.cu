@@ -226,9 +226,9 @@ __global__ void __launch_bounds__(kTile) k_scatter(Batch B) {
     float o[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      // offset from the cell's lower corner, subtracted in binary64, rounded once
-      double corner = g.nc[a] == 1 ? 0.0 : dmul((double)c[a], g.w[a]);
-      o[a] = d2f_rn(dsub(xs[a], corner));
+      // offset from the cell's lower corner: x - c w in one binary64 fused
+      // multiply-add, then rounded once to binary32
+      o[a] = d2f_rn(g.nc[a] == 1 ? xs[a] : __fma_rn(-u2d_exact((uint32_t)c[a]), g.w[a], xs[a]));
     }
     s.mir_a[dst] = make_float4(o[0], o[1], o[2], d2f_rn(vs[0]));
     s.mir_b[dst] = make_float2(d2f_rn(vs[1]), d2f_rn(vs[2]));
