@@ -84,11 +84,13 @@ extern "C" {
 
 /* ---- search kernels (kmc_params.search_kernel) ----------------------------- */
 #define KMC_SEARCH_AUTO 0      /* per step: warp-per-cell search when cells are well
-                                  filled, thread-per-particle search otherwise */
-#define KMC_SEARCH_PARTICLE 1  /* one thread per particle */
+                                  filled, the row search (binary32) or the
+                                  thread-per-particle search (binary64) otherwise */
+#define KMC_SEARCH_PARTICLE 1  /* one thread per particle, cell by cell */
 #define KMC_SEARCH_CELL 2      /* one warp per cell, partners in lanes */
-#define KMC_SEARCH_SEGMENT 3   /* one warp per run of cells of a column, partners in lanes
-                                  (guarded binary32; binary64 uses KMC_SEARCH_CELL) */
+#define KMC_SEARCH_ROW 3       /* one lane per particle walking whole stencil rows as
+                                  partner ranges (guarded binary32; binary64 uses
+                                  KMC_SEARCH_CELL) */
 
 /* Parameters of one simulation.  Zero-initialise, then set the fields. */
 typedef struct kmc_params {
@@ -116,7 +118,7 @@ typedef struct kmc_params {
   uint32_t history_cap;    /* step records kept for KMC_OBS_COUNTS (0: 4096) */
   uint32_t profile_cap;    /* profile snapshots kept for KMC_OBS_PROFILES (0: 64) */
   int32_t search_kernel;   /* KMC_SEARCH_AUTO (0), KMC_SEARCH_PARTICLE (1),
-                              KMC_SEARCH_CELL (2) or KMC_SEARCH_SEGMENT (3).
+                              KMC_SEARCH_CELL (2) or KMC_SEARCH_ROW (3).
                               Never changes results. */
   double split_min_occ;    /* speed split only if the slow grid keeps at least this
                               many particles per cell on average (0: no floor).

@@ -49,7 +49,7 @@ KMC_FLAG_FORCE_SPLIT = 2
 KMC_SEARCH_AUTO = 0
 KMC_SEARCH_PARTICLE = 1
 KMC_SEARCH_CELL = 2
-KMC_SEARCH_SEGMENT = 3
+KMC_SEARCH_ROW = 3
 
 
 class kmc_params(C.Structure):

@@ -193,7 +193,8 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
   for (int a = 0; a < 3; ++a) g.cfast[a] = cfast[a];
   {
     // search kernel for the slow population: warp per cell when cells are well
-    // filled; the binary32 warp-level searches handle no one-cell periodic axis
+    // filled; the binary32 warp-per-cell search handles no one-cell periodic axis
+    // (the row search does)
     const double cells = (double)nc[0] * nc[1] * nc[2];
     const double occ = (double)s.n / cells;
     bool cp = false;
@@ -201,19 +202,12 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
     int mode = s.search_kernel;
     const bool fp32 = s.precision == KMC_GUARDED_FP32;
     if (mode == 0) {
-      if (fp32) mode = occ >= 16.0 ? KMC_SEARCH_CELL : KMC_SEARCH_SEGMENT;
+      if (fp32) mode = occ >= 16.0 ? KMC_SEARCH_CELL : KMC_SEARCH_ROW;
       else mode = occ >= 4.0 ? KMC_SEARCH_CELL : KMC_SEARCH_PARTICLE;
     }
-    if (mode == KMC_SEARCH_SEGMENT && !fp32) mode = KMC_SEARCH_CELL;
-    if ((mode == KMC_SEARCH_CELL || mode == KMC_SEARCH_SEGMENT) && cp && fp32) mode = KMC_SEARCH_PARTICLE;
+    if (mode == KMC_SEARCH_ROW && !fp32) mode = KMC_SEARCH_CELL;
+    if (mode == KMC_SEARCH_CELL && cp && fp32) mode = KMC_SEARCH_ROW;
     g.mode = mode;
-    // segment length: about 48 particles per warp (the staging holds 64), and a run
-    // of S + 2K cells must not wrap onto itself
-    int S = (int)floor(48.0 / (occ > 0.05 ? occ : 0.05) + 0.5);
-    S = S < 1 ? 1 : (S > 32 ? 32 : S);
-    if (nc[0] > 1 && S > nc[0] - 2 * K) S = nc[0] - 2 * K;
-    if (nc[0] == 1 || S < 1) S = 1;
-    g.seg = S;
   }
   for (int a = 0; a < 3; ++a) {
     g.nc[a] = nc[a];
@@ -230,13 +224,13 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
   g.c1 = s.dt * s.dt * (1.0 + 0x1p-40) * (1.0 + 0x1p-50);
 
   // ---- binary32 pre-tests ------------------------------------------------------
+  // The binary32 mirror holds box coordinates and velocities, each rounded once.
   // Error of the binary32 separation against the binary64 one, per component:
-  //   split axis: offsets from the cell corner (x - c w, one binary64 fused
-  //     multiply-add, rounded once to binary32)
-  //     plus the stencil shift of up to Ke = max(K, fast reach) cells, or for x in
-  //     the segment kernel coordinates measured from the segment start:
-  //     u32 w (4 seg + 4 Ke + 4) + 8 u64 L;
-  //   one-cell axis: u32 * 6.1 * extent + 8 u64 L.
+  //   multi-cell axis: both coordinates (u32 L each), a periodic image shifts one
+  //     side by the rounded box length (u32 L) and that sum is rounded (u32 L); the
+  //     difference itself rounds with u32 |r|: 4 u32 L + u32 rb, plus 8 u64 L for the
+  //     binary64 separation's own rounding;
+  //   one-cell axis (minimum image in binary32): u32 * 6.1 * extent + 8 u64 L.
   // Velocity difference: 4.1 u32 V.  Component bounds: |r_k| <= rb_k, |v_k| <= 2V.
   double er = 0.0, rn2 = 0.0, rbmax = 0.0;
   for (int a = 0; a < 3; ++a) {
@@ -247,9 +241,8 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
       e = 6.1 * u32 * L + 8.0 * u64 * L;
       rb = s.bc[a] == KMC_PERIODIC ? 0.5 * L * (1.0 + 8.0 * u32) + 2.0 * e : L;
     } else {
-      const double span = a == 0 ? (4.0 * g.seg + 4.0 * Ke + 4.0) : (4.0 * Ke + 5.0);
-      e = u32 * g.w[a] * span * (1.0 + 1e-3) + 8.0 * u64 * L;
       rb = (Ke + 1.0 + 2.0 * m) * g.w[a];
+      e = u32 * (4.0 * L + rb) * (1.0 + 1e-3) + 8.0 * u64 * L;
     }
     er = e > er ? e : er;
     rbmax = rb > rbmax ? rb : rbmax;

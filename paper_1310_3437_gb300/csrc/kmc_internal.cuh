@@ -41,8 +41,8 @@ enum : uint32_t {
 struct Grid {
   int32_t nc[3];      // cells per axis; 1 means the axis is one cell (no stencil on it)
   int32_t K;          // stencil radius in cells
-  int32_t mode;       // search kernel of this step: KMC_SEARCH_PARTICLE, _CELL or _SEGMENT
-  int32_t seg;        // cells per segment (KMC_SEARCH_SEGMENT) along x
+  int32_t mode;       // search kernel of this step: KMC_SEARCH_PARTICLE, _CELL or _ROW
+  int32_t pad1;
   uint32_t split;     // 1: particles with |v|^2 above s1sq form a second population
   float s1sq;         // binary32 split threshold on the upper bound of |v|^2
   int32_t cfast[3];   // fast particles search cfast cells on each side (split axes)
@@ -200,36 +200,51 @@ __device__ __forceinline__ void key_decode(const Grid& g, uint32_t key, int& cx,
 
 // binary64 -> binary32 conversions on the integer pipes (on this part the hardware
 // conversion issues on the binary64 pipe, which runs at 1/72 of the binary32 rate).
-// Round to nearest even for normal results, identical to the hardware conversion;
-// zero, subnormal and out-of-range inputs take the hardware path.
+// IEEE 754 round to nearest even, with no hardware fallback: a fallback branch that
+// the compiler turns into a predicated conversion would still occupy the binary64
+// pipe.  Normal results round the 29 dropped bits; results below the binary32 normal
+// range are k 2^-149 with k = M 2^(e-926) rounded (M the 53-bit significand);
+// overflow gives infinity and NaN a quiet NaN.
 __device__ __forceinline__ float d2f_rn(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(b >> 63) << 31;
   const int e = (int)((b >> 52) & 0x7FF);
   const int fe = e - 1023 + 127;
-  if (e == 0 || fe <= 0 || fe >= 255) return __double2float_rn(x);
-  const uint32_t top = (uint32_t)((b >> 29) & 0x7FFFFFu);
-  const uint32_t rest = (uint32_t)(b & 0x1FFFFFFFu);
-  const uint32_t up = (rest > 0x10000000u || (rest == 0x10000000u && (top & 1u))) ? 1u : 0u;
-  const uint32_t bits = (uint32_t)((b >> 63) << 31) | (((uint32_t)fe << 23) + top + up);
-  return __uint_as_float(bits);
+  if (fe >= 1 && fe <= 254) {
+    const uint32_t top = (uint32_t)((b >> 29) & 0x7FFFFFu);
+    const uint32_t rest = (uint32_t)(b & 0x1FFFFFFFu);
+    const uint32_t up = (rest > 0x10000000u || (rest == 0x10000000u && (top & 1u))) ? 1u : 0u;
+    return __uint_as_float(sign | (((uint32_t)fe << 23) + top + up));  // carry may reach inf
+  }
+  if (fe > 254) {
+    const bool nan = e == 0x7FF && (b & 0xFFFFFFFFFFFFFull) != 0ull;
+    return __uint_as_float(nan ? 0x7FFFFFFFu : (sign | 0x7F800000u));
+  }
+  const int sh = 926 - e;  // >= 30 here
+  if (e == 0 || sh > 54) return __uint_as_float(sign);  // below half the least subnormal
+  const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  unsigned long long k = M >> sh;
+  const unsigned long long rem = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+  k += (rem > half || (rem == half && (k & 1ull))) ? 1ull : 0ull;
+  return __uint_as_float(sign | (uint32_t)k);
 }
-// exact binary64 value of an unsigned 32-bit integer, built with integer operations
-// (the conversion instruction runs on the binary64 pipe)
-__device__ __forceinline__ double u2d_exact(uint32_t c) {
-  if (c == 0u) return 0.0;
-  const int e = 31 - __clz(c);
-  const unsigned long long mant = ((unsigned long long)c << (52 - e)) & 0xFFFFFFFFFFFFFull;
-  return __longlong_as_double((long long)(((unsigned long long)(1023 + e) << 52) | mant));
-}
-// |x| rounded up to binary32
+// |x| rounded up to binary32 (integer pipes, no hardware fallback)
 __device__ __forceinline__ float d2f_abs_ru(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
   const int e = (int)(b >> 52);
   const int fe = e - 1023 + 127;
-  if (e == 0 || fe <= 0 || fe >= 255) return __double2float_ru(__longlong_as_double((long long)b));
-  const uint32_t top = (uint32_t)((b >> 29) & 0x7FFFFFu);
-  const uint32_t up = (b & 0x1FFFFFFFull) ? 1u : 0u;
-  return __uint_as_float(((uint32_t)fe << 23) + top + up);
+  if (fe >= 1 && fe <= 254) {
+    const uint32_t top = (uint32_t)((b >> 29) & 0x7FFFFFu);
+    const uint32_t up = (b & 0x1FFFFFFFull) ? 1u : 0u;
+    return __uint_as_float(((uint32_t)fe << 23) + top + up);
+  }
+  if (fe > 254) return __uint_as_float(e == 0x7FF && (b & 0xFFFFFFFFFFFFFull) ? 0x7FFFFFFFu : 0x7F800000u);
+  if (b == 0ull) return 0.0f;
+  const int sh = 926 - e;
+  if (e == 0 || sh > 63) return __uint_as_float(1u);  // the least subnormal
+  const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned long long k = (M >> sh) + ((M & ((1ull << sh) - 1ull)) ? 1ull : 0ull);
+  return __uint_as_float((uint32_t)k);
 }
 
 // upper bound of |v|^2 in binary32 (directed rounding; used to size cells and to

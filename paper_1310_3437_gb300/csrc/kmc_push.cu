@@ -42,6 +42,37 @@ __device__ __forceinline__ bool lt_zero(double x) {  // x < 0.0 (false for -0.0)
 }
 
 // ---- k_push ---------------------------------------------------------------- //
+// The boundary fix-ups are rare (particles that crossed a wall or the periodic
+// boundary in this step).  They sit in out-of-line functions so that their binary64
+// operations issue only for the lanes that call them, instead of being predicated
+// into every lane's instruction stream.
+struct XV {
+  double x, v;
+};
+
+// periodic axis: one wrap into [0, L), x == L mapped to 0
+__device__ __noinline__ double wrap_periodic(double x, double L) {
+  if (dbits(x) >= dbits(L)) x = dsub(x, L);
+  if (lt_zero(x)) {
+    x = dadd(x, L);
+    if (dbits(x) == dbits(L)) x = 0.0;
+  }
+  return x;
+}
+
+// reflecting axis: lower wall at 0, upper wall (or piston) at X moving with u
+__device__ __noinline__ XV reflect_walls(double x, double v, double X, double u) {
+  if (lt_zero(x)) {
+    x = -x;
+    v = -v;
+  }
+  if (dbits(X) > 0 ? dbits(x) > dbits(X) : x > X) {
+    x = dsub(dadd(X, X), x);
+    v = dsub(-v, dadd(u, u));
+  }
+  return {x, v};
+}
+
 __global__ void __launch_bounds__(kTile) k_push(Batch B) {
   __shared__ double sX;                       // piston position at the end of the step
   __shared__ uint32_t scnt[kSplitTrials];     // particles above each trial threshold
@@ -67,33 +98,17 @@ __global__ void __launch_bounds__(kTile) k_push(Batch B) {
       double v = s.v[cur][a][p];
       if (q == kNone) x = dadd(x, dmul(v, dt));
       if (s.bc[a] == KMC_PERIODIC) {
-        double L = s.box[a];  // > 0
-        if (dbits(x) >= dbits(L)) x = dsub(x, L);
-        if (lt_zero(x)) {
-          x = dadd(x, L);
-          if (dbits(x) == dbits(L)) x = 0.0;
-        }
+        const double L = s.box[a];  // > 0
+        if (dbits(x) >= dbits(L) || lt_zero(x)) x = wrap_periodic(x, L);
       } else {
-        double X, u;
-        if (a == 0) {
-          u = s.piston_u;
-          X = sX;
-        } else {
-          u = 0.0;
-          X = s.box[a];
+        const double X = a == 0 ? sX : s.box[a];
+        const double u = a == 0 ? s.piston_u : 0.0;
+        if (lt_zero(x) || (dbits(X) > 0 ? dbits(x) > dbits(X) : x > X)) {
+          const XV r = reflect_walls(x, v, X, u);
+          x = r.x;
+          v = r.v;
+          s.v[cur][a][p] = v;
         }
-        bool vchg = false;
-        if (lt_zero(x)) {
-          x = -x;
-          v = -v;
-          vchg = true;
-        }
-        if (dbits(X) > 0 ? dbits(x) > dbits(X) : x > X) {
-          x = dsub(dadd(X, X), x);
-          v = dsub(-v, dadd(u, u));
-          vchg = true;
-        }
-        if (vchg) s.v[cur][a][p] = v;
       }
       s.x[cur][a][p] = x;
       vv[a] = v;

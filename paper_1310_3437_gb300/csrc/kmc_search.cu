@@ -85,31 +85,38 @@ __global__ void __launch_bounds__(kTile) k_search(Batch B) {
     const bool any_cp = cp0 || cp1 || cp2;
     const double L0 = s.box[0], L1 = s.box[1], L2 = s.box[2];
 
+    // a neighbour reached across a periodic boundary is seen as its image: wrap
+    // flags -1 (below 0) or +1 (at or above the extent) per axis
     for (int dz = 0; dz <= Kz; ++dz) {
-      int qz = cz + dz;
+      int qz = cz + dz, wz = 0;
       if (qz >= nz) {
         if (!pz) break;
         qz -= nz;
+        wz = 1;
       }
       for (int dy = (dz == 0 ? 0 : -Ky); dy <= Ky; ++dy) {
-        int qy = cy + dy;
+        int qy = cy + dy, wy = 0;
         if (qy < 0) {
           if (!py) continue;
           qy += ny;
+          wy = -1;
         } else if (qy >= ny) {
           if (!py) continue;
           qy -= ny;
+          wy = 1;
         }
         const uint32_t colbase = col_code(g, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx;
         const int dx0 = (dz == 0 && dy == 0) ? 0 : -Kx;
         for (int dx = dx0; dx <= Kx; ++dx) {
-          int qx = cx + dx;
+          int qx = cx + dx, wx = 0;
           if (qx < 0) {
             if (!px) continue;
             qx += nx;
+            wx = -1;
           } else if (qx >= nx) {
             if (!px) continue;
             qx -= nx;
+            wx = 1;
           }
           const uint32_t key = colbase + (uint32_t)qx;
           uint32_t beg = __ldg(cs + key), end = __ldg(cs + key + 1);
@@ -140,10 +147,10 @@ __global__ void __launch_bounds__(kTile) k_search(Batch B) {
               }
             }
           } else {
-            // own coordinates shifted into the frame of the neighbour cell's corner
-            const float sx = o32.ox - (float)dx * g.wf[0];
-            const float sy = o32.oy - (float)dy * g.wf[1];
-            const float sz = o32.oz - (float)dz * g.wf[2];
+            // own coordinates moved by the image shift (j seen at x_j + w L)
+            const float sx = o32.ox - (float)wx * g.Lf[0];
+            const float sy = o32.oy - (float)wy * g.Lf[1];
+            const float sz = o32.oz - (float)wz * g.Lf[2];
             for (uint32_t j = beg; j < end; ++j) {
               const float4 a = __ldg(MA + j);
               const float2 b = __ldg(MB + j);
@@ -571,7 +578,7 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_cell32(Batch B) {
                pz = s.bc[2] == KMC_PERIODIC;
     const uint32_t nkeys = G.nkeys;
     const uint32_t* __restrict__ cs = s.cell_start;
-    const float wx = G.wf[0], wy = G.wf[1], wz = G.wf[2];
+    const float Lx = G.Lf[0], Ly = G.Lf[1], Lz = G.Lf[2];
     const float c0 = G.s_c0, c1 = G.s_c1;
     const float4* __restrict__ MA = s.mir_a;
     const float2* __restrict__ MB = s.mir_b;
@@ -602,23 +609,27 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_cell32(Batch B) {
         }
         __syncwarp();
         for (int dz = 0; dz <= Kz; ++dz) {
-          int qz = cz + dz;
+          int qz = cz + dz, wrz = 0;
           if (qz >= nz) {
             if (!pz) break;
             qz -= nz;
+            wrz = 1;
           }
           for (int dy = (dz == 0 ? 0 : -Ky); dy <= Ky; ++dy) {
-            int qy = cy + dy;
+            int qy = cy + dy, wry = 0;
             if (qy < 0) {
               if (!py) continue;
               qy += ny;
+              wry = -1;
             } else if (qy >= ny) {
               if (!py) continue;
               qy -= ny;
+              wry = 1;
             }
             const uint32_t colbase = col_code(G, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx;
             const bool own_col = dz == 0 && dy == 0;
-            const float shy = (float)dy * wy, shz = (float)dz * wz;
+            // image shifts of partners reached across a periodic boundary
+            const float shy = (float)wry * Ly, shz = (float)wrz * Lz;
             int dx = own_col ? 0 : -Kx;
             while (dx <= Kx) {
               const int q0 = cx + dx;
@@ -636,9 +647,7 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_cell32(Batch B) {
               dx += m;
               const uint32_t jbeg = __ldg(cs + colbase + qx), jend = __ldg(cs + colbase + qx + m);
               if (jbeg == jend) continue;
-              uint32_t bnd[2 * K];
-#pragma unroll
-              for (int t = 0; t < 2 * K; ++t) bnd[t] = (t + 1 < m) ? __ldg(cs + colbase + qx + t + 1) : jend;
+              const float shx = (float)region * Lx;
               const bool has_own = own_col && dxa <= 0 && dxa + m > 0;
               if (lane == 0) {
                 uint64_t len = jend - jbeg;
@@ -656,11 +665,7 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_cell32(Batch B) {
                 if (j < jend) {
                   const float4 a = __ldg(MA + j);
                   const float2 b = __ldg(MB + j);
-                  int t = 0;
-#pragma unroll
-                  for (int qq = 0; qq < 2 * K; ++qq) t += j >= bnd[qq] ? 1 : 0;
-                  // partner moved into the frame of cell A's corner
-                  jx = a.x + (float)(dxa + t) * wx;
+                  jx = a.x + shx;
                   jy = a.y + shy;
                   jz = a.z + shz;
                   gx = a.w; gy = b.x; gz = b.y;
@@ -685,218 +690,190 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_cell32(Batch B) {
 }
 
 // --------------------------------------------------------------------------- //
-// Binary32 warp-per-segment search, for sparsely filled cells.  A warp owns a run of
-// S consecutive cells of one column (S from the occupancy, about 32 particles), whose
-// particles i are staged in shared memory with x measured from the segment start.
-// For every forward column of the stencil the partner run (S + 2K cells, contiguous
-// in cell order) is loaded 32 at a time, one partner j per lane; each lane then
-// loops over exactly the i's of the segment that lie in its stencil -- a contiguous
-// index range, because cells are ordered along x -- with a warp-uniform trip count
-// (the warp maximum of the range lengths).
+// Row search (binary32), for sparsely filled cells.  One lane per slow particle i,
+// 32 consecutive particles (cell order) per warp.  With the mirror in box
+// coordinates a stencil row -- the 2K+1 cells along x of one forward (y, z) column,
+// or in i's own column the cells from its own on with only j > i -- is one
+// contiguous range of partners; a row that crosses a periodic x boundary splits
+// into two pieces, the far one seen through its image.  Each lane lists its
+// non-empty pieces in shared memory and then walks them as one sequence of tests,
+// one test per iteration, so no per-cell loop and no per-cell shift remain.  The
+// warp runs as many iterations as its busiest lane needs.
 template <int K>
-__global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_seg32(Batch B) {
-  constexpr int ICAP = 64;
-  // staged segment particles (x from the segment start): AoS, 4 + 2 floats
-  __shared__ float4 sia[kCellWarps][ICAP];
-  __shared__ float2 sib[kCellWarps][ICAP];
-  // the chunk's partners and their work: data, first i, range length, group offset
-  __shared__ float sj[kCellWarps][6][32];
-  __shared__ uint32_t sjidx[kCellWarps][32], slo[kCellWarps][32], slen[kCellWarps][32],
-      soff[kCellWarps][32];
-  __shared__ uint2 wbuf[kCellWarps][kWarpBuf];
-  __shared__ uint32_t wcount[kCellWarps];
+struct RowLayout {
+  static constexpr int kCols = 1 + K + K * (2 * K + 1);  // own column + forward columns
+  static constexpr int kPieces = 2 * kCols;             // a row splits at most once
+  static constexpr int kWarps = kTile / 32;
+  static constexpr size_t kPieceBytes = (size_t)kWarps * kPieces * 32 * sizeof(uint2);
+  static constexpr size_t kCodeBytes = (size_t)kWarps * kPieces * 32;
+  static constexpr size_t kBytes = kPieceBytes + kCodeBytes + (size_t)kWarps * kWarpBuf * sizeof(uint2);
+};
+
+// image flags of a piece: bit 0 / 1 = seen at +L / -L along x, bits 2-3 y, bits 4-5 z
+__device__ __forceinline__ uint32_t image_code(int wx, int wy, int wz) {
+  return (uint32_t)(wx > 0) | ((uint32_t)(wx < 0) << 1) | ((uint32_t)(wy > 0) << 2) |
+         ((uint32_t)(wy < 0) << 3) | ((uint32_t)(wz > 0) << 4) | ((uint32_t)(wz < 0) << 5);
+}
+__device__ __forceinline__ float image_shift(uint32_t c, int axis, float L) {
+  const int w = (int)((c >> (2 * axis)) & 1u) - (int)((c >> (2 * axis + 1)) & 1u);
+  return (float)w * L;
+}
+
+template <int K>
+__global__ void __launch_bounds__(kTile) k_search_rows32(Batch B) {
+  using RL = RowLayout<K>;
+  constexpr int NP = RL::kPieces;
+  extern __shared__ __align__(16) unsigned char rows_smem[];
+  __shared__ uint32_t wcount[RL::kWarps];
   __shared__ Guard32 sq;
+  const int k = find_sim(B.ptile, B.nsims, blockIdx.x);
+  SimDev& s = *B.sims[k];
+  if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_ROW) return;
+  const Grid& g = s.d.grid;
+  if (threadIdx.x == 0) {
+    sq.c0 = g.s_c0; sq.c1 = g.s_c1; sq.ag = g.a_g; sq.tg = g.t_g; sq.dtf = g.dtf;
+    sq.d0up = g.d0up; sq.brel = g.b_rel; sq.babs = g.b_abs; sq.we = g.w_e; sq.wrel = g.w_rel;
+  }
+  __syncthreads();
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  const uint32_t gwarp = blockIdx.x * kCellWarps + warp, nwarps = gridDim.x * kCellWarps;
+  const uint32_t nslow = g.split ? __ldg(s.cell_start + g.nkeys) : s.n;
+  const uint32_t p = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
+  if (p - lane >= nslow) return;  // the whole warp is past the slow population
+  uint2* pc = reinterpret_cast<uint2*>(rows_smem) + (size_t)warp * NP * 32;
+  uint8_t* cd = rows_smem + RL::kPieceBytes + (size_t)warp * NP * 32;
+  uint2* buf = reinterpret_cast<uint2*>(rows_smem + RL::kPieceBytes + RL::kCodeBytes) +
+               (size_t)warp * kWarpBuf;
+  uint32_t* cnt = &wcount[warp];
+  if (lane == 0) *cnt = 0;
+  __syncwarp();
 
-  for (int k = 0; k < B.nsims; ++k) {
-    SimDev& s = *B.sims[k];
-    if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_SEGMENT) continue;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const Grid& G0 = s.d.grid;
-      sq.c0 = G0.s_c0; sq.c1 = G0.s_c1; sq.ag = G0.a_g; sq.tg = G0.t_g; sq.dtf = G0.dtf;
-      sq.d0up = G0.d0up; sq.brel = G0.b_rel; sq.babs = G0.b_abs; sq.we = G0.w_e; sq.wrel = G0.w_rel;
-    }
-    if (lane == 0) wcount[warp] = 0;
-    __syncthreads();
-    const Grid& G = s.d.grid;
-    const int nx = G.nc[0], ny = G.nc[1], nz = G.nc[2];
-    const int Kx = nx == 1 ? 0 : K, Ky = ny == 1 ? 0 : K, Kz = nz == 1 ? 0 : K;
-    const bool px = s.bc[0] == KMC_PERIODIC, py = s.bc[1] == KMC_PERIODIC,
-               pz = s.bc[2] == KMC_PERIODIC;
-    const int S = G.seg;
-    const uint32_t nseg = (uint32_t)((nx + S - 1) / S);
-    const uint32_t ncols = G.nkeys / (uint32_t)nx;
-    const uint32_t items = ncols * nseg;
-    const uint32_t* __restrict__ cs = s.cell_start;
-    const float wx = G.wf[0], wy = G.wf[1], wz = G.wf[2];
-    const float c0 = G.s_c0, c1 = G.s_c1;
-    const float4* __restrict__ MA = s.mir_a;
-    const float2* __restrict__ MB = s.mir_b;
-    float4* ia = sia[warp];
-    float2* ib = sib[warp];
-    uint2* buf = wbuf[warp];
-    uint32_t* cnt = &wcount[warp];
-    unsigned long long tests = 0;
+  const bool valid = p < nslow;
+  const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
+  const int Kx = nx == 1 ? 0 : K, Ky = ny == 1 ? 0 : K, Kz = nz == 1 ? 0 : K;
+  const bool px = s.bc[0] == KMC_PERIODIC, py = s.bc[1] == KMC_PERIODIC,
+             pz = s.bc[2] == KMC_PERIODIC;
+  // one-cell periodic axes need the minimum image explicitly
+  const bool cp0 = nx == 1 && px, cp1 = ny == 1 && py, cp2 = nz == 1 && pz;
+  const bool any_cp = cp0 || cp1 || cp2;
+  const uint32_t* __restrict__ cs = s.cell_start;
+  const float4* __restrict__ MA = s.mir_a;
+  const float2* __restrict__ MB = s.mir_b;
+  const float Lx = g.Lf[0], Ly = g.Lf[1], Lz = g.Lf[2];
 
-    for (uint32_t item = gwarp; item < items; item += nwarps) {
-      const uint32_t col = item / nseg, sidx = item - col * nseg;
-      const uint32_t colA = col * (uint32_t)nx;
-      const int cx0 = (int)sidx * S;
-      const int cx1 = (cx0 + S < nx ? cx0 + S : nx) - 1;
-      const uint32_t segA = __ldg(cs + colA + cx0), segB = __ldg(cs + colA + cx1 + 1);
-      if (segA == segB) continue;
-      int tx, cy, cz;
-      key_decode(G, colA, tx, cy, cz);
-      for (uint32_t i0 = segA; i0 < segB; i0 += ICAP) {
-        const uint32_t nI = segB - i0 < (uint32_t)ICAP ? segB - i0 : (uint32_t)ICAP;
-        __syncwarp();
-        for (uint32_t t = lane; t < nI; t += 32) {
-          const uint32_t i = i0 + t;
-          // cell of i inside the segment (largest c with start(c) <= i)
-          int lo = cx0, hi = cx1;
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(cs + colA + mid) <= i) lo = mid; else hi = mid - 1;
-          }
-          const float4 a = MA[i];
-          const float2 b = MB[i];
-          ia[t] = make_float4(fmaf((float)(lo - cx0), wx, a.x), a.y, a.z, a.w);
-          ib[t] = b;
+  // 1. the lane's non-empty pieces, column by column
+  int np = 0;
+  uint32_t total = 0;
+  Own32 o = {0, 0, 0, 0, 0, 0};
+  if (valid) {
+    int cx, cy, cz;
+    key_decode(g, s.skey[p], cx, cy, cz);
+    const float4 a = MA[p];
+    const float2 b = MB[p];
+    o = {a.x, a.y, a.z, a.w, b.x, b.y};
+#pragma unroll
+    for (int c = 0; c < RL::kCols; ++c) {
+      const int dz = c <= K ? 0 : 1 + (c - K - 1) / (2 * K + 1);
+      const int dy = c == 0 ? 0 : (c <= K ? c : (c - K - 1) % (2 * K + 1) - K);
+      if (dz > Kz || dy > Ky || dy < -Ky) continue;
+      int qz = cz + dz, wz = 0;
+      if (qz >= nz) {
+        if (!pz) continue;
+        qz -= nz;
+        wz = 1;
+      }
+      int qy = cy + dy, wy = 0;
+      if (qy < 0) {
+        if (!py) continue;
+        qy += ny;
+        wy = -1;
+      } else if (qy >= ny) {
+        if (!py) continue;
+        qy -= ny;
+        wy = 1;
+      }
+      const uint32_t colb = col_code(g, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx;
+      const int xa = c == 0 ? cx : cx - Kx, xb = cx + Kx;  // cells of the row, unwrapped
+      {
+        const int a0 = xa < 0 ? 0 : xa, b0 = xb >= nx ? nx - 1 : xb;
+        const uint32_t jb = c == 0 ? p + 1 : __ldg(cs + colb + a0);
+        const uint32_t je = __ldg(cs + colb + b0 + 1);
+        if (je > jb) {
+          pc[np * 32 + lane] = make_uint2(jb, je);
+          cd[np * 32 + lane] = (uint8_t)image_code(0, wy, wz);
+          ++np;
+          total += je - jb;
         }
-        __syncwarp();
-        for (int dz = 0; dz <= Kz; ++dz) {
-          int qz = cz + dz;
-          if (qz >= nz) {
-            if (!pz) break;
-            qz -= nz;
-          }
-          for (int dy = (dz == 0 ? 0 : -Ky); dy <= Ky; ++dy) {
-            int qy = cy + dy;
-            if (qy < 0) {
-              if (!py) continue;
-              qy += ny;
-            } else if (qy >= ny) {
-              if (!py) continue;
-              qy -= ny;
-            }
-            const uint32_t colB = col_code(G, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx;
-            const bool own_col = dz == 0 && dy == 0;
-            const float shy = (float)dy * wy, shz = (float)dz * wz;
-            // partner run in unwrapped cell coordinates [ua, ub]
-            const int ua = own_col ? cx0 : cx0 - Kx;
-            const int ub = cx1 + Kx;
-            int u = ua;
-            while (u <= ub) {
-              const int region = u < 0 ? -1 : (u >= nx ? 1 : 0);
-              if (region != 0 && !px) { ++u; continue; }
-              int m = 1;
-              while (u + m <= ub) {
-                const int u2 = u + m;
-                const int r2 = u2 < 0 ? -1 : (u2 >= nx ? 1 : 0);
-                if (r2 != region) break;
-                ++m;
-              }
-              const int qa = u - region * nx;  // first cell of the piece in the column
-              const int ua_piece = u;
-              u += m;
-              const uint32_t jbeg = __ldg(cs + colB + qa), jend = __ldg(cs + colB + qa + m);
-              if (jbeg == jend) continue;
-              for (uint32_t cb = jbeg; cb < jend; cb += 32) {
-                const uint32_t j = cb + lane;
-                uint32_t lo_i = 0, hi_i = 0;
-                if (j < jend) {
-                  // cell of j in the piece
-                  int lo = 0, hi = m - 1;
-                  while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (__ldg(cs + colB + qa + mid) <= j) lo = mid; else hi = mid - 1;
-                  }
-                  const int uj = ua_piece + lo;  // unwrapped cell of j
-                  const float4 a = __ldg(MA + j);
-                  const float2 b = __ldg(MB + j);
-                  sj[warp][0][lane] = fmaf((float)(uj - cx0), wx, a.x);
-                  sj[warp][1][lane] = a.y + shy;
-                  sj[warp][2][lane] = a.z + shz;
-                  sj[warp][3][lane] = a.w;
-                  sj[warp][4][lane] = b.x;
-                  sj[warp][5][lane] = b.y;
-                  // i's of the segment inside j's stencil: cells [uj-K, uj+K] (other
-                  // columns) or [uj-K, uj] with i < j in j's own cell (own column)
-                  int ca = uj - Kx > cx0 ? uj - Kx : cx0;
-                  int cbnd = own_col ? (region == 0 ? uj : uj - 1) : uj + Kx;
-                  cbnd = cbnd < cx1 ? cbnd : cx1;
-                  if (ca <= cbnd) {
-                    lo_i = __ldg(cs + colA + ca);
-                    hi_i = __ldg(cs + colA + cbnd + 1);
-                    if (own_col && region == 0 && hi_i > j) hi_i = j;
-                    if (lo_i < i0) lo_i = i0;
-                    if (hi_i > i0 + nI) hi_i = i0 + nI;
-                    if (hi_i < lo_i) hi_i = lo_i;
-                  }
-                }
-                const uint32_t len = hi_i - lo_i;
-                tests += len;
-                // balanced work: the ranges are cut into groups of 4 pairs and the
-                // groups are dealt out to all lanes
-                const uint32_t g = (len + 3u) >> 2;
-                uint32_t incl = g;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                  const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                  if (lane >= (uint32_t)o) incl += y;
-                }
-                const uint32_t Gtot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-                sjidx[warp][lane] = j;
-                slo[warp][lane] = lo_i - i0;
-                slen[warp][lane] = len;
-                soff[warp][lane] = incl - g;
-                __syncwarp();
-                for (uint32_t kb = 0; kb < Gtot; kb += 32) {
-                  const uint32_t kq = kb + lane;
-                  if (kq < Gtot) {
-                    // owner: the last lane whose first group is at or before kq
-                    int lo = 0, hi = 31;
-                    while (lo < hi) {
-                      const int mid = (lo + hi + 1) >> 1;
-                      if (soff[warp][mid] <= kq) lo = mid; else hi = mid - 1;
-                    }
-                    const uint32_t grp = kq - soff[warp][lo];
-                    const uint32_t tfirst = slo[warp][lo] + 4u * grp;
-                    const uint32_t left = slen[warp][lo] - 4u * grp;
-                    const uint32_t jj = sjidx[warp][lo];
-                    const float jx = sj[warp][0][lo], jy = sj[warp][1][lo], jz = sj[warp][2][lo];
-                    const float gx = sj[warp][3][lo], gy = sj[warp][4][lo], gz = sj[warp][5][lo];
-#pragma unroll
-                    for (uint32_t uu = 0; uu < 4; ++uu) {
-                      if (uu < left) {
-                        const uint32_t ti = tfirst + uu;
-                        const float4 A = ia[ti];
-                        const float2 Bq = ib[ti];
-                        const float rx = jx - A.x, ry = jy - A.y, rz = jz - A.z;
-                        const float vx = gx - A.w, vy = gy - Bq.x, vz = gz - Bq.y;
-                        const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-                        const float Bv = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
-                        if (R <= fmaf(c1, Bv, c0) && full_test32(sq, rx, ry, rz, vx, vy, vz, Bv))
-                          emit_lane(buf, cnt, s, i0 + ti, jj);
-                      }
-                    }
-                  }
-                }
-                __syncwarp();
-                if (*cnt >= (uint32_t)(kWarpBuf / 2)) flush_lanes(buf, cnt, s, lane);
-              }
-            }
-          }
+      }
+      if (px && xa < 0) {  // cells [xa + nx, nx) seen through the image at -L
+        const uint32_t jb = __ldg(cs + colb + xa + nx), je = __ldg(cs + colb + nx);
+        if (je > jb) {
+          pc[np * 32 + lane] = make_uint2(jb, je);
+          cd[np * 32 + lane] = (uint8_t)image_code(-1, wy, wz);
+          ++np;
+          total += je - jb;
+        }
+      }
+      if (px && xb >= nx) {  // cells [0, xb - nx] seen through the image at +L
+        const uint32_t jb = __ldg(cs + colb), je = __ldg(cs + colb + xb - nx + 1);
+        if (je > jb) {
+          pc[np * 32 + lane] = make_uint2(jb, je);
+          cd[np * 32 + lane] = (uint8_t)image_code(1, wy, wz);
+          ++np;
+          total += je - jb;
         }
       }
     }
-    flush_lanes(buf, cnt, s, lane);
-    for (int o = 16; o > 0; o >>= 1) tests += __shfl_down_sync(0xFFFFFFFFu, tests, o);
-    if (lane == 0 && tests) atomicAdd(&s.d.pair_tests, tests);
   }
+
+  // 2. walk the pieces: one test per iteration
+  const uint32_t T = __reduce_max_sync(0xFFFFFFFFu, total);
+  uint32_t j = 0, je = 0;
+  int r = 0;
+  float sx = o.ox, sy = o.oy, sz = o.oz;
+  if (np > 0) {
+    const uint2 q = pc[lane];
+    const uint32_t c = cd[lane];
+    j = q.x;
+    je = q.y;
+    sx = o.ox - image_shift(c, 0, Lx);
+    sy = o.oy - image_shift(c, 1, Ly);
+    sz = o.oz - image_shift(c, 2, Lz);
+  }
+  const float c0 = g.s_c0, c1 = g.s_c1;
+  for (uint32_t t = 0; t < T; ++t) {
+    if (j < je) {
+      const float4 a = __ldg(MA + j);
+      const float2 b = __ldg(MB + j);
+      float rx = a.x - sx, ry = a.y - sy, rz = a.z - sz;
+      bool keep = false;
+      if (any_cp) {
+        if (cp0) min_image_f(rx, g.halfLf[0], g.Lf[0], g.tief[0], keep);
+        if (cp1) min_image_f(ry, g.halfLf[1], g.Lf[1], g.tief[1], keep);
+        if (cp2) min_image_f(rz, g.halfLf[2], g.Lf[2], g.tief[2], keep);
+      }
+      const float gx = a.w - o.vx, gy = b.x - o.vy, gz = b.y - o.vz;
+      const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+      const float Bv = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
+      if (keep || (R <= fmaf(c1, Bv, c0) && full_test32(sq, rx, ry, rz, gx, gy, gz, Bv)))
+        emit_lane(buf, cnt, s, p, j);
+      if (++j == je && r + 1 < np) {
+        ++r;
+        const uint2 q = pc[r * 32 + lane];
+        const uint32_t c = cd[r * 32 + lane];
+        j = q.x;
+        je = q.y;
+        sx = o.ox - image_shift(c, 0, Lx);
+        sy = o.oy - image_shift(c, 1, Ly);
+        sz = o.oz - image_shift(c, 2, Lz);
+      }
+    }
+  }
+  flush_lanes(buf, cnt, s, lane);
+  unsigned long long tests = total;
+  for (int off = 16; off > 0; off >>= 1) tests += __shfl_down_sync(0xFFFFFFFFu, tests, off);
+  if (lane == 0 && tests) atomicAdd(&s.d.pair_tests, tests);
 }
+
 
 // --------------------------------------------------------------------------- //
 // Fast particles of the speed split: one warp per fast particle p, searching cfast
@@ -911,7 +888,7 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
   __shared__ uint2 wbuf[kCellWarps][kWarpBuf];
   __shared__ uint32_t wcount[kCellWarps];
   // per stencil cell of the current batch: candidate offset, slow begin/length, fast begin,
-  // cell offset (dx, dy, dz) packed in bytes
+  // image flags (-1, 0, +1 per axis) packed in bytes
   __shared__ uint32_t soff[kCellWarps][32], sb0[kCellWarps][32], sn0[kCellWarps][32],
       sb1[kCellWarps][32], sd[kCellWarps][32];
   const int k = find_sim(B.ptile, B.nsims, blockIdx.x);
@@ -952,7 +929,7 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
   Guard32 q;
   q.c0 = g.s_c0; q.c1 = g.s_c1; q.ag = g.a_g; q.tg = g.t_g; q.dtf = g.dtf;
   q.d0up = g.d0up; q.brel = g.b_rel; q.babs = g.b_abs; q.we = g.w_e; q.wrel = g.w_rel;
-  const float wf0 = g.wf[0], wf1 = g.wf[1], wf2 = g.wf[2];
+  const float Lf0 = g.Lf[0], Lf1 = g.Lf[1], Lf2 = g.Lf[2];
   unsigned long long tests = 0;
 
   for (uint32_t f = blk * kCellWarps + warp; f < nfast; f += wstride) {
@@ -979,10 +956,13 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
         const int dy = rem / Wx - Cy;
         const int dx = rem - (dy + Cy) * Wx - Cx;
         int qx = cx + dx, qy = cy + dy, qz = cz + dz;
-        bool ok = true;
-        if (qx < 0 || qx >= nx) { ok = ok && px; qx = qx < 0 ? qx + nx : qx - nx; }
-        if (qy < 0 || qy >= ny) { ok = ok && py; qy = qy < 0 ? qy + ny : qy - ny; }
-        if (qz < 0 || qz >= nz) { ok = ok && pz; qz = qz < 0 ? qz + nz : qz - nz; }
+        const int wx = qx < 0 ? -1 : (qx >= nx ? 1 : 0);
+        const int wy = qy < 0 ? -1 : (qy >= ny ? 1 : 0);
+        const int wz = qz < 0 ? -1 : (qz >= nz ? 1 : 0);
+        const bool ok = (wx == 0 || px) && (wy == 0 || py) && (wz == 0 || pz);
+        qx -= wx * nx;
+        qy -= wy * ny;
+        qz -= wz * nz;
         if (ok) {
           const uint32_t key = col_code(g, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx + (uint32_t)qx;
           b0 = __ldg(cs + key);
@@ -992,7 +972,7 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
           if (b1 <= p) b1 = p + 1;
           n1 = e1 > b1 ? e1 - b1 : 0u;
         }
-        dpack = (uint32_t)(dx & 0xFF) | ((uint32_t)(dy & 0xFF) << 8) | ((uint32_t)(dz & 0xFF) << 16);
+        dpack = (uint32_t)(wx & 0xFF) | ((uint32_t)(wy & 0xFF) << 8) | ((uint32_t)(wz & 0xFF) << 16);
       }
       const uint32_t tot = n0 + n1;
       uint32_t incl = tot;
@@ -1037,11 +1017,12 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
             emit = !(Bv >= 0x1p-900 && R > dadd(g.c0, dmul(g.c1, Bv)));
           } else {
             const uint32_t d = sd[warp][lo];
-            const int dx = (int)(int8_t)(d & 0xFF), dy = (int)(int8_t)((d >> 8) & 0xFF),
-                      dz = (int)(int8_t)((d >> 16) & 0xFF);
-            const float sx = o32.ox - (float)dx * wf0;
-            const float sy = o32.oy - (float)dy * wf1;
-            const float sz = o32.oz - (float)dz * wf2;
+            const int wx = (int)(int8_t)(d & 0xFF), wy = (int)(int8_t)((d >> 8) & 0xFF),
+                      wz = (int)(int8_t)((d >> 16) & 0xFF);
+            // own coordinates moved by the image shift (j seen at x_j + w L)
+            const float sx = o32.ox - (float)wx * Lf0;
+            const float sy = o32.oy - (float)wy * Lf1;
+            const float sz = o32.oz - (float)wz * Lf2;
             const float4 a = __ldg(MA + j);
             const float2 b = __ldg(MB + j);
             const float rx = a.x - sx, ry = a.y - sy, rz = a.z - sz;
@@ -1066,6 +1047,16 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
 int cell_search_blocks(int precision, int K, int num_sms) {
   int per_sm = 0;
   cudaError_t e;
+  if (precision == KMC_GUARDED_FP32) {
+    // the row search keeps its piece lists in dynamic shared memory (above 48 KB for
+    // K = 2); set before any launch or capture
+    if (K == 2)
+      cudaFuncSetAttribute(k_search_rows32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)RowLayout<2>::kBytes);
+    else
+      cudaFuncSetAttribute(k_search_rows32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)RowLayout<1>::kBytes);
+  }
   if (precision == KMC_FP64)
     e = K == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_cell<KMC_FP64, 2>, kCellWarps * 32, 0)
                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_cell<KMC_FP64, 1>, kCellWarps * 32, 0);
@@ -1094,11 +1085,11 @@ int launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st) {
     if (K == 2) {
       k_search<KMC_GUARDED_FP32, 2><<<L.ptiles, kTile, 0, st>>>(L.b);
       k_search_cell32<2><<<cb, kCellWarps * 32, 0, st>>>(L.b);
-      k_search_seg32<2><<<cb, kCellWarps * 32, 0, st>>>(L.b);
+      k_search_rows32<2><<<L.ptiles, kTile, RowLayout<2>::kBytes, st>>>(L.b);
     } else {
       k_search<KMC_GUARDED_FP32, 1><<<L.ptiles, kTile, 0, st>>>(L.b);
       k_search_cell32<1><<<cb, kCellWarps * 32, 0, st>>>(L.b);
-      k_search_seg32<1><<<cb, kCellWarps * 32, 0, st>>>(L.b);
+      k_search_rows32<1><<<L.ptiles, kTile, RowLayout<1>::kBytes, st>>>(L.b);
     }
   }
   if (precision == KMC_FP64) k_search_fast<KMC_FP64><<<L.ptiles, kCellWarps * 32, 0, st>>>(L.b);

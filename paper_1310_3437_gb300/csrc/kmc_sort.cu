@@ -7,8 +7,8 @@
 //   scan      segmented exclusive scan of the counts -> cell_start (three launches,
 //             no inter-block waiting); clears the counts for the next step.
 //   k_scatter permutes the binary64 state into the other buffer, writes the
-//             binary32 cell-local mirror for the guarded search and resets the
-//             per-particle step arrays.
+//             binary32 mirror (box coordinates and velocity) for the guarded
+//             search and resets the per-particle step arrays.
 // The order inside a cell depends on atomic timing; nothing downstream depends on
 // it (argmin over a total order, integer counters, order-free profile sums).
 #include "kmc_internal.cuh"
@@ -203,7 +203,6 @@ __global__ void __launch_bounds__(kTile) k_scatter(Batch B) {
   if (!sim_active(s)) return;
   uint32_t p = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
   if (p >= s.n) return;
-  const Grid& g = s.d.grid;
   int src = s.d.parity, dstb = src ^ 1;
   uint32_t key = s.key[p];
   uint32_t dst = s.cell_start[key] + s.rank[p];
@@ -221,16 +220,8 @@ __global__ void __launch_bounds__(kTile) k_scatter(Batch B) {
   s.deg[dst] = 0;
   s.partner[dst] = kNone;
   if (s.precision == KMC_GUARDED_FP32) {
-    int c[3];
-    key_decode(g, key >= g.nkeys ? key - g.nkeys : key, c[0], c[1], c[2]);
-    float o[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      // offset from the cell's lower corner: x - c w in one binary64 fused
-      // multiply-add, then rounded once to binary32
-      o[a] = d2f_rn(g.nc[a] == 1 ? xs[a] : __fma_rn(-u2d_exact((uint32_t)c[a]), g.w[a], xs[a]));
-    }
-    s.mir_a[dst] = make_float4(o[0], o[1], o[2], d2f_rn(vs[0]));
+    // box coordinates and velocity, each rounded once to binary32
+    s.mir_a[dst] = make_float4(d2f_rn(xs[0]), d2f_rn(xs[1]), d2f_rn(xs[2]), d2f_rn(vs[0]));
     s.mir_b[dst] = make_float2(d2f_rn(vs[1]), d2f_rn(vs[2]));
   }
 }

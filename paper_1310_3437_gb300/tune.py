@@ -1,13 +1,14 @@
 """Autotuner for the knobs that change the work of a step but never its result.
 
-Knobs: the search kernel (one warp per cell, one warp per run of cells, one thread
-per particle, or the per-step automatic switch), the stencil (27 cells of width h, or
-125 cells of width h/2), the cell-size multiplier (>= 1: larger cells hold more
-particles) and how far the speed split may thin out the slow grid.  Every
-combination yields bit-identical trajectories (the tests check this), so the tuner
-only has to time them: it runs a few steps of each candidate from the same initial
-state, times them with CUDA events on the simulation's stream and keeps the
-fastest.  Choices are cached by (precision, size bucket, occupancy bucket).
+Knobs: the search kernel (one warp per cell, one lane per particle over whole
+stencil rows, one thread per particle cell by cell, or the per-step automatic
+switch), the stencil (27 cells of width h, or 125 cells of width h/2), the
+cell-size multiplier (>= 1: larger cells hold more particles) and how far the speed
+split may thin out the slow grid.  Every combination yields bit-identical
+trajectories (the tests check this), so the tuner only has to time them: it runs a
+few steps of each candidate from the same initial state, times them with CUDA
+events on the simulation's stream and keeps the fastest.  Choices are cached by
+(precision, size bucket, occupancy bucket).
 """
 from __future__ import annotations
 
@@ -19,7 +20,7 @@ from .sim import Simulation, params_from_setup
 
 DEFAULT_CANDIDATES = [
     # (search_kernel, stencil, cell_scale, split_min_occ): kernels 0 auto, 1 particle,
-    # 2 cell, 3 segment; split_min_occ = smallest mean slow-cell occupancy a speed split
+    # 2 cell, 3 row; split_min_occ = smallest mean slow-cell occupancy a speed split
     # may leave (0: no floor, 1e9: no split)
     (0, 1, 1.0, 0.0), (0, 1, 1.0, 2.0), (0, 1, 1.0, 4.0), (0, 1, 1.0, 8.0),
     (0, 1, 1.0, 1e9), (2, 1, 1.0, 1e9), (2, 1, 1.0, 16.0), (2, 1, 1.0, 8.0),

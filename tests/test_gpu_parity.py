@@ -258,9 +258,9 @@ def test_group_of_uneven_runs_equals_each_run_alone():
 
 
 @pytest.mark.parametrize("stencil", [1, 2])
-def test_segment_search_periodic_x_wrap(stencil):
-    """Short periodic x axis (few cells) with sparse cells: segments reach both column
-    ends, so partner runs wrap."""
+def test_row_search_periodic_x_wrap(stencil):
+    """Short periodic x axis (few cells) with sparse cells: stencil rows of particles
+    near either end wrap and are searched through the periodic image."""
     rng = np.random.default_rng(31)
     n = 3000
     box = (0.3, 1.0, 1.0)
@@ -293,3 +293,38 @@ def test_speed_split_forced_equilibrium_and_no_split(precision):
         sim, st, oc, _ = run_both(s, 30, precision, flags=flags)
         assert_same_counts(sim.counts(), oc)
         assert_same_state(sim, st)
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+@pytest.mark.parametrize("kernel", [0, 3])
+def test_spherical_blast_downscale_bit_exact(precision, kernel):
+    """Hot dense sphere (8x density, 100x temperature) in a periodic cube, the same
+    geometry and background mean free path at 2^16 particles: the fast tail drives the
+    speed split every step.  Trajectory and counts equal the oracle's."""
+    s = ki.blast_setup(n=1 << 16, seed=3, lam_bg=0.005, steps=25)
+    sim, st, oc, _ = run_both(s, 25, precision, search_kernel=kernel)
+    assert_same_counts(sim.counts(), oc)
+    assert_same_state(sim, st)
+    assert sum(c["collisions"] for c in oc) > 1000
+
+
+@pytest.mark.parametrize("kernel", [1, 2, 3])
+def test_long_periodic_box_near_thresholds_binary32_equals_binary64(kernel):
+    """Box coordinates up to 48 (the binary32 mirror's largest rounding errors) with
+    positions and velocities on coarse lattices, so that many pairs sit on or within
+    ulps of the t* = 0, t* = dt and d_min = d0 thresholds, some across the periodic
+    boundary: both precisions give the oracle's candidate list."""
+    rng = np.random.default_rng(77)
+    n = 6000
+    box = (48.0, 0.75, 0.75)
+    pos = [np.minimum(np.round(rng.random(n) * b * 64) / 64, np.nextafter(b, 0)) for b in box]
+    pos[0][:300] = np.nextafter(box[0], 0) - np.round(rng.random(300) * 8) / 64
+    vel = [np.round(rng.normal(0, 1, n) * 8) / 8 for _ in range(3)]
+    s = ki.Setup(n=n, box=box, bc=(0, 0, 0), d0=1 / 32, dt=1 / 16, seed=77,
+                 name="equilibrium_long_lattice")
+    st = oracle.State(pos + vel)
+    pi, pj, _, _ = oracle.candidate_pairs(s, st)
+    assert len(pi) > 200
+    for prec in (FP64, FP32):
+        sim = gpu_sim(s, pos + vel, prec, search_kernel=kernel).step(1).sync()
+        assert np.array_equal(sim.edges(), np.stack([pi, pj], axis=1))
