@@ -107,6 +107,7 @@ struct SimDev {
   float2* mir_b;        // (vy, vz)
   uint32_t* key;        // cell key per particle (pre-sort order)
   uint32_t* rank;       // rank inside the cell (pre-sort order)
+  uint32_t* src;        // pre-sort position of the particle at each sorted position
   uint32_t* skey;       // cell key per particle (sorted order)
   uint32_t* cell_count; // nkeys counters, all zero between steps
   uint32_t* cell_start; // nkeys + 1

@@ -714,10 +714,6 @@ __device__ __forceinline__ uint32_t image_code(int wx, int wy, int wz) {
   return (uint32_t)(wx > 0) | ((uint32_t)(wx < 0) << 1) | ((uint32_t)(wy > 0) << 2) |
          ((uint32_t)(wy < 0) << 3) | ((uint32_t)(wz > 0) << 4) | ((uint32_t)(wz < 0) << 5);
 }
-__device__ __forceinline__ float image_shift(uint32_t c, int axis, float L) {
-  const int w = (int)((c >> (2 * axis)) & 1u) - (int)((c >> (2 * axis + 1)) & 1u);
-  return (float)w * L;
-}
 
 template <int K>
 __global__ void __launch_bounds__(kTile) k_search_rows32(Batch B) {
@@ -726,6 +722,7 @@ __global__ void __launch_bounds__(kTile) k_search_rows32(Batch B) {
   extern __shared__ __align__(16) unsigned char rows_smem[];
   __shared__ uint32_t wcount[RL::kWarps];
   __shared__ Guard32 sq;
+  __shared__ float4 shift_tab[64];  // image shift (x, y, z) of each image code
   const int k = find_sim(B.ptile, B.nsims, blockIdx.x);
   SimDev& s = *B.sims[k];
   if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_ROW) return;
@@ -733,6 +730,13 @@ __global__ void __launch_bounds__(kTile) k_search_rows32(Batch B) {
   if (threadIdx.x == 0) {
     sq.c0 = g.s_c0; sq.c1 = g.s_c1; sq.ag = g.a_g; sq.tg = g.t_g; sq.dtf = g.dtf;
     sq.d0up = g.d0up; sq.brel = g.b_rel; sq.babs = g.b_abs; sq.we = g.w_e; sq.wrel = g.w_rel;
+  }
+  if (threadIdx.x < 64) {
+    const uint32_t c = threadIdx.x;
+    const float w0 = (float)((int)(c & 1u) - (int)((c >> 1) & 1u));
+    const float w1 = (float)((int)((c >> 2) & 1u) - (int)((c >> 3) & 1u));
+    const float w2 = (float)((int)((c >> 4) & 1u) - (int)((c >> 5) & 1u));
+    shift_tab[c] = make_float4(w0 * g.Lf[0], w1 * g.Lf[1], w2 * g.Lf[2], 0.f);
   }
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -758,7 +762,6 @@ __global__ void __launch_bounds__(kTile) k_search_rows32(Batch B) {
   const uint32_t* __restrict__ cs = s.cell_start;
   const float4* __restrict__ MA = s.mir_a;
   const float2* __restrict__ MB = s.mir_b;
-  const float Lx = g.Lf[0], Ly = g.Lf[1], Lz = g.Lf[2];
 
   // 1. the lane's non-empty pieces, column by column
   int np = 0;
@@ -832,12 +835,12 @@ __global__ void __launch_bounds__(kTile) k_search_rows32(Batch B) {
   float sx = o.ox, sy = o.oy, sz = o.oz;
   if (np > 0) {
     const uint2 q = pc[lane];
-    const uint32_t c = cd[lane];
+    const float4 sh = shift_tab[cd[lane]];
     j = q.x;
     je = q.y;
-    sx = o.ox - image_shift(c, 0, Lx);
-    sy = o.oy - image_shift(c, 1, Ly);
-    sz = o.oz - image_shift(c, 2, Lz);
+    sx = o.ox - sh.x;
+    sy = o.oy - sh.y;
+    sz = o.oz - sh.z;
   }
   const float c0 = g.s_c0, c1 = g.s_c1;
   for (uint32_t t = 0; t < T; ++t) {
@@ -859,12 +862,12 @@ __global__ void __launch_bounds__(kTile) k_search_rows32(Batch B) {
       if (++j == je && r + 1 < np) {
         ++r;
         const uint2 q = pc[r * 32 + lane];
-        const uint32_t c = cd[r * 32 + lane];
+        const float4 sh = shift_tab[cd[r * 32 + lane]];
         j = q.x;
         je = q.y;
-        sx = o.ox - image_shift(c, 0, Lx);
-        sy = o.oy - image_shift(c, 1, Ly);
-        sz = o.oz - image_shift(c, 2, Lz);
+        sx = o.ox - sh.x;
+        sy = o.oy - sh.y;
+        sz = o.oz - sh.z;
       }
     }
   }

@@ -6,7 +6,8 @@
 //             atomic increment (lanes with equal keys share one atomic).
 //   scan      segmented exclusive scan of the counts -> cell_start (three launches,
 //             no inter-block waiting); clears the counts for the next step.
-//   k_scatter permutes the binary64 state into the other buffer, writes the
+//   k_scatter records the source of every position of the new order;
+//   k_gather  permutes the binary64 state into the other buffer, writes the
 //             binary32 mirror (box coordinates and velocity) for the guarded
 //             search and resets the per-particle step arrays.
 // The order inside a cell depends on atomic timing; nothing downstream depends on
@@ -197,32 +198,50 @@ __global__ void __launch_bounds__(kTile) k_scan_apply(Batch B, int which) {
 }
 
 // --------------------------------------------------------------------------- //
+// The permutation is applied as a gather: k_scatter only records, for every
+// position of the new cell order, which particle goes there (4 bytes, scattered over
+// nearby positions -- particles move less than a cell per step); k_gather then walks
+// the new order, reads each particle from its old position (nearby reads share
+// sectors) and writes the permuted state, the mirror and the per-particle step
+// arrays with coalesced stores.
 __global__ void __launch_bounds__(kTile) k_scatter(Batch B) {
   int k = find_sim(B.ptile, B.nsims, blockIdx.x);
   SimDev& s = *B.sims[k];
   if (!sim_active(s)) return;
   uint32_t p = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
   if (p >= s.n) return;
-  int src = s.d.parity, dstb = src ^ 1;
-  uint32_t key = s.key[p];
-  uint32_t dst = s.cell_start[key] + s.rank[p];
+  s.src[s.cell_start[s.key[p]] + s.rank[p]] = p;
+}
+
+__global__ void __launch_bounds__(kTile) k_gather(Batch B) {
+  int k = find_sim(B.ptile, B.nsims, blockIdx.x);
+  SimDev& s = *B.sims[k];
+  if (!sim_active(s)) return;
+  uint32_t d = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
+  if (d >= s.n) return;
+  const int from = s.d.parity, to = from ^ 1;
+  const uint32_t p = s.src[d];
   double xs[3], vs[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    xs[a] = s.x[src][a][p];
-    vs[a] = s.v[src][a][p];
-    s.x[dstb][a][dst] = xs[a];
-    s.v[dstb][a][dst] = vs[a];
+    xs[a] = s.x[from][a][p];
+    vs[a] = s.v[from][a][p];
   }
-  s.id[dstb][dst] = s.id[src][p];
-  s.last[dstb][dst] = s.last[src][p];
-  s.skey[dst] = key;
-  s.deg[dst] = 0;
-  s.partner[dst] = kNone;
+  const uint32_t id = s.id[from][p], last = s.last[from][p], key = s.key[p];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    s.x[to][a][d] = xs[a];
+    s.v[to][a][d] = vs[a];
+  }
+  s.id[to][d] = id;
+  s.last[to][d] = last;
+  s.skey[d] = key;
+  s.deg[d] = 0;
+  s.partner[d] = kNone;
   if (s.precision == KMC_GUARDED_FP32) {
     // box coordinates and velocity, each rounded once to binary32
-    s.mir_a[dst] = make_float4(d2f_rn(xs[0]), d2f_rn(xs[1]), d2f_rn(xs[2]), d2f_rn(vs[0]));
-    s.mir_b[dst] = make_float2(d2f_rn(vs[1]), d2f_rn(vs[2]));
+    s.mir_a[d] = make_float4(d2f_rn(xs[0]), d2f_rn(xs[1]), d2f_rn(xs[2]), d2f_rn(vs[0]));
+    s.mir_b[d] = make_float2(d2f_rn(vs[1]), d2f_rn(vs[2]));
   }
 }
 
@@ -239,7 +258,8 @@ int launch_sort(const LaunchPlan& L, cudaStream_t st) {
   k_count<<<L.ptiles, kTile, 0, st>>>(L.b);
   int n = launch_seg_scan(L, 0, st);
   k_scatter<<<L.ptiles, kTile, 0, st>>>(L.b);
-  return n + 2;
+  k_gather<<<L.ptiles, kTile, 0, st>>>(L.b);
+  return n + 3;
 }
 
 }  // namespace kmc
