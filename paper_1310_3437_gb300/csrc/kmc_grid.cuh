@@ -165,6 +165,7 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
   const bool split = best > 0;
   const double S1 = split ? sqrt((double)s1sq) : V;
   g.split = split ? 1u : 0u;
+  g.split_t = best;
   g.s1sq = s1sq;
   // trial thresholds for the next step (counted by the push of this step)
   for (int t = 0; t < kSplitTrials; ++t) {

@@ -42,7 +42,7 @@ struct Grid {
   int32_t nc[3];      // cells per axis; 1 means the axis is one cell (no stencil on it)
   int32_t K;          // stencil radius in cells
   int32_t mode;       // search kernel of this step: KMC_SEARCH_PARTICLE, _CELL or _ROW
-  int32_t pad1;
+  int32_t split_t;    // trial threshold index of the split (0: no split)
   uint32_t split;     // 1: particles with |v|^2 above s1sq form a second population
   float s1sq;         // binary32 split threshold on the upper bound of |v|^2
   int32_t cfast[3];   // fast particles search cfast cells on each side (split axes)
@@ -107,6 +107,8 @@ struct SimDev {
   float2* mir_b;        // (vy, vz)
   uint32_t* key;        // cell key per particle (pre-sort order)
   uint32_t* rank;       // rank inside the cell (pre-sort order)
+  uint8_t* vbucket;     // per particle: how many of the trial split thresholds its
+                        // |v|^2 bound exceeds (written by the push, read by the count)
   uint32_t* src;        // pre-sort position of the particle at each sorted position
   uint32_t* skey;       // cell key per particle (sorted order)
   uint32_t* cell_count; // nkeys counters, all zero between steps
@@ -271,12 +273,17 @@ struct LaunchPlan {
   uint32_t ptiles, stiles_n, stiles_c, prtiles;
   int edge_blocks;
   int cell_blocks;  // persistent grid of the warp-per-cell search
+  int part_blocks;  // grid-stride grids of the particle, row and fast searches
+  int row_blocks;
+  int fast_blocks;
 };
 
 // each returns the number of kernels it launched
 int launch_sort(const LaunchPlan& L, cudaStream_t st);
 int launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st);
-int cell_search_blocks(int precision, int K, int num_sms);
+// resident-block grids of the search kernels (and the row search's shared-memory
+// attribute); called when a launch plan is built, before any capture
+void search_grids(int precision, int K, int num_sms, uint32_t ptiles, LaunchPlan& L);
 int launch_match(const LaunchPlan& L, int max_rounds, cudaStream_t st);
 int launch_push(const LaunchPlan& L, cudaStream_t st);
 int launch_init_grid(const LaunchPlan& L, cudaStream_t st);

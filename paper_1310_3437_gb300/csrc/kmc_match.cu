@@ -41,22 +41,38 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
 // u1, u2 uniform in [-1, 1) from 32-bit words, s = u1^2 + u2^2 accepted if
 // 0 < s < 1, n = (2 u1 sqrt(1-s), 2 u2 sqrt(1-s), 1 - 2 s).  Counter (id, step lo,
 // k, step hi), key (seed lo, seed hi); two attempts per Philox call.
+// u = w 2^-31 - 1 for a 32-bit word w, built with integer operations: the value is
+// (w - 2^31) 2^-31 exactly (32 significant bits at most), so the bits equal those of
+// the binary64 expression, without its conversion, product and difference on the
+// binary64 pipe.
+__device__ __forceinline__ double word_uniform(uint32_t w) {
+  const long long m = (long long)w - 2147483648ll;
+  if (m == 0) return 0.0;
+  const unsigned long long neg = m < 0 ? 1ull : 0ull;
+  const unsigned long long a = (unsigned long long)(m < 0 ? -m : m);  // 1 .. 2^31
+  const int e = 63 - __clzll((long long)a);
+  const unsigned long long mant = (a << (52 - e)) & 0xFFFFFFFFFFFFFull;
+  return __longlong_as_double((long long)((neg << 63) | ((unsigned long long)(1023 + e - 31) << 52) | mant));
+}
+
 __device__ bool sphere_point(uint64_t seed, uint64_t step, uint32_t id, double nv[3]) {
   for (uint32_t k = 0; k < 64; ++k) {
     uint32_t c[4] = {id, (uint32_t)step, k, (uint32_t)(step >> 32)};
     philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      double u1 = dsub(dmul((double)c[2 * a], 0x1p-31), 1.0);
-      double u2 = dsub(dmul((double)c[2 * a + 1], 0x1p-31), 1.0);
-      double s = dadd(dmul(u1, u1), dmul(u2, u2));
-      if (s > 0.0 && s < 1.0) {
-        double q = dsqrt(dsub(1.0, s));
-        nv[0] = dmul(dadd(u1, u1), q);
-        nv[1] = dmul(dadd(u2, u2), q);
-        nv[2] = dsub(1.0, dadd(s, s));
-        return true;
-      }
+    // both attempts of the call are evaluated and the first accepted one is kept, so
+    // that lanes whose first attempt fails do not split the warp
+    const double u1a = word_uniform(c[0]), u2a = word_uniform(c[1]);
+    const double u1b = word_uniform(c[2]), u2b = word_uniform(c[3]);
+    const double sa = dadd(dmul(u1a, u1a), dmul(u2a, u2a));
+    const double sb = dadd(dmul(u1b, u1b), dmul(u2b, u2b));
+    const bool oka = sa > 0.0 && sa < 1.0, okb = sb > 0.0 && sb < 1.0;
+    if (oka || okb) {
+      const double u1 = oka ? u1a : u1b, u2 = oka ? u2a : u2b, s = oka ? sa : sb;
+      const double q = dsqrt(dsub(1.0, s));
+      nv[0] = dmul(dadd(u1, u1), q);
+      nv[1] = dmul(dadd(u2, u2), q);
+      nv[2] = dsub(1.0, dadd(s, s));
+      return true;
     }
   }
   return false;

@@ -118,13 +118,18 @@ __global__ void __launch_bounds__(kTile) k_push(Batch B) {
   }
   if (s.split_ok) {
     // particles above each trial split threshold: warp ballots, shared counters, one
-    // global atomic per block and trial
+    // global atomic per block and trial; each particle keeps how many thresholds it
+    // exceeds, which is all the next step's count needs to classify it
     const bool valid = p < s.n;
+    uint32_t above = 0;
 #pragma unroll
     for (int t = 1; t < kSplitTrials; ++t) {
-      unsigned m = __ballot_sync(0xFFFFFFFFu, valid && vm > s.d.split_thr[t]);
+      const bool hi = valid && vm > s.d.split_thr[t];
+      above += hi ? 1u : 0u;
+      unsigned m = __ballot_sync(0xFFFFFFFFu, hi);
       if ((threadIdx.x & 31) == 0 && m) atomicAdd(&scnt[t], (uint32_t)__popc(m));
     }
+    if (valid) s.vbucket[p] = (uint8_t)above;
   }
   block_max_to(&s.d.vmax2_acc, vm);  // its block barrier also orders the shared counters
   if (s.split_ok && threadIdx.x > 0 && threadIdx.x < kSplitTrials && scnt[threadIdx.x])

@@ -17,6 +17,8 @@
 //                     bounds the binary32 error (kmc_grid.cuh derives the bands).
 // A pair that passes the binary64 predicate is never culled by either variant, so
 // both variants produce exactly the candidate list of the binary64 definition.
+#include <algorithm>
+
 #include "kmc_internal.cuh"
 
 namespace kmc {
@@ -31,183 +33,201 @@ __device__ __forceinline__ void min_image_f(float& r, float halfL, float L, floa
   else if (ar > halfL) r = r > 0.f ? r - L : r + L;
 }
 
+// block-uniform: does any simulation of the batch run this step with the given search
+// (mode < 0: the fast-particle search, i.e. any simulation under the speed split)?
+__device__ __forceinline__ bool batch_uses(const Batch& B, int mode) {
+  bool any = false;
+  for (int q = threadIdx.x; q < B.nsims; q += blockDim.x) {
+    const SimDev& t = *B.sims[q];
+    any = any || (sim_active(t) && (mode < 0 ? t.d.grid.split != 0u : t.d.grid.mode == mode));
+  }
+  return __syncthreads_or(any) != 0;
+}
+
 template <int PREC, int K>
 __global__ void __launch_bounds__(kTile) k_search(Batch B) {
   __shared__ uint2 sbuf[kSearchBuf];
   __shared__ uint32_t scnt, sbase;
   __shared__ unsigned long long stests;
-  int k = find_sim(B.ptile, B.nsims, blockIdx.x);
-  SimDev& s = *B.sims[k];
-  if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_PARTICLE) return;
-  if (threadIdx.x == 0) { scnt = 0; stests = 0; }
-  __syncthreads();
+  // grid-stride over tiles of kTile particles (an occupancy-sized grid: the kernel is
+  // launched every step and exits at once when the step runs another search)
+  if (!batch_uses(B, KMC_SEARCH_PARTICLE)) return;
+  const uint32_t ntiles = B.ptile[B.nsims];
+  for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int k = find_sim(B.ptile, B.nsims, tile);
+    SimDev& s = *B.sims[k];
+    if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_PARTICLE) continue;
+    __syncthreads();  // the previous tile's flush has read the staging buffer
+    if (threadIdx.x == 0) { scnt = 0; stests = 0; }
+    __syncthreads();
 
-  const Grid g = s.d.grid;
-  const uint32_t n = s.n;
-  const int cur = s.d.parity ^ 1;
-  const uint32_t* __restrict__ cs = s.cell_start;
-  const uint32_t edge_cap = s.edge_cap;
-  uint2* __restrict__ edges = s.edge;
-  const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
-  const int Kx = nx == 1 ? 0 : K, Ky = ny == 1 ? 0 : K, Kz = nz == 1 ? 0 : K;
-  const bool px = s.bc[0] == KMC_PERIODIC, py = s.bc[1] == KMC_PERIODIC,
-             pz = s.bc[2] == KMC_PERIODIC;
-  unsigned long long tests = 0;
+    const Grid g = s.d.grid;
+    const uint32_t n = s.n;
+    const int cur = s.d.parity ^ 1;
+    const uint32_t* __restrict__ cs = s.cell_start;
+    const uint32_t edge_cap = s.edge_cap;
+    uint2* __restrict__ edges = s.edge;
+    const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
+    const int Kx = nx == 1 ? 0 : K, Ky = ny == 1 ? 0 : K, Kz = nz == 1 ? 0 : K;
+    const bool px = s.bc[0] == KMC_PERIODIC, py = s.bc[1] == KMC_PERIODIC,
+               pz = s.bc[2] == KMC_PERIODIC;
+    unsigned long long tests = 0;
 
-  uint32_t p = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
-  // with the speed split only the slow population (keys below nkeys) is searched here
-  const uint32_t nslow = g.split ? __ldg(cs + g.nkeys) : n;
-  if (p < nslow) {
-    int cx, cy, cz;
-    key_decode(g, s.skey[p], cx, cy, cz);
+    uint32_t p = (tile - B.ptile[k]) * kTile + threadIdx.x;
+    // with the speed split only the slow population (keys below nkeys) is searched here
+    const uint32_t nslow = g.split ? __ldg(cs + g.nkeys) : n;
+    if (p < nslow) {
+      int cx, cy, cz;
+      key_decode(g, s.skey[p], cx, cy, cz);
 
-    // own record
-    double xo[3], vo[3];
-    Own32 o32;
-    const double* __restrict__ X0 = s.x[cur][0];
-    const double* __restrict__ X1 = s.x[cur][1];
-    const double* __restrict__ X2 = s.x[cur][2];
-    const double* __restrict__ V0 = s.v[cur][0];
-    const double* __restrict__ V1 = s.v[cur][1];
-    const double* __restrict__ V2 = s.v[cur][2];
-    const float4* __restrict__ MA = s.mir_a;
-    const float2* __restrict__ MB = s.mir_b;
-    if (PREC == KMC_FP64) {
-      xo[0] = X0[p]; xo[1] = X1[p]; xo[2] = X2[p];
-      vo[0] = V0[p]; vo[1] = V1[p]; vo[2] = V2[p];
-    } else {
-      float4 a = MA[p];
-      float2 b = MB[p];
-      o32 = {a.x, a.y, a.z, a.w, b.x, b.y};
-    }
-    // one-cell periodic axes need the minimum image explicitly
-    const bool cp0 = nx == 1 && px, cp1 = ny == 1 && py, cp2 = nz == 1 && pz;
-    const bool any_cp = cp0 || cp1 || cp2;
-    const double L0 = s.box[0], L1 = s.box[1], L2 = s.box[2];
-
-    // a neighbour reached across a periodic boundary is seen as its image: wrap
-    // flags -1 (below 0) or +1 (at or above the extent) per axis
-    for (int dz = 0; dz <= Kz; ++dz) {
-      int qz = cz + dz, wz = 0;
-      if (qz >= nz) {
-        if (!pz) break;
-        qz -= nz;
-        wz = 1;
+      // own record
+      double xo[3], vo[3];
+      Own32 o32;
+      const double* __restrict__ X0 = s.x[cur][0];
+      const double* __restrict__ X1 = s.x[cur][1];
+      const double* __restrict__ X2 = s.x[cur][2];
+      const double* __restrict__ V0 = s.v[cur][0];
+      const double* __restrict__ V1 = s.v[cur][1];
+      const double* __restrict__ V2 = s.v[cur][2];
+      const float4* __restrict__ MA = s.mir_a;
+      const float2* __restrict__ MB = s.mir_b;
+      if (PREC == KMC_FP64) {
+        xo[0] = X0[p]; xo[1] = X1[p]; xo[2] = X2[p];
+        vo[0] = V0[p]; vo[1] = V1[p]; vo[2] = V2[p];
+      } else {
+        float4 a = MA[p];
+        float2 b = MB[p];
+        o32 = {a.x, a.y, a.z, a.w, b.x, b.y};
       }
-      for (int dy = (dz == 0 ? 0 : -Ky); dy <= Ky; ++dy) {
-        int qy = cy + dy, wy = 0;
-        if (qy < 0) {
-          if (!py) continue;
-          qy += ny;
-          wy = -1;
-        } else if (qy >= ny) {
-          if (!py) continue;
-          qy -= ny;
-          wy = 1;
+      // one-cell periodic axes need the minimum image explicitly
+      const bool cp0 = nx == 1 && px, cp1 = ny == 1 && py, cp2 = nz == 1 && pz;
+      const bool any_cp = cp0 || cp1 || cp2;
+      const double L0 = s.box[0], L1 = s.box[1], L2 = s.box[2];
+
+      // a neighbour reached across a periodic boundary is seen as its image: wrap
+      // flags -1 (below 0) or +1 (at or above the extent) per axis
+      for (int dz = 0; dz <= Kz; ++dz) {
+        int qz = cz + dz, wz = 0;
+        if (qz >= nz) {
+          if (!pz) break;
+          qz -= nz;
+          wz = 1;
         }
-        const uint32_t colbase = col_code(g, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx;
-        const int dx0 = (dz == 0 && dy == 0) ? 0 : -Kx;
-        for (int dx = dx0; dx <= Kx; ++dx) {
-          int qx = cx + dx, wx = 0;
-          if (qx < 0) {
-            if (!px) continue;
-            qx += nx;
-            wx = -1;
-          } else if (qx >= nx) {
-            if (!px) continue;
-            qx -= nx;
-            wx = 1;
+        for (int dy = (dz == 0 ? 0 : -Ky); dy <= Ky; ++dy) {
+          int qy = cy + dy, wy = 0;
+          if (qy < 0) {
+            if (!py) continue;
+            qy += ny;
+            wy = -1;
+          } else if (qy >= ny) {
+            if (!py) continue;
+            qy -= ny;
+            wy = 1;
           }
-          const uint32_t key = colbase + (uint32_t)qx;
-          uint32_t beg = __ldg(cs + key), end = __ldg(cs + key + 1);
-          if (dz == 0 && dy == 0 && dx == 0) beg = p + 1;
-          if (beg >= end) continue;
-          tests += end - beg;
-          if (PREC == KMC_FP64) {
-            for (uint32_t j = beg; j < end; ++j) {
-              double r0 = dsub(__ldg(X0 + j), xo[0]);
-              double r1 = dsub(__ldg(X1 + j), xo[1]);
-              double r2 = dsub(__ldg(X2 + j), xo[2]);
-              if (px) { if (r0 > 0.5 * L0) r0 = dsub(r0, L0); else if (r0 < -0.5 * L0) r0 = dadd(r0, L0); }
-              if (py) { if (r1 > 0.5 * L1) r1 = dsub(r1, L1); else if (r1 < -0.5 * L1) r1 = dadd(r1, L1); }
-              if (pz) { if (r2 > 0.5 * L2) r2 = dsub(r2, L2); else if (r2 < -0.5 * L2) r2 = dadd(r2, L2); }
-              double g0 = dsub(__ldg(V0 + j), vo[0]);
-              double g1 = dsub(__ldg(V1 + j), vo[1]);
-              double g2 = dsub(__ldg(V2 + j), vo[2]);
-              double R = dadd(dadd(dmul(r0, r0), dmul(r1, r1)), dmul(r2, r2));
-              double Bv = dadd(dadd(dmul(g0, g0), dmul(g1, g1)), dmul(g2, g2));
-              if (Bv >= 0x1p-900 && R > dadd(g.c0, dmul(g.c1, Bv))) continue;
-              uint32_t pos = atomicAdd(&scnt, 1u);
-              if (pos < (uint32_t)kSearchBuf) {
-                sbuf[pos] = make_uint2(p, j);
-              } else {
-                uint32_t gpos = atomicAdd(&s.d.n_raw, 1u);
-                if (gpos < edge_cap) edges[gpos] = make_uint2(p, j);
-                else atomicOr(&s.d.status, ST_EDGE_OVERFLOW);
+          const uint32_t colbase = col_code(g, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx;
+          const int dx0 = (dz == 0 && dy == 0) ? 0 : -Kx;
+          for (int dx = dx0; dx <= Kx; ++dx) {
+            int qx = cx + dx, wx = 0;
+            if (qx < 0) {
+              if (!px) continue;
+              qx += nx;
+              wx = -1;
+            } else if (qx >= nx) {
+              if (!px) continue;
+              qx -= nx;
+              wx = 1;
+            }
+            const uint32_t key = colbase + (uint32_t)qx;
+            uint32_t beg = __ldg(cs + key), end = __ldg(cs + key + 1);
+            if (dz == 0 && dy == 0 && dx == 0) beg = p + 1;
+            if (beg >= end) continue;
+            tests += end - beg;
+            if (PREC == KMC_FP64) {
+              for (uint32_t j = beg; j < end; ++j) {
+                double r0 = dsub(__ldg(X0 + j), xo[0]);
+                double r1 = dsub(__ldg(X1 + j), xo[1]);
+                double r2 = dsub(__ldg(X2 + j), xo[2]);
+                if (px) { if (r0 > 0.5 * L0) r0 = dsub(r0, L0); else if (r0 < -0.5 * L0) r0 = dadd(r0, L0); }
+                if (py) { if (r1 > 0.5 * L1) r1 = dsub(r1, L1); else if (r1 < -0.5 * L1) r1 = dadd(r1, L1); }
+                if (pz) { if (r2 > 0.5 * L2) r2 = dsub(r2, L2); else if (r2 < -0.5 * L2) r2 = dadd(r2, L2); }
+                double g0 = dsub(__ldg(V0 + j), vo[0]);
+                double g1 = dsub(__ldg(V1 + j), vo[1]);
+                double g2 = dsub(__ldg(V2 + j), vo[2]);
+                double R = dadd(dadd(dmul(r0, r0), dmul(r1, r1)), dmul(r2, r2));
+                double Bv = dadd(dadd(dmul(g0, g0), dmul(g1, g1)), dmul(g2, g2));
+                if (Bv >= 0x1p-900 && R > dadd(g.c0, dmul(g.c1, Bv))) continue;
+                uint32_t pos = atomicAdd(&scnt, 1u);
+                if (pos < (uint32_t)kSearchBuf) {
+                  sbuf[pos] = make_uint2(p, j);
+                } else {
+                  uint32_t gpos = atomicAdd(&s.d.n_raw, 1u);
+                  if (gpos < edge_cap) edges[gpos] = make_uint2(p, j);
+                  else atomicOr(&s.d.status, ST_EDGE_OVERFLOW);
+                }
+              }
+            } else {
+              // own coordinates moved by the image shift (j seen at x_j + w L)
+              const float sx = o32.ox - (float)wx * g.Lf[0];
+              const float sy = o32.oy - (float)wy * g.Lf[1];
+              const float sz = o32.oz - (float)wz * g.Lf[2];
+              for (uint32_t j = beg; j < end; ++j) {
+                const float4 a = __ldg(MA + j);
+                const float2 b = __ldg(MB + j);
+                float rx = a.x - sx, ry = a.y - sy, rz = a.z - sz;
+                bool keep = false;
+                if (any_cp) {
+                  // minimum image on one-cell periodic axes; near the tie the two
+                  // images are both possible in binary64: keep the pair unculled
+                  if (cp0) min_image_f(rx, g.halfLf[0], g.Lf[0], g.tief[0], keep);
+                  if (cp1) min_image_f(ry, g.halfLf[1], g.Lf[1], g.tief[1], keep);
+                  if (cp2) min_image_f(rz, g.halfLf[2], g.Lf[2], g.tief[2], keep);
+                }
+                const float gx = a.w - o32.vx, gy = b.x - o32.vy, gz = b.y - o32.vz;
+                const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+                const float Bv = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
+                if (!keep) {
+                  if (R > fmaf(g.s_c1, Bv, g.s_c0)) continue;
+                  // rare: full guarded test on the sphere survivors
+                  const float A = -fmaf(rz, gz, fmaf(ry, gy, rx * gx));
+                  if (A < -g.a_g) continue;
+                  if (fmaf(-g.dtf, Bv, A) > g.t_g) continue;
+                  const float wx = fmaf(ry, gz, -(rz * gy));
+                  const float wy = fmaf(rz, gx, -(rx * gz));
+                  const float wz = fmaf(rx, gy, -(ry * gx));
+                  const float W = fmaf(wz, wz, fmaf(wy, wy, wx * wx));
+                  const float thr = fmaf(g.d0up, sqrtf(fmaf(Bv, g.b_rel, g.b_abs)), g.w_e);
+                  if (W > thr * thr * g.w_rel) continue;
+                }
+                uint32_t pos = atomicAdd(&scnt, 1u);
+                if (pos < (uint32_t)kSearchBuf) {
+                  sbuf[pos] = make_uint2(p, j);
+                } else {
+                  uint32_t gpos = atomicAdd(&s.d.n_raw, 1u);
+                  if (gpos < edge_cap) edges[gpos] = make_uint2(p, j);
+                  else atomicOr(&s.d.status, ST_EDGE_OVERFLOW);
+                }
               }
             }
-          } else {
-            // own coordinates moved by the image shift (j seen at x_j + w L)
-            const float sx = o32.ox - (float)wx * g.Lf[0];
-            const float sy = o32.oy - (float)wy * g.Lf[1];
-            const float sz = o32.oz - (float)wz * g.Lf[2];
-            for (uint32_t j = beg; j < end; ++j) {
-              const float4 a = __ldg(MA + j);
-              const float2 b = __ldg(MB + j);
-              float rx = a.x - sx, ry = a.y - sy, rz = a.z - sz;
-              bool keep = false;
-              if (any_cp) {
-                // minimum image on one-cell periodic axes; near the tie the two
-                // images are both possible in binary64: keep the pair unculled
-                if (cp0) min_image_f(rx, g.halfLf[0], g.Lf[0], g.tief[0], keep);
-                if (cp1) min_image_f(ry, g.halfLf[1], g.Lf[1], g.tief[1], keep);
-                if (cp2) min_image_f(rz, g.halfLf[2], g.Lf[2], g.tief[2], keep);
-              }
-              const float gx = a.w - o32.vx, gy = b.x - o32.vy, gz = b.y - o32.vz;
-              const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-              const float Bv = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
-              if (!keep) {
-                if (R > fmaf(g.s_c1, Bv, g.s_c0)) continue;
-                // rare: full guarded test on the sphere survivors
-                const float A = -fmaf(rz, gz, fmaf(ry, gy, rx * gx));
-                if (A < -g.a_g) continue;
-                if (fmaf(-g.dtf, Bv, A) > g.t_g) continue;
-                const float wx = fmaf(ry, gz, -(rz * gy));
-                const float wy = fmaf(rz, gx, -(rx * gz));
-                const float wz = fmaf(rx, gy, -(ry * gx));
-                const float W = fmaf(wz, wz, fmaf(wy, wy, wx * wx));
-                const float thr = fmaf(g.d0up, sqrtf(fmaf(Bv, g.b_rel, g.b_abs)), g.w_e);
-                if (W > thr * thr * g.w_rel) continue;
-              }
-              uint32_t pos = atomicAdd(&scnt, 1u);
-              if (pos < (uint32_t)kSearchBuf) {
-                sbuf[pos] = make_uint2(p, j);
-              } else {
-                uint32_t gpos = atomicAdd(&s.d.n_raw, 1u);
-                if (gpos < edge_cap) edges[gpos] = make_uint2(p, j);
-                else atomicOr(&s.d.status, ST_EDGE_OVERFLOW);
-              }
-            }
           }
         }
       }
     }
-  }
 
-  // block totals: pair tests and the staged pairs
-  for (int o = 16; o > 0; o >>= 1) tests += __shfl_down_sync(0xFFFFFFFFu, tests, o);
-  if ((threadIdx.x & 31) == 0 && tests) atomicAdd(&stests, tests);
-  __syncthreads();
-  uint32_t cnt = scnt < (uint32_t)kSearchBuf ? scnt : (uint32_t)kSearchBuf;
-  if (threadIdx.x == 0) {
-    if (stests) atomicAdd(&s.d.pair_tests, stests);
-    sbase = cnt ? atomicAdd(&s.d.n_raw, cnt) : 0u;
-  }
-  __syncthreads();
-  for (uint32_t i = threadIdx.x; i < cnt; i += kTile) {
-    uint32_t gpos = sbase + i;
-    if (gpos < edge_cap) edges[gpos] = sbuf[i];
-    else atomicOr(&s.d.status, ST_EDGE_OVERFLOW);
+    // block totals: pair tests and the staged pairs
+    for (int o = 16; o > 0; o >>= 1) tests += __shfl_down_sync(0xFFFFFFFFu, tests, o);
+    if ((threadIdx.x & 31) == 0 && tests) atomicAdd(&stests, tests);
+    __syncthreads();
+    uint32_t cnt = scnt < (uint32_t)kSearchBuf ? scnt : (uint32_t)kSearchBuf;
+    if (threadIdx.x == 0) {
+      if (stests) atomicAdd(&s.d.pair_tests, stests);
+      sbase = cnt ? atomicAdd(&s.d.n_raw, cnt) : 0u;
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < cnt; i += kTile) {
+      uint32_t gpos = sbase + i;
+      if (gpos < edge_cap) edges[gpos] = sbuf[i];
+      else atomicOr(&s.d.status, ST_EDGE_OVERFLOW);
+    }
   }
 }
 
@@ -723,158 +743,165 @@ __global__ void __launch_bounds__(kTile) k_search_rows32(Batch B) {
   __shared__ uint32_t wcount[RL::kWarps];
   __shared__ Guard32 sq;
   __shared__ float4 shift_tab[64];  // image shift (x, y, z) of each image code
-  const int k = find_sim(B.ptile, B.nsims, blockIdx.x);
-  SimDev& s = *B.sims[k];
-  if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_ROW) return;
-  const Grid& g = s.d.grid;
-  if (threadIdx.x == 0) {
-    sq.c0 = g.s_c0; sq.c1 = g.s_c1; sq.ag = g.a_g; sq.tg = g.t_g; sq.dtf = g.dtf;
-    sq.d0up = g.d0up; sq.brel = g.b_rel; sq.babs = g.b_abs; sq.we = g.w_e; sq.wrel = g.w_rel;
-  }
-  if (threadIdx.x < 64) {
-    const uint32_t c = threadIdx.x;
-    const float w0 = (float)((int)(c & 1u) - (int)((c >> 1) & 1u));
-    const float w1 = (float)((int)((c >> 2) & 1u) - (int)((c >> 3) & 1u));
-    const float w2 = (float)((int)((c >> 4) & 1u) - (int)((c >> 5) & 1u));
-    shift_tab[c] = make_float4(w0 * g.Lf[0], w1 * g.Lf[1], w2 * g.Lf[2], 0.f);
-  }
-  __syncthreads();
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  const uint32_t nslow = g.split ? __ldg(s.cell_start + g.nkeys) : s.n;
-  const uint32_t p = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
-  if (p - lane >= nslow) return;  // the whole warp is past the slow population
-  uint2* pc = reinterpret_cast<uint2*>(rows_smem) + (size_t)warp * NP * 32;
-  uint8_t* cd = rows_smem + RL::kPieceBytes + (size_t)warp * NP * 32;
-  uint2* buf = reinterpret_cast<uint2*>(rows_smem + RL::kPieceBytes + RL::kCodeBytes) +
-               (size_t)warp * kWarpBuf;
-  uint32_t* cnt = &wcount[warp];
-  if (lane == 0) *cnt = 0;
-  __syncwarp();
+  // grid-stride over tiles of kTile particles: the kernel is launched every step on an
+  // occupancy-sized grid and exits at once when the step runs another search
+  if (!batch_uses(B, KMC_SEARCH_ROW)) return;
+  const uint32_t ntiles = B.ptile[B.nsims];
+  for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int k = find_sim(B.ptile, B.nsims, tile);
+    SimDev& s = *B.sims[k];
+    if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_ROW) continue;
+    const Grid& g = s.d.grid;
+    __syncthreads();  // the previous tile is done with the shared constants
+    if (threadIdx.x == 0) {
+      sq.c0 = g.s_c0; sq.c1 = g.s_c1; sq.ag = g.a_g; sq.tg = g.t_g; sq.dtf = g.dtf;
+      sq.d0up = g.d0up; sq.brel = g.b_rel; sq.babs = g.b_abs; sq.we = g.w_e; sq.wrel = g.w_rel;
+    }
+    if (threadIdx.x < 64) {
+      const uint32_t c = threadIdx.x;
+      const float w0 = (float)((int)(c & 1u) - (int)((c >> 1) & 1u));
+      const float w1 = (float)((int)((c >> 2) & 1u) - (int)((c >> 3) & 1u));
+      const float w2 = (float)((int)((c >> 4) & 1u) - (int)((c >> 5) & 1u));
+      shift_tab[c] = make_float4(w0 * g.Lf[0], w1 * g.Lf[1], w2 * g.Lf[2], 0.f);
+    }
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t nslow = g.split ? __ldg(s.cell_start + g.nkeys) : s.n;
+    const uint32_t p = (tile - B.ptile[k]) * kTile + threadIdx.x;
+    if (p - lane >= nslow) continue;  // the whole warp is past the slow population
+    uint2* pc = reinterpret_cast<uint2*>(rows_smem) + (size_t)warp * NP * 32;
+    uint8_t* cd = rows_smem + RL::kPieceBytes + (size_t)warp * NP * 32;
+    uint2* buf = reinterpret_cast<uint2*>(rows_smem + RL::kPieceBytes + RL::kCodeBytes) +
+                 (size_t)warp * kWarpBuf;
+    uint32_t* cnt = &wcount[warp];
+    if (lane == 0) *cnt = 0;
+    __syncwarp();
 
-  const bool valid = p < nslow;
-  const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
-  const int Kx = nx == 1 ? 0 : K, Ky = ny == 1 ? 0 : K, Kz = nz == 1 ? 0 : K;
-  const bool px = s.bc[0] == KMC_PERIODIC, py = s.bc[1] == KMC_PERIODIC,
-             pz = s.bc[2] == KMC_PERIODIC;
-  // one-cell periodic axes need the minimum image explicitly
-  const bool cp0 = nx == 1 && px, cp1 = ny == 1 && py, cp2 = nz == 1 && pz;
-  const bool any_cp = cp0 || cp1 || cp2;
-  const uint32_t* __restrict__ cs = s.cell_start;
-  const float4* __restrict__ MA = s.mir_a;
-  const float2* __restrict__ MB = s.mir_b;
+    const bool valid = p < nslow;
+    const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
+    const int Kx = nx == 1 ? 0 : K, Ky = ny == 1 ? 0 : K, Kz = nz == 1 ? 0 : K;
+    const bool px = s.bc[0] == KMC_PERIODIC, py = s.bc[1] == KMC_PERIODIC,
+               pz = s.bc[2] == KMC_PERIODIC;
+    // one-cell periodic axes need the minimum image explicitly
+    const bool cp0 = nx == 1 && px, cp1 = ny == 1 && py, cp2 = nz == 1 && pz;
+    const bool any_cp = cp0 || cp1 || cp2;
+    const uint32_t* __restrict__ cs = s.cell_start;
+    const float4* __restrict__ MA = s.mir_a;
+    const float2* __restrict__ MB = s.mir_b;
 
-  // 1. the lane's non-empty pieces, column by column
-  int np = 0;
-  uint32_t total = 0;
-  Own32 o = {0, 0, 0, 0, 0, 0};
-  if (valid) {
-    int cx, cy, cz;
-    key_decode(g, s.skey[p], cx, cy, cz);
-    const float4 a = MA[p];
-    const float2 b = MB[p];
-    o = {a.x, a.y, a.z, a.w, b.x, b.y};
-#pragma unroll
-    for (int c = 0; c < RL::kCols; ++c) {
-      const int dz = c <= K ? 0 : 1 + (c - K - 1) / (2 * K + 1);
-      const int dy = c == 0 ? 0 : (c <= K ? c : (c - K - 1) % (2 * K + 1) - K);
-      if (dz > Kz || dy > Ky || dy < -Ky) continue;
-      int qz = cz + dz, wz = 0;
-      if (qz >= nz) {
-        if (!pz) continue;
-        qz -= nz;
-        wz = 1;
-      }
-      int qy = cy + dy, wy = 0;
-      if (qy < 0) {
-        if (!py) continue;
-        qy += ny;
-        wy = -1;
-      } else if (qy >= ny) {
-        if (!py) continue;
-        qy -= ny;
-        wy = 1;
-      }
-      const uint32_t colb = col_code(g, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx;
-      const int xa = c == 0 ? cx : cx - Kx, xb = cx + Kx;  // cells of the row, unwrapped
-      {
-        const int a0 = xa < 0 ? 0 : xa, b0 = xb >= nx ? nx - 1 : xb;
-        const uint32_t jb = c == 0 ? p + 1 : __ldg(cs + colb + a0);
-        const uint32_t je = __ldg(cs + colb + b0 + 1);
-        if (je > jb) {
-          pc[np * 32 + lane] = make_uint2(jb, je);
-          cd[np * 32 + lane] = (uint8_t)image_code(0, wy, wz);
-          ++np;
-          total += je - jb;
+    // 1. the lane's non-empty pieces, column by column
+    int np = 0;
+    uint32_t total = 0;
+    Own32 o = {0, 0, 0, 0, 0, 0};
+    if (valid) {
+      int cx, cy, cz;
+      key_decode(g, s.skey[p], cx, cy, cz);
+      const float4 a = MA[p];
+      const float2 b = MB[p];
+      o = {a.x, a.y, a.z, a.w, b.x, b.y};
+  #pragma unroll
+      for (int c = 0; c < RL::kCols; ++c) {
+        const int dz = c <= K ? 0 : 1 + (c - K - 1) / (2 * K + 1);
+        const int dy = c == 0 ? 0 : (c <= K ? c : (c - K - 1) % (2 * K + 1) - K);
+        if (dz > Kz || dy > Ky || dy < -Ky) continue;
+        int qz = cz + dz, wz = 0;
+        if (qz >= nz) {
+          if (!pz) continue;
+          qz -= nz;
+          wz = 1;
         }
-      }
-      if (px && xa < 0) {  // cells [xa + nx, nx) seen through the image at -L
-        const uint32_t jb = __ldg(cs + colb + xa + nx), je = __ldg(cs + colb + nx);
-        if (je > jb) {
-          pc[np * 32 + lane] = make_uint2(jb, je);
-          cd[np * 32 + lane] = (uint8_t)image_code(-1, wy, wz);
-          ++np;
-          total += je - jb;
+        int qy = cy + dy, wy = 0;
+        if (qy < 0) {
+          if (!py) continue;
+          qy += ny;
+          wy = -1;
+        } else if (qy >= ny) {
+          if (!py) continue;
+          qy -= ny;
+          wy = 1;
         }
-      }
-      if (px && xb >= nx) {  // cells [0, xb - nx] seen through the image at +L
-        const uint32_t jb = __ldg(cs + colb), je = __ldg(cs + colb + xb - nx + 1);
-        if (je > jb) {
-          pc[np * 32 + lane] = make_uint2(jb, je);
-          cd[np * 32 + lane] = (uint8_t)image_code(1, wy, wz);
-          ++np;
-          total += je - jb;
+        const uint32_t colb = col_code(g, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx;
+        const int xa = c == 0 ? cx : cx - Kx, xb = cx + Kx;  // cells of the row, unwrapped
+        {
+          const int a0 = xa < 0 ? 0 : xa, b0 = xb >= nx ? nx - 1 : xb;
+          const uint32_t jb = c == 0 ? p + 1 : __ldg(cs + colb + a0);
+          const uint32_t je = __ldg(cs + colb + b0 + 1);
+          if (je > jb) {
+            pc[np * 32 + lane] = make_uint2(jb, je);
+            cd[np * 32 + lane] = (uint8_t)image_code(0, wy, wz);
+            ++np;
+            total += je - jb;
+          }
+        }
+        if (px && xa < 0) {  // cells [xa + nx, nx) seen through the image at -L
+          const uint32_t jb = __ldg(cs + colb + xa + nx), je = __ldg(cs + colb + nx);
+          if (je > jb) {
+            pc[np * 32 + lane] = make_uint2(jb, je);
+            cd[np * 32 + lane] = (uint8_t)image_code(-1, wy, wz);
+            ++np;
+            total += je - jb;
+          }
+        }
+        if (px && xb >= nx) {  // cells [0, xb - nx] seen through the image at +L
+          const uint32_t jb = __ldg(cs + colb), je = __ldg(cs + colb + xb - nx + 1);
+          if (je > jb) {
+            pc[np * 32 + lane] = make_uint2(jb, je);
+            cd[np * 32 + lane] = (uint8_t)image_code(1, wy, wz);
+            ++np;
+            total += je - jb;
+          }
         }
       }
     }
-  }
 
-  // 2. walk the pieces: one test per iteration
-  const uint32_t T = __reduce_max_sync(0xFFFFFFFFu, total);
-  uint32_t j = 0, je = 0;
-  int r = 0;
-  float sx = o.ox, sy = o.oy, sz = o.oz;
-  if (np > 0) {
-    const uint2 q = pc[lane];
-    const float4 sh = shift_tab[cd[lane]];
-    j = q.x;
-    je = q.y;
-    sx = o.ox - sh.x;
-    sy = o.oy - sh.y;
-    sz = o.oz - sh.z;
-  }
-  const float c0 = g.s_c0, c1 = g.s_c1;
-  for (uint32_t t = 0; t < T; ++t) {
-    if (j < je) {
-      const float4 a = __ldg(MA + j);
-      const float2 b = __ldg(MB + j);
-      float rx = a.x - sx, ry = a.y - sy, rz = a.z - sz;
-      bool keep = false;
-      if (any_cp) {
-        if (cp0) min_image_f(rx, g.halfLf[0], g.Lf[0], g.tief[0], keep);
-        if (cp1) min_image_f(ry, g.halfLf[1], g.Lf[1], g.tief[1], keep);
-        if (cp2) min_image_f(rz, g.halfLf[2], g.Lf[2], g.tief[2], keep);
-      }
-      const float gx = a.w - o.vx, gy = b.x - o.vy, gz = b.y - o.vz;
-      const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-      const float Bv = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
-      if (keep || (R <= fmaf(c1, Bv, c0) && full_test32(sq, rx, ry, rz, gx, gy, gz, Bv)))
-        emit_lane(buf, cnt, s, p, j);
-      if (++j == je && r + 1 < np) {
-        ++r;
-        const uint2 q = pc[r * 32 + lane];
-        const float4 sh = shift_tab[cd[r * 32 + lane]];
-        j = q.x;
-        je = q.y;
-        sx = o.ox - sh.x;
-        sy = o.oy - sh.y;
-        sz = o.oz - sh.z;
+    // 2. walk the pieces: one test per iteration
+    const uint32_t T = __reduce_max_sync(0xFFFFFFFFu, total);
+    uint32_t j = 0, je = 0;
+    int r = 0;
+    float sx = o.ox, sy = o.oy, sz = o.oz;
+    if (np > 0) {
+      const uint2 q = pc[lane];
+      const float4 sh = shift_tab[cd[lane]];
+      j = q.x;
+      je = q.y;
+      sx = o.ox - sh.x;
+      sy = o.oy - sh.y;
+      sz = o.oz - sh.z;
+    }
+    const float c0 = g.s_c0, c1 = g.s_c1;
+    for (uint32_t t = 0; t < T; ++t) {
+      if (j < je) {
+        const float4 a = __ldg(MA + j);
+        const float2 b = __ldg(MB + j);
+        float rx = a.x - sx, ry = a.y - sy, rz = a.z - sz;
+        bool keep = false;
+        if (any_cp) {
+          if (cp0) min_image_f(rx, g.halfLf[0], g.Lf[0], g.tief[0], keep);
+          if (cp1) min_image_f(ry, g.halfLf[1], g.Lf[1], g.tief[1], keep);
+          if (cp2) min_image_f(rz, g.halfLf[2], g.Lf[2], g.tief[2], keep);
+        }
+        const float gx = a.w - o.vx, gy = b.x - o.vy, gz = b.y - o.vz;
+        const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+        const float Bv = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
+        if (keep || (R <= fmaf(c1, Bv, c0) && full_test32(sq, rx, ry, rz, gx, gy, gz, Bv)))
+          emit_lane(buf, cnt, s, p, j);
+        if (++j == je && r + 1 < np) {
+          ++r;
+          const uint2 q = pc[r * 32 + lane];
+          const float4 sh = shift_tab[cd[r * 32 + lane]];
+          j = q.x;
+          je = q.y;
+          sx = o.ox - sh.x;
+          sy = o.oy - sh.y;
+          sz = o.oz - sh.z;
+        }
       }
     }
+    flush_lanes(buf, cnt, s, lane);
+    unsigned long long tests = total;
+    for (int off = 16; off > 0; off >>= 1) tests += __shfl_down_sync(0xFFFFFFFFu, tests, off);
+    if (lane == 0 && tests) atomicAdd(&s.d.pair_tests, tests);
   }
-  flush_lanes(buf, cnt, s, lane);
-  unsigned long long tests = total;
-  for (int off = 16; off > 0; off >>= 1) tests += __shfl_down_sync(0xFFFFFFFFu, tests, off);
-  if (lane == 0 && tests) atomicAdd(&s.d.pair_tests, tests);
 }
 
 
@@ -894,209 +921,232 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
   // image flags (-1, 0, +1 per axis) packed in bytes
   __shared__ uint32_t soff[kCellWarps][32], sb0[kCellWarps][32], sn0[kCellWarps][32],
       sb1[kCellWarps][32], sd[kCellWarps][32];
-  const int k = find_sim(B.ptile, B.nsims, blockIdx.x);
-  SimDev& s = *B.sims[k];
-  if (!sim_active(s) || !s.d.grid.split) return;
-  const Grid& g = s.d.grid;
-  const uint32_t* __restrict__ cs = s.cell_start;
-  const uint32_t nk = g.nkeys;
-  const uint32_t n = s.n;
-  const uint32_t nslow = __ldg(cs + nk);
-  const uint32_t nfast = n - nslow;
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  const uint32_t blk = blockIdx.x - B.ptile[k];
-  // blocks past the fast population have nothing to do (no block-wide barrier below)
-  if (blk * kCellWarps >= nfast) return;
-  const uint32_t wstride = (B.ptile[k + 1] - B.ptile[k]) * kCellWarps;
-  uint2* buf = wbuf[warp];
-  uint32_t* cnt = &wcount[warp];
-  if (lane == 0) *cnt = 0;
-  __syncwarp();
+  // grid-stride over tiles (an occupancy-sized grid); the warps of tile t take the
+  // fast particles f = 8 (t - first tile) + warp, stepping by 8 tiles per simulation
+  if (!batch_uses(B, -1)) return;
+  const uint32_t ntiles = B.ptile[B.nsims];
+  for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int k = find_sim(B.ptile, B.nsims, tile);
+    SimDev& s = *B.sims[k];
+    if (!sim_active(s) || !s.d.grid.split) continue;
+    const Grid& g = s.d.grid;
+    const uint32_t* __restrict__ cs = s.cell_start;
+    const uint32_t nk = g.nkeys;
+    const uint32_t n = s.n;
+    const uint32_t nslow = __ldg(cs + nk);
+    const uint32_t nfast = n - nslow;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t blk = tile - B.ptile[k];
+    // tiles past the fast population have nothing to do (no block-wide barrier below)
+    if (blk * kCellWarps >= nfast) continue;
+    const uint32_t wstride = (B.ptile[k + 1] - B.ptile[k]) * kCellWarps;
+    uint2* buf = wbuf[warp];
+    uint32_t* cnt = &wcount[warp];
+    if (lane == 0) *cnt = 0;
+    __syncwarp();
 
-  const int cur = s.d.parity ^ 1;
-  const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
-  const int Cx = g.cfast[0], Cy = g.cfast[1], Cz = g.cfast[2];
-  const int Wx = 2 * Cx + 1, Wxy = Wx * (2 * Cy + 1);
-  const int ncell = Wxy * (2 * Cz + 1);
-  const bool px = s.bc[0] == KMC_PERIODIC, py = s.bc[1] == KMC_PERIODIC,
-             pz = s.bc[2] == KMC_PERIODIC;
-  const double* __restrict__ X0 = s.x[cur][0];
-  const double* __restrict__ X1 = s.x[cur][1];
-  const double* __restrict__ X2 = s.x[cur][2];
-  const double* __restrict__ V0 = s.v[cur][0];
-  const double* __restrict__ V1 = s.v[cur][1];
-  const double* __restrict__ V2 = s.v[cur][2];
-  const float4* __restrict__ MA = s.mir_a;
-  const float2* __restrict__ MB = s.mir_b;
-  const double L0 = s.box[0], L1 = s.box[1], L2 = s.box[2];
-  Guard32 q;
-  q.c0 = g.s_c0; q.c1 = g.s_c1; q.ag = g.a_g; q.tg = g.t_g; q.dtf = g.dtf;
-  q.d0up = g.d0up; q.brel = g.b_rel; q.babs = g.b_abs; q.we = g.w_e; q.wrel = g.w_rel;
-  const float Lf0 = g.Lf[0], Lf1 = g.Lf[1], Lf2 = g.Lf[2];
-  unsigned long long tests = 0;
+    const int cur = s.d.parity ^ 1;
+    const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
+    const int Cx = g.cfast[0], Cy = g.cfast[1], Cz = g.cfast[2];
+    const int Wx = 2 * Cx + 1, Wxy = Wx * (2 * Cy + 1);
+    const int ncell = Wxy * (2 * Cz + 1);
+    const bool px = s.bc[0] == KMC_PERIODIC, py = s.bc[1] == KMC_PERIODIC,
+               pz = s.bc[2] == KMC_PERIODIC;
+    const double* __restrict__ X0 = s.x[cur][0];
+    const double* __restrict__ X1 = s.x[cur][1];
+    const double* __restrict__ X2 = s.x[cur][2];
+    const double* __restrict__ V0 = s.v[cur][0];
+    const double* __restrict__ V1 = s.v[cur][1];
+    const double* __restrict__ V2 = s.v[cur][2];
+    const float4* __restrict__ MA = s.mir_a;
+    const float2* __restrict__ MB = s.mir_b;
+    const double L0 = s.box[0], L1 = s.box[1], L2 = s.box[2];
+    Guard32 q;
+    q.c0 = g.s_c0; q.c1 = g.s_c1; q.ag = g.a_g; q.tg = g.t_g; q.dtf = g.dtf;
+    q.d0up = g.d0up; q.brel = g.b_rel; q.babs = g.b_abs; q.we = g.w_e; q.wrel = g.w_rel;
+    const float Lf0 = g.Lf[0], Lf1 = g.Lf[1], Lf2 = g.Lf[2];
+    unsigned long long tests = 0;
 
-  for (uint32_t f = blk * kCellWarps + warp; f < nfast; f += wstride) {
-    const uint32_t p = nslow + f;
-    int cx, cy, cz;
-    key_decode(g, s.skey[p] - nk, cx, cy, cz);
-    double xo[3] = {0, 0, 0}, vo[3] = {0, 0, 0};
-    Own32 o32 = {0, 0, 0, 0, 0, 0};
-    if (PREC == KMC_FP64) {
-      xo[0] = X0[p]; xo[1] = X1[p]; xo[2] = X2[p];
-      vo[0] = V0[p]; vo[1] = V1[p]; vo[2] = V2[p];
-    } else {
-      const float4 a = MA[p];
-      const float2 b = MB[p];
-      o32 = {a.x, a.y, a.z, a.w, b.x, b.y};
-    }
-    for (int c0 = 0; c0 < ncell; c0 += 32) {
-      // this lane's stencil cell and its two candidate ranges
-      const int c = c0 + (int)lane;
-      uint32_t b0 = 0, n0 = 0, b1 = 0, n1 = 0, dpack = 0;
-      if (c < ncell) {
-        const int dz = c / Wxy - Cz;
-        const int rem = c - (dz + Cz) * Wxy;
-        const int dy = rem / Wx - Cy;
-        const int dx = rem - (dy + Cy) * Wx - Cx;
-        int qx = cx + dx, qy = cy + dy, qz = cz + dz;
-        const int wx = qx < 0 ? -1 : (qx >= nx ? 1 : 0);
-        const int wy = qy < 0 ? -1 : (qy >= ny ? 1 : 0);
-        const int wz = qz < 0 ? -1 : (qz >= nz ? 1 : 0);
-        const bool ok = (wx == 0 || px) && (wy == 0 || py) && (wz == 0 || pz);
-        qx -= wx * nx;
-        qy -= wy * ny;
-        qz -= wz * nz;
-        if (ok) {
-          const uint32_t key = col_code(g, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx + (uint32_t)qx;
-          b0 = __ldg(cs + key);
-          n0 = __ldg(cs + key + 1) - b0;
-          b1 = __ldg(cs + nk + key);
-          const uint32_t e1 = __ldg(cs + nk + key + 1);
-          if (b1 <= p) b1 = p + 1;
-          n1 = e1 > b1 ? e1 - b1 : 0u;
+    for (uint32_t f = blk * kCellWarps + warp; f < nfast; f += wstride) {
+      const uint32_t p = nslow + f;
+      int cx, cy, cz;
+      key_decode(g, s.skey[p] - nk, cx, cy, cz);
+      double xo[3] = {0, 0, 0}, vo[3] = {0, 0, 0};
+      Own32 o32 = {0, 0, 0, 0, 0, 0};
+      if (PREC == KMC_FP64) {
+        xo[0] = X0[p]; xo[1] = X1[p]; xo[2] = X2[p];
+        vo[0] = V0[p]; vo[1] = V1[p]; vo[2] = V2[p];
+      } else {
+        const float4 a = MA[p];
+        const float2 b = MB[p];
+        o32 = {a.x, a.y, a.z, a.w, b.x, b.y};
+      }
+      for (int c0 = 0; c0 < ncell; c0 += 32) {
+        // this lane's stencil cell and its two candidate ranges
+        const int c = c0 + (int)lane;
+        uint32_t b0 = 0, n0 = 0, b1 = 0, n1 = 0, dpack = 0;
+        if (c < ncell) {
+          const int dz = c / Wxy - Cz;
+          const int rem = c - (dz + Cz) * Wxy;
+          const int dy = rem / Wx - Cy;
+          const int dx = rem - (dy + Cy) * Wx - Cx;
+          int qx = cx + dx, qy = cy + dy, qz = cz + dz;
+          const int wx = qx < 0 ? -1 : (qx >= nx ? 1 : 0);
+          const int wy = qy < 0 ? -1 : (qy >= ny ? 1 : 0);
+          const int wz = qz < 0 ? -1 : (qz >= nz ? 1 : 0);
+          const bool ok = (wx == 0 || px) && (wy == 0 || py) && (wz == 0 || pz);
+          qx -= wx * nx;
+          qy -= wy * ny;
+          qz -= wz * nz;
+          if (ok) {
+            const uint32_t key = col_code(g, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx + (uint32_t)qx;
+            b0 = __ldg(cs + key);
+            n0 = __ldg(cs + key + 1) - b0;
+            b1 = __ldg(cs + nk + key);
+            const uint32_t e1 = __ldg(cs + nk + key + 1);
+            if (b1 <= p) b1 = p + 1;
+            n1 = e1 > b1 ? e1 - b1 : 0u;
+          }
+          dpack = (uint32_t)(wx & 0xFF) | ((uint32_t)(wy & 0xFF) << 8) | ((uint32_t)(wz & 0xFF) << 16);
         }
-        dpack = (uint32_t)(wx & 0xFF) | ((uint32_t)(wy & 0xFF) << 8) | ((uint32_t)(wz & 0xFF) << 16);
-      }
-      const uint32_t tot = n0 + n1;
-      uint32_t incl = tot;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= (uint32_t)o) incl += y;
-      }
-      const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-      tests += tot;
-      soff[warp][lane] = incl - tot;
-      sb0[warp][lane] = b0;
-      sn0[warp][lane] = n0;
-      sb1[warp][lane] = b1;
-      sd[warp][lane] = dpack;
-      __syncwarp();
-      for (uint32_t kb = 0; kb < total; kb += 32) {
-        const uint32_t qi = kb + lane;
-        if (qi < total) {
-          // owner: the last cell whose first candidate is at or before qi
-          int lo = 0, hi = 31;
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (soff[warp][mid] <= qi) lo = mid; else hi = mid - 1;
+        const uint32_t tot = n0 + n1;
+        uint32_t incl = tot;
+  #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+          if (lane >= (uint32_t)o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        tests += tot;
+        soff[warp][lane] = incl - tot;
+        sb0[warp][lane] = b0;
+        sn0[warp][lane] = n0;
+        sb1[warp][lane] = b1;
+        sd[warp][lane] = dpack;
+        __syncwarp();
+        for (uint32_t kb = 0; kb < total; kb += 32) {
+          const uint32_t qi = kb + lane;
+          if (qi < total) {
+            // owner: the last cell whose first candidate is at or before qi
+            int lo = 0, hi = 31;
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              if (soff[warp][mid] <= qi) lo = mid; else hi = mid - 1;
+            }
+            const uint32_t o = qi - soff[warp][lo];
+            const uint32_t m0 = sn0[warp][lo];
+            const uint32_t j = o < m0 ? sb0[warp][lo] + o : sb1[warp][lo] + (o - m0);
+            bool emit;
+            if (PREC == KMC_FP64) {
+              double r0 = dsub(__ldg(X0 + j), xo[0]);
+              double r1 = dsub(__ldg(X1 + j), xo[1]);
+              double r2 = dsub(__ldg(X2 + j), xo[2]);
+              if (px) { if (r0 > 0.5 * L0) r0 = dsub(r0, L0); else if (r0 < -0.5 * L0) r0 = dadd(r0, L0); }
+              if (py) { if (r1 > 0.5 * L1) r1 = dsub(r1, L1); else if (r1 < -0.5 * L1) r1 = dadd(r1, L1); }
+              if (pz) { if (r2 > 0.5 * L2) r2 = dsub(r2, L2); else if (r2 < -0.5 * L2) r2 = dadd(r2, L2); }
+              const double g0 = dsub(__ldg(V0 + j), vo[0]);
+              const double g1 = dsub(__ldg(V1 + j), vo[1]);
+              const double g2 = dsub(__ldg(V2 + j), vo[2]);
+              const double R = dadd(dadd(dmul(r0, r0), dmul(r1, r1)), dmul(r2, r2));
+              const double Bv = dadd(dadd(dmul(g0, g0), dmul(g1, g1)), dmul(g2, g2));
+              emit = !(Bv >= 0x1p-900 && R > dadd(g.c0, dmul(g.c1, Bv)));
+            } else {
+              const uint32_t d = sd[warp][lo];
+              const int wx = (int)(int8_t)(d & 0xFF), wy = (int)(int8_t)((d >> 8) & 0xFF),
+                        wz = (int)(int8_t)((d >> 16) & 0xFF);
+              // own coordinates moved by the image shift (j seen at x_j + w L)
+              const float sx = o32.ox - (float)wx * Lf0;
+              const float sy = o32.oy - (float)wy * Lf1;
+              const float sz = o32.oz - (float)wz * Lf2;
+              const float4 a = __ldg(MA + j);
+              const float2 b = __ldg(MB + j);
+              const float rx = a.x - sx, ry = a.y - sy, rz = a.z - sz;
+              const float gx = a.w - o32.vx, gy = b.x - o32.vy, gz = b.y - o32.vz;
+              const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+              const float Bv = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
+              emit = R <= fmaf(q.c1, Bv, q.c0) && full_test32(q, rx, ry, rz, gx, gy, gz, Bv);
+            }
+            if (emit) emit_lane(buf, cnt, s, p, j);
           }
-          const uint32_t o = qi - soff[warp][lo];
-          const uint32_t m0 = sn0[warp][lo];
-          const uint32_t j = o < m0 ? sb0[warp][lo] + o : sb1[warp][lo] + (o - m0);
-          bool emit;
-          if (PREC == KMC_FP64) {
-            double r0 = dsub(__ldg(X0 + j), xo[0]);
-            double r1 = dsub(__ldg(X1 + j), xo[1]);
-            double r2 = dsub(__ldg(X2 + j), xo[2]);
-            if (px) { if (r0 > 0.5 * L0) r0 = dsub(r0, L0); else if (r0 < -0.5 * L0) r0 = dadd(r0, L0); }
-            if (py) { if (r1 > 0.5 * L1) r1 = dsub(r1, L1); else if (r1 < -0.5 * L1) r1 = dadd(r1, L1); }
-            if (pz) { if (r2 > 0.5 * L2) r2 = dsub(r2, L2); else if (r2 < -0.5 * L2) r2 = dadd(r2, L2); }
-            const double g0 = dsub(__ldg(V0 + j), vo[0]);
-            const double g1 = dsub(__ldg(V1 + j), vo[1]);
-            const double g2 = dsub(__ldg(V2 + j), vo[2]);
-            const double R = dadd(dadd(dmul(r0, r0), dmul(r1, r1)), dmul(r2, r2));
-            const double Bv = dadd(dadd(dmul(g0, g0), dmul(g1, g1)), dmul(g2, g2));
-            emit = !(Bv >= 0x1p-900 && R > dadd(g.c0, dmul(g.c1, Bv)));
-          } else {
-            const uint32_t d = sd[warp][lo];
-            const int wx = (int)(int8_t)(d & 0xFF), wy = (int)(int8_t)((d >> 8) & 0xFF),
-                      wz = (int)(int8_t)((d >> 16) & 0xFF);
-            // own coordinates moved by the image shift (j seen at x_j + w L)
-            const float sx = o32.ox - (float)wx * Lf0;
-            const float sy = o32.oy - (float)wy * Lf1;
-            const float sz = o32.oz - (float)wz * Lf2;
-            const float4 a = __ldg(MA + j);
-            const float2 b = __ldg(MB + j);
-            const float rx = a.x - sx, ry = a.y - sy, rz = a.z - sz;
-            const float gx = a.w - o32.vx, gy = b.x - o32.vy, gz = b.y - o32.vz;
-            const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-            const float Bv = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
-            emit = R <= fmaf(q.c1, Bv, q.c0) && full_test32(q, rx, ry, rz, gx, gy, gz, Bv);
-          }
-          if (emit) emit_lane(buf, cnt, s, p, j);
+          __syncwarp();
+          if (*cnt >= (uint32_t)(kWarpBuf / 2)) flush_lanes(buf, cnt, s, lane);
         }
         __syncwarp();
-        if (*cnt >= (uint32_t)(kWarpBuf / 2)) flush_lanes(buf, cnt, s, lane);
       }
-      __syncwarp();
     }
+    flush_lanes(buf, cnt, s, lane);
+    for (int o = 16; o > 0; o >>= 1) tests += __shfl_down_sync(0xFFFFFFFFu, tests, o);
+    if (lane == 0 && tests) atomicAdd(&s.d.pair_tests, tests);
   }
-  flush_lanes(buf, cnt, s, lane);
-  for (int o = 16; o > 0; o >>= 1) tests += __shfl_down_sync(0xFFFFFFFFu, tests, o);
-  if (lane == 0 && tests) atomicAdd(&s.d.pair_tests, tests);
 }
 
-int cell_search_blocks(int precision, int K, int num_sms) {
+namespace {
+// resident blocks of a kernel on the whole GPU (occupancy x SMs)
+template <typename F>
+int resident_blocks(F kernel, int threads, size_t smem, int num_sms) {
   int per_sm = 0;
-  cudaError_t e;
-  if (precision == KMC_GUARDED_FP32) {
-    // the row search keeps its piece lists in dynamic shared memory (above 48 KB for
-    // K = 2); set before any launch or capture
-    if (K == 2)
-      cudaFuncSetAttribute(k_search_rows32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)RowLayout<2>::kBytes);
-    else
-      cudaFuncSetAttribute(k_search_rows32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)RowLayout<1>::kBytes);
-  }
-  if (precision == KMC_FP64)
-    e = K == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_cell<KMC_FP64, 2>, kCellWarps * 32, 0)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_cell<KMC_FP64, 1>, kCellWarps * 32, 0);
-  else
-    e = K == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_cell32<2>, kCellWarps * 32, 0)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_cell32<1>, kCellWarps * 32, 0);
-  if (e != cudaSuccess || per_sm < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+      per_sm < 1) {
     cudaGetLastError();
     per_sm = 2;
   }
   return per_sm * num_sms;
 }
+}  // namespace
+
+void search_grids(int precision, int K, int num_sms, uint32_t ptiles, LaunchPlan& L) {
+  auto cap = [&](int blocks) { return (int)std::min<uint32_t>((uint32_t)blocks, std::max(ptiles, 1u)); };
+  if (precision == KMC_FP64) {
+    L.cell_blocks = K == 2 ? resident_blocks(k_search_cell<KMC_FP64, 2>, kCellWarps * 32, 0, num_sms)
+                           : resident_blocks(k_search_cell<KMC_FP64, 1>, kCellWarps * 32, 0, num_sms);
+    L.part_blocks = cap(K == 2 ? resident_blocks(k_search<KMC_FP64, 2>, kTile, 0, num_sms)
+                               : resident_blocks(k_search<KMC_FP64, 1>, kTile, 0, num_sms));
+    L.row_blocks = 0;
+    L.fast_blocks = cap(resident_blocks(k_search_fast<KMC_FP64>, kCellWarps * 32, 0, num_sms));
+    return;
+  }
+  // the row search keeps its piece lists in dynamic shared memory (above 48 KB for
+  // K = 2); set before any launch or capture
+  if (K == 2) {
+    cudaFuncSetAttribute(k_search_rows32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)RowLayout<2>::kBytes);
+    L.cell_blocks = resident_blocks(k_search_cell32<2>, kCellWarps * 32, 0, num_sms);
+    L.part_blocks = cap(resident_blocks(k_search<KMC_GUARDED_FP32, 2>, kTile, 0, num_sms));
+    L.row_blocks = cap(resident_blocks(k_search_rows32<2>, kTile, RowLayout<2>::kBytes, num_sms));
+  } else {
+    cudaFuncSetAttribute(k_search_rows32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)RowLayout<1>::kBytes);
+    L.cell_blocks = resident_blocks(k_search_cell32<1>, kCellWarps * 32, 0, num_sms);
+    L.part_blocks = cap(resident_blocks(k_search<KMC_GUARDED_FP32, 1>, kTile, 0, num_sms));
+    L.row_blocks = cap(resident_blocks(k_search_rows32<1>, kTile, RowLayout<1>::kBytes, num_sms));
+  }
+  L.fast_blocks = cap(resident_blocks(k_search_fast<KMC_GUARDED_FP32>, kCellWarps * 32, 0, num_sms));
+}
 
 int launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st) {
-  // both kernels are launched; each simulation runs in the one its grid selected
+  // every search kernel is launched; each simulation runs in the one its grid selected
   const int cb = L.cell_blocks;
   if (precision == KMC_FP64) {
     if (K == 2) {
-      k_search<KMC_FP64, 2><<<L.ptiles, kTile, 0, st>>>(L.b);
+      k_search<KMC_FP64, 2><<<L.part_blocks, kTile, 0, st>>>(L.b);
       k_search_cell<KMC_FP64, 2><<<cb, kCellWarps * 32, 0, st>>>(L.b);
     } else {
-      k_search<KMC_FP64, 1><<<L.ptiles, kTile, 0, st>>>(L.b);
+      k_search<KMC_FP64, 1><<<L.part_blocks, kTile, 0, st>>>(L.b);
       k_search_cell<KMC_FP64, 1><<<cb, kCellWarps * 32, 0, st>>>(L.b);
     }
   } else {
     if (K == 2) {
-      k_search<KMC_GUARDED_FP32, 2><<<L.ptiles, kTile, 0, st>>>(L.b);
+      k_search<KMC_GUARDED_FP32, 2><<<L.part_blocks, kTile, 0, st>>>(L.b);
       k_search_cell32<2><<<cb, kCellWarps * 32, 0, st>>>(L.b);
-      k_search_rows32<2><<<L.ptiles, kTile, RowLayout<2>::kBytes, st>>>(L.b);
+      k_search_rows32<2><<<L.row_blocks, kTile, RowLayout<2>::kBytes, st>>>(L.b);
     } else {
-      k_search<KMC_GUARDED_FP32, 1><<<L.ptiles, kTile, 0, st>>>(L.b);
+      k_search<KMC_GUARDED_FP32, 1><<<L.part_blocks, kTile, 0, st>>>(L.b);
       k_search_cell32<1><<<cb, kCellWarps * 32, 0, st>>>(L.b);
-      k_search_rows32<1><<<L.ptiles, kTile, RowLayout<1>::kBytes, st>>>(L.b);
+      k_search_rows32<1><<<L.row_blocks, kTile, RowLayout<1>::kBytes, st>>>(L.b);
     }
   }
-  if (precision == KMC_FP64) k_search_fast<KMC_FP64><<<L.ptiles, kCellWarps * 32, 0, st>>>(L.b);
-  else k_search_fast<KMC_GUARDED_FP32><<<L.ptiles, kCellWarps * 32, 0, st>>>(L.b);
+  if (precision == KMC_FP64) k_search_fast<KMC_FP64><<<L.fast_blocks, kCellWarps * 32, 0, st>>>(L.b);
+  else k_search_fast<KMC_GUARDED_FP32><<<L.fast_blocks, kCellWarps * 32, 0, st>>>(L.b);
   return precision == KMC_FP64 ? 3 : 4;
 }
 

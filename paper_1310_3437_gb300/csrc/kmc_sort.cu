@@ -32,7 +32,9 @@ __global__ void __launch_bounds__(kTile) k_count(Batch B) {
     int cz = cell_coord(g, 2, s.x[par][2][p]);
     key = col_code(g, (uint32_t)cy, (uint32_t)cz) * (uint32_t)g.nc[0] + (uint32_t)cx;
     // fast particles (speed bound above the split threshold) form the second population
-    if (g.split && vmag2_up(s.v[par][0][p], s.v[par][1][p], s.v[par][2][p]) > g.s1sq) key += g.nkeys;
+    // (the trial thresholds decrease with their index, so |v|^2 > threshold[split_t]
+    // exactly when the bound exceeds at least 7 - split_t of the six trial values)
+    if (g.split && (int)s.vbucket[p] >= kSplitTrials - g.split_t) key += g.nkeys;
   }
   // warp aggregation: one atomic per distinct key in the warp
   unsigned active = __ballot_sync(0xFFFFFFFFu, valid);
