@@ -34,8 +34,11 @@ struct CellPlan {
   bool ok;
 };
 
-// cells for search radius h (before the stencil split); key space capped by max_keys
-__device__ inline CellPlan plan_cells(const double ext[3], double h, int K, uint64_t max_keys) {
+// cells for search radius h (before the stencil split); key space capped by max_keys.
+// Along x the radius is split into K * kxm cells (kxm = 2: narrow cells along the rows
+// of the row search), along y and z into K.
+__device__ inline CellPlan plan_cells(const double ext[3], double h, int K, uint64_t max_keys,
+                                      int kxm = 1) {
   const double u32 = 0x1p-24;
   CellPlan p;
   p.ok = false;
@@ -48,16 +51,17 @@ __device__ inline CellPlan plan_cells(const double ext[3], double h, int K, uint
     // margin for binary32 cell assignment: index error <= 4 u32 n per particle
     double nmax = 0.0;
     for (int a = 0; a < 3; ++a) {
-      double q = ext[a] * K / h;
+      double q = ext[a] * (a == 0 ? K * kxm : K) / h;
       nmax = q > nmax ? q : nmax;
     }
     if (nmax > 65535.0) nmax = 65535.0;
     p.m = 1e-4 + 16.0 * u32 * nmax;
-    double wt = h * (1.0 + p.m) / K;  // target cell width
     for (int a = 0; a < 3; ++a) {
+      const int Ka = a == 0 ? K * kxm : K;
+      const double wt = h * (1.0 + p.m) / Ka;  // target cell width
       double q = floor(ext[a] / wt);
       int c = q > 65535.0 ? 65535 : (int)q;
-      if (c < 2 * K + 1) c = 1;
+      if (c < 2 * Ka + 1) c = 1;
       p.nc[a] = c;
     }
     // key space of the tiled column order: T x T Morton tiles, T = 2^t <= 8
@@ -174,8 +178,37 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
     s.d.split_cnt[t] = 0;
   }
 
-  const CellPlan p = plan_cells(ext, (s.d0 + 2.0 * S1 * s.dt) * scale, K,
-                                (uint64_t)s.cell_cap / (split ? 2 : 1));
+  CellPlan p = plan_cells(ext, (s.d0 + 2.0 * S1 * s.dt) * scale, K,
+                          (uint64_t)s.cell_cap / (split ? 2 : 1));
+  {
+    // search kernel for the slow population: warp per cell when cells are well
+    // filled; the binary32 warp-per-cell search handles no one-cell periodic axis
+    // (the row search does)
+    const double cells = (double)p.nc[0] * p.nc[1] * p.nc[2];
+    const double occ = (double)s.n / cells;
+    bool cp = false;
+    for (int a = 0; a < 3; ++a) cp = cp || (p.nc[a] == 1 && s.bc[a] == KMC_PERIODIC);
+    int mode = s.search_kernel;
+    const bool fp32 = s.precision == KMC_GUARDED_FP32;
+    if (mode == 0) {
+      if (fp32) mode = occ >= 16.0 ? KMC_SEARCH_CELL : KMC_SEARCH_ROW;
+      else mode = occ >= 4.0 ? KMC_SEARCH_CELL : KMC_SEARCH_PARTICLE;
+    }
+    if (mode == KMC_SEARCH_ROW && !fp32) mode = KMC_SEARCH_CELL;
+    if (mode == KMC_SEARCH_CELL && cp && fp32) mode = KMC_SEARCH_ROW;
+    g.mode = mode;
+    g.kx = K;
+    if (mode == KMC_SEARCH_ROW && p.nc[0] > 1) {
+      // rows of half-width cells: each particle's row is trimmed to its reach in
+      // half-cell steps (the grid is otherwise the same)
+      const CellPlan q = plan_cells(ext, (s.d0 + 2.0 * S1 * s.dt) * scale, K,
+                                    (uint64_t)s.cell_cap / (split ? 2 : 1), 2);
+      if (q.ok && q.nc[0] > 1 && q.nc[1] == p.nc[1] && q.nc[2] == p.nc[2]) {
+        p = q;
+        g.kx = 2 * K;
+      }
+    }
+  }
   if (!p.ok) s.d.status |= ST_CELL_OVERFLOW;
   const int* nc = p.nc;
   const double m = p.m;
@@ -186,30 +219,13 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
   int cfast[3] = {0, 0, 0};
   for (int a = 0; a < 3; ++a) {
     if (!split || nc[a] == 1) continue;
+    const int Ka = a == 0 ? g.kx : K;
     const double w = ext[a] / nc[a];
     int c = (int)ceil(Rfull * (1.0 + m) / w);
-    if (c < K) c = K;
+    if (c < Ka) c = Ka;
     cfast[a] = c;
   }
   for (int a = 0; a < 3; ++a) g.cfast[a] = cfast[a];
-  {
-    // search kernel for the slow population: warp per cell when cells are well
-    // filled; the binary32 warp-per-cell search handles no one-cell periodic axis
-    // (the row search does)
-    const double cells = (double)nc[0] * nc[1] * nc[2];
-    const double occ = (double)s.n / cells;
-    bool cp = false;
-    for (int a = 0; a < 3; ++a) cp = cp || (nc[a] == 1 && s.bc[a] == KMC_PERIODIC);
-    int mode = s.search_kernel;
-    const bool fp32 = s.precision == KMC_GUARDED_FP32;
-    if (mode == 0) {
-      if (fp32) mode = occ >= 16.0 ? KMC_SEARCH_CELL : KMC_SEARCH_ROW;
-      else mode = occ >= 4.0 ? KMC_SEARCH_CELL : KMC_SEARCH_PARTICLE;
-    }
-    if (mode == KMC_SEARCH_ROW && !fp32) mode = KMC_SEARCH_CELL;
-    if (mode == KMC_SEARCH_CELL && cp && fp32) mode = KMC_SEARCH_ROW;
-    g.mode = mode;
-  }
   for (int a = 0; a < 3; ++a) {
     g.nc[a] = nc[a];
     g.w[a] = nc[a] == 1 ? ext[a] : ext[a] / nc[a];
@@ -236,7 +252,8 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
   double er = 0.0, rn2 = 0.0, rbmax = 0.0;
   for (int a = 0; a < 3; ++a) {
     const double L = s.box[a] > ext[a] ? s.box[a] : ext[a];
-    const int Ke = cfast[a] > K ? cfast[a] : K;
+    const int Ka = a == 0 ? g.kx : K;
+    const int Ke = cfast[a] > Ka ? cfast[a] : Ka;
     double e, rb;
     if (nc[a] == 1) {
       e = 6.1 * u32 * L + 8.0 * u64 * L;
@@ -251,6 +268,18 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
     g.Lf[a] = (float)s.box[a];
     g.halfLf[a] = (float)(0.5 * s.box[a]);
     g.tief[a] = f_up(4.0 * e);
+  }
+  {
+    // row trimming: a slow-slow candidate has |r| < d0 + (|v_i| + |v_j|) dt <= d0 + 2 S1 dt
+    double Lmax = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      const double L = s.box[a] > ext[a] ? s.box[a] : ext[a];
+      Lmax = L > Lmax ? L : Lmax;
+    }
+    const double reach = (s.d0 + 2.0 * S1 * s.dt) * (1.0 + 1e-6);
+    g.row_r2 = f_up(reach * reach * (1.0 + 1e-6));
+    g.row_eps = f_up(16.0 * u32 * Lmax);
+    g.row_pad = f_up(4.0 * u32 * Lmax);
   }
   const double rn = sqrt(rn2) * (1.0 + 1e-6);
   const double ev = 4.1 * u32 * V;

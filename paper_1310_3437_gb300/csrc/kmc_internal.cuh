@@ -49,7 +49,7 @@ struct Grid {
   uint32_t nkeys;     // size of the key space (padded Morton columns x nc[0])
   uint32_t col_shift; // log2 of the Morton tile edge T (T <= 8)
   uint32_t col_tz;    // tiles along z
-  uint32_t pad0;
+  int32_t kx;         // cells per stencil radius along x (K, or 2K under the row search)
   double w[3];        // cell widths
   float wf[3];        // cell widths (binary32)
   float inv_wf[3];    // cells per unit length (binary32, cell assignment)
@@ -59,6 +59,10 @@ struct Grid {
   float t_g, dtf;     // time test: drop if A - dtf * B > t_g
   float d0up, b_rel, b_abs, w_e, w_rel;  // distance test (see kmc_search.cu)
   float Lf[3], halfLf[3], tief[3];        // one-cell periodic axes: minimum image
+  // row trimming of the binary32 row search: slow-slow candidates lie within the reach
+  // d0 + 2 S1 dt; r2 bounds its square, eps the binary32 error of a distance from a
+  // cell edge, pad the error of a coordinate (all rounded up)
+  float row_r2, row_eps, row_pad;
   // binary64 sphere pre-test: drop if R > c0 + c1 * B (B >= 2^-900)
   double c0, c1;
 };

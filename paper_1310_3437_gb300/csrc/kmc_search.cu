@@ -736,7 +736,7 @@ __device__ __forceinline__ uint32_t image_code(int wx, int wy, int wz) {
 }
 
 template <int K>
-__global__ void __launch_bounds__(kTile) k_search_rows32(Batch B) {
+__global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
   using RL = RowLayout<K>;
   constexpr int NP = RL::kPieces;
   extern __shared__ __align__(16) unsigned char rows_smem[];
@@ -779,7 +779,8 @@ __global__ void __launch_bounds__(kTile) k_search_rows32(Batch B) {
 
     const bool valid = p < nslow;
     const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
-    const int Kx = nx == 1 ? 0 : K, Ky = ny == 1 ? 0 : K, Kz = nz == 1 ? 0 : K;
+    // along x the grid may have narrower cells under the row search (kx per radius)
+    const int Kx = nx == 1 ? 0 : g.kx, Ky = ny == 1 ? 0 : K, Kz = nz == 1 ? 0 : K;
     const bool px = s.bc[0] == KMC_PERIODIC, py = s.bc[1] == KMC_PERIODIC,
                pz = s.bc[2] == KMC_PERIODIC;
     // one-cell periodic axes need the minimum image explicitly
@@ -799,7 +800,15 @@ __global__ void __launch_bounds__(kTile) k_search_rows32(Batch B) {
       const float4 a = MA[p];
       const float2 b = MB[p];
       o = {a.x, a.y, a.z, a.w, b.x, b.y};
-  #pragma unroll
+      // row trimming: the part of each row within the reach of this particle.  A
+      // column whose cells lie farther than the reach in (y, z) is skipped; in the
+      // others only the cells with x within sqrt(reach^2 - d^2) are kept (d the
+      // column's distance in (y, z), taken from the cell edges and rounded down; the
+      // x extent rounded up).  Rows that cross a periodic x boundary keep their full
+      // length on the crossing side.
+      const float R2 = g.row_r2, eps = g.row_eps, pad = g.row_pad;
+      const float wyf = g.wf[1], wzf = g.wf[2], ivx = g.inv_wf[0];
+#pragma unroll 1
       for (int c = 0; c < RL::kCols; ++c) {
         const int dz = c <= K ? 0 : 1 + (c - K - 1) / (2 * K + 1);
         const int dy = c == 0 ? 0 : (c <= K ? c : (c - K - 1) % (2 * K + 1) - K);
@@ -820,8 +829,28 @@ __global__ void __launch_bounds__(kTile) k_search_rows32(Batch B) {
           qy -= ny;
           wy = 1;
         }
+        float d2 = 0.f;
+        if (dy != 0) {
+          const float e = dy > 0 ? (float)(cy + dy) * wyf - o.oy : o.oy - (float)(cy + dy + 1) * wyf;
+          const float el = fmaxf(e - eps, 0.f);
+          d2 = el * el;
+        }
+        if (dz != 0) {  // forward columns only: dz > 0
+          const float e = (float)(cz + dz) * wzf - o.oz;
+          const float el = fmaxf(e - eps, 0.f);
+          d2 = fmaf(el, el, d2);
+        }
+        d2 *= 0.9999995f;
+        if (d2 >= R2) continue;
+        const float ex = fmaf(sqrtf(R2 - d2), 1.000001f, pad);
+        int xa = c == 0 ? cx : cx - Kx, xb = cx + Kx;  // cells of the row, unwrapped
+        if (Kx > 0) {
+          const int ta = (int)floorf((o.ox - ex) * ivx), tb = (int)floorf((o.ox + ex) * ivx);
+          if (ta >= 0 && ta > xa) xa = ta;
+          if (tb <= nx - 1 && tb < xb) xb = tb;
+          if (xb < xa) continue;
+        }
         const uint32_t colb = col_code(g, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx;
-        const int xa = c == 0 ? cx : cx - Kx, xb = cx + Kx;  // cells of the row, unwrapped
         {
           const int a0 = xa < 0 ? 0 : xa, b0 = xb >= nx ? nx - 1 : xb;
           const uint32_t jb = c == 0 ? p + 1 : __ldg(cs + colb + a0);
@@ -1011,7 +1040,7 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
         }
         const uint32_t tot = n0 + n1;
         uint32_t incl = tot;
-  #pragma unroll
+#pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
           if (lane >= (uint32_t)o) incl += y;
