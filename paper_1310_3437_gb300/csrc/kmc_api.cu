@@ -128,7 +128,7 @@ size_t bytes_for(const Sizes& z) {
   size_t b = 0;
   b += 2 * 6 * n * sizeof(double) + 2 * 2 * n * sizeof(uint32_t);  // state, double-buffered
   if (z.fp32) b += n * (sizeof(float4) + sizeof(float2));
-  b += 4 * n * sizeof(uint32_t) + n;                                  // key, rank, src, skey, speed class
+  b += 3 * n * sizeof(uint32_t) + n;                                  // key, rank, src, speed class
   b += 2 * ((size_t)z.cell_cap + 1) * sizeof(uint32_t);               // cell count / start
   b += n * sizeof(uint32_t) + (n + 1) * sizeof(uint32_t);             // deg, off
   b += 4 * n * sizeof(uint32_t);                                      // best, best_e, partner, medge
@@ -524,7 +524,6 @@ int sim_create(const kmc_params* p, const double* x, const double* y, const doub
   if ((rc = dalloc(s, &h.rank, n))) return fail(rc);
   if ((rc = dalloc(s, &h.src, n))) return fail(rc);
   if ((rc = dalloc(s, &h.vbucket, n))) return fail(rc);
-  if ((rc = dalloc(s, &h.skey, n))) return fail(rc);
   if ((rc = dalloc(s, &h.cell_count, (size_t)zs.cell_cap + 1))) return fail(rc);
   if ((rc = dalloc(s, &h.cell_start, (size_t)zs.cell_cap + 1))) return fail(rc);
   if ((rc = dalloc(s, &h.deg, n))) return fail(rc);

@@ -114,7 +114,6 @@ struct SimDev {
   uint8_t* vbucket;     // per particle: how many of the trial split thresholds its
                         // |v|^2 bound exceeds (written by the push, read by the count)
   uint32_t* src;        // pre-sort position of the particle at each sorted position
-  uint32_t* skey;       // cell key per particle (sorted order)
   uint32_t* cell_count; // nkeys counters, all zero between steps
   uint32_t* cell_start; // nkeys + 1
   uint32_t* deg;        // candidate pairs per particle
@@ -261,14 +260,18 @@ __device__ __forceinline__ float vmag2_up(double vx, double vy, double vz) {
   return __fadd_ru(__fadd_ru(__fmul_ru(ax, ax), __fmul_ru(ay, ay)), __fmul_ru(az, az));
 }
 
-// cell coordinate along one axis, binary32 (only the speed depends on it)
-__device__ __forceinline__ int cell_coord(const Grid& g, int k, double x) {
+// cell coordinate along one axis, binary32 (only the speed depends on it); from the
+// binary32 coordinate (the mirror's) it is the same cell as from the binary64 one
+__device__ __forceinline__ int cell_coord_f(const Grid& g, int k, float xf) {
   if (g.nc[k] == 1) return 0;
-  float f = floorf(d2f_rn(x) * g.inv_wf[k]);
+  float f = floorf(xf * g.inv_wf[k]);
   int c = (int)f;
   c = c < 0 ? 0 : c;
   c = c >= g.nc[k] ? g.nc[k] - 1 : c;
   return c;
+}
+__device__ __forceinline__ int cell_coord(const Grid& g, int k, double x) {
+  return cell_coord_f(g, k, d2f_rn(x));
 }
 
 // ---- launch helpers (host) ----------------------------------------------- //

@@ -77,8 +77,9 @@ __global__ void __launch_bounds__(kTile) k_search(Batch B) {
     // with the speed split only the slow population (keys below nkeys) is searched here
     const uint32_t nslow = g.split ? __ldg(cs + g.nkeys) : n;
     if (p < nslow) {
-      int cx, cy, cz;
-      key_decode(g, s.skey[p], cx, cy, cz);
+      // the particle's cell, recomputed as the sort computed it
+      const int cx = cell_coord(g, 0, s.x[cur][0][p]), cy = cell_coord(g, 1, s.x[cur][1][p]),
+                cz = cell_coord(g, 2, s.x[cur][2][p]);
 
       // own record
       double xo[3], vo[3];
@@ -795,11 +796,12 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
     uint32_t total = 0;
     Own32 o = {0, 0, 0, 0, 0, 0};
     if (valid) {
-      int cx, cy, cz;
-      key_decode(g, s.skey[p], cx, cy, cz);
       const float4 a = MA[p];
       const float2 b = MB[p];
       o = {a.x, a.y, a.z, a.w, b.x, b.y};
+      // the particle's cell, recomputed from the mirror as the sort computed it
+      const int cx = cell_coord_f(g, 0, a.x), cy = cell_coord_f(g, 1, a.y),
+                cz = cell_coord_f(g, 2, a.z);
       // row trimming: the part of each row within the reach of this particle.  A
       // column whose cells lie farther than the reach in (y, z) is skipped; in the
       // others only the cells with x within sqrt(reach^2 - d^2) are kept (d the
@@ -998,8 +1000,8 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
 
     for (uint32_t f = blk * kCellWarps + warp; f < nfast; f += wstride) {
       const uint32_t p = nslow + f;
-      int cx, cy, cz;
-      key_decode(g, s.skey[p] - nk, cx, cy, cz);
+      // the particle's cell, recomputed as the sort computed it
+      const int cx = cell_coord(g, 0, X0[p]), cy = cell_coord(g, 1, X1[p]), cz = cell_coord(g, 2, X2[p]);
       double xo[3] = {0, 0, 0}, vo[3] = {0, 0, 0};
       Own32 o32 = {0, 0, 0, 0, 0, 0};
       if (PREC == KMC_FP64) {

@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kTile) k_gather(Batch B) {
     xs[a] = s.x[from][a][p];
     vs[a] = s.v[from][a][p];
   }
-  const uint32_t id = s.id[from][p], last = s.last[from][p], key = s.key[p];
+  const uint32_t id = s.id[from][p], last = s.last[from][p];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     s.x[to][a][d] = xs[a];
@@ -237,7 +237,6 @@ __global__ void __launch_bounds__(kTile) k_gather(Batch B) {
   }
   s.id[to][d] = id;
   s.last[to][d] = last;
-  s.skey[d] = key;
   s.deg[d] = 0;
   s.partner[d] = kNone;
   if (s.precision == KMC_GUARDED_FP32) {
