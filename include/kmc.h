@@ -70,9 +70,12 @@ extern "C" {
 #define KMC_OBS_STEP 6     /* one uint64: absolute index of the next step */
 #define KMC_OBS_LAUNCHES 7 /* one uint64: kernel launches enqueued for this simulation
                               (steps of its group included) */
-#define KMC_OBS_PHASE_MS 8 /* 5 binary64: milliseconds spent in the sort, search,
-                              matching (exact test, lists, rounds, scatter) and push
-                              phases while timing was on, then the number of timed steps */
+#define KMC_OBS_PHASE_MS 8 /* 5 or 6 binary64 (as dst holds): milliseconds spent in the
+                              sort, search, matching (exact test, lists, rounds,
+                              scatter) and push phases while timing was on, the number
+                              of timed steps, then the milliseconds of the main search
+                              kernel alone (the one that searches the slow population:
+                              row, cell or particle search), part of the search phase */
 
 #define KMC_NONE 0xFFFFFFFFu
 
@@ -134,6 +137,8 @@ typedef struct kmc_step_counts {
   uint32_t survivors;       /* pairs that passed the search pre-tests */
   uint32_t cells;           /* cells of the search grid */
   uint64_t pair_tests;      /* pair tests done by the search */
+  uint64_t fast_tests;      /* the part of pair_tests done for the fast particles of the
+                               speed split (the rest is the slow-population search) */
 } kmc_step_counts;
 
 typedef struct kmc_sim kmc_sim;

@@ -74,7 +74,7 @@ class kmc_step_counts(C.Structure):
     _fields_ = [
         ("step", C.c_uint64), ("collisions", C.c_uint32), ("edges", C.c_uint32),
         ("round_pairs", C.c_uint32 * 4), ("survivors", C.c_uint32), ("cells", C.c_uint32),
-        ("pair_tests", C.c_uint64),
+        ("pair_tests", C.c_uint64), ("fast_tests", C.c_uint64),
     ]
 
 

@@ -71,7 +71,7 @@ struct kmc_sim {
   uint64_t hist_read = 0, prof_read = 0;
   uint64_t launches = 0;     // kernel launches enqueued for this simulation
   bool timing = false;       // per-phase CUDA-event timing (no graph)
-  double phase_ms[4] = {0, 0, 0, 0};
+  double phase_ms[5] = {0, 0, 0, 0, 0};  // sort, search, match, push; slow search kernels
   uint64_t timed_steps = 0;
   std::string err;
 };
@@ -119,8 +119,9 @@ Sizes sizes_of(const kmc_params& p) {
 }
 
 size_t edge_bytes(uint32_t cap) {
+  // pairs, keys, slots; candidate lists (2 per pair) and the two round work lists
   return (size_t)cap * (sizeof(uint2) + 2 * sizeof(double) + sizeof(uint2)) +
-         (size_t)2 * cap * 3 * sizeof(uint32_t);
+         (size_t)2 * cap * (sizeof(uint2) + 2 * sizeof(uint32_t));
 }
 
 size_t bytes_for(const Sizes& z) {
@@ -130,7 +131,7 @@ size_t bytes_for(const Sizes& z) {
   if (z.fp32) b += n * (sizeof(float4) + sizeof(float2));
   b += 3 * n * sizeof(uint32_t) + n;                                  // key, rank, src, speed class
   b += 2 * ((size_t)z.cell_cap + 1) * sizeof(uint32_t);               // cell count / start
-  b += n * sizeof(uint32_t) + (n + 1) * sizeof(uint32_t);             // deg, off
+  b += n * sizeof(uint32_t) + (n + 1) * sizeof(uint32_t);             // deg, list starts
   b += 4 * n * sizeof(uint32_t);                                      // best, best_e, partner, medge
   b += (n / 2 + 1) * sizeof(uint32_t);                                // pair list
   b += edge_bytes(z.edge_cap);
@@ -202,19 +203,19 @@ int alloc_edges(kmc_sim* s, uint32_t cap) {
   if ((rc = dalloc(s, &h.e_d2, cap))) return rc;
   if ((rc = dalloc(s, &h.e_t, cap))) return rc;
   if ((rc = dalloc(s, &h.e_slot, cap))) return rc;
-  if ((rc = dalloc(s, &h.adj_owner, 2 * (size_t)cap))) return rc;
-  if ((rc = dalloc(s, &h.adj_other, 2 * (size_t)cap))) return rc;
-  if ((rc = dalloc(s, &h.adj_edge, 2 * (size_t)cap))) return rc;
+  if ((rc = dalloc(s, &h.adj, 2 * (size_t)cap))) return rc;
+  if ((rc = dalloc(s, &h.wl[0], 2 * (size_t)cap))) return rc;
+  if ((rc = dalloc(s, &h.wl[1], 2 * (size_t)cap))) return rc;
   h.edge_cap = cap;
   return KMC_OK;
 }
 
 void free_edges(kmc_sim* s) {
   SimDev& h = s->h;
-  void* ptrs[] = {h.edge, h.e_d2, h.e_t, h.e_slot, h.adj_owner, h.adj_other, h.adj_edge};
+  void* ptrs[] = {h.edge, h.e_d2, h.e_t, h.e_slot, h.adj, h.wl[0], h.wl[1]};
   for (void* q : ptrs) dfree(s, q);
   h.edge = nullptr; h.e_d2 = nullptr; h.e_t = nullptr; h.e_slot = nullptr;
-  h.adj_owner = h.adj_other = h.adj_edge = nullptr;
+  h.adj = nullptr; h.wl[0] = h.wl[1] = nullptr;
 }
 
 // ---- plans ----------------------------------------------------------------- //
@@ -228,9 +229,9 @@ void free_plan(Plan& P) {
 int build_plan(Plan& P, const std::vector<kmc_sim*>& sims, cudaStream_t st, std::string& err) {
   free_plan(P);
   int m = (int)sims.size();
-  std::vector<uint32_t> pt(m + 1), sn(m + 1), sc(m + 1), pr(m + 1);
+  std::vector<uint32_t> pt(m + 1), sc(m + 1), pr(m + 1);
   std::vector<SimDev*> table(m);
-  pt[0] = sn[0] = sc[0] = pr[0] = 0;
+  pt[0] = sc[0] = pr[0] = 0;
   P.precision = sims[0]->h.precision;
   P.K = sims[0]->h.K;
   P.max_rounds = 0;
@@ -238,14 +239,13 @@ int build_plan(Plan& P, const std::vector<kmc_sim*>& sims, cudaStream_t st, std:
     const SimDev& h = sims[k]->h;
     table[k] = sims[k]->d;
     pt[k + 1] = pt[k] + ceil_div(h.n, kTile);
-    sn[k + 1] = sn[k] + ceil_div((uint64_t)h.n + 1, kScanTile);
     sc[k + 1] = sc[k] + ceil_div((uint64_t)h.cell_cap + 1, kScanTile);
     pr[k + 1] = pr[k] + ceil_div(h.n, kProfTile);
     P.max_rounds = std::max(P.max_rounds, h.max_rounds);
     if (h.profile_bins > 0) P.has_profiles = true;
   }
-  size_t scratch = std::max(sn[m], sc[m]) + 1;
-  size_t words = 4 * (size_t)(m + 1) + scratch;
+  size_t scratch = (size_t)sc[m] + 1;
+  size_t words = 3 * (size_t)(m + 1) + scratch;
   if (cudaMalloc(&P.d_table, sizeof(SimDev*) * m) != cudaSuccess ||
       cudaMalloc(&P.d_pre, words * sizeof(uint32_t)) != cudaSuccess) {
     cudaGetLastError();
@@ -253,11 +253,10 @@ int build_plan(Plan& P, const std::vector<kmc_sim*>& sims, cudaStream_t st, std:
     free_plan(P);
     return KMC_ENOMEM;
   }
-  std::vector<uint32_t> host(4 * (m + 1));
+  std::vector<uint32_t> host(3 * (m + 1));
   std::copy(pt.begin(), pt.end(), host.begin());
-  std::copy(sn.begin(), sn.end(), host.begin() + (m + 1));
-  std::copy(sc.begin(), sc.end(), host.begin() + 2 * (m + 1));
-  std::copy(pr.begin(), pr.end(), host.begin() + 3 * (m + 1));
+  std::copy(sc.begin(), sc.end(), host.begin() + (m + 1));
+  std::copy(pr.begin(), pr.end(), host.begin() + 2 * (m + 1));
   KCHECK(cudaMemcpyAsync(P.d_table, table.data(), sizeof(SimDev*) * m, cudaMemcpyHostToDevice, st), err);
   KCHECK(cudaMemcpyAsync(P.d_pre, host.data(), host.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st), err);
   KCHECK(cudaStreamSynchronize(st), err);
@@ -265,12 +264,10 @@ int build_plan(Plan& P, const std::vector<kmc_sim*>& sims, cudaStream_t st, std:
   L.b.sims = P.d_table;
   L.b.nsims = m;
   L.b.ptile = P.d_pre;
-  L.b.stile_n = P.d_pre + (m + 1);
-  L.b.stile_c = P.d_pre + 2 * (m + 1);
-  L.b.prtile = P.d_pre + 3 * (m + 1);
-  L.b.tile_sums = P.d_pre + 4 * (m + 1);
+  L.b.stile_c = P.d_pre + (m + 1);
+  L.b.prtile = P.d_pre + 2 * (m + 1);
+  L.b.tile_sums = P.d_pre + 3 * (m + 1);
   L.ptiles = pt[m];
-  L.stiles_n = sn[m];
   L.stiles_c = sc[m];
   L.prtiles = pr[m];
   L.edge_blocks = 8 * num_sms();
@@ -289,15 +286,15 @@ int enqueue_step(const Plan& P, cudaStream_t st) {
 // Diagnostic stepping: phases launched one by one between CUDA events on the
 // stream, waiting for each step.
 int run_steps_timed(Plan& P, cudaStream_t st, uint64_t nsteps, kmc_sim* s) {
-  cudaEvent_t ev[5];
-  for (int i = 0; i < 5; ++i) KCHECK(cudaEventCreate(&ev[i]), s->err);
+  cudaEvent_t ev[7];
+  for (int i = 0; i < 7; ++i) KCHECK(cudaEventCreate(&ev[i]), s->err);
   int rc = KMC_OK;
   for (uint64_t k = 0; k < nsteps && rc == KMC_OK; ++k) {
     int n = 0;
     cudaEventRecord(ev[0], st);
     n += launch_sort(P.L, st);
     cudaEventRecord(ev[1], st);
-    n += launch_search(P.L, P.precision, P.K, st);
+    n += launch_search(P.L, P.precision, P.K, st, ev + 5);
     cudaEventRecord(ev[2], st);
     n += launch_match(P.L, P.max_rounds, st);
     cudaEventRecord(ev[3], st);
@@ -314,10 +311,13 @@ int run_steps_timed(Plan& P, cudaStream_t st, uint64_t nsteps, kmc_sim* s) {
       cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
       s->phase_ms[i] += ms;
     }
+    float ms_slow = 0.f;
+    cudaEventElapsedTime(&ms_slow, ev[5], ev[6]);
+    s->phase_ms[4] += ms_slow;
     s->timed_steps += 1;
     s->launches += n;
   }
-  for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+  for (int i = 0; i < 7; ++i) cudaEventDestroy(ev[i]);
   return rc;
 }
 
@@ -390,7 +390,10 @@ int recover_overflow(kmc_sim* s, Dyn& dy, cudaStream_t st) {
   dy.n_edges = 0;
   for (int r = 0; r < 4; ++r) dy.round_pairs[r] = 0;
   dy.n_pairs = 0;
+  dy.adj_used = 0;
+  for (int r = 0; r < 5; ++r) dy.wl_len[r] = 0;
   dy.pair_tests = 0;
+  dy.fast_tests = 0;
   // the push of the failed step never ran: keep the bound of the previous step
   dy.vmax2_acc = 0;
   return write_dyn(s, &dy, st);
@@ -740,9 +743,11 @@ int64_t sim_observe(kmc_sim* s, int what, void* dst, size_t dst_bytes) {
     }
     case KMC_OBS_PHASE_MS: {
       if (dst_bytes < 5 * sizeof(double)) { s->err = "dst too small for PHASE_MS"; return KMC_EINVAL; }
-      double v[5] = {s->phase_ms[0], s->phase_ms[1], s->phase_ms[2], s->phase_ms[3], (double)s->timed_steps};
-      KCHECK(cudaMemcpy(dst, v, sizeof(v), cudaMemcpyDefault), s->err);
-      return 5;
+      double v[6] = {s->phase_ms[0], s->phase_ms[1], s->phase_ms[2], s->phase_ms[3],
+                     (double)s->timed_steps, s->phase_ms[4]};
+      const size_t m = dst_bytes >= sizeof(v) ? 6 : 5;
+      KCHECK(cudaMemcpy(dst, v, m * sizeof(double), cudaMemcpyDefault), s->err);
+      return (int64_t)m;
     }
     case KMC_OBS_STEP: {
       if (dst_bytes < sizeof(uint64_t)) { s->err = "dst too small for STEP"; return KMC_EINVAL; }

@@ -61,8 +61,9 @@ struct Grid {
   float Lf[3], halfLf[3], tief[3];        // one-cell periodic axes: minimum image
   // row trimming of the binary32 row search: slow-slow candidates lie within the reach
   // d0 + 2 S1 dt; r2 bounds its square, eps the binary32 error of a distance from a
-  // cell edge, pad the error of a coordinate (all rounded up)
-  float row_r2, row_eps, row_pad;
+  // cell edge, pad the error of a coordinate (all rounded up).  Per particle i the
+  // reach is d0 + (|v_i| + S1) dt: at most row_a + row_b |v_i| (both rounded up)
+  float row_r2, row_eps, row_pad, row_a, row_b;
   // binary64 sphere pre-test: drop if R > c0 + c1 * B (B >= 2^-900)
   double c0, c1;
 };
@@ -79,7 +80,11 @@ struct Dyn {
   uint32_t n_edges;     // candidate pairs after the exact test
   uint32_t round_pairs[4];
   uint32_t n_pairs;     // entries of the pair list
+  uint32_t adj_used;    // candidate-list entries handed out this step
+  uint32_t wl_len[5];   // particles on the work list of matching round r (0: all with
+                        // candidates; r + 1 is filled by round r)
   unsigned long long pair_tests;
+  unsigned long long fast_tests;  // the part of pair_tests done by the fast-particle search
   uint32_t last_raw;    // n_raw of the last completed step (its pair buffer is kept)
   uint32_t have_counts; // split_cnt holds counts of the current state
   float split_thr[kSplitTrials];     // trial thresholds on |v|^2 (set with the grid)
@@ -117,14 +122,14 @@ struct SimDev {
   uint32_t* cell_count; // nkeys counters, all zero between steps
   uint32_t* cell_start; // nkeys + 1
   uint32_t* deg;        // candidate pairs per particle
-  uint32_t* off;        // n + 1, exclusive scan of deg
+  uint32_t* off;        // start of each particle's candidate list in adj (set for deg > 0)
   uint2* edge;          // emitted pairs (sorted indices, owner first)
   double* e_d2;         // binary64 key of each pair
   double* e_t;
   uint2* e_slot;        // slot of the pair in each endpoint's list, x = kNone if rejected
-  uint32_t* adj_owner;  // adjacency (CSR by owner): owner, other end, pair index
-  uint32_t* adj_other;
-  uint32_t* adj_edge;
+  uint2* adj;           // candidate lists, each particle's contiguous: (other end, pair)
+  uint32_t* wl[2];      // work lists of the matching rounds (unmatched particles that
+                        // still had an unmatched candidate), used alternately
   uint32_t* best;       // best unmatched candidate (sorted index) in the current round
   uint32_t* best_e;
   uint32_t* partner;    // partner (sorted index) this step, kNone if none
@@ -141,7 +146,6 @@ struct Batch {
   SimDev* const* sims;     // device table
   int nsims;
   const uint32_t* ptile;   // prefix of ceil(n / kTile) per simulation
-  const uint32_t* stile_n; // prefix of ceil((n + 1) / kScanTile)
   const uint32_t* stile_c; // prefix of ceil((cell_cap + 1) / kScanTile)
   const uint32_t* prtile;  // prefix of ceil(n / kProfTile)
   uint32_t* tile_sums;      // scratch for the segmented scans
@@ -277,7 +281,7 @@ __device__ __forceinline__ int cell_coord(const Grid& g, int k, double x) {
 // ---- launch helpers (host) ----------------------------------------------- //
 struct LaunchPlan {
   Batch b;
-  uint32_t ptiles, stiles_n, stiles_c, prtiles;
+  uint32_t ptiles, stiles_c, prtiles;
   int edge_blocks;
   int cell_blocks;  // persistent grid of the warp-per-cell search
   int part_blocks;  // grid-stride grids of the particle, row and fast searches
@@ -287,14 +291,16 @@ struct LaunchPlan {
 
 // each returns the number of kernels it launched
 int launch_sort(const LaunchPlan& L, cudaStream_t st);
-int launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st);
+// ev_slow (optional, two events): recorded around the slow-population search kernels
+int launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st,
+                  cudaEvent_t* ev_slow = nullptr);
 // resident-block grids of the search kernels (and the row search's shared-memory
 // attribute); called when a launch plan is built, before any capture
 void search_grids(int precision, int K, int num_sms, uint32_t ptiles, LaunchPlan& L);
 int launch_match(const LaunchPlan& L, int max_rounds, cudaStream_t st);
 int launch_push(const LaunchPlan& L, cudaStream_t st);
 int launch_init_grid(const LaunchPlan& L, cudaStream_t st);
-int launch_seg_scan(const LaunchPlan& L, int which, cudaStream_t st);
+int launch_cell_scan(const LaunchPlan& L, cudaStream_t st);
 
 // observe helpers
 void launch_gather_state(SimDev* d, uint32_t n, void* out, cudaStream_t st);

@@ -13,12 +13,17 @@
 //             0 <= t* < dt, d_min^2 < d0^2, and the pair is not the pair that last
 //             collided for both of its members.  Survivors take a slot in each
 //             endpoint's candidate list.
-//   k_fill    candidate lists in CSR form (owner, other end, pair).
-//   k_best    per round: every unmatched particle picks its unmatched candidate of
-//             least key (d_min^2, t*, partner id) -- a total order, so the choice does
-//             not depend on the order of the list.
-//   k_mutual  per round: pairs that picked each other are matched; the count uses
-//             warp ballots (one atomic per warp).
+//   k_alloc   each particle with candidates gets a contiguous list (one warp-
+//             aggregated atomic per warp) and a place on the first round's work list;
+//             only the particles with candidates are touched, no pass over all n.
+//   k_fill    the lists: (other end, pair) per slot.
+//   k_best    per round, over the round's work list: every unmatched particle picks
+//             its unmatched candidate of least key (d_min^2, t*, partner id) -- a
+//             total order, so the choice does not depend on the order of the list.
+//   k_mutual  per round, over the same list: pairs that picked each other are
+//             matched (warp-aggregated appends); a particle left unmatched that still
+//             had an unmatched candidate goes on the next round's list, so later
+//             rounds only visit the few particles they can still match.
 //   k_collide isotropic centre-of-mass scatter at the time of closest approach.
 #include "kmc_internal.cuh"
 
@@ -134,7 +139,51 @@ __global__ void __launch_bounds__(kEdgeBlock) k_refine(Batch B) {
   }
 }
 
-// ---- k_fill -------------------------------------------------------------- //
+// ---- candidate lists -------------------------------------------------------- //
+// warp-aggregated append: returns this lane's first index in a buffer of which
+// *counter entries are in use; every lane of the warp must call it
+__device__ __forceinline__ uint32_t warp_append(uint32_t* counter, uint32_t want) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t incl = want;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= (uint32_t)o) incl += y;
+  }
+  const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+  uint32_t base = 0;
+  if (lane == 31 && total) base = atomicAdd(counter, total);
+  base = __shfl_sync(0xFFFFFFFFu, base, 31);
+  return base + incl - want;
+}
+
+// the pair whose slot is 0 at an endpoint opens that endpoint's list
+__global__ void __launch_bounds__(kEdgeBlock) k_alloc(Batch B) {
+  for (int k = 0; k < B.nsims; ++k) {
+    SimDev& s = *B.sims[k];
+    if (!sim_active(s)) continue;
+    const uint32_t nraw = s.d.n_raw < s.edge_cap ? s.d.n_raw : s.edge_cap;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    // uniform trip count per warp: the appends are warp-wide
+    const uint32_t span = ((nraw + stride - 1) / stride) * stride;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < span; e += stride) {
+      uint32_t i = kNone, j = kNone, di = 0, dj = 0;
+      if (e < nraw) {
+        const uint2 sl = s.e_slot[e];
+        if (sl.x != kNone) {
+          const uint2 pr = s.edge[e];
+          if (sl.x == 0) { i = pr.x; di = s.deg[i]; }
+          if (sl.y == 0) { j = pr.y; dj = s.deg[j]; }
+        }
+      }
+      const uint32_t at = warp_append(&s.d.adj_used, di + dj);
+      const uint32_t wa = warp_append(&s.d.wl_len[0], (i != kNone ? 1u : 0u) + (j != kNone ? 1u : 0u));
+      if (i != kNone) { s.off[i] = at; s.wl[0][wa] = i; }
+      if (j != kNone) { s.off[j] = at + di; s.wl[0][wa + (i != kNone ? 1u : 0u)] = j; }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kEdgeBlock) k_fill(Batch B) {
   for (int k = 0; k < B.nsims; ++k) {
     SimDev& s = *B.sims[k];
@@ -144,9 +193,8 @@ __global__ void __launch_bounds__(kEdgeBlock) k_fill(Batch B) {
       uint2 sl = s.e_slot[e];
       if (sl.x == kNone) continue;
       uint2 pr = s.edge[e];
-      uint32_t a = s.off[pr.x] + sl.x, b = s.off[pr.y] + sl.y;
-      s.adj_owner[a] = pr.x; s.adj_other[a] = pr.y; s.adj_edge[a] = e;
-      s.adj_owner[b] = pr.y; s.adj_other[b] = pr.x; s.adj_edge[b] = e;
+      s.adj[s.off[pr.x] + sl.x] = make_uint2(pr.y, e);
+      s.adj[s.off[pr.y] + sl.y] = make_uint2(pr.x, e);
     }
   }
 }
@@ -161,26 +209,31 @@ __device__ __forceinline__ bool key_less(double d2a, double ta, uint32_t ja, dou
   return ja < jb;
 }
 
-__global__ void __launch_bounds__(kEdgeBlock) k_best(Batch B) {
+// The work list of round r holds every particle that is unmatched after round r - 1
+// and had an unmatched candidate in round r - 1 (round 0: every particle with a
+// candidate).  A particle left off it has no unmatched candidate, so it can neither
+// pick nor be picked: the rounds over the lists match exactly the pairs that rounds
+// over all particles would.
+__global__ void __launch_bounds__(kEdgeBlock) k_best(Batch B, int round) {
   for (int k = 0; k < B.nsims; ++k) {
     SimDev& s = *B.sims[k];
-    if (!sim_active(s)) continue;
+    if (!sim_active(s) || round >= s.max_rounds) continue;
     const int cur = s.d.parity ^ 1;
-    const uint32_t total = s.off[s.n];
-    for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < total; a += gridDim.x * blockDim.x) {
-      uint32_t i = s.adj_owner[a];
-      if (a > 0 && s.adj_owner[a - 1] == i) continue;  // not the head of i's list
-      if (s.partner[i] != kNone) continue;
+    const uint32_t len = s.d.wl_len[round];
+    const uint32_t* __restrict__ list = s.wl[round & 1];
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < len; t += gridDim.x * blockDim.x) {
+      const uint32_t i = list[t];
+      const uint32_t q0 = s.off[i], q1 = q0 + s.deg[i];
       uint32_t bj = kNone, be = kNone, bid = kNone;
       double bd2 = 0.0, bt = 0.0;
-      for (uint32_t q = a; q < total && s.adj_owner[q] == i; ++q) {
-        uint32_t j = s.adj_other[q];
+      for (uint32_t q = q0; q < q1; ++q) {
+        const uint2 a = s.adj[q];
+        const uint32_t j = a.x;
         if (s.partner[j] != kNone) continue;
-        uint32_t e = s.adj_edge[q];
-        double d2 = s.e_d2[e], t = s.e_t[e];
-        uint32_t idj = s.id[cur][j];
-        if (bj == kNone || key_less(d2, t, idj, bd2, bt, bid)) {
-          bj = j; be = e; bid = idj; bd2 = d2; bt = t;
+        const double d2 = s.e_d2[a.y], tt = s.e_t[a.y];
+        const uint32_t idj = s.id[cur][j];
+        if (bj == kNone || key_less(d2, tt, idj, bd2, bt, bid)) {
+          bj = j; be = a.y; bid = idj; bd2 = d2; bt = tt;
         }
       }
       s.best[i] = bj;
@@ -192,38 +245,37 @@ __global__ void __launch_bounds__(kEdgeBlock) k_best(Batch B) {
 __global__ void __launch_bounds__(kEdgeBlock) k_mutual(Batch B, int round) {
   for (int k = 0; k < B.nsims; ++k) {
     SimDev& s = *B.sims[k];
-    if (!sim_active(s)) continue;
-    if (round >= s.max_rounds) continue;
+    if (!sim_active(s) || round >= s.max_rounds) continue;
     const int cur = s.d.parity ^ 1;
-    const uint32_t total = s.off[s.n];
+    const uint32_t len = s.d.wl_len[round];
+    const uint32_t* __restrict__ list = s.wl[round & 1];
+    uint32_t* __restrict__ next = s.wl[(round + 1) & 1];
     const uint32_t stride = gridDim.x * blockDim.x;
-    // uniform trip count per warp so that the ballot sees every lane
-    const uint32_t span = ((total + stride - 1) / stride) * stride;
-    for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < span; a += stride) {
-      bool pair = false;
-      if (a < total) {
-        uint32_t i = s.adj_owner[a];
-        bool head = a == 0 || s.adj_owner[a - 1] != i;
-        if (head && s.partner[i] == kNone) {
-          uint32_t j = s.best[i];
-          if (j != kNone && s.best[j] == i) {
+    // uniform trip count per warp: the appends are warp-wide
+    const uint32_t span = ((len + stride - 1) / stride) * stride;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < span; t += stride) {
+      bool pair = false, again = false;
+      uint32_t i = kNone;
+      if (t < len) {
+        i = list[t];
+        const uint32_t j = s.best[i];
+        if (j != kNone) {
+          if (s.best[j] == i) {
             s.partner[i] = j;
             s.medge[i] = s.best_e[i];
             pair = s.id[cur][i] < s.id[cur][j];
+          } else {
+            again = true;
           }
         }
       }
-      // warp-aggregated append to the pair list (one atomic per warp)
-      unsigned m = __ballot_sync(0xFFFFFFFFu, pair);
-      if (m) {
-        const unsigned lane = threadIdx.x & 31u;
-        uint32_t base = 0;
-        if (lane == 0) {
-          base = atomicAdd(&s.d.n_pairs, (uint32_t)__popc(m));
-          atomicAdd(&s.d.round_pairs[round], (uint32_t)__popc(m));
-        }
-        base = __shfl_sync(0xFFFFFFFFu, base, 0);
-        if (pair) s.pairs[base + __popc(m & ((1u << lane) - 1u))] = s.adj_owner[a];
+      const uint32_t at = warp_append(&s.d.n_pairs, pair ? 1u : 0u);
+      if (pair) s.pairs[at] = i;
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, pair);
+      if ((threadIdx.x & 31u) == 0 && m) atomicAdd(&s.d.round_pairs[round], (uint32_t)__popc(m));
+      if (round + 1 < s.max_rounds) {
+        const uint32_t w = warp_append(&s.d.wl_len[round + 1], again ? 1u : 0u);
+        if (again) next[w] = i;
       }
     }
   }
@@ -279,14 +331,14 @@ __global__ void __launch_bounds__(kEdgeBlock) k_collide(Batch B) {
 int launch_match(const LaunchPlan& L, int max_rounds, cudaStream_t st) {
   int nb = L.edge_blocks;
   k_refine<<<nb, kEdgeBlock, 0, st>>>(L.b);
-  int n = launch_seg_scan(L, 1, st);
+  k_alloc<<<nb, kEdgeBlock, 0, st>>>(L.b);
   k_fill<<<nb, kEdgeBlock, 0, st>>>(L.b);
   for (int r = 0; r < max_rounds; ++r) {
-    k_best<<<nb, kEdgeBlock, 0, st>>>(L.b);
+    k_best<<<nb, kEdgeBlock, 0, st>>>(L.b, r);
     k_mutual<<<nb, kEdgeBlock, 0, st>>>(L.b, r);
   }
   k_collide<<<nb, kEdgeBlock, 0, st>>>(L.b);
-  return n + 3 + 2 * max_rounds;
+  return 4 + 2 * max_rounds;
 }
 
 }  // namespace kmc

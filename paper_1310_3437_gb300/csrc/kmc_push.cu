@@ -199,7 +199,10 @@ __device__ void reset_step_counters(SimDev& s) {
   s.d.n_edges = 0;
   for (int r = 0; r < 4; ++r) s.d.round_pairs[r] = 0;
   s.d.n_pairs = 0;
+  s.d.adj_used = 0;
+  for (int r = 0; r < 5; ++r) s.d.wl_len[r] = 0;
   s.d.pair_tests = 0;
+  s.d.fast_tests = 0;
   s.d.vmax2_acc = 0;
 }
 
@@ -224,6 +227,7 @@ __global__ void k_finalize(Batch B) {
     rec.survivors = s.d.n_raw;
     rec.cells = s.d.grid.nkeys;
     rec.pair_tests = s.d.pair_tests;
+    rec.fast_tests = s.d.fast_tests;
     s.hist[s.d.hist_count % s.hist_cap] = rec;
     s.d.hist_count += 1;
     if (s.d.prof_due) {

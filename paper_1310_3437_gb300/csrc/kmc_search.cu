@@ -725,9 +725,23 @@ struct RowLayout {
   static constexpr int kCols = 1 + K + K * (2 * K + 1);  // own column + forward columns
   static constexpr int kPieces = 2 * kCols;             // a row splits at most once
   static constexpr int kWarps = kTile / 32;
+  // per warp: the lanes' pieces (j range), the owners' records (position and
+  // velocity, 16 + 8 bytes), the pair staging buffer, the pieces' image codes and the
+  // lanes' piece counts; every array starts on a 16-byte boundary
   static constexpr size_t kPieceBytes = (size_t)kWarps * kPieces * 32 * sizeof(uint2);
+  static constexpr size_t kOwnABytes = (size_t)kWarps * 32 * sizeof(float4);
+  static constexpr size_t kOwnBBytes = (size_t)kWarps * 32 * sizeof(float2);
+  static constexpr size_t kBufBytes = (size_t)kWarps * kWarpBuf * sizeof(uint2);
   static constexpr size_t kCodeBytes = (size_t)kWarps * kPieces * 32;
-  static constexpr size_t kBytes = kPieceBytes + kCodeBytes + (size_t)kWarps * kWarpBuf * sizeof(uint2);
+  static constexpr size_t kNpBytes = (size_t)kWarps * 32;
+  static constexpr size_t kOwnA = kPieceBytes;
+  static constexpr size_t kOwnB = kOwnA + kOwnABytes;
+  static constexpr size_t kBuf = kOwnB + kOwnBBytes;
+  static constexpr size_t kCode = kBuf + kBufBytes;
+  static constexpr size_t kNp = kCode + kCodeBytes;
+  static constexpr size_t kBytes = kNp + kNpBytes;
+  static_assert(kOwnA % 16 == 0 && kOwnB % 16 == 0 && kBuf % 16 == 0 && kCode % 16 == 0 &&
+                    kNp % 16 == 0, "row search shared-memory layout");
 };
 
 // image flags of a piece: bit 0 / 1 = seen at +L / -L along x, bits 2-3 y, bits 4-5 z
@@ -771,9 +785,11 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
     const uint32_t p = (tile - B.ptile[k]) * kTile + threadIdx.x;
     if (p - lane >= nslow) continue;  // the whole warp is past the slow population
     uint2* pc = reinterpret_cast<uint2*>(rows_smem) + (size_t)warp * NP * 32;
-    uint8_t* cd = rows_smem + RL::kPieceBytes + (size_t)warp * NP * 32;
-    uint2* buf = reinterpret_cast<uint2*>(rows_smem + RL::kPieceBytes + RL::kCodeBytes) +
-                 (size_t)warp * kWarpBuf;
+    float4* own_a = reinterpret_cast<float4*>(rows_smem + RL::kOwnA) + (size_t)warp * 32;
+    float2* own_b = reinterpret_cast<float2*>(rows_smem + RL::kOwnB) + (size_t)warp * 32;
+    uint2* buf = reinterpret_cast<uint2*>(rows_smem + RL::kBuf) + (size_t)warp * kWarpBuf;
+    uint8_t* cd = rows_smem + RL::kCode + (size_t)warp * NP * 32;
+    uint8_t* nps = rows_smem + RL::kNp + (size_t)warp * 32;
     uint32_t* cnt = &wcount[warp];
     if (lane == 0) *cnt = 0;
     __syncwarp();
@@ -808,7 +824,14 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
       // column's distance in (y, z), taken from the cell edges and rounded down; the
       // x extent rounded up).  Rows that cross a periodic x boundary keep their full
       // length on the crossing side.
-      const float R2 = g.row_r2, eps = g.row_eps, pad = g.row_pad;
+      // the reach of this particle: |v_i| from its binary32 velocity (each component
+      // within u32 of the binary64 one, the sum of squares within 3 u32, the square
+      // root correctly rounded) times 1 + 2e-6 bounds |v_i| from above; the products
+      // and the square get 1e-6 each.  The smaller of this and the common reach holds.
+      const float si = sqrtf(fmaf(o.vz, o.vz, fmaf(o.vy, o.vy, o.vx * o.vx))) * 1.000002f;
+      const float Ri = fmaf(si, g.row_b, g.row_a) * 1.000001f;
+      const float R2 = fminf(g.row_r2, Ri * Ri * 1.000001f);
+      const float eps = g.row_eps, pad = g.row_pad;
       const float wyf = g.wf[1], wzf = g.wf[2], ivx = g.inv_wf[0];
 #pragma unroll 1
       for (int c = 0; c < RL::kCols; ++c) {
@@ -885,23 +908,63 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
       }
     }
 
-    // 2. walk the pieces: one test per iteration
-    const uint32_t T = __reduce_max_sync(0xFFFFFFFFu, total);
+    // 2. walk the pieces with the tests dealt out evenly over the lanes.  The warp's W
+    //    tests, laid out owner by owner (lane order) and piece by piece, are cut into
+    //    32 runs of consecutive tests, lane l taking tests [l W / 32, (l + 1) W / 32);
+    //    a run may start inside one owner's pieces and end inside a later owner's.
+    uint32_t incl = total;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+      if (lane >= (uint32_t)off) incl += y;
+    }
+    const uint32_t W = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    const uint32_t excl = incl - total;
+    own_a[lane] = make_float4(o.ox, o.oy, o.oz, o.vx);
+    own_b[lane] = make_float2(o.vy, o.vz);
+    nps[lane] = (uint8_t)np;
+    __syncwarp();
+    const uint32_t ta = (uint32_t)(((unsigned long long)lane * W) >> 5);
+    const uint32_t run = (uint32_t)(((unsigned long long)(lane + 1) * W) >> 5) - ta;
+    // owner of test ta: the last lane whose first test is at or before ta (lanes
+    // without tests share their successor's first test and are passed over)
+    uint32_t u = 0;
+#pragma unroll
+    for (uint32_t step = 16; step > 0; step >>= 1) {
+      const uint32_t v = __shfl_sync(0xFFFFFFFFu, excl, u + step);
+      if (v <= ta) u += step;
+    }
+    const uint32_t q0 = ta - __shfl_sync(0xFFFFFFFFu, excl, u);
     uint32_t j = 0, je = 0;
     int r = 0;
-    float sx = o.ox, sy = o.oy, sz = o.oz;
-    if (np > 0) {
-      const uint2 q = pc[lane];
-      const float4 sh = shift_tab[cd[lane]];
-      j = q.x;
-      je = q.y;
-      sx = o.ox - sh.x;
-      sy = o.oy - sh.y;
-      sz = o.oz - sh.z;
+    float sx = 0.f, sy = 0.f, sz = 0.f, ovx = 0.f, ovy = 0.f, ovz = 0.f;
+    float4 oa = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (run > 0) {
+      // the piece of owner u holding its test q0
+      uint32_t q = q0;
+      uint2 pq = pc[u];
+      while (q >= pq.y - pq.x && r + 1 < (int)nps[u]) {
+        q -= pq.y - pq.x;
+        ++r;
+        pq = pc[r * 32 + u];
+      }
+      j = pq.x + q;
+      je = pq.y;
+      oa = own_a[u];
+      const float2 ob = own_b[u];
+      ovx = oa.w;
+      ovy = ob.x;
+      ovz = ob.y;
+      const float4 sh = shift_tab[cd[r * 32 + u]];
+      sx = oa.x - sh.x;
+      sy = oa.y - sh.y;
+      sz = oa.z - sh.z;
     }
+    const uint32_t T = (W + 31u) >> 5;  // the longest run
     const float c0 = g.s_c0, c1 = g.s_c1;
+    const uint32_t p0 = p - lane;
     for (uint32_t t = 0; t < T; ++t) {
-      if (j < je) {
+      if (t < run) {
         const float4 a = __ldg(MA + j);
         const float2 b = __ldg(MB + j);
         float rx = a.x - sx, ry = a.y - sy, rz = a.z - sz;
@@ -911,27 +974,36 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
           if (cp1) min_image_f(ry, g.halfLf[1], g.Lf[1], g.tief[1], keep);
           if (cp2) min_image_f(rz, g.halfLf[2], g.Lf[2], g.tief[2], keep);
         }
-        const float gx = a.w - o.vx, gy = b.x - o.vy, gz = b.y - o.vz;
+        const float gx = a.w - ovx, gy = b.x - ovy, gz = b.y - ovz;
         const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
         const float Bv = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
         if (keep || (R <= fmaf(c1, Bv, c0) && full_test32(sq, rx, ry, rz, gx, gy, gz, Bv)))
-          emit_lane(buf, cnt, s, p, j);
-        if (++j == je && r + 1 < np) {
-          ++r;
-          const uint2 q = pc[r * 32 + lane];
-          const float4 sh = shift_tab[cd[r * 32 + lane]];
-          j = q.x;
-          je = q.y;
-          sx = o.ox - sh.x;
-          sy = o.oy - sh.y;
-          sz = o.oz - sh.z;
+          emit_lane(buf, cnt, s, p0 + u, j);
+        if (++j == je && t + 1 < run) {
+          // next piece of this owner, else the first piece of the next owner with tests
+          if (++r >= (int)nps[u]) {
+            r = 0;
+            do {
+              ++u;
+            } while (u < 31 && nps[u] == 0);  // a later owner holds the run's remaining tests
+            oa = own_a[u];
+            const float2 ob = own_b[u];
+            ovx = oa.w;
+            ovy = ob.x;
+            ovz = ob.y;
+          }
+          const uint2 pq = pc[r * 32 + u];
+          const float4 sh = shift_tab[cd[r * 32 + u]];
+          j = pq.x;
+          je = pq.y;
+          sx = oa.x - sh.x;
+          sy = oa.y - sh.y;
+          sz = oa.z - sh.z;
         }
       }
     }
     flush_lanes(buf, cnt, s, lane);
-    unsigned long long tests = total;
-    for (int off = 16; off > 0; off >>= 1) tests += __shfl_down_sync(0xFFFFFFFFu, tests, off);
-    if (lane == 0 && tests) atomicAdd(&s.d.pair_tests, tests);
+    if (lane == 0 && W) atomicAdd(&s.d.pair_tests, (unsigned long long)W);
   }
 }
 
@@ -1107,7 +1179,10 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
     }
     flush_lanes(buf, cnt, s, lane);
     for (int o = 16; o > 0; o >>= 1) tests += __shfl_down_sync(0xFFFFFFFFu, tests, o);
-    if (lane == 0 && tests) atomicAdd(&s.d.pair_tests, tests);
+    if (lane == 0 && tests) {
+      atomicAdd(&s.d.pair_tests, tests);
+      atomicAdd(&s.d.fast_tests, tests);
+    }
   }
 }
 
@@ -1154,9 +1229,11 @@ void search_grids(int precision, int K, int num_sms, uint32_t ptiles, LaunchPlan
   L.fast_blocks = cap(resident_blocks(k_search_fast<KMC_GUARDED_FP32>, kCellWarps * 32, 0, num_sms));
 }
 
-int launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st) {
+int launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st, cudaEvent_t* ev_slow) {
   // every search kernel is launched; each simulation runs in the one its grid selected
+  // (the others return at once)
   const int cb = L.cell_blocks;
+  if (ev_slow) cudaEventRecord(ev_slow[0], st);
   if (precision == KMC_FP64) {
     if (K == 2) {
       k_search<KMC_FP64, 2><<<L.part_blocks, kTile, 0, st>>>(L.b);
@@ -1176,6 +1253,7 @@ int launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st) {
       k_search_rows32<1><<<L.row_blocks, kTile, RowLayout<1>::kBytes, st>>>(L.b);
     }
   }
+  if (ev_slow) cudaEventRecord(ev_slow[1], st);
   if (precision == KMC_FP64) k_search_fast<KMC_FP64><<<L.fast_blocks, kCellWarps * 32, 0, st>>>(L.b);
   else k_search_fast<KMC_GUARDED_FP32><<<L.fast_blocks, kCellWarps * 32, 0, st>>>(L.b);
   return precision == KMC_FP64 ? 3 : 4;

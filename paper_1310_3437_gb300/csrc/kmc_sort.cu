@@ -52,9 +52,8 @@ __global__ void __launch_bounds__(kTile) k_count(Batch B) {
 }
 
 // --------------------------------------------------------------------------- //
-// Segmented exclusive scan.  which = 0: cell counts -> cell_start (and clear the
-// counts); which = 1: degrees -> CSR offsets.  Element `len` is a virtual zero, so
-// out[len] receives the total.
+// Segmented exclusive scan of the cell counts -> cell_start (the counts are cleared
+// for the next step).  Element `len` is a virtual zero, so out[len] receives the total.
 struct ScanView {
   const uint32_t* in;
   uint32_t* out;
@@ -62,14 +61,10 @@ struct ScanView {
   uint32_t len;
 };
 
-__device__ __forceinline__ ScanView scan_view(SimDev& s, int which) {
+__device__ __forceinline__ ScanView scan_view(SimDev& s) {
   ScanView v;
-  if (which == 0) {
-    v.in = s.cell_count; v.out = s.cell_start; v.clear = s.cell_count;
-    v.len = s.d.grid.nkeys * (s.d.grid.split ? 2u : 1u);
-  } else {
-    v.in = s.deg; v.out = s.off; v.clear = nullptr; v.len = s.n;
-  }
+  v.in = s.cell_count; v.out = s.cell_start; v.clear = s.cell_count;
+  v.len = s.d.grid.nkeys * (s.d.grid.split ? 2u : 1u);
   return v;
 }
 
@@ -100,13 +95,13 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* t
   return r;
 }
 
-__global__ void __launch_bounds__(kTile) k_scan_reduce(Batch B, int which) {
-  const uint32_t* pre = which == 0 ? B.stile_c : B.stile_n;
+__global__ void __launch_bounds__(kTile) k_scan_reduce(Batch B) {
+  const uint32_t* pre = B.stile_c;
   int k = find_sim(pre, B.nsims, blockIdx.x);
   SimDev& s = *B.sims[k];
   uint32_t sum = 0;
   if (sim_active(s)) {
-    ScanView v = scan_view(s, which);
+    ScanView v = scan_view(s);
     uint32_t base = (blockIdx.x - pre[k]) * kScanTile;
     for (int i = threadIdx.x; i < kScanTile; i += kTile) {
       uint32_t e = base + i;
@@ -125,8 +120,8 @@ __global__ void __launch_bounds__(kTile) k_scan_reduce(Batch B, int which) {
 }
 
 // one block: exclusive scan of the tile sums inside each simulation's segment
-__global__ void __launch_bounds__(1024) k_scan_tiles(Batch B, int which, uint32_t ntiles) {
-  const uint32_t* pre = which == 0 ? B.stile_c : B.stile_n;
+__global__ void __launch_bounds__(1024) k_scan_tiles(Batch B, uint32_t ntiles) {
+  const uint32_t* pre = B.stile_c;
   __shared__ uint32_t warp_sums[32];
   __shared__ uint32_t carry;
   if (threadIdx.x == 0) carry = 0;
@@ -171,12 +166,12 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Batch B, int which, uint32_
   }
 }
 
-__global__ void __launch_bounds__(kTile) k_scan_apply(Batch B, int which) {
-  const uint32_t* pre = which == 0 ? B.stile_c : B.stile_n;
+__global__ void __launch_bounds__(kTile) k_scan_apply(Batch B) {
+  const uint32_t* pre = B.stile_c;
   int k = find_sim(pre, B.nsims, blockIdx.x);
   SimDev& s = *B.sims[k];
   if (!sim_active(s)) return;
-  ScanView v = scan_view(s, which);
+  ScanView v = scan_view(s);
   uint32_t base = (blockIdx.x - pre[k]) * kScanTile;
   if (base > v.len) return;
   constexpr int PER = kScanTile / kTile;
@@ -247,17 +242,17 @@ __global__ void __launch_bounds__(kTile) k_gather(Batch B) {
 }
 
 // --------------------------------------------------------------------------- //
-int launch_seg_scan(const LaunchPlan& L, int which, cudaStream_t st) {
-  uint32_t nt = which == 0 ? L.stiles_c : L.stiles_n;
-  k_scan_reduce<<<nt, kTile, 0, st>>>(L.b, which);
-  k_scan_tiles<<<1, 1024, 0, st>>>(L.b, which, nt);
-  k_scan_apply<<<nt, kTile, 0, st>>>(L.b, which);
+int launch_cell_scan(const LaunchPlan& L, cudaStream_t st) {
+  const uint32_t nt = L.stiles_c;
+  k_scan_reduce<<<nt, kTile, 0, st>>>(L.b);
+  k_scan_tiles<<<1, 1024, 0, st>>>(L.b, nt);
+  k_scan_apply<<<nt, kTile, 0, st>>>(L.b);
   return 3;
 }
 
 int launch_sort(const LaunchPlan& L, cudaStream_t st) {
   k_count<<<L.ptiles, kTile, 0, st>>>(L.b);
-  int n = launch_seg_scan(L, 0, st);
+  int n = launch_cell_scan(L, st);
   k_scatter<<<L.ptiles, kTile, 0, st>>>(L.b);
   k_gather<<<L.ptiles, kTile, 0, st>>>(L.b);
   return n + 3;

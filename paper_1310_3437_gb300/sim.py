@@ -144,7 +144,8 @@ class Simulation:
         cnt = sim_observe(self.handle, KMC_OBS_COUNTS, C.addressof(arr), C.sizeof(arr))
         return [{"step": int(r.step), "collisions": int(r.collisions), "edges": int(r.edges),
                  "round_pairs": [int(x) for x in r.round_pairs], "survivors": int(r.survivors),
-                 "cells": int(r.cells), "pair_tests": int(r.pair_tests)} for r in arr[:cnt]]
+                 "cells": int(r.cells), "pair_tests": int(r.pair_tests),
+                 "fast_tests": int(r.fast_tests)} for r in arr[:cnt]]
 
     def profiles(self):
         bins = int(self.params.profile_bins)
@@ -164,12 +165,13 @@ class Simulation:
         sim_set_timing(self.handle, enable)
 
     def phase_ms(self):
-        """Accumulated ms of the sort, search, matching and push phases, and the number
-        of steps timed (after set_timing(True))."""
-        out = np.zeros(5)
+        """Accumulated ms of the sort, search, matching and push phases, the number of
+        steps timed (after set_timing(True)), and the ms of the slow-population search
+        kernels alone (part of the search phase)."""
+        out = np.zeros(6)
         sim_observe(self.handle, KMC_OBS_PHASE_MS, out.ctypes.data, out.nbytes)
         return {"sort": out[0], "search": out[1], "match": out[2], "push": out[3],
-                "steps": int(out[4])}
+                "steps": int(out[4]), "search_slow": out[5]}
 
     def step_index(self) -> int:
         out = np.zeros(1, dtype=np.uint64)
