@@ -281,6 +281,7 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
     // per particle: (i, j) with j slow has |r| < d0 + (|v_i| + |v_j|) dt <= d0 + S1 dt + |v_i| dt
     g.row_a = f_up((s.d0 + S1 * s.dt) * (1.0 + 1e-6));
     g.row_b = f_up(s.dt * (1.0 + 1e-6));
+    g.fast_a = f_up((s.d0 + V * s.dt) * (1.0 + 1e-6));
     g.row_eps = f_up(16.0 * u32 * Lmax);
     g.row_pad = f_up(4.0 * u32 * Lmax);
   }

@@ -62,8 +62,9 @@ struct Grid {
   // row trimming of the binary32 row search: slow-slow candidates lie within the reach
   // d0 + 2 S1 dt; r2 bounds its square, eps the binary32 error of a distance from a
   // cell edge, pad the error of a coordinate (all rounded up).  Per particle i the
-  // reach is d0 + (|v_i| + S1) dt: at most row_a + row_b |v_i| (both rounded up)
-  float row_r2, row_eps, row_pad, row_a, row_b;
+  // reach is d0 + (|v_i| + S1) dt: at most row_a + row_b |v_i| (both rounded up); for a
+  // fast particle i (partners up to the bound V of max |v|) at most fast_a + row_b |v_i|
+  float row_r2, row_eps, row_pad, row_a, row_b, fast_a;
   // binary64 sphere pre-test: drop if R > c0 + c1 * B (B >= 2^-900)
   double c0, c1;
 };

@@ -725,23 +725,9 @@ struct RowLayout {
   static constexpr int kCols = 1 + K + K * (2 * K + 1);  // own column + forward columns
   static constexpr int kPieces = 2 * kCols;             // a row splits at most once
   static constexpr int kWarps = kTile / 32;
-  // per warp: the lanes' pieces (j range), the owners' records (position and
-  // velocity, 16 + 8 bytes), the pair staging buffer, the pieces' image codes and the
-  // lanes' piece counts; every array starts on a 16-byte boundary
   static constexpr size_t kPieceBytes = (size_t)kWarps * kPieces * 32 * sizeof(uint2);
-  static constexpr size_t kOwnABytes = (size_t)kWarps * 32 * sizeof(float4);
-  static constexpr size_t kOwnBBytes = (size_t)kWarps * 32 * sizeof(float2);
-  static constexpr size_t kBufBytes = (size_t)kWarps * kWarpBuf * sizeof(uint2);
   static constexpr size_t kCodeBytes = (size_t)kWarps * kPieces * 32;
-  static constexpr size_t kNpBytes = (size_t)kWarps * 32;
-  static constexpr size_t kOwnA = kPieceBytes;
-  static constexpr size_t kOwnB = kOwnA + kOwnABytes;
-  static constexpr size_t kBuf = kOwnB + kOwnBBytes;
-  static constexpr size_t kCode = kBuf + kBufBytes;
-  static constexpr size_t kNp = kCode + kCodeBytes;
-  static constexpr size_t kBytes = kNp + kNpBytes;
-  static_assert(kOwnA % 16 == 0 && kOwnB % 16 == 0 && kBuf % 16 == 0 && kCode % 16 == 0 &&
-                    kNp % 16 == 0, "row search shared-memory layout");
+  static constexpr size_t kBytes = kPieceBytes + kCodeBytes + (size_t)kWarps * kWarpBuf * sizeof(uint2);
 };
 
 // image flags of a piece: bit 0 / 1 = seen at +L / -L along x, bits 2-3 y, bits 4-5 z
@@ -785,11 +771,9 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
     const uint32_t p = (tile - B.ptile[k]) * kTile + threadIdx.x;
     if (p - lane >= nslow) continue;  // the whole warp is past the slow population
     uint2* pc = reinterpret_cast<uint2*>(rows_smem) + (size_t)warp * NP * 32;
-    float4* own_a = reinterpret_cast<float4*>(rows_smem + RL::kOwnA) + (size_t)warp * 32;
-    float2* own_b = reinterpret_cast<float2*>(rows_smem + RL::kOwnB) + (size_t)warp * 32;
-    uint2* buf = reinterpret_cast<uint2*>(rows_smem + RL::kBuf) + (size_t)warp * kWarpBuf;
-    uint8_t* cd = rows_smem + RL::kCode + (size_t)warp * NP * 32;
-    uint8_t* nps = rows_smem + RL::kNp + (size_t)warp * 32;
+    uint8_t* cd = rows_smem + RL::kPieceBytes + (size_t)warp * NP * 32;
+    uint2* buf = reinterpret_cast<uint2*>(rows_smem + RL::kPieceBytes + RL::kCodeBytes) +
+                 (size_t)warp * kWarpBuf;
     uint32_t* cnt = &wcount[warp];
     if (lane == 0) *cnt = 0;
     __syncwarp();
@@ -833,7 +817,7 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
       const float R2 = fminf(g.row_r2, Ri * Ri * 1.000001f);
       const float eps = g.row_eps, pad = g.row_pad;
       const float wyf = g.wf[1], wzf = g.wf[2], ivx = g.inv_wf[0];
-#pragma unroll 1
+#pragma unroll
       for (int c = 0; c < RL::kCols; ++c) {
         const int dz = c <= K ? 0 : 1 + (c - K - 1) / (2 * K + 1);
         const int dy = c == 0 ? 0 : (c <= K ? c : (c - K - 1) % (2 * K + 1) - K);
@@ -867,7 +851,11 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
         }
         d2 *= 0.9999995f;
         if (d2 >= R2) continue;
-        const float ex = fmaf(sqrtf(R2 - d2), 1.000001f, pad);
+        // x extent sqrt(R2 - d2) from the approximate reciprocal square root (at most
+        // 2 ulp off, 3 ulp with the product), widened by 33 ulp; the argument is kept
+        // normal, which only widens it
+        const float t2 = fmaxf(R2 - d2, 1e-30f);
+        const float ex = fmaf(t2 * rsqrtf(t2), 1.000004f, pad);
         int xa = c == 0 ? cx : cx - Kx, xb = cx + Kx;  // cells of the row, unwrapped
         if (Kx > 0) {
           const int ta = (int)floorf((o.ox - ex) * ivx), tb = (int)floorf((o.ox + ex) * ivx);
@@ -908,63 +896,23 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
       }
     }
 
-    // 2. walk the pieces with the tests dealt out evenly over the lanes.  The warp's W
-    //    tests, laid out owner by owner (lane order) and piece by piece, are cut into
-    //    32 runs of consecutive tests, lane l taking tests [l W / 32, (l + 1) W / 32);
-    //    a run may start inside one owner's pieces and end inside a later owner's.
-    uint32_t incl = total;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, off);
-      if (lane >= (uint32_t)off) incl += y;
-    }
-    const uint32_t W = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    const uint32_t excl = incl - total;
-    own_a[lane] = make_float4(o.ox, o.oy, o.oz, o.vx);
-    own_b[lane] = make_float2(o.vy, o.vz);
-    nps[lane] = (uint8_t)np;
-    __syncwarp();
-    const uint32_t ta = (uint32_t)(((unsigned long long)lane * W) >> 5);
-    const uint32_t run = (uint32_t)(((unsigned long long)(lane + 1) * W) >> 5) - ta;
-    // owner of test ta: the last lane whose first test is at or before ta (lanes
-    // without tests share their successor's first test and are passed over)
-    uint32_t u = 0;
-#pragma unroll
-    for (uint32_t step = 16; step > 0; step >>= 1) {
-      const uint32_t v = __shfl_sync(0xFFFFFFFFu, excl, u + step);
-      if (v <= ta) u += step;
-    }
-    const uint32_t q0 = ta - __shfl_sync(0xFFFFFFFFu, excl, u);
+    // 2. walk the pieces: one test per iteration
+    const uint32_t T = __reduce_max_sync(0xFFFFFFFFu, total);
     uint32_t j = 0, je = 0;
     int r = 0;
-    float sx = 0.f, sy = 0.f, sz = 0.f, ovx = 0.f, ovy = 0.f, ovz = 0.f;
-    float4 oa = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (run > 0) {
-      // the piece of owner u holding its test q0
-      uint32_t q = q0;
-      uint2 pq = pc[u];
-      while (q >= pq.y - pq.x && r + 1 < (int)nps[u]) {
-        q -= pq.y - pq.x;
-        ++r;
-        pq = pc[r * 32 + u];
-      }
-      j = pq.x + q;
-      je = pq.y;
-      oa = own_a[u];
-      const float2 ob = own_b[u];
-      ovx = oa.w;
-      ovy = ob.x;
-      ovz = ob.y;
-      const float4 sh = shift_tab[cd[r * 32 + u]];
-      sx = oa.x - sh.x;
-      sy = oa.y - sh.y;
-      sz = oa.z - sh.z;
+    float sx = o.ox, sy = o.oy, sz = o.oz;
+    if (np > 0) {
+      const uint2 q = pc[lane];
+      const float4 sh = shift_tab[cd[lane]];
+      j = q.x;
+      je = q.y;
+      sx = o.ox - sh.x;
+      sy = o.oy - sh.y;
+      sz = o.oz - sh.z;
     }
-    const uint32_t T = (W + 31u) >> 5;  // the longest run
     const float c0 = g.s_c0, c1 = g.s_c1;
-    const uint32_t p0 = p - lane;
     for (uint32_t t = 0; t < T; ++t) {
-      if (t < run) {
+      if (j < je) {
         const float4 a = __ldg(MA + j);
         const float2 b = __ldg(MB + j);
         float rx = a.x - sx, ry = a.y - sy, rz = a.z - sz;
@@ -974,36 +922,27 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
           if (cp1) min_image_f(ry, g.halfLf[1], g.Lf[1], g.tief[1], keep);
           if (cp2) min_image_f(rz, g.halfLf[2], g.Lf[2], g.tief[2], keep);
         }
-        const float gx = a.w - ovx, gy = b.x - ovy, gz = b.y - ovz;
+        const float gx = a.w - o.vx, gy = b.x - o.vy, gz = b.y - o.vz;
         const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
         const float Bv = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
         if (keep || (R <= fmaf(c1, Bv, c0) && full_test32(sq, rx, ry, rz, gx, gy, gz, Bv)))
-          emit_lane(buf, cnt, s, p0 + u, j);
-        if (++j == je && t + 1 < run) {
-          // next piece of this owner, else the first piece of the next owner with tests
-          if (++r >= (int)nps[u]) {
-            r = 0;
-            do {
-              ++u;
-            } while (u < 31 && nps[u] == 0);  // a later owner holds the run's remaining tests
-            oa = own_a[u];
-            const float2 ob = own_b[u];
-            ovx = oa.w;
-            ovy = ob.x;
-            ovz = ob.y;
-          }
-          const uint2 pq = pc[r * 32 + u];
-          const float4 sh = shift_tab[cd[r * 32 + u]];
-          j = pq.x;
-          je = pq.y;
-          sx = oa.x - sh.x;
-          sy = oa.y - sh.y;
-          sz = oa.z - sh.z;
+          emit_lane(buf, cnt, s, p, j);
+        if (++j == je && r + 1 < np) {
+          ++r;
+          const uint2 q = pc[r * 32 + lane];
+          const float4 sh = shift_tab[cd[r * 32 + lane]];
+          j = q.x;
+          je = q.y;
+          sx = o.ox - sh.x;
+          sy = o.oy - sh.y;
+          sz = o.oz - sh.z;
         }
       }
     }
     flush_lanes(buf, cnt, s, lane);
-    if (lane == 0 && W) atomicAdd(&s.d.pair_tests, (unsigned long long)W);
+    unsigned long long tests = total;
+    for (int off = 16; off > 0; off >>= 1) tests += __shfl_down_sync(0xFFFFFFFFu, tests, off);
+    if (lane == 0 && tests) atomicAdd(&s.d.pair_tests, tests);
   }
 }
 
@@ -1079,11 +1018,23 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
       if (PREC == KMC_FP64) {
         xo[0] = X0[p]; xo[1] = X1[p]; xo[2] = X2[p];
         vo[0] = V0[p]; vo[1] = V1[p]; vo[2] = V2[p];
+        // binary32 position and velocity for the cell trimming only
+        o32 = {d2f_rn(xo[0]), d2f_rn(xo[1]), d2f_rn(xo[2]), d2f_rn(vo[0]), d2f_rn(vo[1]),
+               d2f_rn(vo[2])};
       } else {
         const float4 a = MA[p];
         const float2 b = MB[p];
         o32 = {a.x, a.y, a.z, a.w, b.x, b.y};
       }
+      // cell trimming: a pair (p, j) has |r| < d0 + (|v_p| + |v_j|) dt <= d0 + (|v_p| + V) dt,
+      // so a stencil cell farther than that from p holds no candidate.  |v_p| from the
+      // binary32 velocity times 1 + 2e-6 bounds it from above; the distance to a cell is
+      // taken from its edges less eps (the binary32 error of a coordinate against a
+      // cell edge), rounded down.
+      const float sp = sqrtf(fmaf(o32.vz, o32.vz, fmaf(o32.vy, o32.vy, o32.vx * o32.vx))) * 1.000002f;
+      const float Rp = fmaf(sp, g.row_b, g.fast_a) * 1.000001f;
+      const float Rp2 = Rp * Rp * 1.000001f;
+      const float teps = g.row_eps;
       for (int c0 = 0; c0 < ncell; c0 += 32) {
         // this lane's stencil cell and its two candidate ranges
         const int c = c0 + (int)lane;
@@ -1097,7 +1048,30 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
           const int wx = qx < 0 ? -1 : (qx >= nx ? 1 : 0);
           const int wy = qy < 0 ? -1 : (qy >= ny ? 1 : 0);
           const int wz = qz < 0 ? -1 : (qz >= nz ? 1 : 0);
-          const bool ok = (wx == 0 || px) && (wy == 0 || py) && (wz == 0 || pz);
+          bool ok = (wx == 0 || px) && (wy == 0 || py) && (wz == 0 || pz);
+          {
+            // squared distance from p to the cell (unwrapped: the image frame of p)
+            float d2 = 0.f;
+            if (dx != 0 && nx > 1) {
+              const float e = dx > 0 ? (float)(cx + dx) * g.wf[0] - o32.ox
+                                     : o32.ox - (float)(cx + dx + 1) * g.wf[0];
+              const float el = fmaxf(e - teps, 0.f);
+              d2 = el * el;
+            }
+            if (dy != 0 && ny > 1) {
+              const float e = dy > 0 ? (float)(cy + dy) * g.wf[1] - o32.oy
+                                     : o32.oy - (float)(cy + dy + 1) * g.wf[1];
+              const float el = fmaxf(e - teps, 0.f);
+              d2 = fmaf(el, el, d2);
+            }
+            if (dz != 0 && nz > 1) {
+              const float e = dz > 0 ? (float)(cz + dz) * g.wf[2] - o32.oz
+                                     : o32.oz - (float)(cz + dz + 1) * g.wf[2];
+              const float el = fmaxf(e - teps, 0.f);
+              d2 = fmaf(el, el, d2);
+            }
+            if (d2 * 0.9999995f >= Rp2) ok = false;
+          }
           qx -= wx * nx;
           qy -= wy * ny;
           qz -= wz * nz;

@@ -3,7 +3,8 @@
 //
 // GB300 form: a counting sort into a column-Morton cell order.
 //   k_count   cell key per particle; rank inside the cell by a warp-aggregated
-//             atomic increment (lanes with equal keys share one atomic).
+//             atomic increment (a run of equal keys in neighbouring lanes shares one
+//             atomic).
 //   scan      segmented exclusive scan of the counts -> cell_start (three launches,
 //             no inter-block waiting); clears the counts for the next step.
 //   k_scatter records the source of every position of the new order;
@@ -36,18 +37,29 @@ __global__ void __launch_bounds__(kTile) k_count(Batch B) {
     // exactly when the bound exceeds at least 7 - split_t of the six trial values)
     if (g.split && (int)s.vbucket[p] >= kSplitTrials - g.split_t) key += g.nkeys;
   }
-  // warp aggregation: one atomic per distinct key in the warp
-  unsigned active = __ballot_sync(0xFFFFFFFFu, valid);
+  // warp aggregation over runs of equal keys: the particles come in the previous
+  // step's cell order, so equal keys mostly sit in neighbouring lanes.  Each run of
+  // equal keys in consecutive lanes takes one atomic for all its members (a key that
+  // appears in two runs takes two; the ranks stay distinct either way).
+  const unsigned lane = threadIdx.x & 31u;
+  const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, key, 1);
+  const bool head = valid && (lane == 0 || prev != key);  // valid lanes are a prefix
+  const unsigned heads = __ballot_sync(0xFFFFFFFFu, head);
+  const unsigned vmask = __ballot_sync(0xFFFFFFFFu, valid);
+  // this lane's run: from the last head at or below it to the next head (or the end
+  // of the valid lanes)
+  const unsigned le = heads & (0xFFFFFFFFu >> (31u - lane));
+  const int lead = 31 - __clz((int)le);
+  uint32_t base = 0;
+  if (head) {
+    const unsigned above = heads & ~(0xFFFFFFFFu >> (31u - lane));  // heads past this lane
+    const int next = above ? __ffs((int)above) - 1 : 32 - __clz((int)vmask);
+    base = atomicAdd(&s.cell_count[key], (uint32_t)(next - (int)lane));
+  }
+  base = __shfl_sync(0xFFFFFFFFu, base, lead < 0 ? 0 : lead);
   if (valid) {
-    unsigned peers = __match_any_sync(active, key);
-    int leader = __ffs(peers) - 1;
-    unsigned lane = threadIdx.x & 31u;
-    uint32_t base = 0;
-    if ((int)lane == leader) base = atomicAdd(&s.cell_count[key], (uint32_t)__popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    uint32_t below = __popc(peers & ((1u << lane) - 1u));
     s.key[p] = key;
-    s.rank[p] = base + below;
+    s.rank[p] = base + (lane - (uint32_t)lead);
   }
 }
 
