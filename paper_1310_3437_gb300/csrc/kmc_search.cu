@@ -489,6 +489,15 @@ __device__ __forceinline__ bool full_test32(const Guard32& q, float rx, float ry
   return !(W > thr * thr * q.wrel);
 }
 
+// The same test behind a real call: inlined, the compiler predicates it into every
+// lane's instruction stream (about 30 instructions per pair although only the rare
+// sphere survivors need it); as a call it issues only when some lane of the warp
+// takes the branch.
+__device__ __noinline__ bool full_test32_call(const Guard32& q, float rx, float ry, float rz,
+                                              float vx, float vy, float vz, float Bv) {
+  return full_test32(q, rx, ry, rz, vx, vy, vz, Bv);
+}
+
 // Emission from divergent lanes: a shared-memory counter per warp; entries that do
 // not fit in the warp's buffer go straight to the global list.
 __device__ __forceinline__ void emit_lane(uint2* buf, uint32_t* count, SimDev& s, uint32_t i,
@@ -795,13 +804,38 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
     int np = 0;
     uint32_t total = 0;
     Own32 o = {0, 0, 0, 0, 0, 0};
+    int cx = 0, cy = 0, cz = 0;
     if (valid) {
       const float4 a = MA[p];
       const float2 b = MB[p];
       o = {a.x, a.y, a.z, a.w, b.x, b.y};
       // the particle's cell, recomputed from the mirror as the sort computed it
-      const int cx = cell_coord_f(g, 0, a.x), cy = cell_coord_f(g, 1, a.y),
-                cz = cell_coord_f(g, 2, a.z);
+      cx = cell_coord_f(g, 0, a.x);
+      cy = cell_coord_f(g, 1, a.y);
+      cz = cell_coord_f(g, 2, a.z);
+    }
+    // Nearly every warp lies in one (y, z) column (a column holds thousands of
+    // particles in cell order).  Then the forward columns are the same for all lanes:
+    // lane c works out column c (whether it exists, its key base, its image code)
+    // once for the warp.  Lane 0 is valid whenever any lane is.
+    const int cy0 = __shfl_sync(0xFFFFFFFFu, cy, 0), cz0 = __shfl_sync(0xFFFFFFFFu, cz, 0);
+    const bool uni = __all_sync(0xFFFFFFFFu, !valid || (cy == cy0 && cz == cz0));
+    uint32_t ctab = kNone, ctag = 0;
+    if (uni && lane < (uint32_t)RL::kCols) {
+      const int c = (int)lane;
+      const int dz = c <= K ? 0 : 1 + (c - K - 1) / (2 * K + 1);
+      const int dy = c == 0 ? 0 : (c <= K ? c : (c - K - 1) % (2 * K + 1) - K);
+      int qz = cz0 + dz, wz = 0, qy = cy0 + dy, wy = 0;
+      bool ok = !(dz > Kz || dy > Ky || dy < -Ky);
+      if (qz >= nz) { ok = ok && pz; qz -= nz; wz = 1; }
+      if (qy < 0) { ok = ok && py; qy += ny; wy = -1; }
+      else if (qy >= ny) { ok = ok && py; qy -= ny; wy = 1; }
+      if (ok) {
+        ctab = col_code(g, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx;
+        ctag = (uint32_t)(wy & 3) | ((uint32_t)(wz & 3) << 2);
+      }
+    }
+    {
       // row trimming: the part of each row within the reach of this particle.  A
       // column whose cells lie farther than the reach in (y, z) is skipped; in the
       // others only the cells with x within sqrt(reach^2 - d^2) are kept (d the
@@ -821,23 +855,36 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
       for (int c = 0; c < RL::kCols; ++c) {
         const int dz = c <= K ? 0 : 1 + (c - K - 1) / (2 * K + 1);
         const int dy = c == 0 ? 0 : (c <= K ? c : (c - K - 1) % (2 * K + 1) - K);
-        if (dz > Kz || dy > Ky || dy < -Ky) continue;
-        int qz = cz + dz, wz = 0;
-        if (qz >= nz) {
-          if (!pz) continue;
-          qz -= nz;
-          wz = 1;
+        // the column's key base and image flags (warp table, or this lane's own)
+        uint32_t colb, wtag;
+        if (uni) {
+          colb = __shfl_sync(0xFFFFFFFFu, ctab, c);
+          wtag = __shfl_sync(0xFFFFFFFFu, ctag, c);
+          if (colb == kNone) continue;
+        } else {
+          if (dz > Kz || dy > Ky || dy < -Ky) continue;
+          int qz = cz + dz, wz = 0;
+          if (qz >= nz) {
+            if (!pz) continue;
+            qz -= nz;
+            wz = 1;
+          }
+          int qy = cy + dy, wy = 0;
+          if (qy < 0) {
+            if (!py) continue;
+            qy += ny;
+            wy = -1;
+          } else if (qy >= ny) {
+            if (!py) continue;
+            qy -= ny;
+            wy = 1;
+          }
+          colb = col_code(g, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx;
+          wtag = (uint32_t)(wy & 3) | ((uint32_t)(wz & 3) << 2);
         }
-        int qy = cy + dy, wy = 0;
-        if (qy < 0) {
-          if (!py) continue;
-          qy += ny;
-          wy = -1;
-        } else if (qy >= ny) {
-          if (!py) continue;
-          qy -= ny;
-          wy = 1;
-        }
+        if (!valid) continue;
+        const int wy = (wtag & 3u) == 3u ? -1 : (int)(wtag & 3u);
+        const int wz = (int)((wtag >> 2) & 3u);
         float d2 = 0.f;
         if (dy != 0) {
           const float e = dy > 0 ? (float)(cy + dy) * wyf - o.oy : o.oy - (float)(cy + dy + 1) * wyf;
@@ -863,7 +910,6 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
           if (tb <= nx - 1 && tb < xb) xb = tb;
           if (xb < xa) continue;
         }
-        const uint32_t colb = col_code(g, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx;
         {
           const int a0 = xa < 0 ? 0 : xa, b0 = xb >= nx ? nx - 1 : xb;
           const uint32_t jb = c == 0 ? p + 1 : __ldg(cs + colb + a0);
@@ -925,7 +971,7 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
         const float gx = a.w - o.vx, gy = b.x - o.vy, gz = b.y - o.vz;
         const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
         const float Bv = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
-        if (keep || (R <= fmaf(c1, Bv, c0) && full_test32(sq, rx, ry, rz, gx, gy, gz, Bv)))
+        if (keep || (R <= fmaf(c1, Bv, c0) && full_test32_call(sq, rx, ry, rz, gx, gy, gz, Bv)))
           emit_lane(buf, cnt, s, p, j);
         if (++j == je && r + 1 < np) {
           ++r;
