@@ -757,24 +757,31 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
   // occupancy-sized grid and exits at once when the step runs another search
   if (!batch_uses(B, KMC_SEARCH_ROW)) return;
   const uint32_t ntiles = B.ptile[B.nsims];
+  int kcur = -1;  // simulation whose constants the shared tables hold
   for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int k = find_sim(B.ptile, B.nsims, tile);
     SimDev& s = *B.sims[k];
     if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_ROW) continue;
     const Grid& g = s.d.grid;
-    __syncthreads();  // the previous tile is done with the shared constants
-    if (threadIdx.x == 0) {
-      sq.c0 = g.s_c0; sq.c1 = g.s_c1; sq.ag = g.a_g; sq.tg = g.t_g; sq.dtf = g.dtf;
-      sq.d0up = g.d0up; sq.brel = g.b_rel; sq.babs = g.b_abs; sq.we = g.w_e; sq.wrel = g.w_rel;
+    // The shared constants change only with the simulation (block-uniform: every warp
+    // walks the same tiles), so the warps of a block need not wait for each other at
+    // every tile: each runs on to its part of the next tile.
+    if (k != kcur) {
+      __syncthreads();  // every warp is done with the previous simulation's constants
+      if (threadIdx.x == 0) {
+        sq.c0 = g.s_c0; sq.c1 = g.s_c1; sq.ag = g.a_g; sq.tg = g.t_g; sq.dtf = g.dtf;
+        sq.d0up = g.d0up; sq.brel = g.b_rel; sq.babs = g.b_abs; sq.we = g.w_e; sq.wrel = g.w_rel;
+      }
+      if (threadIdx.x < 64) {
+        const uint32_t c = threadIdx.x;
+        const float w0 = (float)((int)(c & 1u) - (int)((c >> 1) & 1u));
+        const float w1 = (float)((int)((c >> 2) & 1u) - (int)((c >> 3) & 1u));
+        const float w2 = (float)((int)((c >> 4) & 1u) - (int)((c >> 5) & 1u));
+        shift_tab[c] = make_float4(w0 * g.Lf[0], w1 * g.Lf[1], w2 * g.Lf[2], 0.f);
+      }
+      __syncthreads();
+      kcur = k;
     }
-    if (threadIdx.x < 64) {
-      const uint32_t c = threadIdx.x;
-      const float w0 = (float)((int)(c & 1u) - (int)((c >> 1) & 1u));
-      const float w1 = (float)((int)((c >> 2) & 1u) - (int)((c >> 3) & 1u));
-      const float w2 = (float)((int)((c >> 4) & 1u) - (int)((c >> 5) & 1u));
-      shift_tab[c] = make_float4(w0 * g.Lf[0], w1 * g.Lf[1], w2 * g.Lf[2], 0.f);
-    }
-    __syncthreads();
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t nslow = g.split ? __ldg(s.cell_start + g.nkeys) : s.n;
     const uint32_t p = (tile - B.ptile[k]) * kTile + threadIdx.x;
