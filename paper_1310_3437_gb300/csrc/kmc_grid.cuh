@@ -92,7 +92,9 @@ __device__ inline double search_cost(double n, double rho, int K) {
   return n * st * rho * eff;
 }
 
-__device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step) {
+// Called by all 32 lanes of a warp: lane t < kSplitTrials estimates the cost of
+// trial threshold t, lane 0 chooses and writes the grid (the others only read).
+__device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step, uint32_t lane) {
   Grid& g = s.d.grid;
   const double u32 = 0x1p-24, u64 = 0x1p-53;
   const int K = s.K;
@@ -109,30 +111,32 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
     }
   }
 
-  // ---- split threshold: estimated pair-test cost of each trial ----------------
-  bool feasible[kSplitTrials];
-  double cost[kSplitTrials];
+  // ---- split threshold: estimated pair-test cost of each trial (one lane each) --
   const bool can_split = s.split_ok && s.d.have_counts;
-  for (int t = 0; t < kSplitTrials; ++t) {
-    feasible[t] = false;
-    cost[t] = 0.0;
-    if (t > 0 && !can_split) continue;
+  bool my_feasible = false;
+  double my_cost = 0.0;
+  if (lane < (uint32_t)kSplitTrials) {
+    const int t = (int)lane;
+    bool feasible_t = false;
+    double cost_t = 0.0;
+    do {
+    if (t > 0 && !can_split) break;
     // trial thresholds were set from the previous step's bound; the slow cell must
     // cover the threshold actually used for classification (a binary32 square)
     const float sq = t == 0 ? 0.0f : s.d.split_thr[t];
     const double S1 = t == 0 ? V : sqrt((double)sq);
-    if (t > 0 && !(S1 < V)) continue;
+    if (t > 0 && !(S1 < V)) break;
     const double hs = (s.d0 + 2.0 * S1 * s.dt) * scale;
     CellPlan p = plan_cells(ext, hs, K, (uint64_t)s.cell_cap / (t == 0 ? 1 : 2));
-    if (!p.ok) continue;
+    if (!p.ok) break;
     const double cells = (double)p.nc[0] * p.nc[1] * p.nc[2];
     const double rho = (double)s.n / cells;
     if (t == 0) {
-      cost[t] = search_cost((double)s.n, rho, K);
-      feasible[t] = true;
-      continue;
+      cost_t = search_cost((double)s.n, rho, K);
+      feasible_t = true;
+      break;
     }
-    if (s.split_ok == 1 && rho < s.split_min_occ) continue;
+    if (s.split_ok == 1 && rho < s.split_min_occ) break;
     // fast stencil: c cells on each side per split axis; periodic axes must hold it,
     // and no axis may be a one-cell periodic axis (no minimum-image test there)
     const double nfast = (double)s.d.split_cnt[t];
@@ -149,10 +153,20 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step)
       if (s.bc[a] == KMC_PERIODIC && p.nc[a] < 2 * c + 2) fits = false;
       fast_cells *= (2.0 * c + 1.0);
     }
-    if (!fits) continue;
-    cost[t] = search_cost((double)s.n - nfast, rho, K) + nfast * fast_cells * rho * 3.0;
-    feasible[t] = true;
+    if (!fits) break;
+    cost_t = search_cost((double)s.n - nfast, rho, K) + nfast * fast_cells * rho * 3.0;
+    feasible_t = true;
+    } while (false);
+    my_feasible = feasible_t;
+    my_cost = cost_t;
   }
+  bool feasible[kSplitTrials];
+  double cost[kSplitTrials];
+  for (int t = 0; t < kSplitTrials; ++t) {
+    feasible[t] = __shfl_sync(0xFFFFFFFFu, my_feasible ? 1 : 0, t) != 0;
+    cost[t] = __shfl_sync(0xFFFFFFFFu, my_cost, t);
+  }
+  if (lane != 0) return;  // lane 0 chooses the threshold and writes the grid
   int best = 0;
   if (s.split_ok == 2) {
     // forced: cycle through the feasible trial thresholds step by step

@@ -286,7 +286,8 @@ struct LaunchPlan {
   int edge_blocks;
   int cell_blocks;  // persistent grid of the warp-per-cell search
   int part_blocks;  // grid-stride grids of the particle, row and fast searches
-  int row_blocks;
+  int row_blocks;     // row search, no periodic x axis
+  int row_blocks_px;  // row search, periodic x axis
   int fast_blocks;
 };
 

@@ -211,43 +211,53 @@ __device__ void set_prof_due(SimDev& s) {
                   (s.d.step + 1) % (uint64_t)s.profile_every == 0) ? 1u : 0u;
 }
 
+// one warp per simulation: lane 0 keeps the books, the warp builds the next grid
 __global__ void k_finalize(Batch B) {
-  for (int k = threadIdx.x; k < B.nsims; k += blockDim.x) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const int nwarps = (int)(gridDim.x * blockDim.x / 32u);
+  for (int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) / 32u); k < B.nsims; k += nwarps) {
     SimDev& s = *B.sims[k];
     if (!sim_active(s)) continue;
-    kmc_step_counts rec;
-    rec.step = s.d.step;
-    uint32_t coll = 0;
-    for (int r = 0; r < 4; ++r) {
-      rec.round_pairs[r] = s.d.round_pairs[r];
-      coll += s.d.round_pairs[r];
+    if (lane == 0) {
+      kmc_step_counts rec;
+      rec.step = s.d.step;
+      uint32_t coll = 0;
+      for (int r = 0; r < 4; ++r) {
+        rec.round_pairs[r] = s.d.round_pairs[r];
+        coll += s.d.round_pairs[r];
+      }
+      rec.collisions = coll;
+      rec.edges = s.d.n_edges;
+      rec.survivors = s.d.n_raw;
+      rec.cells = s.d.grid.nkeys;
+      rec.pair_tests = s.d.pair_tests;
+      rec.fast_tests = s.d.fast_tests;
+      s.hist[s.d.hist_count % s.hist_cap] = rec;
+      s.d.hist_count += 1;
+      if (s.d.prof_due) {
+        s.prof_step[s.d.prof_count % s.prof_cap] = s.d.step;
+        s.d.prof_count += 1;
+      }
+      s.d.last_raw = s.d.n_raw;
+      s.d.have_counts = s.split_ok ? 1u : 0u;
+      s.d.parity ^= 1u;
+      s.d.step += 1;
+      s.d.steps_left -= 1;
+      s.d.vmax2 = __uint_as_float(s.d.vmax2_acc);
     }
-    rec.collisions = coll;
-    rec.edges = s.d.n_edges;
-    rec.survivors = s.d.n_raw;
-    rec.cells = s.d.grid.nkeys;
-    rec.pair_tests = s.d.pair_tests;
-    rec.fast_tests = s.d.fast_tests;
-    s.hist[s.d.hist_count % s.hist_cap] = rec;
-    s.d.hist_count += 1;
-    if (s.d.prof_due) {
-      s.prof_step[s.d.prof_count % s.prof_cap] = s.d.step;
-      s.d.prof_count += 1;
+    __syncwarp();
+    compute_grid(s, s.d.vmax2, s.d.step, lane);
+    __syncwarp();
+    if (lane == 0) {
+      reset_step_counters(s);
+      set_prof_due(s);
     }
-    s.d.last_raw = s.d.n_raw;
-    s.d.have_counts = s.split_ok ? 1u : 0u;
-    s.d.parity ^= 1u;
-    s.d.step += 1;
-    s.d.steps_left -= 1;
-    float vm = __uint_as_float(s.d.vmax2_acc);
-    s.d.vmax2 = vm;
-    compute_grid(s, vm, s.d.step);
-    reset_step_counters(s);
-    set_prof_due(s);
+    __syncwarp();
     if (s.d.prof_due) {
       long long* out = s.prof_acc + (size_t)(s.d.prof_count % s.prof_cap) * s.profile_bins * kProfQ;
-      for (int i = 0; i < s.profile_bins * kProfQ; ++i) out[i] = 0;
+      for (int i = (int)lane; i < s.profile_bins * kProfQ; i += 32) out[i] = 0;
     }
+    __syncwarp();
   }
 }
 
@@ -264,19 +274,29 @@ __global__ void __launch_bounds__(kTile) k_vmax(Batch B) {
   block_max_to(&s.d.vmax2_acc, vm);
 }
 
+// one warp per simulation, as k_finalize
 __global__ void k_init_grid(Batch B) {
-  for (int k = threadIdx.x; k < B.nsims; k += blockDim.x) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const int nwarps = (int)(gridDim.x * blockDim.x / 32u);
+  for (int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) / 32u); k < B.nsims; k += nwarps) {
     SimDev& s = *B.sims[k];
-    float vm = __uint_as_float(s.d.vmax2_acc);
-    s.d.vmax2 = vm;
-    s.d.have_counts = 0;
-    compute_grid(s, vm, s.d.step);
-    reset_step_counters(s);
-    set_prof_due(s);
+    if (lane == 0) {
+      s.d.vmax2 = __uint_as_float(s.d.vmax2_acc);
+      s.d.have_counts = 0;
+    }
+    __syncwarp();
+    compute_grid(s, s.d.vmax2, s.d.step, lane);
+    __syncwarp();
+    if (lane == 0) {
+      reset_step_counters(s);
+      set_prof_due(s);
+    }
+    __syncwarp();
     if (s.d.prof_due && s.prof_acc) {
       long long* out = s.prof_acc + (size_t)(s.d.prof_count % s.prof_cap) * s.profile_bins * kProfQ;
-      for (int i = 0; i < s.profile_bins * kProfQ; ++i) out[i] = 0;
+      for (int i = (int)lane; i < s.profile_bins * kProfQ; i += 32) out[i] = 0;
     }
+    __syncwarp();
   }
 }
 
@@ -287,14 +307,14 @@ __global__ void k_zero_vmax(Batch B) {
 int launch_init_grid(const LaunchPlan& L, cudaStream_t st) {
   k_zero_vmax<<<1, 256, 0, st>>>(L.b);
   k_vmax<<<L.ptiles, kTile, 0, st>>>(L.b);
-  k_init_grid<<<1, 256, 0, st>>>(L.b);
+  k_init_grid<<<(L.b.nsims + 7) / 8, 256, 0, st>>>(L.b);
   return 3;
 }
 
 int launch_push(const LaunchPlan& L, cudaStream_t st) {
   k_push<<<L.ptiles, kTile, 0, st>>>(L.b);
   k_profile<<<L.prtiles, kTile, 256 * kProfQ * sizeof(long long), st>>>(L.b);
-  k_finalize<<<1, 256, 0, st>>>(L.b);
+  k_finalize<<<(L.b.nsims + 7) / 8, 256, 0, st>>>(L.b);
   return 3;
 }
 

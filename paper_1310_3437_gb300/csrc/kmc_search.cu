@@ -728,11 +728,13 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_cell32(Batch B) {
 // into two pieces, the far one seen through its image.  Each lane lists its
 // non-empty pieces in shared memory and then walks them as one sequence of tests,
 // one test per iteration, so no per-cell loop and no per-cell shift remain.  The
-// warp runs as many iterations as its busiest lane needs.
-template <int K>
+// warp runs as many iterations as its busiest lane needs.  Rows split only on a
+// periodic x axis (PX); without one the piece lists take half the shared memory,
+// which leaves more of the SM's L1 to cache the partner records.
+template <int K, bool PX>
 struct RowLayout {
   static constexpr int kCols = 1 + K + K * (2 * K + 1);  // own column + forward columns
-  static constexpr int kPieces = 2 * kCols;             // a row splits at most once
+  static constexpr int kPieces = PX ? 2 * kCols : kCols; // a row splits at most once
   static constexpr int kWarps = kTile / 32;
   static constexpr size_t kPieceBytes = (size_t)kWarps * kPieces * 32 * sizeof(uint2);
   static constexpr size_t kCodeBytes = (size_t)kWarps * kPieces * 32;
@@ -745,9 +747,9 @@ __device__ __forceinline__ uint32_t image_code(int wx, int wy, int wz) {
          ((uint32_t)(wy < 0) << 3) | ((uint32_t)(wz > 0) << 4) | ((uint32_t)(wz < 0) << 5);
 }
 
-template <int K>
+template <int K, bool PX>
 __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
-  using RL = RowLayout<K>;
+  using RL = RowLayout<K, PX>;
   constexpr int NP = RL::kPieces;
   extern __shared__ __align__(16) unsigned char rows_smem[];
   __shared__ uint32_t wcount[RL::kWarps];
@@ -761,7 +763,8 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
   for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int k = find_sim(B.ptile, B.nsims, tile);
     SimDev& s = *B.sims[k];
-    if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_ROW) continue;
+    if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_ROW || (s.bc[0] == KMC_PERIODIC) != PX)
+      continue;
     const Grid& g = s.d.grid;
     // The shared constants change only with the simulation (block-uniform: every warp
     // walks the same tiles), so the warps of a block need not wait for each other at
@@ -798,8 +801,8 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
     const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
     // along x the grid may have narrower cells under the row search (kx per radius)
     const int Kx = nx == 1 ? 0 : g.kx, Ky = ny == 1 ? 0 : K, Kz = nz == 1 ? 0 : K;
-    const bool px = s.bc[0] == KMC_PERIODIC, py = s.bc[1] == KMC_PERIODIC,
-               pz = s.bc[2] == KMC_PERIODIC;
+    constexpr bool px = PX;
+    const bool py = s.bc[1] == KMC_PERIODIC, pz = s.bc[2] == KMC_PERIODIC;
     // one-cell periodic axes need the minimum image explicitly
     const bool cp0 = nx == 1 && px, cp1 = ny == 1 && py, cp2 = nz == 1 && pz;
     const bool any_cp = cp0 || cp1 || cp2;
@@ -1235,23 +1238,30 @@ void search_grids(int precision, int K, int num_sms, uint32_t ptiles, LaunchPlan
     L.part_blocks = cap(K == 2 ? resident_blocks(k_search<KMC_FP64, 2>, kTile, 0, num_sms)
                                : resident_blocks(k_search<KMC_FP64, 1>, kTile, 0, num_sms));
     L.row_blocks = 0;
+    L.row_blocks_px = 0;
     L.fast_blocks = cap(resident_blocks(k_search_fast<KMC_FP64>, kCellWarps * 32, 0, num_sms));
     return;
   }
   // the row search keeps its piece lists in dynamic shared memory (above 48 KB for
   // K = 2); set before any launch or capture
   if (K == 2) {
-    cudaFuncSetAttribute(k_search_rows32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)RowLayout<2>::kBytes);
+    cudaFuncSetAttribute(k_search_rows32<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)RowLayout<2, true>::kBytes);
+    cudaFuncSetAttribute(k_search_rows32<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)RowLayout<2, false>::kBytes);
     L.cell_blocks = resident_blocks(k_search_cell32<2>, kCellWarps * 32, 0, num_sms);
     L.part_blocks = cap(resident_blocks(k_search<KMC_GUARDED_FP32, 2>, kTile, 0, num_sms));
-    L.row_blocks = cap(resident_blocks(k_search_rows32<2>, kTile, RowLayout<2>::kBytes, num_sms));
+    L.row_blocks = cap(resident_blocks(k_search_rows32<2, false>, kTile, RowLayout<2, false>::kBytes, num_sms));
+    L.row_blocks_px = cap(resident_blocks(k_search_rows32<2, true>, kTile, RowLayout<2, true>::kBytes, num_sms));
   } else {
-    cudaFuncSetAttribute(k_search_rows32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)RowLayout<1>::kBytes);
+    cudaFuncSetAttribute(k_search_rows32<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)RowLayout<1, true>::kBytes);
+    cudaFuncSetAttribute(k_search_rows32<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)RowLayout<1, false>::kBytes);
     L.cell_blocks = resident_blocks(k_search_cell32<1>, kCellWarps * 32, 0, num_sms);
     L.part_blocks = cap(resident_blocks(k_search<KMC_GUARDED_FP32, 1>, kTile, 0, num_sms));
-    L.row_blocks = cap(resident_blocks(k_search_rows32<1>, kTile, RowLayout<1>::kBytes, num_sms));
+    L.row_blocks = cap(resident_blocks(k_search_rows32<1, false>, kTile, RowLayout<1, false>::kBytes, num_sms));
+    L.row_blocks_px = cap(resident_blocks(k_search_rows32<1, true>, kTile, RowLayout<1, true>::kBytes, num_sms));
   }
   L.fast_blocks = cap(resident_blocks(k_search_fast<KMC_GUARDED_FP32>, kCellWarps * 32, 0, num_sms));
 }
@@ -1273,17 +1283,19 @@ int launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st, cu
     if (K == 2) {
       k_search<KMC_GUARDED_FP32, 2><<<L.part_blocks, kTile, 0, st>>>(L.b);
       k_search_cell32<2><<<cb, kCellWarps * 32, 0, st>>>(L.b);
-      k_search_rows32<2><<<L.row_blocks, kTile, RowLayout<2>::kBytes, st>>>(L.b);
+      k_search_rows32<2, false><<<L.row_blocks, kTile, RowLayout<2, false>::kBytes, st>>>(L.b);
+      k_search_rows32<2, true><<<L.row_blocks_px, kTile, RowLayout<2, true>::kBytes, st>>>(L.b);
     } else {
       k_search<KMC_GUARDED_FP32, 1><<<L.part_blocks, kTile, 0, st>>>(L.b);
       k_search_cell32<1><<<cb, kCellWarps * 32, 0, st>>>(L.b);
-      k_search_rows32<1><<<L.row_blocks, kTile, RowLayout<1>::kBytes, st>>>(L.b);
+      k_search_rows32<1, false><<<L.row_blocks, kTile, RowLayout<1, false>::kBytes, st>>>(L.b);
+      k_search_rows32<1, true><<<L.row_blocks_px, kTile, RowLayout<1, true>::kBytes, st>>>(L.b);
     }
   }
   if (ev_slow) cudaEventRecord(ev_slow[1], st);
   if (precision == KMC_FP64) k_search_fast<KMC_FP64><<<L.fast_blocks, kCellWarps * 32, 0, st>>>(L.b);
   else k_search_fast<KMC_GUARDED_FP32><<<L.fast_blocks, kCellWarps * 32, 0, st>>>(L.b);
-  return precision == KMC_FP64 ? 3 : 4;
+  return precision == KMC_FP64 ? 3 : 5;
 }
 
 }  // namespace kmc
