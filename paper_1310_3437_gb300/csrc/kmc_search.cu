@@ -1006,19 +1006,25 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
 // --------------------------------------------------------------------------- //
 // Fast particles of the speed split: one warp per fast particle p, searching cfast
 // cells on each side over both populations -- every slow particle, and the fast
-// particles j > p (each fast-fast pair once).  The lanes first take one stencil cell
-// each and read its two candidate ranges; a warp prefix sum over the range lengths
-// then deals the candidates of 32 cells out to the lanes, so every lane tests a pair
-// in every iteration whatever the cell occupancies.  The pair tests are those of the
+// particles j > p (each fast-fast pair once).  The stencil is walked by (y, z)
+// columns: the lanes take one column each, trim its row of cells along x to p's
+// reach (as the row search does) and read its slow and fast partner ranges -- a row
+// is contiguous in the cell order, so a column costs four loads of the cell table
+// whatever its length.  A warp prefix sum over the lanes' test counts then deals the
+// tests of 32 columns out to the lanes, so every lane tests a pair in every
+// iteration whatever the occupancies.  The pair tests are those of the
 // thread-per-particle search.
 template <int PREC>
 __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
   __shared__ uint2 wbuf[kCellWarps][kWarpBuf];
   __shared__ uint32_t wcount[kCellWarps];
-  // per stencil cell of the current batch: candidate offset, slow begin/length, fast begin,
-  // image flags (-1, 0, +1 per axis) packed in bytes
-  __shared__ uint32_t soff[kCellWarps][32], sb0[kCellWarps][32], sn0[kCellWarps][32],
-      sb1[kCellWarps][32], sd[kCellWarps][32];
+  // per column of the current batch (one per lane): its first test within the batch,
+  // and up to four partner ranges (slow and fast population, each in at most two x
+  // segments on a periodic x axis): first partner, length, image flags of the segment
+  constexpr int kFastPieces = 4;
+  __shared__ uint32_t soff[kCellWarps][32];
+  __shared__ uint32_t sjb[kCellWarps][kFastPieces][32], sln[kCellWarps][kFastPieces][32];
+  __shared__ uint8_t scd[kCellWarps][kFastPieces][32];
   // grid-stride over tiles (an occupancy-sized grid); the warps of tile t take the
   // fast particles f = 8 (t - first tile) + warp, stepping by 8 tiles per simulation
   if (!batch_uses(B, -1)) return;
@@ -1046,8 +1052,6 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
     const int cur = s.d.parity ^ 1;
     const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
     const int Cx = g.cfast[0], Cy = g.cfast[1], Cz = g.cfast[2];
-    const int Wx = 2 * Cx + 1, Wxy = Wx * (2 * Cy + 1);
-    const int ncell = Wxy * (2 * Cz + 1);
     const bool px = s.bc[0] == KMC_PERIODIC, py = s.bc[1] == KMC_PERIODIC,
                pz = s.bc[2] == KMC_PERIODIC;
     const double* __restrict__ X0 = s.x[cur][0];
@@ -1091,58 +1095,85 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
       const float Rp = fmaf(sp, g.row_b, g.fast_a) * 1.000001f;
       const float Rp2 = Rp * Rp * 1.000001f;
       const float teps = g.row_eps;
-      for (int c0 = 0; c0 < ncell; c0 += 32) {
-        // this lane's stencil cell and its two candidate ranges
+      const int Wy = 2 * Cy + 1;
+      const int ncol = Wy * (2 * Cz + 1);
+      const float ivx = g.inv_wf[0], pad = g.row_pad;
+      for (int c0 = 0; c0 < ncol; c0 += 32) {
+        // this lane's column: its row of cells trimmed to p's reach, split at a periodic
+        // x boundary, and the slow and fast partner ranges of each segment
         const int c = c0 + (int)lane;
-        uint32_t b0 = 0, n0 = 0, b1 = 0, n1 = 0, dpack = 0;
-        if (c < ncell) {
-          const int dz = c / Wxy - Cz;
-          const int rem = c - (dz + Cz) * Wxy;
-          const int dy = rem / Wx - Cy;
-          const int dx = rem - (dy + Cy) * Wx - Cx;
-          int qx = cx + dx, qy = cy + dy, qz = cz + dz;
-          const int wx = qx < 0 ? -1 : (qx >= nx ? 1 : 0);
+        int np = 0;
+        uint32_t tot = 0;
+        if (c < ncol) {
+          const int dz = c / Wy - Cz;
+          const int dy = c - (dz + Cz) * Wy - Cy;
+          int qy = cy + dy, qz = cz + dz;
           const int wy = qy < 0 ? -1 : (qy >= ny ? 1 : 0);
           const int wz = qz < 0 ? -1 : (qz >= nz ? 1 : 0);
-          bool ok = (wx == 0 || px) && (wy == 0 || py) && (wz == 0 || pz);
-          {
-            // squared distance from p to the cell (unwrapped: the image frame of p)
-            float d2 = 0.f;
-            if (dx != 0 && nx > 1) {
-              const float e = dx > 0 ? (float)(cx + dx) * g.wf[0] - o32.ox
-                                     : o32.ox - (float)(cx + dx + 1) * g.wf[0];
-              const float el = fmaxf(e - teps, 0.f);
-              d2 = el * el;
-            }
-            if (dy != 0 && ny > 1) {
-              const float e = dy > 0 ? (float)(cy + dy) * g.wf[1] - o32.oy
-                                     : o32.oy - (float)(cy + dy + 1) * g.wf[1];
-              const float el = fmaxf(e - teps, 0.f);
-              d2 = fmaf(el, el, d2);
-            }
-            if (dz != 0 && nz > 1) {
-              const float e = dz > 0 ? (float)(cz + dz) * g.wf[2] - o32.oz
-                                     : o32.oz - (float)(cz + dz + 1) * g.wf[2];
-              const float el = fmaxf(e - teps, 0.f);
-              d2 = fmaf(el, el, d2);
-            }
-            if (d2 * 0.9999995f >= Rp2) ok = false;
+          bool ok = (wy == 0 || py) && (wz == 0 || pz);
+          // squared distance from p to the column (unwrapped: the image frame of p)
+          float d2 = 0.f;
+          if (dy != 0 && ny > 1) {
+            const float e = dy > 0 ? (float)(cy + dy) * g.wf[1] - o32.oy
+                                   : o32.oy - (float)(cy + dy + 1) * g.wf[1];
+            const float el = fmaxf(e - teps, 0.f);
+            d2 = el * el;
           }
-          qx -= wx * nx;
-          qy -= wy * ny;
-          qz -= wz * nz;
+          if (dz != 0 && nz > 1) {
+            const float e = dz > 0 ? (float)(cz + dz) * g.wf[2] - o32.oz
+                                   : o32.oz - (float)(cz + dz + 1) * g.wf[2];
+            const float el = fmaxf(e - teps, 0.f);
+            d2 = fmaf(el, el, d2);
+          }
+          if (d2 * 0.9999995f >= Rp2) ok = false;
           if (ok) {
-            const uint32_t key = col_code(g, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx + (uint32_t)qx;
-            b0 = __ldg(cs + key);
-            n0 = __ldg(cs + key + 1) - b0;
-            b1 = __ldg(cs + nk + key);
-            const uint32_t e1 = __ldg(cs + nk + key + 1);
-            if (b1 <= p) b1 = p + 1;
-            n1 = e1 > b1 ? e1 - b1 : 0u;
+            qy -= wy * ny;
+            qz -= wz * nz;
+            const uint32_t colb = col_code(g, (uint32_t)qy, (uint32_t)qz) * (uint32_t)nx;
+            // the cells along x within the reach: sqrt(Rp2 - d2) from the approximate
+            // reciprocal square root (3 ulp), widened by 33 ulp and the coordinate error
+            int xa = 0, xb = 0;
+            if (nx > 1) {
+              const float t2 = fmaxf(Rp2 - d2, 1e-30f);
+              const float ex = fmaf(t2 * rsqrtf(t2), 1.000004f, pad);
+              const int ta = (int)floorf((o32.ox - ex) * ivx), tb = (int)floorf((o32.ox + ex) * ivx);
+              xa = ta > cx - Cx ? ta : cx - Cx;
+              xb = tb < cx + Cx ? tb : cx + Cx;
+              if (!px) {
+                xa = xa < 0 ? 0 : xa;
+                xb = xb > nx - 1 ? nx - 1 : xb;
+              }
+            }
+            const uint32_t code_yz = (uint32_t)((wy > 0) ? 4 : 0) | (uint32_t)((wy < 0) ? 8 : 0) |
+                                     (uint32_t)((wz > 0) ? 16 : 0) | (uint32_t)((wz < 0) ? 32 : 0);
+            // x segments: [xa, xb] within [0, nx), and the part past a periodic boundary
+            auto segment = [&](int a0, int b0, uint32_t code) {
+              const uint32_t k0 = colb + (uint32_t)a0, k1 = colb + (uint32_t)b0 + 1u;
+              const uint32_t sb0 = __ldg(cs + k0), se0 = __ldg(cs + k1);
+              uint32_t sb1 = __ldg(cs + nk + k0);
+              const uint32_t se1 = __ldg(cs + nk + k1);
+              if (sb1 <= p) sb1 = p + 1;  // fast partners j > p only
+              if (se0 > sb0) {
+                sjb[warp][np][lane] = sb0; sln[warp][np][lane] = se0 - sb0; scd[warp][np][lane] = (uint8_t)code;
+                tot += se0 - sb0;
+                ++np;
+              }
+              if (se1 > sb1) {
+                sjb[warp][np][lane] = sb1; sln[warp][np][lane] = se1 - sb1; scd[warp][np][lane] = (uint8_t)code;
+                tot += se1 - sb1;
+                ++np;
+              }
+            };
+            if (xb >= xa) {
+              const int a0 = xa < 0 ? 0 : xa, b0 = xb > nx - 1 ? nx - 1 : xb;
+              if (b0 >= a0) segment(a0, b0, code_yz);
+              if (xa < 0) segment(xa + nx, nx - 1, code_yz | 2u);            // seen at -L
+              else if (xb > nx - 1) segment(0, xb - nx, code_yz | 1u);      // seen at +L
+            }
           }
-          dpack = (uint32_t)(wx & 0xFF) | ((uint32_t)(wy & 0xFF) << 8) | ((uint32_t)(wz & 0xFF) << 16);
         }
-        const uint32_t tot = n0 + n1;
+        // pieces past np have length zero
+        for (int t = np; t < kFastPieces; ++t) sln[warp][t][lane] = 0u;
         uint32_t incl = tot;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1152,23 +1183,24 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
         const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
         tests += tot;
         soff[warp][lane] = incl - tot;
-        sb0[warp][lane] = b0;
-        sn0[warp][lane] = n0;
-        sb1[warp][lane] = b1;
-        sd[warp][lane] = dpack;
         __syncwarp();
         for (uint32_t kb = 0; kb < total; kb += 32) {
           const uint32_t qi = kb + lane;
           if (qi < total) {
-            // owner: the last cell whose first candidate is at or before qi
+            // owner: the last column whose first test is at or before qi
             int lo = 0, hi = 31;
             while (lo < hi) {
               const int mid = (lo + hi + 1) >> 1;
               if (soff[warp][mid] <= qi) lo = mid; else hi = mid - 1;
             }
-            const uint32_t o = qi - soff[warp][lo];
-            const uint32_t m0 = sn0[warp][lo];
-            const uint32_t j = o < m0 ? sb0[warp][lo] + o : sb1[warp][lo] + (o - m0);
+            uint32_t o = qi - soff[warp][lo];
+            int r = 0;
+            while (o >= sln[warp][r][lo]) {
+              o -= sln[warp][r][lo];
+              ++r;
+            }
+            const uint32_t j = sjb[warp][r][lo] + o;
+            const uint32_t d = scd[warp][r][lo];
             bool emit;
             if (PREC == KMC_FP64) {
               double r0 = dsub(__ldg(X0 + j), xo[0]);
@@ -1184,13 +1216,13 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
               const double Bv = dadd(dadd(dmul(g0, g0), dmul(g1, g1)), dmul(g2, g2));
               emit = !(Bv >= 0x1p-900 && R > dadd(g.c0, dmul(g.c1, Bv)));
             } else {
-              const uint32_t d = sd[warp][lo];
-              const int wx = (int)(int8_t)(d & 0xFF), wy = (int)(int8_t)((d >> 8) & 0xFF),
-                        wz = (int)(int8_t)((d >> 16) & 0xFF);
               // own coordinates moved by the image shift (j seen at x_j + w L)
-              const float sx = o32.ox - (float)wx * Lf0;
-              const float sy = o32.oy - (float)wy * Lf1;
-              const float sz = o32.oz - (float)wz * Lf2;
+              const float wxf = (float)((int)(d & 1u) - (int)((d >> 1) & 1u));
+              const float wyf = (float)((int)((d >> 2) & 1u) - (int)((d >> 3) & 1u));
+              const float wzf = (float)((int)((d >> 4) & 1u) - (int)((d >> 5) & 1u));
+              const float sx = o32.ox - wxf * Lf0;
+              const float sy = o32.oy - wyf * Lf1;
+              const float sz = o32.oz - wzf * Lf2;
               const float4 a = __ldg(MA + j);
               const float2 b = __ldg(MB + j);
               const float rx = a.x - sx, ry = a.y - sy, rz = a.z - sz;
