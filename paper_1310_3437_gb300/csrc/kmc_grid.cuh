@@ -84,12 +84,18 @@ __device__ inline CellPlan plan_cells(const double ext[3], double h, int K, uint
   return p;
 }
 
-__device__ inline double search_cost(double n, double rho, int K) {
-  // pair tests of the half stencil, inflated when cells hold fewer particles than a
-  // warp's lanes can use
-  double st = (2 * K + 1.0) * (2 * K + 1.0) * (2 * K + 1.0) * 0.5;
-  double eff = rho < 16.0 ? sqrt(16.0 / (rho > 0.25 ? rho : 0.25)) : 1.0;
-  return n * st * rho * eff;
+// Cost estimates for the choice of the split threshold, in units of one pair test of
+// the row search (measured on GB300 at 2^24 particles; only the ratios matter):
+// a slow particle costs its trimmed half-stencil, about 5 tests per particle per cell
+// (rho = particles per cell of width w), plus its set-up (about 6 tests' time; the
+// warp-per-cell search at high occupancy tests 13.5 rho pairs per particle at about 2.6
+// times the rate, the same cost); a fast particle costs its reach-trimmed stencil
+// (about 1.4 times the sphere of radius R_f, at about 2 tests' time per test) plus 15
+// per (y, z) column it walks.
+__device__ inline double slow_cost(double n, double rho) { return n * (5.0 * rho + 6.0); }
+__device__ inline double fast_cost(double nfast, double rho, double rf_cells, double ncol) {
+  const double tests = rho * 1.4 * 4.18879 * rf_cells * rf_cells * rf_cells;
+  return nfast * (2.0 * tests + 15.0 * ncol);
 }
 
 // Called by all 32 lanes of a warp: lane t < kSplitTrials estimates the cost of
@@ -132,7 +138,7 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step,
     const double cells = (double)p.nc[0] * p.nc[1] * p.nc[2];
     const double rho = (double)s.n / cells;
     if (t == 0) {
-      cost_t = search_cost((double)s.n, rho, K);
+      cost_t = slow_cost((double)s.n, rho);
       feasible_t = true;
       break;
     }
@@ -140,7 +146,7 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step,
     // fast stencil: c cells on each side per split axis; periodic axes must hold it,
     // and no axis may be a one-cell periodic axis (no minimum-image test there)
     const double nfast = (double)s.d.split_cnt[t];
-    double fast_cells = 1.0;
+    double ncol = 1.0, wmin = 0.0;
     bool fits = true;
     for (int a = 0; a < 3; ++a) {
       if (p.nc[a] == 1) {
@@ -148,13 +154,17 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step,
         continue;
       }
       const double w = ext[a] / p.nc[a];
+      wmin = wmin == 0.0 || w < wmin ? w : wmin;
       int c = (int)ceil(Rfull * (1.0 + p.m) / w);
       if (c < K) c = K;
       if (s.bc[a] == KMC_PERIODIC && p.nc[a] < 2 * c + 2) fits = false;
-      fast_cells *= (2.0 * c + 1.0);
+      if (a > 0) ncol *= (2.0 * c + 1.0);
     }
     if (!fits) break;
-    cost_t = search_cost((double)s.n - nfast, rho, K) + nfast * fast_cells * rho * 3.0;
+    // a fast particle's reach, its speed taken just above the threshold
+    const double rf = s.d0 + (1.15 * S1 + V) * s.dt;
+    const double rf_cells = wmin > 0.0 ? rf / wmin : 1.0;
+    cost_t = slow_cost((double)s.n - nfast, rho) + fast_cost(nfast, rho, rf_cells, ncol);
     feasible_t = true;
     } while (false);
     my_feasible = feasible_t;

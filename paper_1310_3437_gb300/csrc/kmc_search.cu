@@ -1022,9 +1022,12 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
   // and up to four partner ranges (slow and fast population, each in at most two x
   // segments on a periodic x axis): first partner, length, image flags of the segment
   constexpr int kFastPieces = 4;
-  __shared__ uint32_t soff[kCellWarps][32];
   __shared__ uint32_t sjb[kCellWarps][kFastPieces][32], sln[kCellWarps][kFastPieces][32];
   __shared__ uint8_t scd[kCellWarps][kFastPieces][32];
+  // the batch's pieces laid end to end (column by column): first test, first partner,
+  // image flags
+  __shared__ uint32_t fst[kCellWarps][kFastPieces * 32], fjb[kCellWarps][kFastPieces * 32];
+  __shared__ uint8_t fcd[kCellWarps][kFastPieces * 32];
   // grid-stride over tiles (an occupancy-sized grid); the warps of tile t take the
   // fast particles f = 8 (t - first tile) + warp, stepping by 8 tiles per simulation
   if (!batch_uses(B, -1)) return;
@@ -1172,35 +1175,46 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
             }
           }
         }
-        // pieces past np have length zero
-        for (int t = np; t < kFastPieces; ++t) sln[warp][t][lane] = 0u;
-        uint32_t incl = tot;
+        // lay the batch's pieces end to end: piece base and first test of each column
+        uint32_t incl = tot, pincl = (uint32_t)np;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-          if (lane >= (uint32_t)o) incl += y;
+          const uint32_t z = __shfl_up_sync(0xFFFFFFFFu, pincl, o);
+          if (lane >= (uint32_t)o) {
+            incl += y;
+            pincl += z;
+          }
         }
         const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        const uint32_t npw = __shfl_sync(0xFFFFFFFFu, pincl, 31);
         tests += tot;
-        soff[warp][lane] = incl - tot;
+        {
+          uint32_t at = pincl - (uint32_t)np, st = incl - tot;
+          for (int r = 0; r < np; ++r) {
+            fst[warp][at] = st;
+            fjb[warp][at] = sjb[warp][r][lane];
+            fcd[warp][at] = scd[warp][r][lane];
+            st += sln[warp][r][lane];
+            ++at;
+          }
+        }
         __syncwarp();
+        // walk the batch's tests 32 at a time: lane l takes test kb + l.  P is the piece
+        // holding test kb; the pieces starting inside the pass (at most 31, each
+        // non-empty) are among P + 1 .. P + 31 and mark their first test in one OR
+        uint32_t P = 0;
         for (uint32_t kb = 0; kb < total; kb += 32) {
+          const uint32_t qp = P + lane;
+          const uint32_t st = qp < npw ? fst[warp][qp] : 0xFFFFFFFFu;
+          const uint32_t bit = (st >= kb && st - kb < 32u) ? 1u << (st - kb) : 0u;
+          const uint32_t mask = __reduce_or_sync(0xFFFFFFFFu, bit);
+          const uint32_t before = __shfl_sync(0xFFFFFFFFu, st < kb ? 1u : 0u, 0);
+          const uint32_t pi = P - 1u + before + __popc(mask & (0xFFFFFFFFu >> (31u - lane)));
           const uint32_t qi = kb + lane;
           if (qi < total) {
-            // owner: the last column whose first test is at or before qi
-            int lo = 0, hi = 31;
-            while (lo < hi) {
-              const int mid = (lo + hi + 1) >> 1;
-              if (soff[warp][mid] <= qi) lo = mid; else hi = mid - 1;
-            }
-            uint32_t o = qi - soff[warp][lo];
-            int r = 0;
-            while (o >= sln[warp][r][lo]) {
-              o -= sln[warp][r][lo];
-              ++r;
-            }
-            const uint32_t j = sjb[warp][r][lo] + o;
-            const uint32_t d = scd[warp][r][lo];
+            const uint32_t j = fjb[warp][pi] + (qi - fst[warp][pi]);
+            const uint32_t d = fcd[warp][pi];
             bool emit;
             if (PREC == KMC_FP64) {
               double r0 = dsub(__ldg(X0 + j), xo[0]);
@@ -1233,6 +1247,13 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
             }
             if (emit) emit_lane(buf, cnt, s, p, j);
           }
+          // the next pass starts in lane 31's piece or in the one after it
+          uint32_t nextP = 0;
+          if (lane == 31u) {
+            const uint32_t end = pi + 1u < npw ? fst[warp][pi + 1u] : total;
+            nextP = kb + 32u >= end ? pi + 1u : pi;
+          }
+          P = __shfl_sync(0xFFFFFFFFu, nextP, 31);
           __syncwarp();
           if (*cnt >= (uint32_t)(kWarpBuf / 2)) flush_lanes(buf, cnt, s, lane);
         }
