@@ -93,6 +93,15 @@ __device__ inline CellPlan plan_cells(const double ext[3], double h, int K, uint
 // (about 1.4 times the sphere of radius R_f, at about 2 tests' time per test) plus 15
 // per (y, z) column it walks.
 __device__ inline double slow_cost(double n, double rho) { return n * (5.0 * rho + 6.0); }
+// The binary64 path has no row search (thread per particle or warp per cell, whole
+// stencil, binary64 pre-tests): its cost is the half stencil's pair tests, inflated
+// when cells hold fewer particles than a warp's lanes can use; a fast particle costs
+// its whole stencil at 3 units per test.
+__device__ inline double slow_cost_f64(double n, double rho, int K) {
+  const double st = (2 * K + 1.0) * (2 * K + 1.0) * (2 * K + 1.0) * 0.5;
+  const double eff = rho < 16.0 ? sqrt(16.0 / (rho > 0.25 ? rho : 0.25)) : 1.0;
+  return n * st * rho * eff;
+}
 __device__ inline double fast_cost(double nfast, double rho, double rf_cells, double ncol) {
   const double tests = rho * 1.4 * 4.18879 * rf_cells * rf_cells * rf_cells;
   return nfast * (2.0 * tests + 15.0 * ncol);
@@ -137,8 +146,9 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step,
     if (!p.ok) break;
     const double cells = (double)p.nc[0] * p.nc[1] * p.nc[2];
     const double rho = (double)s.n / cells;
+    const bool f64 = s.precision == KMC_FP64;
     if (t == 0) {
-      cost_t = slow_cost((double)s.n, rho);
+      cost_t = f64 ? slow_cost_f64((double)s.n, rho, K) : slow_cost((double)s.n, rho);
       feasible_t = true;
       break;
     }
@@ -146,7 +156,7 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step,
     // fast stencil: c cells on each side per split axis; periodic axes must hold it,
     // and no axis may be a one-cell periodic axis (no minimum-image test there)
     const double nfast = (double)s.d.split_cnt[t];
-    double ncol = 1.0, wmin = 0.0;
+    double ncol = 1.0, wmin = 0.0, fast_cells = 1.0;
     bool fits = true;
     for (int a = 0; a < 3; ++a) {
       if (p.nc[a] == 1) {
@@ -159,12 +169,14 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step,
       if (c < K) c = K;
       if (s.bc[a] == KMC_PERIODIC && p.nc[a] < 2 * c + 2) fits = false;
       if (a > 0) ncol *= (2.0 * c + 1.0);
+      fast_cells *= (2.0 * c + 1.0);
     }
     if (!fits) break;
     // a fast particle's reach, its speed taken just above the threshold
     const double rf = s.d0 + (1.15 * S1 + V) * s.dt;
     const double rf_cells = wmin > 0.0 ? rf / wmin : 1.0;
-    cost_t = slow_cost((double)s.n - nfast, rho) + fast_cost(nfast, rho, rf_cells, ncol);
+    cost_t = f64 ? slow_cost_f64((double)s.n - nfast, rho, K) + nfast * fast_cells * rho * 3.0
+                 : slow_cost((double)s.n - nfast, rho) + fast_cost(nfast, rho, rf_cells, ncol);
     feasible_t = true;
     } while (false);
     my_feasible = feasible_t;

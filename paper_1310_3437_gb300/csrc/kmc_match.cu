@@ -25,6 +25,8 @@
 //             had an unmatched candidate goes on the next round's list, so later
 //             rounds only visit the few particles they can still match.
 //   k_collide isotropic centre-of-mass scatter at the time of closest approach.
+#include <algorithm>
+
 #include "kmc_internal.cuh"
 
 namespace kmc {
@@ -334,8 +336,11 @@ int launch_match(const LaunchPlan& L, int max_rounds, cudaStream_t st) {
   k_alloc<<<nb, kEdgeBlock, 0, st>>>(L.b);
   k_fill<<<nb, kEdgeBlock, 0, st>>>(L.b);
   for (int r = 0; r < max_rounds; ++r) {
-    k_best<<<nb, kEdgeBlock, 0, st>>>(L.b, r);
-    k_mutual<<<nb, kEdgeBlock, 0, st>>>(L.b, r);
+    // the later rounds' work lists hold a few percent of the first round's: a grid of
+    // one block per SM covers them (grid-stride) without launching idle blocks
+    const int nr = r == 0 ? nb : std::max(1, nb / 8);
+    k_best<<<nr, kEdgeBlock, 0, st>>>(L.b, r);
+    k_mutual<<<nr, kEdgeBlock, 0, st>>>(L.b, r);
   }
   k_collide<<<nb, kEdgeBlock, 0, st>>>(L.b);
   return 4 + 2 * max_rounds;

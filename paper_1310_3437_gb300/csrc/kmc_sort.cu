@@ -18,30 +18,12 @@
 namespace kmc {
 
 // --------------------------------------------------------------------------- //
-__global__ void __launch_bounds__(kTile) k_count(Batch B) {
-  int k = find_sim(B.ptile, B.nsims, blockIdx.x);
-  SimDev& s = *B.sims[k];
-  if (!sim_active(s)) return;
-  const Grid& g = s.d.grid;
-  uint32_t p = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
-  bool valid = p < s.n;
-  uint32_t key = 0;
-  if (valid) {
-    int par = s.d.parity;
-    int cx = cell_coord(g, 0, s.x[par][0][p]);
-    int cy = cell_coord(g, 1, s.x[par][1][p]);
-    int cz = cell_coord(g, 2, s.x[par][2][p]);
-    key = col_code(g, (uint32_t)cy, (uint32_t)cz) * (uint32_t)g.nc[0] + (uint32_t)cx;
-    // fast particles (speed bound above the split threshold) form the second population
-    // (the trial thresholds decrease with their index, so |v|^2 > threshold[split_t]
-    // exactly when the bound exceeds at least 7 - split_t of the six trial values)
-    if (g.split && (int)s.vbucket[p] >= kSplitTrials - g.split_t) key += g.nkeys;
-  }
+// run of equal keys in consecutive lanes: rank of each valid lane, one atomic per run
+__device__ __forceinline__ uint32_t run_rank(uint32_t* counts, uint32_t key, bool valid, uint32_t lane) {
   // warp aggregation over runs of equal keys: the particles come in the previous
   // step's cell order, so equal keys mostly sit in neighbouring lanes.  Each run of
   // equal keys in consecutive lanes takes one atomic for all its members (a key that
   // appears in two runs takes two; the ranks stay distinct either way).
-  const unsigned lane = threadIdx.x & 31u;
   const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, key, 1);
   const bool head = valid && (lane == 0 || prev != key);  // valid lanes are a prefix
   const unsigned heads = __ballot_sync(0xFFFFFFFFu, head);
@@ -54,12 +36,52 @@ __global__ void __launch_bounds__(kTile) k_count(Batch B) {
   if (head) {
     const unsigned above = heads & ~(0xFFFFFFFFu >> (31u - lane));  // heads past this lane
     const int next = above ? __ffs((int)above) - 1 : 32 - __clz((int)vmask);
-    base = atomicAdd(&s.cell_count[key], (uint32_t)(next - (int)lane));
+    base = atomicAdd(&counts[key], (uint32_t)(next - (int)lane));
   }
   base = __shfl_sync(0xFFFFFFFFu, base, lead < 0 ? 0 : lead);
-  if (valid) {
-    s.key[p] = key;
-    s.rank[p] = base + (lane - (uint32_t)lead);
+  return base + (lane - (uint32_t)lead);
+}
+
+// two particles per thread, half a tile apart: both sets of loads are in flight
+// before either key is needed (the kernel is bound by memory latency)
+__global__ void __launch_bounds__(kTile / 2) k_count(Batch B) {
+  int k = find_sim(B.ptile, B.nsims, blockIdx.x);
+  SimDev& s = *B.sims[k];
+  if (!sim_active(s)) return;
+  const Grid& g = s.d.grid;
+  const uint32_t p0 = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
+  const uint32_t pp[2] = {p0, p0 + kTile / 2};
+  const int par = s.d.parity;
+  double xs[2][3];
+  uint32_t vb[2];
+  bool valid[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    valid[h] = pp[h] < s.n;
+    const uint32_t q = valid[h] ? pp[h] : 0u;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) xs[h][a] = s.x[par][a][q];
+    vb[h] = g.split ? (uint32_t)s.vbucket[q] : 0u;
+  }
+  const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint32_t key = 0;
+    if (valid[h]) {
+      const int cx = cell_coord(g, 0, xs[h][0]);
+      const int cy = cell_coord(g, 1, xs[h][1]);
+      const int cz = cell_coord(g, 2, xs[h][2]);
+      key = col_code(g, (uint32_t)cy, (uint32_t)cz) * (uint32_t)g.nc[0] + (uint32_t)cx;
+      // fast particles (speed bound above the split threshold) form the second population
+      // (the trial thresholds decrease with their index, so |v|^2 > threshold[split_t]
+      // exactly when the bound exceeds at least 7 - split_t of the six trial values)
+      if (g.split && (int)vb[h] >= kSplitTrials - g.split_t) key += g.nkeys;
+    }
+    const uint32_t rank = run_rank(s.cell_count, key, valid[h], lane);
+    if (valid[h]) {
+      s.key[pp[h]] = key;
+      s.rank[pp[h]] = rank;
+    }
   }
 }
 
@@ -263,7 +285,7 @@ int launch_cell_scan(const LaunchPlan& L, cudaStream_t st) {
 }
 
 int launch_sort(const LaunchPlan& L, cudaStream_t st) {
-  k_count<<<L.ptiles, kTile, 0, st>>>(L.b);
+  k_count<<<L.ptiles, kTile / 2, 0, st>>>(L.b);
   int n = launch_cell_scan(L, st);
   k_scatter<<<L.ptiles, kTile, 0, st>>>(L.b);
   k_gather<<<L.ptiles, kTile, 0, st>>>(L.b);
