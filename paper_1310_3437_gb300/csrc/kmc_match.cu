@@ -92,6 +92,43 @@ __device__ __forceinline__ double min_image(double r, double L) {
   return r;
 }
 
+// Block-aggregated append: one atomic per block on the shared counter (a counter that
+// every warp of the grid hits is a hot spot: its atomics serialise in L2).  Every
+// thread of the block must call it; *also, if given, is advanced by the same total.
+// Returns this thread's first index in the buffer behind *counter.
+__device__ __forceinline__ uint32_t block_append(uint32_t* counter, uint32_t want,
+                                                 uint32_t* also = nullptr) {
+  constexpr int kW = kEdgeBlock / 32;
+  __shared__ uint32_t wsum[kW], wbase[kW], bbase;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint32_t incl = want;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= (uint32_t)o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t v = lane < (uint32_t)kW ? wsum[lane] : 0u;
+    uint32_t vi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, vi, o);
+      if (lane >= (uint32_t)o) vi += y;
+    }
+    if (lane < (uint32_t)kW) wbase[lane] = vi - v;
+    if (lane == (uint32_t)kW - 1) {
+      bbase = vi ? atomicAdd(counter, vi) : 0u;
+      if (also && vi) atomicAdd(also, vi);
+    }
+  }
+  __syncthreads();
+  const uint32_t r = bbase + wbase[warp] + incl - want;
+  __syncthreads();  // the slots are free for the next call
+  return r;
+}
+
 // ---- k_refine ------------------------------------------------------------ //
 __global__ void __launch_bounds__(kEdgeBlock) k_refine(Batch B) {
   for (int k = 0; k < B.nsims; ++k) {
@@ -136,28 +173,11 @@ __global__ void __launch_bounds__(kEdgeBlock) k_refine(Batch B) {
         s.e_slot[e] = make_uint2(kNone, kNone);
       }
     }
-    for (int o = 16; o > 0; o >>= 1) found += __shfl_down_sync(0xFFFFFFFFu, found, o);
-    if ((threadIdx.x & 31) == 0 && found) atomicAdd(&s.d.n_edges, found);
+    block_append(&s.d.n_edges, found);  // one atomic per block
   }
 }
 
 // ---- candidate lists -------------------------------------------------------- //
-// warp-aggregated append: returns this lane's first index in a buffer of which
-// *counter entries are in use; every lane of the warp must call it
-__device__ __forceinline__ uint32_t warp_append(uint32_t* counter, uint32_t want) {
-  const uint32_t lane = threadIdx.x & 31u;
-  uint32_t incl = want;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= (uint32_t)o) incl += y;
-  }
-  const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-  uint32_t base = 0;
-  if (lane == 31 && total) base = atomicAdd(counter, total);
-  base = __shfl_sync(0xFFFFFFFFu, base, 31);
-  return base + incl - want;
-}
 
 // the pair whose slot is 0 at an endpoint opens that endpoint's list
 __global__ void __launch_bounds__(kEdgeBlock) k_alloc(Batch B) {
@@ -166,7 +186,7 @@ __global__ void __launch_bounds__(kEdgeBlock) k_alloc(Batch B) {
     if (!sim_active(s)) continue;
     const uint32_t nraw = s.d.n_raw < s.edge_cap ? s.d.n_raw : s.edge_cap;
     const uint32_t stride = gridDim.x * blockDim.x;
-    // uniform trip count per warp: the appends are warp-wide
+    // uniform trip count: the appends are block-wide
     const uint32_t span = ((nraw + stride - 1) / stride) * stride;
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < span; e += stride) {
       uint32_t i = kNone, j = kNone, di = 0, dj = 0;
@@ -178,8 +198,8 @@ __global__ void __launch_bounds__(kEdgeBlock) k_alloc(Batch B) {
           if (sl.y == 0) { j = pr.y; dj = s.deg[j]; }
         }
       }
-      const uint32_t at = warp_append(&s.d.adj_used, di + dj);
-      const uint32_t wa = warp_append(&s.d.wl_len[0], (i != kNone ? 1u : 0u) + (j != kNone ? 1u : 0u));
+      const uint32_t at = block_append(&s.d.adj_used, di + dj);
+      const uint32_t wa = block_append(&s.d.wl_len[0], (i != kNone ? 1u : 0u) + (j != kNone ? 1u : 0u));
       if (i != kNone) { s.off[i] = at; s.wl[0][wa] = i; }
       if (j != kNone) { s.off[j] = at + di; s.wl[0][wa + (i != kNone ? 1u : 0u)] = j; }
     }
@@ -253,7 +273,7 @@ __global__ void __launch_bounds__(kEdgeBlock) k_mutual(Batch B, int round) {
     const uint32_t* __restrict__ list = s.wl[round & 1];
     uint32_t* __restrict__ next = s.wl[(round + 1) & 1];
     const uint32_t stride = gridDim.x * blockDim.x;
-    // uniform trip count per warp: the appends are warp-wide
+    // uniform trip count: the appends are block-wide
     const uint32_t span = ((len + stride - 1) / stride) * stride;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < span; t += stride) {
       bool pair = false, again = false;
@@ -271,12 +291,10 @@ __global__ void __launch_bounds__(kEdgeBlock) k_mutual(Batch B, int round) {
           }
         }
       }
-      const uint32_t at = warp_append(&s.d.n_pairs, pair ? 1u : 0u);
+      const uint32_t at = block_append(&s.d.n_pairs, pair ? 1u : 0u, &s.d.round_pairs[round]);
       if (pair) s.pairs[at] = i;
-      const unsigned m = __ballot_sync(0xFFFFFFFFu, pair);
-      if ((threadIdx.x & 31u) == 0 && m) atomicAdd(&s.d.round_pairs[round], (uint32_t)__popc(m));
       if (round + 1 < s.max_rounds) {
-        const uint32_t w = warp_append(&s.d.wl_len[round + 1], again ? 1u : 0u);
+        const uint32_t w = block_append(&s.d.wl_len[round + 1], again ? 1u : 0u);
         if (again) next[w] = i;
       }
     }

@@ -760,6 +760,27 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
   if (!batch_uses(B, KMC_SEARCH_ROW)) return;
   const uint32_t ntiles = B.ptile[B.nsims];
   int kcur = -1;  // simulation whose constants the shared tables hold
+  // The warp's pair tests and emitted pairs go to the simulation's counters only when
+  // the simulation changes, the staging buffer is half full, or at the end: per-tile
+  // atomics on these two counters from every warp serialise in L2.  The running
+  // counts live in shared memory (registers are the row search's limit).
+  __shared__ unsigned long long wtests[RL::kWarps];
+  auto warp_buf = [&]() {
+    return reinterpret_cast<uint2*>(rows_smem + RL::kPieceBytes + RL::kCodeBytes) +
+           (size_t)(threadIdx.x >> 5) * kWarpBuf;
+  };
+  auto warp_flush = [&](SimDev& f) {
+    const uint32_t w = threadIdx.x >> 5, l = threadIdx.x & 31u;
+    flush_lanes(warp_buf(), &wcount[w], f, l);
+    if (l == 0 && wtests[w]) atomicAdd(&f.d.pair_tests, wtests[w]);
+    if (l == 0) wtests[w] = 0;
+    __syncwarp();
+  };
+  if ((threadIdx.x & 31u) == 0) {
+    wcount[threadIdx.x >> 5] = 0;
+    wtests[threadIdx.x >> 5] = 0;
+  }
+  __syncwarp();
   for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int k = find_sim(B.ptile, B.nsims, tile);
     SimDev& s = *B.sims[k];
@@ -770,6 +791,7 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
     // walks the same tiles), so the warps of a block need not wait for each other at
     // every tile: each runs on to its part of the next tile.
     if (k != kcur) {
+      if (kcur >= 0) warp_flush(*B.sims[kcur]);  // staged pairs and counts of the last one
       __syncthreads();  // every warp is done with the previous simulation's constants
       if (threadIdx.x == 0) {
         sq.c0 = g.s_c0; sq.c1 = g.s_c1; sq.ag = g.a_g; sq.tg = g.t_g; sq.dtf = g.dtf;
@@ -791,11 +813,8 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
     if (p - lane >= nslow) continue;  // the whole warp is past the slow population
     uint2* pc = reinterpret_cast<uint2*>(rows_smem) + (size_t)warp * NP * 32;
     uint8_t* cd = rows_smem + RL::kPieceBytes + (size_t)warp * NP * 32;
-    uint2* buf = reinterpret_cast<uint2*>(rows_smem + RL::kPieceBytes + RL::kCodeBytes) +
-                 (size_t)warp * kWarpBuf;
+    uint2* buf = warp_buf();
     uint32_t* cnt = &wcount[warp];
-    if (lane == 0) *cnt = 0;
-    __syncwarp();
 
     const bool valid = p < nslow;
     const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
@@ -995,11 +1014,13 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
         }
       }
     }
-    flush_lanes(buf, cnt, s, lane);
+    __syncwarp();
+    if (*cnt >= (uint32_t)(kWarpBuf / 2)) flush_lanes(buf, cnt, s, lane);
     unsigned long long tests = total;
     for (int off = 16; off > 0; off >>= 1) tests += __shfl_down_sync(0xFFFFFFFFu, tests, off);
-    if (lane == 0 && tests) atomicAdd(&s.d.pair_tests, tests);
+    if (lane == 0) wtests[warp] += tests;
   }
+  if (kcur >= 0) warp_flush(*B.sims[kcur]);
 }
 
 
