@@ -27,6 +27,33 @@ struct Own32 {
   float ox, oy, oz, vx, vy, vz;
 };
 
+// Two binary32 values in one 64-bit register, and the packed (f32x2) arithmetic of
+// sm_100-class GPUs on them: each half is rounded exactly as the scalar operation.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pack2(float a, float b) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpack2(f32x2 r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 __device__ __forceinline__ void min_image_f(float& r, float halfL, float L, float tie, bool& keep) {
   float ar = fabsf(r);
   if (fabsf(ar - halfL) <= tie) keep = true;
@@ -748,7 +775,7 @@ __device__ __forceinline__ uint32_t image_code(int wx, int wy, int wz) {
 }
 
 template <int K, bool PX>
-__global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
+__global__ void __launch_bounds__(kTile, 4) k_search_rows32(Batch B) {
   using RL = RowLayout<K, PX>;
   constexpr int NP = RL::kPieces;
   extern __shared__ __align__(16) unsigned char rows_smem[];
@@ -831,7 +858,7 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
 
     // 1. the lane's non-empty pieces, column by column
     int np = 0;
-    uint32_t total = 0;
+    uint32_t total = 0, iters = 0;  // tests; iterations of up to two tests of one piece
     Own32 o = {0, 0, 0, 0, 0, 0};
     int cx = 0, cy = 0, cz = 0;
     if (valid) {
@@ -948,6 +975,7 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
             cd[np * 32 + lane] = (uint8_t)image_code(0, wy, wz);
             ++np;
             total += je - jb;
+            iters += (je - jb + 1u) >> 1;
           }
         }
         if (px && xa < 0) {  // cells [xa + nx, nx) seen through the image at -L
@@ -957,6 +985,7 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
             cd[np * 32 + lane] = (uint8_t)image_code(-1, wy, wz);
             ++np;
             total += je - jb;
+            iters += (je - jb + 1u) >> 1;
           }
         }
         if (px && xb >= nx) {  // cells [0, xb - nx] seen through the image at +L
@@ -966,13 +995,15 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
             cd[np * 32 + lane] = (uint8_t)image_code(1, wy, wz);
             ++np;
             total += je - jb;
+            iters += (je - jb + 1u) >> 1;
           }
         }
       }
     }
 
-    // 2. walk the pieces: one test per iteration
-    const uint32_t T = __reduce_max_sync(0xFFFFFFFFu, total);
+    // 2. walk the pieces, two tests of one piece per iteration (one at a piece's odd
+    //    end), the binary32 pre-tests of both in packed f32x2 arithmetic
+    const uint32_t T = __reduce_max_sync(0xFFFFFFFFu, any_cp ? total : iters);
     uint32_t j = 0, je = 0;
     int r = 0;
     float sx = o.ox, sy = o.oy, sz = o.oz;
@@ -986,31 +1017,79 @@ __global__ void __launch_bounds__(kTile, 5) k_search_rows32(Batch B) {
       sz = o.oz - sh.z;
     }
     const float c0 = g.s_c0, c1 = g.s_c1;
-    for (uint32_t t = 0; t < T; ++t) {
-      if (j < je) {
-        const float4 a = __ldg(MA + j);
-        const float2 b = __ldg(MB + j);
-        float rx = a.x - sx, ry = a.y - sy, rz = a.z - sz;
-        bool keep = false;
-        if (any_cp) {
+    if (any_cp) {
+      // one-cell periodic axes (thin slabs): one test per iteration with the minimum image
+      for (uint32_t t = 0; t < T; ++t) {
+        if (j < je) {
+          const float4 a = __ldg(MA + j);
+          const float2 b = __ldg(MB + j);
+          float rx = a.x - sx, ry = a.y - sy, rz = a.z - sz;
+          bool keep = false;
           if (cp0) min_image_f(rx, g.halfLf[0], g.Lf[0], g.tief[0], keep);
           if (cp1) min_image_f(ry, g.halfLf[1], g.Lf[1], g.tief[1], keep);
           if (cp2) min_image_f(rz, g.halfLf[2], g.Lf[2], g.tief[2], keep);
+          const float gx = a.w - o.vx, gy = b.x - o.vy, gz = b.y - o.vz;
+          const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+          const float Bv = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
+          if (keep || (R <= fmaf(c1, Bv, c0) && full_test32_call(sq, rx, ry, rz, gx, gy, gz, Bv)))
+            emit_lane(buf, cnt, s, p, j);
+          if (++j == je && r + 1 < np) {
+            ++r;
+            const uint2 q = pc[r * 32 + lane];
+            const float4 sh = shift_tab[cd[r * 32 + lane]];
+            j = q.x;
+            je = q.y;
+            sx = o.ox - sh.x;
+            sy = o.oy - sh.y;
+            sz = o.oz - sh.z;
+          }
         }
-        const float gx = a.w - o.vx, gy = b.x - o.vy, gz = b.y - o.vz;
-        const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-        const float Bv = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
-        if (keep || (R <= fmaf(c1, Bv, c0) && full_test32_call(sq, rx, ry, rz, gx, gy, gz, Bv)))
-          emit_lane(buf, cnt, s, p, j);
-        if (++j == je && r + 1 < np) {
-          ++r;
-          const uint2 q = pc[r * 32 + lane];
-          const float4 sh = shift_tab[cd[r * 32 + lane]];
-          j = q.x;
-          je = q.y;
-          sx = o.ox - sh.x;
-          sy = o.oy - sh.y;
-          sz = o.oz - sh.z;
+      }
+    } else {
+      const f32x2 C0 = pack2(c0, c0), C1 = pack2(c1, c1);
+      const f32x2 VX = pack2(o.vx, o.vx), VY = pack2(o.vy, o.vy), VZ = pack2(o.vz, o.vz);
+      f32x2 SX = pack2(sx, sx), SY = pack2(sy, sy), SZ = pack2(sz, sz);
+      for (uint32_t t = 0; t < T; ++t) {
+        if (j < je) {
+          const bool two = j + 1u < je;
+          const uint32_t j1 = two ? j + 1u : j;  // without a second test the first is repeated
+          const float4 a0 = __ldg(MA + j), a1 = __ldg(MA + j1);
+          const float2 b0 = __ldg(MB + j), b1 = __ldg(MB + j1);
+          const f32x2 rx = sub2(pack2(a0.x, a1.x), SX), ry = sub2(pack2(a0.y, a1.y), SY),
+                      rz = sub2(pack2(a0.z, a1.z), SZ);
+          const f32x2 gx = sub2(pack2(a0.w, a1.w), VX), gy = sub2(pack2(b0.x, b1.x), VY),
+                      gz = sub2(pack2(b0.y, b1.y), VZ);
+          const f32x2 R = fma2(rz, rz, fma2(ry, ry, mul2(rx, rx)));
+          const f32x2 Bv = fma2(gz, gz, fma2(gy, gy, mul2(gx, gx)));
+          const f32x2 bound = fma2(C1, Bv, C0);
+          float R0, R1, T0, T1;
+          unpack2(R, R0, R1);
+          unpack2(bound, T0, T1);
+          if (R0 <= T0 || (two && R1 <= T1)) {  // rare: a sphere survivor
+            float rx0, rx1, ry0, ry1, rz0, rz1, gx0, gx1, gy0, gy1, gz0, gz1, B0, B1;
+            unpack2(rx, rx0, rx1);
+            unpack2(ry, ry0, ry1);
+            unpack2(rz, rz0, rz1);
+            unpack2(gx, gx0, gx1);
+            unpack2(gy, gy0, gy1);
+            unpack2(gz, gz0, gz1);
+            unpack2(Bv, B0, B1);
+            if (R0 <= T0 && full_test32_call(sq, rx0, ry0, rz0, gx0, gy0, gz0, B0))
+              emit_lane(buf, cnt, s, p, j);
+            if (two && R1 <= T1 && full_test32_call(sq, rx1, ry1, rz1, gx1, gy1, gz1, B1))
+              emit_lane(buf, cnt, s, p, j + 1u);
+          }
+          j += two ? 2u : 1u;
+          if (j == je && r + 1 < np) {
+            ++r;
+            const uint2 q = pc[r * 32 + lane];
+            const float4 sh = shift_tab[cd[r * 32 + lane]];
+            j = q.x;
+            je = q.y;
+            SX = pack2(o.ox - sh.x, o.ox - sh.x);
+            SY = pack2(o.oy - sh.y, o.oy - sh.y);
+            SZ = pack2(o.oz - sh.z, o.oz - sh.z);
+          }
         }
       }
     }
