@@ -571,26 +571,34 @@ __device__ __forceinline__ void cell32_sweep(const float* __restrict__ si, uint3
   const float* su = si + 3 * 64;
   const float* sv = si + 4 * 64;
   const float* sw = si + 5 * 64;
+  // the four own particles of an iteration as two packed pairs (adjacent in shared
+  // memory), the lane's partner broadcast to both halves
+  const f32x2 JX = pack2(jx, jx), JY = pack2(jy, jy), JZ = pack2(jz, jz);
+  const f32x2 GX = pack2(gx, gx), GY = pack2(gy, gy), GZ = pack2(gz, gz);
+  const f32x2 C0 = pack2(c0, c0), C1 = pack2(c1, c1);
   for (uint32_t ii = 0; ii < nI4; ii += 4) {
-    const float4 X = *reinterpret_cast<const float4*>(sx + ii);
-    const float4 Y = *reinterpret_cast<const float4*>(sy + ii);
-    const float4 Z = *reinterpret_cast<const float4*>(sz + ii);
-    const float4 U = *reinterpret_cast<const float4*>(su + ii);
-    const float4 V = *reinterpret_cast<const float4*>(sv + ii);
-    const float4 W = *reinterpret_cast<const float4*>(sw + ii);
-    const float xs[4] = {X.x, X.y, X.z, X.w}, ys[4] = {Y.x, Y.y, Y.z, Y.w},
-                zs[4] = {Z.x, Z.y, Z.z, Z.w}, us[4] = {U.x, U.y, U.z, U.w},
-                vs[4] = {V.x, V.y, V.z, V.w}, ws[4] = {W.x, W.y, W.z, W.w};
+    const ulonglong2 X = *reinterpret_cast<const ulonglong2*>(sx + ii);
+    const ulonglong2 Y = *reinterpret_cast<const ulonglong2*>(sy + ii);
+    const ulonglong2 Z = *reinterpret_cast<const ulonglong2*>(sz + ii);
+    const ulonglong2 U = *reinterpret_cast<const ulonglong2*>(su + ii);
+    const ulonglong2 V = *reinterpret_cast<const ulonglong2*>(sv + ii);
+    const ulonglong2 W = *reinterpret_cast<const ulonglong2*>(sw + ii);
     unsigned mask = 0;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const float rx = jx - xs[u], ry = jy - ys[u], rz = jz - zs[u];
-      const float vx = gx - us[u], vy = gy - vs[u], vz = gz - ws[u];
-      const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-      const float Bv = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
-      bool c = R <= fmaf(c1, Bv, c0);
-      if (OWN) c = c && (!jown || j > i0 + ii + (uint32_t)u);
-      mask |= c ? (1u << u) : 0u;
+    for (int h = 0; h < 2; ++h) {
+      const f32x2 rx = sub2(JX, h ? X.y : X.x), ry = sub2(JY, h ? Y.y : Y.x), rz = sub2(JZ, h ? Z.y : Z.x);
+      const f32x2 vx = sub2(GX, h ? U.y : U.x), vy = sub2(GY, h ? V.y : V.x), vz = sub2(GZ, h ? W.y : W.x);
+      const f32x2 R = fma2(rz, rz, fma2(ry, ry, mul2(rx, rx)));
+      const f32x2 Bv = fma2(vz, vz, fma2(vy, vy, mul2(vx, vx)));
+      float R0, R1, T0, T1;
+      unpack2(R, R0, R1);
+      unpack2(fma2(C1, Bv, C0), T0, T1);
+      bool c_0 = R0 <= T0, c_1 = R1 <= T1;
+      if (OWN) {
+        c_0 = c_0 && (!jown || j > i0 + ii + (uint32_t)(2 * h));
+        c_1 = c_1 && (!jown || j > i0 + ii + (uint32_t)(2 * h + 1));
+      }
+      mask |= (c_0 ? (1u << (2 * h)) : 0u) | (c_1 ? (2u << (2 * h)) : 0u);
     }
     if (mask) {
       // rare and divergent: only the lanes with sphere survivors run the full test
@@ -1115,7 +1123,7 @@ __global__ void __launch_bounds__(kTile, 4) k_search_rows32(Batch B) {
 // iteration whatever the occupancies.  The pair tests are those of the
 // thread-per-particle search.
 template <int PREC>
-__global__ void __launch_bounds__(kCellWarps * 32) k_search_fast(Batch B) {
+__global__ void __launch_bounds__(kCellWarps * 32, 4) k_search_fast(Batch B) {
   __shared__ uint2 wbuf[kCellWarps][kWarpBuf];
   __shared__ uint32_t wcount[kCellWarps];
   // per column of the current batch (one per lane): its first test within the batch,
