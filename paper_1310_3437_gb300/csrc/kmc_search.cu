@@ -908,9 +908,12 @@ __global__ void __launch_bounds__(kTile, 4) k_search_rows32(Batch B) {
       // length on the crossing side.
       // the reach of this particle: |v_i| from its binary32 velocity (each component
       // within u32 of the binary64 one, the sum of squares within 3 u32, the square
-      // root correctly rounded) times 1 + 2e-6 bounds |v_i| from above; the products
-      // and the square get 1e-6 each.  The smaller of this and the common reach holds.
-      const float si = sqrtf(fmaf(o.vz, o.vz, fmaf(o.vy, o.vy, o.vx * o.vx))) * 1.000002f;
+      // root within 3 ulp; the argument kept normal, which only enlarges it) times
+      // 1 + 4e-6 bounds |v_i| from above; the products and the square get 1e-6 each.
+      // The smaller of this and the common reach holds.
+      const float sv2 = fmaxf(fmaf(o.vz, o.vz, fmaf(o.vy, o.vy, o.vx * o.vx)), 1e-30f);
+      // (the square root from the approximate reciprocal root: 3 ulp, inside the margin)
+      const float si = sv2 * rsqrtf(sv2) * 1.000004f;
       const float Ri = fmaf(si, g.row_b, g.row_a) * 1.000001f;
       const float R2 = fminf(g.row_r2, Ri * Ri * 1.000001f);
       const float eps = g.row_eps, pad = g.row_pad;
