@@ -84,6 +84,14 @@ extern "C" {
                                   (the speed split changes the work, never a result) */
 #define KMC_FLAG_FORCE_SPLIT 2u /* split whenever possible, cycling the threshold through
                                   the trial values step by step (exercises the split) */
+#define KMC_FLAG_PLANAR 4u     /* two-dimensional dynamics in the x-y plane (the paper's
+                                  2D runs, Sec. 2 and Sec. 4: 8 neighbouring bins): every
+                                  vz must be 0, z stays constant, scatter directions are
+                                  isotropic in the plane (uniform on the unit circle, von
+                                  Neumann's method from the same Philox draws).  Give the
+                                  z axis an extent below 3 cells (one cell: a 9-cell
+                                  stencil) and reflecting walls.  sim_create fails with
+                                  KMC_EINVAL if a vz is not 0. */
 
 /* ---- search kernels (kmc_params.search_kernel) ----------------------------- */
 #define KMC_SEARCH_AUTO 0      /* per step: warp-per-cell search when cells are well

@@ -13,6 +13,10 @@ Workloads (all with m = 1 and kT/m = 1 unless stated):
   reflecting wall at x = 0 and a piston at x = 8 moving inward at u_p.
 * ``spherical_blast``: periodic unit cube with a central sphere of radius 0.1 at 8x
   the background number density and 100x its temperature.
+* ``equal_speed``: the paper's timing runs (Sec. 3 and Sec. 4): uniform positions,
+  all particles at the same speed in uniformly random directions, reflecting walls;
+  in three dimensions or in the x-y plane (``planar``: vz = 0, z fixed at the middle
+  of a thin z extent).
 
 The hard-sphere mean free path is lambda = 1/(sqrt(2) n sigma) with
 sigma = pi d0^2, so d0 = sqrt(1/(sqrt(2) pi n lambda)).
@@ -46,6 +50,7 @@ class Setup:
     profile_range: float = 1.0
     steps: int = 1
     name: str = ""
+    planar: bool = False  # two-dimensional dynamics in the x-y plane
     extra: dict = field(default_factory=dict)
 
     def with_(self, **kw) -> "Setup":
@@ -138,8 +143,38 @@ def blast_setup(n: int = 1 << 27, seed: int = 3, lam_bg: float = 0.005,
                  steps=steps, name=f"spherical_blast_n{n}", extra={"n_hot": n_hot})
 
 
+def equal_speed_state(n: int, seed: int, box, speed: float = 1.0, planar: bool = False):
+    """Uniform positions; velocities of one speed in uniformly random directions (in the
+    x-y plane with vz = 0 and z at the middle of the box if planar)."""
+    rng = np.random.default_rng(seed)
+    pos = [_uniform(rng, n, float(box[k])) for k in range(3)]
+    if planar:
+        pos[2] = np.full(n, 0.5 * float(box[2]))
+        th = rng.random(n) * (2.0 * math.pi)
+        vel = [speed * np.cos(th), speed * np.sin(th), np.zeros(n)]
+    else:
+        g = rng.standard_normal((3, n))
+        norm = np.sqrt((g * g).sum(axis=0))
+        vel = [speed * g[k] / norm for k in range(3)]
+    return pos + vel
+
+
+def equal_speed_setup(n: int = 4096, seed: int = 11, L: float = 1.0, d0: float = 0.002,
+                      dt: float = 0.005, speed: float = 1.0, planar: bool = True,
+                      steps: int = 100) -> Setup:
+    """The paper's timing workload: a box with reflecting walls, one speed, random
+    directions.  Planar: an L x L square, z extent d0 (one cell), a 9-cell stencil."""
+    box = (L, L, d0 if planar else L)
+    return Setup(n=n, box=box, bc=(REFLECT,) * 3, piston_x0=L, piston_u=0.0, d0=d0, dt=dt,
+                 seed=seed, steps=steps, planar=planar,
+                 name=f"equal_speed_{'2d' if planar else '3d'}_n{n}", extra={"speed": speed})
+
+
 def initial_state(setup: Setup):
     """Six float64 arrays (x, y, z, vx, vy, vz) in particle-id order."""
+    if setup.name.startswith("equal_speed"):
+        return equal_speed_state(setup.n, setup.seed, setup.box, setup.extra.get("speed", 1.0),
+                                 setup.planar)
     if setup.name.startswith("equilibrium"):
         return equilibrium_state(setup.n, setup.seed, setup.box[0])
     if setup.name.startswith("piston"):

@@ -37,6 +37,7 @@ class Params(C.Structure):
         ("profile_bins", C.c_int32), ("profile_every", C.c_int32),
         ("profile_range", C.c_double),
         ("search", C.c_int32), ("threads", C.c_int32),
+        ("planar", C.c_int32), ("pad1", C.c_int32),
     ]
 
 
@@ -70,6 +71,8 @@ def lib():
             L.or_philox4x32_10.argtypes = [up, up, up]
             L.or_unit_vector.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, dp]
             L.or_unit_vector.restype = C.c_int
+            L.or_circle_vector.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, dp]
+            L.or_circle_vector.restype = C.c_int
             L.or_pair.argtypes = [C.POINTER(Params), C.POINTER(dp), up, C.c_uint32, C.c_uint32,
                                   dp, dp]
             L.or_pair.restype = C.c_int
@@ -114,6 +117,7 @@ def params_from(setup, search: int = 1, threads: int = 0) -> Params:
     p.profile_range = float(setup.profile_range)
     p.search = int(search)
     p.threads = int(threads)
+    p.planar = 1 if getattr(setup, "planar", False) else 0
     return p
 
 
@@ -146,6 +150,13 @@ def philox4x32_10(ctr, key):
 def unit_vector(seed: int, step: int, pid: int):
     out = np.zeros(3)
     tries = lib().or_unit_vector(seed, step, pid, _dp(out))
+    return out, tries
+
+
+def circle_vector(seed: int, step: int, pid: int):
+    """Scatter direction of the planar mode (unit vector in the x-y plane)."""
+    out = np.zeros(3)
+    tries = lib().or_circle_vector(seed, step, pid, _dp(out))
     return out, tries
 
 

@@ -26,7 +26,9 @@
  *   - Collision update: Sec. 2 says only that positions and velocities are updated;
  *     the update used is an isotropic centre-of-mass elastic scatter whose
  *     direction comes from Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and
- *     Marsaglia's (1972) method for a point on the unit sphere.
+ *     Marsaglia's (1972) method for a point on the unit sphere; in the planar mode
+ *     (the paper's two-dimensional runs, Sec. 2 and Sec. 4: 8 neighbouring bins)
+ *     the direction is uniform on the unit circle (von Neumann's method).
  *   - Boundaries: Sec. 2 (reflective or periodic box), plus a moving piston wall.
  */
 #include <math.h>
@@ -54,6 +56,9 @@ typedef struct or_params {
   double profile_range;
   int32_t search;  /* 0: brute force O(N^2), 1: cell search */
   int32_t threads; /* 0: library default */
+  int32_t planar;  /* 1: two-dimensional dynamics in the x-y plane (z and vz constant,
+                      vz = 0); scatter directions isotropic in the plane */
+  int32_t pad1;
 } or_params;
 
 /* Per-step record: collisions (matched pairs), candidate pairs, and the pairs
@@ -114,6 +119,34 @@ int or_unit_vector(uint64_t seed, uint64_t step, uint32_t id, double nvec[3]) {
         nvec[0] = (u1 + u1) * q;
         nvec[1] = (u2 + u2) * q;
         nvec[2] = 1.0 - (s + s);
+        return (int)(2 * k + a + 1);
+      }
+    }
+  }
+  return -1;
+}
+
+/* Unit vector in the x-y plane for the planar (two-dimensional) mode, from the same
+ * counters as or_unit_vector.  A point (u1, u2) uniform in the unit disk (the same
+ * rejection) has a uniform polar angle phi; the vector at twice that angle,
+ * (cos 2phi, sin 2phi) = ((u1^2 - u2^2)/s, (2 u1 u2)/s) with s = u1^2 + u2^2, is
+ * uniform on the unit circle (von Neumann's method, no trigonometric function).
+ * Written n = ((u1*u1 - u2*u2) / s, ((u1 + u1) * u2) / s, 0).
+ * Returns the number of attempts used (1..128) or -1 if all 128 were rejected. */
+int or_circle_vector(uint64_t seed, uint64_t step, uint32_t id, double nvec[3]) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (uint32_t k = 0; k < 64; ++k) {
+    uint32_t ctr[4] = {id, (uint32_t)step, k, (uint32_t)(step >> 32)};
+    uint32_t w[4];
+    or_philox4x32_10(ctr, key, w);
+    for (int a = 0; a < 2; ++a) {
+      double u1 = (double)w[2 * a] * 0x1p-31 - 1.0;
+      double u2 = (double)w[2 * a + 1] * 0x1p-31 - 1.0;
+      double s = u1 * u1 + u2 * u2;
+      if (s > 0.0 && s < 1.0) {
+        nvec[0] = (u1 * u1 - u2 * u2) / s;
+        nvec[1] = ((u1 + u1) * u2) / s;
+        nvec[2] = 0.0;
         return (int)(2 * k + a + 1);
       }
     }
@@ -532,7 +565,10 @@ int or_step(const or_params* p, double* const st[6], uint32_t* last, uint64_t st
     ++coll;
     double t = a.t[pedge[ia]];
     double nv[3];
-    if (or_unit_vector(p->seed, step, ia, nv) < 0) { rc = -2; continue; }
+    if ((p->planar ? or_circle_vector(p->seed, step, ia, nv) : or_unit_vector(p->seed, step, ia, nv)) < 0) {
+      rc = -2;
+      continue;
+    }
     double g[3], V[3];
     for (int k = 0; k < 3; ++k) {
       g[k] = st[3 + k][ia] - st[3 + k][ib];

@@ -45,6 +45,7 @@ KMC_NONE = 0xFFFFFFFF
 
 KMC_FLAG_NO_SPLIT = 1
 KMC_FLAG_FORCE_SPLIT = 2
+KMC_FLAG_PLANAR = 4
 
 KMC_SEARCH_AUTO = 0
 KMC_SEARCH_PARTICLE = 1

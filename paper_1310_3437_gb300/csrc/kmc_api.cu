@@ -144,7 +144,7 @@ size_t bytes_for(const Sizes& z) {
 int validate(const kmc_params* p, std::string& err) {
   if (!p) { err = "params is NULL"; return KMC_EINVAL; }
   if (p->n == 0) { err = "n must be >= 1"; return KMC_EINVAL; }
-  if (p->flags & ~(uint32_t)(KMC_FLAG_NO_SPLIT | KMC_FLAG_FORCE_SPLIT)) { err = "unknown flags"; return KMC_EINVAL; }
+  if (p->flags & ~(uint32_t)(KMC_FLAG_NO_SPLIT | KMC_FLAG_FORCE_SPLIT | KMC_FLAG_PLANAR)) { err = "unknown flags"; return KMC_EINVAL; }
   if ((p->flags & KMC_FLAG_NO_SPLIT) && (p->flags & KMC_FLAG_FORCE_SPLIT)) { err = "conflicting split flags"; return KMC_EINVAL; }
   for (int a = 0; a < 3; ++a) {
     if (!(p->box[a] > 0.0)) { err = "box extents must be > 0"; return KMC_EINVAL; }
@@ -488,6 +488,7 @@ int sim_create(const kmc_params* p, const double* x, const double* y, const doub
   h.K = p->stencil ? p->stencil : 1;
   h.search_kernel = p->search_kernel;
   h.split_ok = (p->flags & KMC_FLAG_NO_SPLIT) ? 0 : ((p->flags & KMC_FLAG_FORCE_SPLIT) ? 2 : 1);
+  h.planar = (p->flags & KMC_FLAG_PLANAR) ? 1 : 0;
   h.split_min_occ = p->split_min_occ;
   h.piston_x0 = p->bc[0] == KMC_REFLECT ? p->piston_x0 : p->box[0];
   h.piston_u = p->bc[0] == KMC_REFLECT ? p->piston_u : 0.0;
@@ -584,7 +585,8 @@ int sim_create(const kmc_params* p, const double* x, const double* y, const doub
     return fail(KMC_ECUDA);
   dfree(s, bad);
   if (nbad) {
-    s->err = std::to_string(nbad) + " particle(s) outside the box or with non-finite velocity";
+    s->err = std::to_string(nbad) + " particle(s) outside the box or with non-finite velocity" +
+             std::string(h.planar ? " (or, planar, with vz != 0)" : "");
     return fail(KMC_EINVAL);
   }
   if ((rc = ensure_solo(s))) return fail(rc);

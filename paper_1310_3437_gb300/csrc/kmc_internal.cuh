@@ -101,6 +101,7 @@ struct SimDev {
   int32_t bc[3];
   int32_t max_rounds, precision, profile_bins, profile_every, K, search_kernel;
   int32_t split_ok;     // 0: never split, 1: split when cheaper, 2: split whenever possible
+  int32_t planar;       // 1: x-y dynamics (vz = 0), scatter directions in the plane
   double split_min_occ; // smallest mean occupancy of the slow grid under a split
   double box[3];
   double piston_x0, piston_u, d0, dt, d0sq;

@@ -85,6 +85,30 @@ __device__ bool sphere_point(uint64_t seed, uint64_t step, uint32_t id, double n
   return false;
 }
 
+// Planar mode: a direction uniform on the unit circle from the same counters.  A point
+// (u1, u2) uniform in the unit disk (the same rejection) has a uniform polar angle;
+// the vector at twice that angle, ((u1^2 - u2^2)/s, (2 u1 u2)/s), is uniform on the
+// circle (von Neumann's method, no trigonometric function).
+__device__ bool circle_point(uint64_t seed, uint64_t step, uint32_t id, double nv[3]) {
+  for (uint32_t k = 0; k < 64; ++k) {
+    uint32_t c[4] = {id, (uint32_t)step, k, (uint32_t)(step >> 32)};
+    philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const double u1a = word_uniform(c[0]), u2a = word_uniform(c[1]);
+    const double u1b = word_uniform(c[2]), u2b = word_uniform(c[3]);
+    const double sa = dadd(dmul(u1a, u1a), dmul(u2a, u2a));
+    const double sb = dadd(dmul(u1b, u1b), dmul(u2b, u2b));
+    const bool oka = sa > 0.0 && sa < 1.0, okb = sb > 0.0 && sb < 1.0;
+    if (oka || okb) {
+      const double u1 = oka ? u1a : u1b, u2 = oka ? u2a : u2b, s = oka ? sa : sb;
+      nv[0] = ddiv(dsub(dmul(u1, u1), dmul(u2, u2)), s);
+      nv[1] = ddiv(dmul(dadd(u1, u1), u2), s);
+      nv[2] = 0.0;
+      return true;
+    }
+  }
+  return false;
+}
+
 __device__ __forceinline__ double min_image(double r, double L) {
   double h = dmul(L, 0.5);
   if (r > h) return dsub(r, L);
@@ -318,7 +342,7 @@ __global__ void __launch_bounds__(kEdgeBlock) k_collide(Batch B) {
       const uint32_t ida = s.id[cur][i];
       double t = s.e_t[s.medge[i]];
       double nv[3];
-      if (!sphere_point(s.seed, s.d.step, ida, nv)) {
+      if (!(s.planar ? circle_point(s.seed, s.d.step, ida, nv) : sphere_point(s.seed, s.d.step, ida, nv))) {
         atomicOr(&s.d.status, ST_RANDOM);
         continue;
       }

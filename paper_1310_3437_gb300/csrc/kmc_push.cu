@@ -400,6 +400,7 @@ __global__ void k_validate(SimDev* d, uint32_t* bad) {
     if (!(q >= 0.0) || (periodic ? !(q < hi) : !(q <= hi))) out = true;
     if (!(fabs(s.v[s.d.parity][a][p]) < 1e15)) out = true;
   }
+  if (s.planar && s.v[s.d.parity][2][p] != 0.0) out = true;
   if (out) atomicAdd(bad, 1u);
 }
 

@@ -45,7 +45,7 @@ def params_from_setup(setup, precision=KMC_FP64, stencil=1, cell_scale=1.0, step
     p.profile_cap = int(profile_cap)
     p.search_kernel = int(search_kernel)
     p.split_min_occ = float(split_min_occ)
-    p.flags = int(flags)
+    p.flags = int(flags) | (4 if getattr(setup, "planar", False) else 0)  # KMC_FLAG_PLANAR
     return p
 
 

@@ -28,7 +28,7 @@ def gpu_sim(setup, arrays, precision=FP64, stencil=1, cell_scale=1.0, last=None,
             edge_cap=0, search_kernel=0, flags=0):
     p = kmc.params_from_setup(setup, precision=precision, stencil=stencil, cell_scale=cell_scale,
                               step0=step0, edge_cap=edge_cap, search_kernel=search_kernel)
-    p.flags = flags
+    p.flags |= flags
     return kmc.Simulation(p, arrays, last=last)
 
 
@@ -328,3 +328,44 @@ def test_long_periodic_box_near_thresholds_binary32_equals_binary64(kernel):
     for prec in (FP64, FP32):
         sim = gpu_sim(s, pos + vel, prec, search_kernel=kernel).step(1).sync()
         assert np.array_equal(sim.edges(), np.stack([pi, pj], axis=1))
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
+def test_planar_equal_speed_reflecting_square_bit_exact(precision, kernel):
+    """The paper's 2D runs: equal speeds in random in-plane directions, reflecting
+    walls, a z extent of one cell (9-cell stencil), isotropic in-plane scatter."""
+    s = ki.equal_speed_setup(n=8192, seed=12, d0=0.002, dt=0.005, steps=120)
+    sim, st, oc, _ = run_both(s, 120, precision, search_kernel=kernel)
+    assert_same_counts(sim.counts(), oc)
+    assert_same_state(sim, st)
+    assert sum(c["collisions"] for c in oc) > 20000
+    arrays, _ = sim.state()
+    assert np.all(arrays[5] == 0.0)
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_planar_periodic_square_pair_lists_and_forced_split(precision):
+    s = ki.equal_speed_setup(n=6000, seed=13, d0=0.004, dt=0.01)
+    s = s.with_(bc=(ki.PERIODIC, ki.PERIODIC, ki.REFLECT))
+    arrays = ki.initial_state(s)
+    st = oracle.State(arrays)
+    sim = gpu_sim(s, arrays, precision=precision, flags=kmc.KMC_FLAG_FORCE_SPLIT)
+    for step in range(8):
+        pi, pj, _, _ = oracle.candidate_pairs(s, st)
+        counts, partner, _ = oracle.step(s, st, step)
+        sim.step(1).sync()
+        e = sim.edges()
+        assert np.array_equal(e, np.stack([pi, pj], axis=1)), f"step {step}"
+        assert np.array_equal(sim.partners(), partner), f"step {step}"
+    assert_same_state(sim, st)
+
+
+def test_planar_rejects_out_of_plane_velocity():
+    s = ki.equal_speed_setup(n=512, seed=14)
+    arrays = ki.initial_state(s)
+    arrays[5] = arrays[5].copy()
+    arrays[5][77] = 1e-300
+    with pytest.raises(kmc.KmcError) as e:
+        gpu_sim(s, arrays)
+    assert e.value.code == kmc.KMC_EINVAL and "vz" in str(e.value)
