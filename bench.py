@@ -210,8 +210,13 @@ def run_serving(args, stream, dev):
                                  steps_lo=st_lo, steps_hi=st_hi)
     cal, rest = setups[:16], setups[16:]
     # calibration: 16 requests admitted at once
-    reqs = [Request(rid=k, setup=q, steps=q.steps, arrival=0.0, arrays=ki.initial_state(q))
-            for k, q in enumerate(cal)]
+    def req(k, q, arrival):
+        if args.serve_host_init:
+            return Request(rid=k, setup=q, steps=q.steps, arrival=arrival,
+                           arrays=(lambda q=q: ki.initial_state(q)))
+        return Request(rid=k, setup=q, steps=q.steps, arrival=arrival, init=ki.init_spec(q))
+
+    reqs = [req(k, q, 0.0) for k, q in enumerate(cal)]
     server = Server(budget_bytes=args.serve_budget_gb * 1e9, keep_state=False,
                     stream=stream.cuda_stream)
     done, wall = server.run(reqs)
@@ -220,8 +225,7 @@ def run_serving(args, stream, dev):
     rate = 0.7 * S / W
     rng = np.random.default_rng(7)
     t = np.cumsum(rng.exponential(1.0 / rate, size=len(rest)))
-    reqs = [Request(rid=k, setup=q, steps=q.steps, arrival=float(t[k]),
-                    arrays=(lambda q=q: ki.initial_state(q))) for k, q in enumerate(rest)]
+    reqs = [req(k, q, float(t[k])) for k, q in enumerate(rest)]
     server = Server(budget_bytes=args.serve_budget_gb * 1e9, keep_state=True,
                     stream=stream.cuda_stream)
     done, wall = server.run(reqs)
@@ -235,6 +239,8 @@ def run_serving(args, stream, dev):
         "mix": f"equilibrium boxes and piston tubes, N log-uniform [{n_lo}, {n_hi}], steps "
                f"U[{st_lo}, {st_hi}], guarded FP32, SplitMix64 seeds from master seed 7",
         "latency": "arrival -> final state and step counts on the host",
+        "init": ("NumPy arrays generated on the host at admission" if args.serve_host_init
+                 else "state drawn on the device at admission (sim_create_init)"),
     }
 
 
@@ -331,7 +337,9 @@ def run_gpu(args):
         setup = headline_setup(n)
     if world > 1:
         setup = setup.with_(seed=setup.seed + rank)
+    t_gen = time.perf_counter()
     arrays = ki.initial_state(setup)
+    host_generate_s = time.perf_counter() - t_gen
     dev_arrays = [torch.from_numpy(a).to(dev) for a in arrays]
 
     def barrier():
@@ -433,6 +441,30 @@ def run_gpu(args):
                "h2d_bytes_per_step": 48 * n / ke, "d2h_bytes_per_step": 52 * n / ke,
                "job": f"create from pinned host arrays, {ke} steps, state read back"}
 
+    # ---- end to end with the state drawn on the device (no host arrays) ----
+    e2e_dinit = None
+    if not args.skip_e2e:
+        out = torch.empty(52 * n, dtype=torch.uint8).pin_memory()
+        ke = args.steps
+        spec = ki.init_spec(setup)
+        params = kmc.params_from_setup(setup, precision=kmc.KMC_GUARDED_FP32, **knobs)
+        barrier()
+        t0 = time.perf_counter()
+        sim = kmc.Simulation(params, init=spec, stream=stream.cuda_stream)
+        torch.cuda.synchronize(dev)
+        tc = time.perf_counter() - t0
+        sim.step(ke)
+        kmc.sim_observe(sim.handle, kmc.KMC_OBS_STATE, out.data_ptr(), out.numel())
+        torch.cuda.synchronize(dev)
+        te = max_over_ranks(time.perf_counter() - t0)
+        sim.close()
+        e2e_dinit = {"value": world * n * ke / te, "unit": UNIT, "h2d_bytes_per_step": 0,
+                     "d2h_bytes_per_step": 52 * n / ke, "create_ms": tc * 1e3,
+                     "host_generate_ms": host_generate_s * 1e3,
+                     "job": f"sim_create_init (state drawn on the device), {ke} steps, state "
+                            f"read back; host_generate_ms: NumPy generation of the same "
+                            f"workload's arrays, which sim_create_init replaces"}
+
     serve = None
     if not args.skip_serve and rank == 0:
         serve = run_serving(args, stream, dev)
@@ -502,6 +534,7 @@ def run_gpu(args):
         "candidate_pairs_per_step": edges_mean, "collisions_per_step": coll_mean,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "e2e_device_init": e2e_dinit,
         "serve": serve,
         "ensemble": ensemble,
         "tuning": tuning,
@@ -530,6 +563,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--serve-host-init", action="store_true",
+                    help="serving requests carry host arrays instead of a device-init descriptor")
     ap.add_argument("--skip-ensemble", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--ensemble-steps", type=int, default=100)

@@ -162,6 +162,44 @@ int sim_create(const kmc_params* p, const double* x, const double* y, const doub
                const double* vx, const double* vy, const double* vz, const uint32_t* last,
                void* stream, kmc_sim** out);
 
+/* ---- device-side initial states (sim_create_init) ------------------------ */
+#define KMC_INIT_MAXWELL 1     /* positions uniform in the box, velocity components
+                                  i.i.d. N(0, sigma^2) (the equilibrium box and the
+                                  piston tube) */
+#define KMC_INIT_EQUAL_SPEED 2 /* positions uniform in the box, |v| = speed, direction
+                                  uniform on the sphere (the paper's timing runs,
+                                  Sec. 3 and Sec. 4) or, planar, on the circle */
+#define KMC_INIT_BLAST 3       /* ids below n_hot uniform in the ball |x - center| <
+                                  radius with N(0, sigma_hot^2) components, the others
+                                  uniform in the box outside it with N(0, sigma^2) */
+
+/* Initial-state descriptor.  Draws: Philox4x32-10 keyed by params.seed, counter
+ * (id, 0xFFFFFFFF, k, 0xFFFFFFFF) -- the collision counter of step 2^64 - 1, which
+ * no run reaches; blocks k = 0..127 for positions (53-bit uniforms, rejection for
+ * the blast's ball), k = 128..191 for velocities (Marsaglia's polar method with a
+ * logarithm built from +, -, *, /; directions as in the collision update).  Planar
+ * (KMC_FLAG_PLANAR): z = box[2]/2, vz = 0.  The arrays depend only on (params,
+ * descriptor), bit for bit, not on the GPU or the launch. */
+typedef struct kmc_init {
+  uint32_t kind;      /* KMC_INIT_* */
+  uint32_t pad0;
+  uint64_t n_hot;     /* BLAST: number of hot particles (ids 0..n_hot-1), <= n */
+  double sigma;       /* MAXWELL, BLAST (outside): per-component standard deviation */
+  double speed;       /* EQUAL_SPEED: the common speed */
+  double sigma_hot;   /* BLAST (inside) */
+  double center[3];   /* BLAST: ball centre; the ball must lie strictly inside the box */
+  double radius;      /* BLAST: ball radius > 0 */
+} kmc_init;
+
+/* Create a simulation whose initial state is drawn on the device (no host arrays,
+ * no host-to-device copy of the state): ids 0..n-1, no last partners.  Same
+ * parameters, stream and ownership rules as sim_create.  Errors: KMC_EINVAL (bad
+ * parameter or descriptor: unknown kind, negative or non-finite sigma/speed, a ball
+ * not strictly inside the box, n_hot > n, BLAST with KMC_FLAG_PLANAR),
+ * KMC_ERANDOM (a rejection loop ran out of its 64 attempts; probability below
+ * 1e-20 per particle), KMC_ENOMEM, KMC_ECUDA.  On error *out is NULL. */
+int sim_create_init(const kmc_params* p, const kmc_init* init, void* stream, kmc_sim** out);
+
 /* Enqueue nsteps time steps (Sec. 2: sort, detect, collide, stream, boundaries).
  * Errors: KMC_ESTATE if the simulation belongs to a group, KMC_ECUDA. */
 int sim_step(kmc_sim* s, uint32_t nsteps);

@@ -140,7 +140,8 @@ def blast_setup(n: int = 1 << 27, seed: int = 3, lam_bg: float = 0.005,
     d0 = d0_for_mean_free_path(n_bg, lam_bg)
     dt = 0.05 * lam_bg / 1.0  # v_th of the background read as sqrt(kT/m) = 1
     return Setup(n=n, box=(1.0, 1.0, 1.0), bc=(PERIODIC,) * 3, d0=d0, dt=dt, seed=seed,
-                 steps=steps, name=f"spherical_blast_n{n}", extra={"n_hot": n_hot})
+                 steps=steps, name=f"spherical_blast_n{n}",
+                 extra={"n_hot": n_hot, "radius": radius, "temperature_ratio": 100.0})
 
 
 def equal_speed_state(n: int, seed: int, box, speed: float = 1.0, planar: bool = False):
@@ -168,6 +169,24 @@ def equal_speed_setup(n: int = 4096, seed: int = 11, L: float = 1.0, d0: float =
     return Setup(n=n, box=box, bc=(REFLECT,) * 3, piston_x0=L, piston_u=0.0, d0=d0, dt=dt,
                  seed=seed, steps=steps, planar=planar,
                  name=f"equal_speed_{'2d' if planar else '3d'}_n{n}", extra={"speed": speed})
+
+
+def init_spec(setup: Setup) -> dict:
+    """Parameters of the same workload for the Philox-based (device-side)
+    initialisation: kind 1 = uniform box with Gaussian velocity components of
+    standard deviation ``sigma``; 2 = uniform box, one speed, random directions;
+    3 = blast (ids below ``n_hot`` uniform in the central sphere with ``sigma_hot``,
+    the rest uniform outside it).  The draws themselves are defined by the
+    initialisation (not by NumPy), so its arrays differ from ``initial_state``'s
+    while following the same distributions."""
+    if setup.name.startswith("equal_speed"):
+        return {"kind": 2, "speed": float(setup.extra.get("speed", 1.0))}
+    if setup.name.startswith("spherical_blast"):
+        r = float(setup.extra.get("radius", 0.1))
+        return {"kind": 3, "n_hot": int(setup.extra["n_hot"]), "sigma": 1.0,
+                "sigma_hot": math.sqrt(float(setup.extra.get("temperature_ratio", 100.0))),
+                "center": tuple(0.5 * float(b) for b in setup.box), "radius": r}
+    return {"kind": 1, "sigma": 1.0}
 
 
 def initial_state(setup: Setup):

@@ -41,6 +41,13 @@ class Params(C.Structure):
     ]
 
 
+class Init(C.Structure):
+    """Initial-state descriptor of the Philox initialisation (``or_init``)."""
+    _fields_ = [("kind", C.c_int32), ("pad0", C.c_int32), ("n_hot", C.c_uint64),
+                ("sigma", C.c_double), ("speed", C.c_double), ("sigma_hot", C.c_double),
+                ("center", C.c_double * 3), ("radius", C.c_double)]
+
+
 class Counts(C.Structure):
     _fields_ = [("step", C.c_uint64), ("collisions", C.c_uint32), ("edges", C.c_uint32),
                 ("round_pairs", C.c_uint32 * 4)]
@@ -88,6 +95,12 @@ def lib():
             L.or_vmax2.argtypes = [C.c_uint32, dp, dp, dp]
             L.or_vmax2.restype = C.c_double
             L.or_max_threads.restype = C.c_int
+            L.or_log.argtypes = [C.c_double]
+            L.or_log.restype = C.c_double
+            L.or_log_many.argtypes = [dp, dp, C.c_int64]
+            L.or_init_particles.argtypes = [C.POINTER(Init), C.POINTER(Params), up, C.c_int64,
+                                            C.POINTER(dp)]
+            L.or_init_particles.restype = C.c_int64
             _lib = L
     return _lib
 
@@ -144,6 +157,42 @@ def philox4x32_10(ctr, key):
     k = np.asarray(key, dtype=np.uint32).copy()
     out = np.zeros(4, dtype=np.uint32)
     lib().or_philox4x32_10(_up(c), _up(k), _up(out))
+    return out
+
+
+def log(s):
+    """The oracle's own natural logarithm (+, -, *, / only) of an array or scalar."""
+    a = np.ascontiguousarray(np.atleast_1d(np.asarray(s, dtype=np.float64)))
+    out = np.empty_like(a)
+    lib().or_log_many(_dp(a), _dp(out), a.shape[0])
+    return out if np.ndim(s) else float(out[0])
+
+
+def init_struct(spec: dict) -> Init:
+    d = Init()
+    d.kind = int(spec["kind"])
+    d.n_hot = int(spec.get("n_hot", 0))
+    d.sigma = float(spec.get("sigma", 1.0))
+    d.speed = float(spec.get("speed", 1.0))
+    d.sigma_hot = float(spec.get("sigma_hot", 1.0))
+    for k, c in enumerate(spec.get("center", (0.5, 0.5, 0.5))):
+        d.center[k] = float(c)
+    d.radius = float(spec.get("radius", 0.0))
+    return d
+
+
+def init_particles(setup, spec: dict, ids=None):
+    """Initial state of the Philox initialisation: six float64 arrays for ``ids``
+    (all particles of ``setup`` if None)."""
+    ids = (np.arange(setup.n, dtype=np.uint32) if ids is None
+           else np.ascontiguousarray(ids, dtype=np.uint32))
+    out = [np.zeros(ids.shape[0]) for _ in range(6)]
+    ptrs = (C.POINTER(C.c_double) * 6)(*[_dp(x) for x in out])
+    d = init_struct(spec)
+    p = params_from(setup)
+    fails = lib().or_init_particles(C.byref(d), C.byref(p), _up(ids), ids.shape[0], ptrs)
+    if fails:
+        raise RuntimeError(f"{fails} particle(s) ran out of rejection attempts")
     return out
 
 

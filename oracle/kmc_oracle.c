@@ -661,3 +661,170 @@ int or_max_threads(void) {
   return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------- */
+/* Initial states drawn from Philox4x32-10 (the library's device-side
+ * initialisation).  The paper describes its initial states only in words (Sec. 2:
+ * particles in a box; Sec. 3 and Sec. 4: random positions, one speed, random
+ * directions); this generator fixes one counter-based reading so that two
+ * independent implementations produce the same arrays.
+ *
+ * Draws for particle `id`: key (seed lo, seed hi), counter (id, 0xFFFFFFFF, k,
+ * 0xFFFFFFFF), i.e. the scatter counter of step 2^64 - 1, a step no run reaches.
+ *   positions: attempt a (0..63) uses blocks k = 2a, 2a+1; each coordinate is a
+ *     53-bit uniform u = ((w0 >> 5) 2^26 + (w1 >> 6)) 2^-53 in [0, 1) from two
+ *     words (x: block 2a words 0-1, y: block 2a words 2-3, z: block 2a+1 words 0-1);
+ *     x = u L (the largest double below L if the product rounds to L).  Box
+ *     states accept attempt 0.  The blast's hot particles (id < n_hot) take
+ *     x = (c - r) + (2r) u per axis and accept |x - c|^2 < r^2; the others take
+ *     x = u L and accept |x - c|^2 >= r^2, with |x - c|^2 summed as (dx^2 + dy^2) + dz^2.
+ *   velocities: blocks k = 128 + j (j = 0..63), two attempts per block (words 0-1,
+ *     words 2-3), u = w 2^-31 - 1, s = u1^2 + u2^2, accept 0 < s < 1.
+ *     Gaussian (Marsaglia's polar method, SIAM Rev. 6, 1964): f = sqrt((-2 ln s) / s),
+ *     the first accepted attempt gives (u1 f, u2 f) = (gx, gy), the second gives
+ *     gz (its u1 f); v = sigma g.  Equal speed: the first accepted attempt gives the
+ *     direction n (sphere: (2 u1 sqrt(1-s), 2 u2 sqrt(1-s), 1 - 2s); planar:
+ *     ((u1^2 - u2^2)/s, (2 u1) u2 / s, 0)), v = speed n.
+ *   planar: z = box_z / 2 and vz = 0 (only two Gaussians are used).
+ * ln s is or_log below. */
+
+/* Natural logarithm from +, -, *, / only (so that two implementations that follow
+ * the same operations agree bit for bit): s = m 2^e with m in [1, 2) read from the
+ * bits (exact), m halved and e raised when m > sqrt(2) (the double nearest sqrt 2),
+ * so m in (0.707, 1.415); ln m = 2 atanh(f) with f = (m - 1)/(m + 1), |f| < 0.172,
+ * by the series 2 f (1 + f^2/3 + f^4/5 + ... + f^22/23) (f^24/25 < 2^-63) in
+ * Horner form with coefficients 1/(2k+1) formed by one division each; then
+ * ln s = e ln2 + ln m with ln2 the double nearest ln 2.  For positive normal s. */
+double or_log(double s) {
+  uint64_t b;
+  memcpy(&b, &s, sizeof b);
+  int e = (int)((b >> 52) & 0x7FF) - 1023;
+  b = (b & 0x000FFFFFFFFFFFFFull) | ((uint64_t)1023 << 52);
+  double m;
+  memcpy(&m, &b, sizeof m);
+  if (m > 0x1.6a09e667f3bcdp+0) {
+    m = m * 0.5;
+    e = e + 1;
+  }
+  double f = (m - 1.0) / (m + 1.0);
+  double z = f * f;
+  double poly = 1.0 / 23.0;
+  for (int k = 10; k >= 0; --k) poly = poly * z + 1.0 / (double)(2 * k + 1);
+  double lnm = (f + f) * poly;
+  return (double)e * 0x1.62e42fefa39efp-1 + lnm;
+}
+
+typedef struct or_init {
+  int32_t kind;   /* 1 Maxwellian box, 2 equal speed, 3 blast */
+  int32_t pad0;
+  uint64_t n_hot; /* blast: ids below n_hot are hot */
+  double sigma;   /* Maxwellian / blast background: per-component standard deviation */
+  double speed;   /* equal speed */
+  double sigma_hot;
+  double center[3];
+  double radius;
+} or_init;
+
+static double u53(uint32_t w0, uint32_t w1) {
+  return ((double)(w0 >> 5) * 67108864.0 + (double)(w1 >> 6)) * 0x1p-53;
+}
+
+static double below(double L) { return nextafter(L, 0.0); }
+
+static double scale_into(double u, double L) {
+  double x = u * L;
+  return x < L ? x : below(L);
+}
+
+/* one particle; returns 0, or -1 when a rejection loop ran out of attempts */
+static int init_one(const or_init* in, const or_params* p, uint32_t id, double out[6]) {
+  const uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
+  const int blast = in->kind == 3;
+  const int hot = blast && (uint64_t)id < in->n_hot;
+  int placed = 0;
+  for (uint32_t a = 0; a < 64 && !placed; ++a) {
+    uint32_t c0[4] = {id, 0xFFFFFFFFu, 2 * a, 0xFFFFFFFFu}, c1[4] = {id, 0xFFFFFFFFu, 2 * a + 1, 0xFFFFFFFFu};
+    uint32_t w0[4], w1[4];
+    or_philox4x32_10(c0, key, w0);
+    or_philox4x32_10(c1, key, w1);
+    double u[3] = {u53(w0[0], w0[1]), u53(w0[2], w0[3]), u53(w1[0], w1[1])};
+    double x[3];
+    for (int k = 0; k < 3; ++k) {
+      if (hot) {
+        x[k] = (in->center[k] - in->radius) + (in->radius + in->radius) * u[k];
+      } else {
+        x[k] = scale_into(u[k], p->box[k]);
+      }
+    }
+    if (p->planar) x[2] = p->box[2] * 0.5;
+    if (blast) {
+      double d[3];
+      for (int k = 0; k < 3; ++k) d[k] = x[k] - in->center[k];
+      double r2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+      int inside = r2 < in->radius * in->radius;
+      if (inside != hot) continue;
+    }
+    for (int k = 0; k < 3; ++k) out[k] = x[k];
+    placed = 1;
+  }
+  if (!placed) return -1;
+  /* velocities */
+  double g[4];
+  int got = 0;
+  const int want = in->kind == 2 ? 1 : (p->planar ? 1 : 2); /* accepted attempts needed */
+  for (uint32_t j = 0; j < 64 && got < want; ++j) {
+    uint32_t c[4] = {id, 0xFFFFFFFFu, 128 + j, 0xFFFFFFFFu};
+    uint32_t w[4];
+    or_philox4x32_10(c, key, w);
+    for (int h = 0; h < 2 && got < want; ++h) {
+      double u1 = (double)w[2 * h] * 0x1p-31 - 1.0;
+      double u2 = (double)w[2 * h + 1] * 0x1p-31 - 1.0;
+      double s = u1 * u1 + u2 * u2;
+      if (!(s > 0.0 && s < 1.0)) continue;
+      if (in->kind == 2) {
+        if (p->planar) {
+          out[3] = in->speed * ((u1 * u1 - u2 * u2) / s);
+          out[4] = in->speed * (((u1 + u1) * u2) / s);
+          out[5] = 0.0;
+        } else {
+          double q = sqrt(1.0 - s);
+          out[3] = in->speed * ((u1 + u1) * q);
+          out[4] = in->speed * ((u2 + u2) * q);
+          out[5] = in->speed * (1.0 - (s + s));
+        }
+      } else {
+        double f = sqrt((-2.0 * or_log(s)) / s);
+        g[2 * got] = u1 * f;
+        g[2 * got + 1] = u2 * f;
+      }
+      ++got;
+    }
+  }
+  if (got < want) return -1;
+  if (in->kind != 2) {
+    double sg = hot ? in->sigma_hot : in->sigma;
+    out[3] = sg * g[0];
+    out[4] = sg * g[1];
+    out[5] = p->planar ? 0.0 : sg * g[2];
+  }
+  return 0;
+}
+
+/* Initial state of the listed particle ids (out[k][i] for ids[i]); returns the
+ * number of ids whose rejection loops ran out of attempts (0 normally). */
+int64_t or_init_particles(const or_init* in, const or_params* p, const uint32_t* ids, int64_t m,
+                          double* const out[6]) {
+  int64_t fails = 0;
+#pragma omp parallel for schedule(static) reduction(+ : fails)
+  for (int64_t i = 0; i < m; ++i) {
+    double o[6] = {0, 0, 0, 0, 0, 0};
+    if (init_one(in, p, ids[i], o)) ++fails;
+    for (int k = 0; k < 6; ++k) out[k][i] = o[k];
+  }
+  return fails;
+}
+
+/* or_log over an array (for tests) */
+void or_log_many(const double* s, double* out, int64_t m) {
+  for (int64_t i = 0; i < m; ++i) out[i] = or_log(s[i]);
+}

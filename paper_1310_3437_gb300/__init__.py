@@ -47,6 +47,10 @@ KMC_FLAG_NO_SPLIT = 1
 KMC_FLAG_FORCE_SPLIT = 2
 KMC_FLAG_PLANAR = 4
 
+KMC_INIT_MAXWELL = 1
+KMC_INIT_EQUAL_SPEED = 2
+KMC_INIT_BLAST = 3
+
 KMC_SEARCH_AUTO = 0
 KMC_SEARCH_PARTICLE = 1
 KMC_SEARCH_CELL = 2
@@ -69,6 +73,12 @@ class kmc_params(C.Structure):
         ("profile_cap", C.c_uint32), ("search_kernel", C.c_int32),
         ("split_min_occ", C.c_double),
     ]
+
+
+class kmc_init(C.Structure):
+    _fields_ = [("kind", C.c_uint32), ("pad0", C.c_uint32), ("n_hot", C.c_uint64),
+                ("sigma", C.c_double), ("speed", C.c_double), ("sigma_hot", C.c_double),
+                ("center", C.c_double * 3), ("radius", C.c_double)]
 
 
 class kmc_step_counts(C.Structure):
@@ -101,6 +111,9 @@ def lib():
             L.sim_create.argtypes = [C.POINTER(kmc_params), _P, _P, _P, _P, _P, _P, _P, _P,
                                      C.POINTER(_P)]
             L.sim_create.restype = C.c_int
+            L.sim_create_init.argtypes = [C.POINTER(kmc_params), C.POINTER(kmc_init), _P,
+                                          C.POINTER(_P)]
+            L.sim_create_init.restype = C.c_int
             L.sim_step.argtypes = [_P, C.c_uint32]
             L.sim_step.restype = C.c_int
             L.sim_sync.argtypes = [_P]
@@ -152,6 +165,27 @@ def sim_create(params: kmc_params, x, y, z, vx, vy, vz, last=None, stream=None):
     rc = lib().sim_create(C.byref(params), x, y, z, vx, vy, vz, last, stream, C.byref(out))
     _check(rc, None)
     return out.value
+
+
+def sim_create_init(params: kmc_params, init: kmc_init, stream=None):
+    out = _P()
+    rc = lib().sim_create_init(C.byref(params), C.byref(init), stream, C.byref(out))
+    _check(rc, None)
+    return out.value
+
+
+def init_from_spec(spec: dict) -> kmc_init:
+    """kmc_init from a dict with the descriptor's field names."""
+    d = kmc_init()
+    d.kind = int(spec["kind"])
+    d.n_hot = int(spec.get("n_hot", 0))
+    d.sigma = float(spec.get("sigma", 1.0))
+    d.speed = float(spec.get("speed", 1.0))
+    d.sigma_hot = float(spec.get("sigma_hot", 1.0))
+    for k, c in enumerate(spec.get("center", (0.5, 0.5, 0.5))):
+        d.center[k] = float(c)
+    d.radius = float(spec.get("radius", 0.0))
+    return d
 
 
 def sim_step(sim, nsteps: int):

@@ -29,6 +29,7 @@ SOURCES = {
     "kmc_push.cu": ["-fmad=false"],
     "kmc_api.cu": ["-fmad=false"],
     "kmc_noalloc.cu": ["-fmad=false"],
+    "kmc_init.cu": ["-fmad=false"],
 }
 
 

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
@@ -453,14 +454,52 @@ int sim_destroy(kmc_sim* s) {
   return KMC_OK;
 }
 
-int sim_create(const kmc_params* p, const double* x, const double* y, const double* z,
-               const double* vx, const double* vy, const double* vz, const uint32_t* last,
-               void* stream, kmc_sim** out) {
+}  // extern "C"
+
+namespace {
+
+int validate_init(const kmc_params* p, const kmc_init* in, std::string& err) {
+  if (!in) { err = "init descriptor is NULL"; return KMC_EINVAL; }
+  const bool planar = (p->flags & KMC_FLAG_PLANAR) != 0;
+  switch (in->kind) {
+    case KMC_INIT_MAXWELL:
+      if (!(in->sigma >= 0.0) || !std::isfinite(in->sigma)) { err = "sigma must be finite and >= 0"; return KMC_EINVAL; }
+      break;
+    case KMC_INIT_EQUAL_SPEED:
+      if (!(in->speed >= 0.0) || !std::isfinite(in->speed)) { err = "speed must be finite and >= 0"; return KMC_EINVAL; }
+      break;
+    case KMC_INIT_BLAST:
+      if (planar) { err = "BLAST cannot be planar"; return KMC_EINVAL; }
+      if (!(in->sigma >= 0.0) || !std::isfinite(in->sigma) || !(in->sigma_hot >= 0.0) ||
+          !std::isfinite(in->sigma_hot)) {
+        err = "sigma and sigma_hot must be finite and >= 0";
+        return KMC_EINVAL;
+      }
+      if (in->n_hot > p->n) { err = "n_hot exceeds n"; return KMC_EINVAL; }
+      if (!(in->radius > 0.0) || !std::isfinite(in->radius)) { err = "radius must be finite and > 0"; return KMC_EINVAL; }
+      for (int a = 0; a < 3; ++a) {
+        if (!(in->center[a] - in->radius > 0.0) || !(in->center[a] + in->radius < p->box[a])) {
+          err = "the ball must lie strictly inside the box";
+          return KMC_EINVAL;
+        }
+      }
+      break;
+    default:
+      err = "unknown init kind";
+      return KMC_EINVAL;
+  }
+  return KMC_OK;
+}
+
+// shared body of sim_create (src: six state arrays) and sim_create_init (init)
+int create_impl(const kmc_params* p, const double* const* src6, const uint32_t* last,
+                const kmc_init* init, void* stream, kmc_sim** out) {
   if (out) *out = nullptr;
   g_create_error.clear();
   int rc = validate(p, g_create_error);
   if (rc) return rc;
-  if (!out || !x || !y || !z || !vx || !vy || !vz) {
+  if (init && (rc = validate_init(p, init, g_create_error))) return rc;
+  if (!out || (!init && (!src6[0] || !src6[1] || !src6[2] || !src6[3] || !src6[4] || !src6[5]))) {
     g_create_error = "NULL array or output pointer";
     return KMC_EINVAL;
   }
@@ -552,16 +591,44 @@ int sim_create(const kmc_params* p, const double* x, const double* y, const doub
     return true;
   };
   bool ok = true;
-  const double* src[6] = {x, y, z, vx, vy, vz};
-  for (int a = 0; a < 3 && ok; ++a) {
-    ok = ck(cudaMemcpyAsync(h.x[0][a], src[a], n * sizeof(double), cudaMemcpyDefault, st)) &&
-         ck(cudaMemcpyAsync(h.v[0][a], src[3 + a], n * sizeof(double), cudaMemcpyDefault, st));
+  // bad[0]: particles outside the box / non-finite; bad[1]: exhausted init draws
+  uint32_t* bad = nullptr;
+  if ((rc = dalloc(s, &bad, 2))) return fail(rc);
+  ok = ck(cudaMemsetAsync(bad, 0, 2 * sizeof(uint32_t), st));
+  if (init) {
+    InitLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.n = p->n;
+    L.kind = (int32_t)init->kind;
+    L.planar = h.planar;
+    L.n_hot = init->n_hot;
+    L.seed = p->seed;
+    L.sigma = init->sigma;
+    L.speed = init->speed;
+    L.sigma_hot = init->sigma_hot;
+    L.radius = init->radius;
+    for (int a = 0; a < 3; ++a) {
+      L.center[a] = init->center[a];
+      L.box[a] = p->box[a];
+      L.x[a] = h.x[0][a];
+      L.v[a] = h.v[0][a];
+    }
+    L.id = h.id[0];
+    L.last = h.last[0];
+    L.fails = bad + 1;
+    if (ok) launch_init_state(L, st);
+    ok = ok && ck(cudaGetLastError());
+  } else {
+    for (int a = 0; a < 3 && ok; ++a) {
+      ok = ck(cudaMemcpyAsync(h.x[0][a], src6[a], n * sizeof(double), cudaMemcpyDefault, st)) &&
+           ck(cudaMemcpyAsync(h.v[0][a], src6[3 + a], n * sizeof(double), cudaMemcpyDefault, st));
+    }
+    std::vector<uint32_t> ids(n);
+    for (size_t i = 0; i < n; ++i) ids[i] = (uint32_t)i;
+    ok = ok && ck(cudaMemcpyAsync(h.id[0], ids.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    if (last) ok = ok && ck(cudaMemcpyAsync(h.last[0], last, n * sizeof(uint32_t), cudaMemcpyDefault, st));
+    else ok = ok && ck(cudaMemsetAsync(h.last[0], 0xFF, n * sizeof(uint32_t), st));
   }
-  std::vector<uint32_t> ids(n);
-  for (size_t i = 0; i < n; ++i) ids[i] = (uint32_t)i;
-  ok = ok && ck(cudaMemcpyAsync(h.id[0], ids.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-  if (last) ok = ok && ck(cudaMemcpyAsync(h.last[0], last, n * sizeof(uint32_t), cudaMemcpyDefault, st));
-  else ok = ok && ck(cudaMemsetAsync(h.last[0], 0xFF, n * sizeof(uint32_t), st));
   ok = ok && ck(cudaMemsetAsync(h.cell_count, 0, ((size_t)zs.cell_cap + 1) * sizeof(uint32_t), st));
   ok = ok && ck(cudaMemsetAsync(h.partner, 0xFF, n * sizeof(uint32_t), st));
   ok = ok && ck(cudaMemsetAsync(h.e_slot, 0xFF, (size_t)h.edge_cap * sizeof(uint2), st));
@@ -575,17 +642,18 @@ int sim_create(const kmc_params* p, const double* x, const double* y, const doub
   if (!ck(cudaMemcpyAsync(s->d, &h, sizeof(SimDev), cudaMemcpyHostToDevice, st))) return fail(KMC_ECUDA);
   if (!ck(cudaMemcpyAsync(&s->d->d, &dy, sizeof(Dyn), cudaMemcpyHostToDevice, st))) return fail(KMC_ECUDA);
   // positions must lie in the box, velocities must be finite
-  uint32_t* bad = nullptr;
-  if ((rc = dalloc(s, &bad, 1))) return fail(rc);
-  uint32_t nbad = 0;
-  if (!ck(cudaMemsetAsync(bad, 0, sizeof(uint32_t), st))) return fail(KMC_ECUDA);
+  uint32_t nbad[2] = {0, 0};
   launch_validate(s->d, p->n, bad, st);
-  if (!ck(cudaMemcpyAsync(&nbad, bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) ||
+  if (!ck(cudaMemcpyAsync(nbad, bad, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) ||
       !ck(cudaStreamSynchronize(st)))
     return fail(KMC_ECUDA);
   dfree(s, bad);
-  if (nbad) {
-    s->err = std::to_string(nbad) + " particle(s) outside the box or with non-finite velocity" +
+  if (nbad[1]) {
+    s->err = std::to_string(nbad[1]) + " particle(s) ran out of initialisation draws";
+    return fail(KMC_ERANDOM);
+  }
+  if (nbad[0]) {
+    s->err = std::to_string(nbad[0]) + " particle(s) outside the box or with non-finite velocity" +
              std::string(h.planar ? " (or, planar, with vz != 0)" : "");
     return fail(KMC_EINVAL);
   }
@@ -594,6 +662,26 @@ int sim_create(const kmc_params* p, const double* x, const double* y, const doub
   if (!ck(cudaGetLastError()) || !ck(cudaStreamSynchronize(st))) return fail(KMC_ECUDA);
   *out = s;
   return KMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sim_create(const kmc_params* p, const double* x, const double* y, const double* z,
+               const double* vx, const double* vy, const double* vz, const uint32_t* last,
+               void* stream, kmc_sim** out) {
+  const double* src[6] = {x, y, z, vx, vy, vz};
+  return create_impl(p, src, last, nullptr, stream, out);
+}
+
+int sim_create_init(const kmc_params* p, const kmc_init* init, void* stream, kmc_sim** out) {
+  if (out) *out = nullptr;
+  if (!init) {
+    g_create_error = "init descriptor is NULL";
+    return KMC_EINVAL;
+  }
+  return create_impl(p, nullptr, nullptr, init, stream, out);
 }
 
 int sim_step(kmc_sim* s, uint32_t nsteps) {

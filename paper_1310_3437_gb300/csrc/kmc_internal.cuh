@@ -314,4 +314,23 @@ void launch_profile_convert(SimDev* d, uint32_t first, uint32_t count, uint32_t 
 void launch_add_steps(SimDev* d, uint64_t nsteps, cudaStream_t st);
 void launch_validate(SimDev* d, uint32_t n, uint32_t* bad, cudaStream_t st);
 
+// device-side initial state (kmc_init.cu): writes buffer 0 of the state in id order,
+// the ids and last = kNone; counts particles whose rejection loops ran out in *fails
+struct InitLaunch {
+  uint32_t n;
+  int32_t kind;
+  int32_t planar;
+  uint64_t n_hot;
+  uint64_t seed;
+  double sigma, speed, sigma_hot, radius;
+  double center[3];
+  double box[3];
+  double* x[3];
+  double* v[3];
+  uint32_t* id;
+  uint32_t* last;
+  uint32_t* fails;
+};
+void launch_init_state(const InitLaunch& L, cudaStream_t st);
+
 }  // namespace kmc

@@ -1,7 +1,7 @@
 """Serving loop: simulation requests admitted by HBM budget and stepped together.
 
-Requests arrive over time (each with its own parameters, initial state and step
-count).  The server admits queued requests in arrival order while their device
+Requests arrive over time (each with its own parameters, initial state -- arrays,
+or a descriptor of a state drawn on the device -- and step count).  The server admits queued requests in arrival order while their device
 footprint (``sim_bytes_required``) fits the HBM budget, adds each admitted
 simulation to one group with a step budget equal to its requested steps, and
 advances the group in short bursts: one launch per kernel per step covers every
@@ -29,6 +29,7 @@ class Request:
     steps: int
     arrival: float             # seconds after the start of the run
     arrays: object = None      # six float64 arrays, or a callable returning them
+    init: dict = None          # or a kmc_init descriptor (dict): state drawn on the device
     precision: int = KMC_GUARDED_FP32
     # filled in by the server
     admitted: float = None
@@ -61,8 +62,11 @@ class Server:
     def _admit(self, req: Request, now: float):
         params = params_from_setup(req.setup, precision=req.precision,
                                    history_cap=max(64, int(req.steps) + 8))
-        arrays = req.arrays() if callable(req.arrays) else req.arrays
-        sim = Simulation(params, arrays, stream=self.stream)
+        if req.init is not None:
+            sim = Simulation(params, init=req.init, stream=self.stream)
+        else:
+            arrays = req.arrays() if callable(req.arrays) else req.arrays
+            sim = Simulation(params, arrays, stream=self.stream)
         req.arrays = None
         if self.group is None:
             self.group = Group([sim], stream=self.stream)

@@ -12,7 +12,7 @@ import numpy as np
 from . import (KMC_FP64, KMC_GUARDED_FP32, KMC_NONE, KMC_OBS_COUNTS, KMC_OBS_EDGES,
                KMC_OBS_LAUNCHES, KMC_OBS_PARTNERS, KMC_OBS_PHASE_MS, KMC_OBS_PROFILES,
                KMC_OBS_STATE, KMC_OBS_STEP, kmc_params, sim_set_timing,
-               kmc_step_counts, sim_create, sim_destroy, sim_group_add, sim_group_budget,
+               kmc_step_counts, sim_create, sim_create_init, init_from_spec, sim_destroy, sim_group_add, sim_group_budget,
                sim_group_create, sim_group_destroy, sim_group_remove, sim_group_step,
                sim_group_steps_left, sim_group_sync, sim_observe, sim_step, sim_sync)
 
@@ -74,9 +74,19 @@ def _torch_stream():
 class Simulation:
     """One simulation: state on the device, stepped by the library's kernels."""
 
-    def __init__(self, params: kmc_params, arrays, last=None, stream=None):
+    def __init__(self, params: kmc_params, arrays=None, last=None, stream=None, init=None):
+        """From host or device arrays (x, y, z, vx, vy, vz) and optional last partners,
+        or, with ``init`` (a dict with kmc_init's fields), from a state drawn on the
+        device."""
         self.params = params
         self.n = int(params.n)
+        self.group = None
+        if init is not None:
+            if stream is None:
+                stream = _torch_stream()
+            self._init = init_from_spec(init)
+            self.handle = sim_create_init(params, self._init, stream)
+            return
         cols = [np.asarray(a, dtype=np.float64) if not hasattr(a, "data_ptr") else a for a in arrays]
         ptrs, self._keep = [], []
         for a in cols:

@@ -78,3 +78,31 @@ def test_null_arguments_are_rejected():
     assert kmc.lib().sim_step(None, 1) == kmc.KMC_EINVAL
     assert kmc.lib().sim_sync(None) == kmc.KMC_EINVAL
     assert kmc.lib().sim_destroy(None) == kmc.KMC_OK
+
+
+def test_init_descriptor_layout_and_host_checks():
+    assert C.sizeof(kmc.kmc_init) == 4 + 4 + 8 + 8 * 3 + 24 + 8
+    assert "sim_create_init" in _declared_functions()
+    s = equilibrium_setup(n=1000)
+    good_blast = {"kind": kmc.KMC_INIT_BLAST, "n_hot": 10, "sigma": 1.0, "sigma_hot": 10.0,
+                  "center": (0.5, 0.5, 0.5), "radius": 0.1}
+    bad = [
+        ({"kind": 0}, 0), ({"kind": 4}, 0), ({"kind": kmc.KMC_INIT_MAXWELL, "sigma": -1.0}, 0),
+        ({"kind": kmc.KMC_INIT_MAXWELL, "sigma": float("nan")}, 0),
+        ({"kind": kmc.KMC_INIT_EQUAL_SPEED, "speed": float("inf")}, 0),
+        (dict(good_blast, n_hot=1001), 0), (dict(good_blast, radius=0.0), 0),
+        (dict(good_blast, center=(0.5, 0.5, 0.95)), 0), (dict(good_blast, center=(0.1, 0.5, 0.5)), 0),
+        (good_blast, kmc.KMC_FLAG_PLANAR),
+    ]
+    for spec, flags in bad:
+        p = kmc.params_from_setup(s)
+        p.flags = flags
+        out = C.c_void_p()
+        rc = kmc.lib().sim_create_init(C.byref(p), C.byref(kmc.init_from_spec(spec)), None,
+                                       C.byref(out))
+        assert rc == kmc.KMC_EINVAL, spec
+        assert out.value is None
+        assert kmc.sim_last_error(None) != ""
+    out = C.c_void_p()
+    assert kmc.lib().sim_create_init(C.byref(kmc.params_from_setup(s)), None, None,
+                                     C.byref(out)) == kmc.KMC_EINVAL

@@ -72,3 +72,22 @@ def test_admission_never_exceeds_the_budget():
     done, _ = server.run(reqs)
     assert len(done) == 10
     assert peak["v"] <= budget
+
+
+def test_requests_with_device_drawn_states_equal_the_oracle_run():
+    """Requests that carry an init descriptor (state drawn on the device at
+    admission) end in the oracle's state for the same descriptor."""
+    import oracle
+    setups = ki.serving_requests(6, master_seed=13, n_lo=1 << 10, n_hi=1 << 12,
+                                 steps_lo=5, steps_hi=20)
+    reqs = [Request(rid=k, setup=s, steps=s.steps, arrival=0.001 * k, init=ki.init_spec(s))
+            for k, s in enumerate(setups)]
+    server = Server(budget_bytes=64e9, burst_steps=4)
+    done, _ = server.run(reqs)
+    for r in done:
+        st = oracle.State(oracle.init_particles(r.setup, ki.init_spec(r.setup)))
+        oracle.run(r.setup, st, 0, r.steps)
+        got, glast = r.state
+        for a, b in zip(st.a, got):
+            assert np.array_equal(a, b), f"request {r.rid}"
+        assert np.array_equal(st.last, glast)
