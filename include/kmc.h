@@ -50,6 +50,11 @@ extern "C" {
 /* ---- boundary kinds per axis (Sec. 2: reflective or periodic box) -------- */
 #define KMC_PERIODIC 0
 #define KMC_REFLECT 1  /* walls at 0 and at the box end; on x the end wall may move */
+#define KMC_ABSORB 2   /* absorptive walls (Sec. 2) at 0 and at the box end: a particle
+                          whose end-of-step position lies beyond one (x < 0 or x > L)
+                          leaves the gas: it keeps that position and its velocity, its
+                          last partner becomes KMC_ABSORBED, and it is neither searched,
+                          moved nor profiled again.  Live particles lie in [0, L]. */
 
 /* ---- precision of the pair tests --------------------------------------- */
 #define KMC_FP64 0          /* every pair test in binary64 */
@@ -78,6 +83,9 @@ extern "C" {
                               row, cell or particle search), part of the search phase */
 
 #define KMC_NONE 0xFFFFFFFFu
+#define KMC_ABSORBED 0xFFFFFFFEu /* last-partner value of a particle that has left
+                                    through an absorbing wall (KMC_OBS_STATE; may be
+                                    passed back to sim_create to resume) */
 
 /* ---- flags (kmc_params.flags) --------------------------------------------- */
 #define KMC_FLAG_NO_SPLIT 1u   /* never split fast particles into a second population
@@ -108,7 +116,7 @@ typedef struct kmc_params {
   uint32_t n;              /* particles, >= 1 */
   uint32_t flags;          /* 0 or KMC_FLAG_* bits */
   double box[3];           /* box extents L_x, L_y, L_z; particles live in [0, L) */
-  int32_t bc[3];           /* KMC_PERIODIC or KMC_REFLECT per axis */
+  int32_t bc[3];           /* KMC_PERIODIC, KMC_REFLECT or KMC_ABSORB per axis */
   int32_t max_rounds;      /* mutual-choice rounds per step, 1..4 (0 means 4) */
   double piston_x0;        /* reflecting x axis: upper wall at piston_x0 - piston_u*t */
   double piston_u;         /*   (set piston_x0 = box[0], piston_u = 0 for a fixed wall) */
@@ -147,6 +155,8 @@ typedef struct kmc_step_counts {
   uint64_t pair_tests;      /* pair tests done by the search */
   uint64_t fast_tests;      /* the part of pair_tests done for the fast particles of the
                                speed split (the rest is the slow-population search) */
+  uint32_t absorbed;        /* particles that left through absorbing walls this step */
+  uint32_t live;            /* particles in the gas after the step */
 } kmc_step_counts;
 
 typedef struct kmc_sim kmc_sim;

@@ -30,6 +30,7 @@ import numpy as np
 
 PERIODIC = 0
 REFLECT = 1
+ABSORB = 2
 
 
 @dataclass

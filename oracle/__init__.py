@@ -23,6 +23,7 @@ _lock = threading.Lock()
 _lib = None
 
 NONE = 0xFFFFFFFF
+ABSORBED = 0xFFFFFFFE  # last-partner value of a particle that left through an absorbing wall
 
 
 class Params(C.Structure):
@@ -50,7 +51,7 @@ class Init(C.Structure):
 
 class Counts(C.Structure):
     _fields_ = [("step", C.c_uint64), ("collisions", C.c_uint32), ("edges", C.c_uint32),
-                ("round_pairs", C.c_uint32 * 4)]
+                ("round_pairs", C.c_uint32 * 4), ("absorbed", C.c_uint32), ("live", C.c_uint32)]
 
 
 def build(force: bool = False) -> str:
@@ -253,7 +254,8 @@ def step(setup, state: State, step_index: int, search: int = 1, threads: int = 0
 
 def counts_dict(c: Counts):
     return {"step": int(c.step), "collisions": int(c.collisions), "edges": int(c.edges),
-            "round_pairs": [int(x) for x in c.round_pairs]}
+            "round_pairs": [int(x) for x in c.round_pairs], "absorbed": int(c.absorbed),
+            "live": int(c.live)}
 
 
 def run(setup, state: State, step0: int, nsteps: int, search: int = 1, threads: int = 0):

@@ -42,6 +42,8 @@
 #define OR_NONE 0xFFFFFFFFu
 #define OR_PERIODIC 0
 #define OR_REFLECT 1
+#define OR_ABSORB 2           /* walls at 0 and L remove the particles that cross them */
+#define OR_ABSORBED 0xFFFFFFFEu /* last-partner value of a particle that has left */
 
 typedef struct or_params {
   uint32_t n;
@@ -68,7 +70,11 @@ typedef struct or_counts {
   uint32_t collisions;
   uint32_t edges;
   uint32_t round_pairs[4];
+  uint32_t absorbed; /* particles that left through an absorbing wall in this step */
+  uint32_t live;     /* particles still in the box after the step */
 } or_counts;
+
+static int is_gone(const uint32_t* last, uint32_t i) { return last != NULL && last[i] == OR_ABSORBED; }
 
 /* ------------------------------------------------------------------------- */
 /* Philox4x32-10 (Salmon et al., SC'11, Sec. "Philox"): ten rounds of the
@@ -187,6 +193,7 @@ static void make_geo(const or_params* p, geo* g) {
 static int pair_test(const geo* g, const double* const st[6], const uint32_t* last,
                      uint32_t i, uint32_t j, double* d2_out, double* t_out) {
   if (last != NULL && last[i] == j && last[j] == i) return 0;
+  if (is_gone(last, i) || is_gone(last, j)) return 0; /* absorbed: out of the gas */
   double r[3], v[3];
   for (int k = 0; k < 3; ++k) {
     double d = st[k][j] - st[k][i];
@@ -266,10 +273,14 @@ typedef struct cgrid {
   uint32_t* perm; /* particles grouped by cell, increasing id inside a cell */
 } cgrid;
 
-static int build_cells(const or_params* p, const double* const st[6], cgrid* cg) {
+static int build_cells(const or_params* p, const double* const st[6], const uint32_t* last,
+                       cgrid* cg) {
   uint32_t n = p->n;
   double vmax2 = 0.0;
+  uint32_t first = 0; /* first particle still in the box (absorbed ones are not binned) */
+  while (first < n && is_gone(last, first)) ++first;
   for (uint32_t i = 0; i < n; ++i) {
+    if (is_gone(last, i)) continue;
     double s = (st[3][i] * st[3][i] + st[4][i] * st[4][i]) + st[5][i] * st[5][i];
     if (s > vmax2) vmax2 = s;
   }
@@ -279,8 +290,10 @@ static int build_cells(const or_params* p, const double* const st[6], cgrid* cg)
     if (p->bc[k] == OR_PERIODIC) {
       lo = 0.0; hi = p->box[k];
     } else {
-      lo = st[k][0]; hi = st[k][0];
-      for (uint32_t i = 1; i < n; ++i) {
+      lo = first < n ? st[k][first] : 0.0;
+      hi = lo;
+      for (uint32_t i = first; i < n; ++i) {
+        if (is_gone(last, i)) continue;
         if (st[k][i] < lo) lo = st[k][i];
         if (st[k][i] > hi) hi = st[k][i];
       }
@@ -300,6 +313,7 @@ static int build_cells(const or_params* p, const double* const st[6], cgrid* cg)
   if (!cg->start || !cg->perm || !cell) { free(cell); return -1; }
   for (uint32_t i = 0; i < n; ++i) {
     int64_t c[3];
+    if (is_gone(last, i)) { cell[i] = -1; continue; }
     for (int k = 0; k < 3; ++k) {
       double f = floor((st[k][i] - cg->lo[k]) / cg->w[k]);
       int64_t ci = (f < 0.0) ? 0 : (f >= cg->nc[k] ? cg->nc[k] - 1 : (int64_t)f);
@@ -312,7 +326,8 @@ static int build_cells(const or_params* p, const double* const st[6], cgrid* cg)
   int64_t* fill = (int64_t*)malloc((size_t)cg->ncell * sizeof(int64_t));
   if (!fill) { free(cell); return -1; }
   memcpy(fill, cg->start, (size_t)cg->ncell * sizeof(int64_t));
-  for (uint32_t i = 0; i < n; ++i) cg->perm[fill[cell[i]]++] = i; /* ids increase */
+  for (uint32_t i = 0; i < n; ++i)
+    if (cell[i] >= 0) cg->perm[fill[cell[i]]++] = i; /* ids increase */
   free(fill);
   free(cell);
   return 0;
@@ -341,7 +356,7 @@ int or_candidates_csr(const or_params* p, const double* const st[6], const uint3
   cgrid cg;
   memset(&cg, 0, sizeof(cg));
   if (p->search == 1 && n > 0) {
-    if (build_cells(p, st, &cg)) { free_cells(&cg); return -1; }
+    if (build_cells(p, st, last, &cg)) { free_cells(&cg); return -1; }
   }
   const int64_t chunk = 512;
   int64_t nchunks = ((int64_t)n + chunk - 1) / chunk;
@@ -366,7 +381,7 @@ int or_candidates_csr(const or_params* p, const double* const st[6], const uint3
             if (ebuf_push(b, j, d2, t)) fail = 1;
           }
         }
-      } else {
+      } else if (!is_gone(last, i)) {
         int c[3];
         cell_of(&cg, p, st, i, c);
         int lo[3], hi[3];
@@ -511,7 +526,12 @@ static void match(const or_params* p, const adjacency* a, uint32_t* partner, int
 /* Boundaries after streaming.  Periodic: one wrap into [0, L) with x == L mapped
  * to 0.  Reflecting: lower wall at 0; upper wall at L, or for the x axis at the
  * piston X = x0 - u*((step+1)*dt) (end of the step); specular reflection in the
- * frame of the wall: x -> 2X - x, v -> -v - 2u. */
+ * frame of the wall: x -> 2X - x, v -> -v - 2u.  Absorbing (Sec. 2 names
+ * absorptive walls beside reflective and periodic ones): walls at 0 and L that
+ * remove a particle whose end-of-step position lies beyond them (x < 0 or x > L,
+ * the reflecting test); it keeps that position and its velocity, its last partner
+ * becomes OR_ABSORBED, and it takes no further part (no search, no streaming, no
+ * profile).  Tested on every absorbing axis before the other axes' boundaries. */
 static void apply_bc(const or_params* p, uint64_t step, double* x, double* v, int k) {
   if (p->bc[k] == OR_PERIODIC) {
     double L = p->box[k];
@@ -591,13 +611,26 @@ int or_step(const or_params* p, double* const st[6], uint32_t* last, uint64_t st
     moved[ia] = moved[ib] = 1;
   }
   counts->collisions = coll;
+  uint32_t absorbed = 0, live = 0;
   for (uint32_t i = 0; i < n; ++i) {
-    for (int k = 0; k < 3; ++k) {
+    if (is_gone(last, i)) continue;
+    for (int k = 0; k < 3; ++k)
       if (!moved[i]) st[k][i] = st[k][i] + st[3 + k][i] * p->dt;
-      apply_bc(p, step, &st[k][i], &st[3 + k][i], k);
+    int gone = 0;
+    for (int k = 0; k < 3; ++k)
+      if (p->bc[k] == OR_ABSORB && (st[k][i] < 0.0 || st[k][i] > p->box[k])) gone = 1;
+    if (gone) {
+      last[i] = OR_ABSORBED;
+      ++absorbed;
+      continue;
     }
+    for (int k = 0; k < 3; ++k)
+      if (p->bc[k] != OR_ABSORB) apply_bc(p, step, &st[k][i], &st[3 + k][i], k);
     if (partner[i] != OR_NONE) last[i] = partner[i];
+    ++live;
   }
+  counts->absorbed = absorbed;
+  counts->live = live;
   if (partner_out) memcpy(partner_out, partner, (size_t)n * sizeof(uint32_t));
   if (profiled) *profiled = 0;
   if (prof && p->profile_every > 0 && p->profile_bins > 0 &&
@@ -607,7 +640,7 @@ int or_step(const or_params* p, double* const st[6], uint32_t* last, uint64_t st
     memset(prof, 0, (size_t)nb * 7 * sizeof(double));
     for (uint32_t i = 0; i < n; ++i) {
       double x = st[0][i];
-      if (!(x >= 0.0)) continue;
+      if (is_gone(last, i) || !(x >= 0.0)) continue;
       double f = x * scale;
       if (f >= (double)nb) continue;
       int b = (int)f;

@@ -29,6 +29,7 @@ KMC_ERANDOM = -7
 
 KMC_PERIODIC = 0
 KMC_REFLECT = 1
+KMC_ABSORB = 2
 KMC_FP64 = 0
 KMC_GUARDED_FP32 = 1
 
@@ -42,6 +43,7 @@ KMC_OBS_LAUNCHES = 7
 KMC_OBS_PHASE_MS = 8
 
 KMC_NONE = 0xFFFFFFFF
+KMC_ABSORBED = 0xFFFFFFFE
 
 KMC_FLAG_NO_SPLIT = 1
 KMC_FLAG_FORCE_SPLIT = 2
@@ -86,6 +88,7 @@ class kmc_step_counts(C.Structure):
         ("step", C.c_uint64), ("collisions", C.c_uint32), ("edges", C.c_uint32),
         ("round_pairs", C.c_uint32 * 4), ("survivors", C.c_uint32), ("cells", C.c_uint32),
         ("pair_tests", C.c_uint64), ("fast_tests", C.c_uint64),
+        ("absorbed", C.c_uint32), ("live", C.c_uint32),
     ]
 
 

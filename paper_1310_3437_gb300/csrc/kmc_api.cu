@@ -131,7 +131,7 @@ size_t bytes_for(const Sizes& z) {
   b += 2 * 6 * n * sizeof(double) + 2 * 2 * n * sizeof(uint32_t);  // state, double-buffered
   if (z.fp32) b += n * (sizeof(float4) + sizeof(float2));
   b += 3 * n * sizeof(uint32_t) + n;                                  // key, rank, src, speed class
-  b += 2 * ((size_t)z.cell_cap + 1) * sizeof(uint32_t);               // cell count / start
+  b += 2 * ((size_t)z.cell_cap + 2) * sizeof(uint32_t);               // cell count / start
   b += n * sizeof(uint32_t) + (n + 1) * sizeof(uint32_t);             // deg, list starts
   b += 4 * n * sizeof(uint32_t);                                      // best, best_e, partner, medge
   b += (n / 2 + 1) * sizeof(uint32_t);                                // pair list
@@ -149,7 +149,10 @@ int validate(const kmc_params* p, std::string& err) {
   if ((p->flags & KMC_FLAG_NO_SPLIT) && (p->flags & KMC_FLAG_FORCE_SPLIT)) { err = "conflicting split flags"; return KMC_EINVAL; }
   for (int a = 0; a < 3; ++a) {
     if (!(p->box[a] > 0.0)) { err = "box extents must be > 0"; return KMC_EINVAL; }
-    if (p->bc[a] != KMC_PERIODIC && p->bc[a] != KMC_REFLECT) { err = "bad boundary kind"; return KMC_EINVAL; }
+    if (p->bc[a] != KMC_PERIODIC && p->bc[a] != KMC_REFLECT && p->bc[a] != KMC_ABSORB) {
+      err = "bad boundary kind";
+      return KMC_EINVAL;
+    }
   }
   if (!(p->d0 > 0.0) || !(p->dt > 0.0)) { err = "d0 and dt must be > 0"; return KMC_EINVAL; }
   if (p->max_rounds < 0 || p->max_rounds > 4) { err = "max_rounds must be in 0..4"; return KMC_EINVAL; }
@@ -240,7 +243,7 @@ int build_plan(Plan& P, const std::vector<kmc_sim*>& sims, cudaStream_t st, std:
     const SimDev& h = sims[k]->h;
     table[k] = sims[k]->d;
     pt[k + 1] = pt[k] + ceil_div(h.n, kTile);
-    sc[k + 1] = sc[k] + ceil_div((uint64_t)h.cell_cap + 1, kScanTile);
+    sc[k + 1] = sc[k] + ceil_div((uint64_t)h.cell_cap + 2, kScanTile);
     pr[k + 1] = pr[k] + ceil_div(h.n, kProfTile);
     P.max_rounds = std::max(P.max_rounds, h.max_rounds);
     if (h.profile_bins > 0) P.has_profiles = true;
@@ -528,6 +531,7 @@ int create_impl(const kmc_params* p, const double* const* src6, const uint32_t* 
   h.search_kernel = p->search_kernel;
   h.split_ok = (p->flags & KMC_FLAG_NO_SPLIT) ? 0 : ((p->flags & KMC_FLAG_FORCE_SPLIT) ? 2 : 1);
   h.planar = (p->flags & KMC_FLAG_PLANAR) ? 1 : 0;
+  h.absorb = (p->bc[0] == KMC_ABSORB || p->bc[1] == KMC_ABSORB || p->bc[2] == KMC_ABSORB) ? 1 : 0;
   h.split_min_occ = p->split_min_occ;
   h.piston_x0 = p->bc[0] == KMC_REFLECT ? p->piston_x0 : p->box[0];
   h.piston_u = p->bc[0] == KMC_REFLECT ? p->piston_u : 0.0;
@@ -567,8 +571,9 @@ int create_impl(const kmc_params* p, const double* const* src6, const uint32_t* 
   if ((rc = dalloc(s, &h.rank, n))) return fail(rc);
   if ((rc = dalloc(s, &h.src, n))) return fail(rc);
   if ((rc = dalloc(s, &h.vbucket, n))) return fail(rc);
-  if ((rc = dalloc(s, &h.cell_count, (size_t)zs.cell_cap + 1))) return fail(rc);
-  if ((rc = dalloc(s, &h.cell_start, (size_t)zs.cell_cap + 1))) return fail(rc);
+  // cell keys (at most cell_cap), the absorbed particles' key, the total
+  if ((rc = dalloc(s, &h.cell_count, (size_t)zs.cell_cap + 2))) return fail(rc);
+  if ((rc = dalloc(s, &h.cell_start, (size_t)zs.cell_cap + 2))) return fail(rc);
   if ((rc = dalloc(s, &h.deg, n))) return fail(rc);
   if ((rc = dalloc(s, &h.off, n + 1))) return fail(rc);
   if ((rc = dalloc(s, &h.best, n))) return fail(rc);
@@ -629,7 +634,7 @@ int create_impl(const kmc_params* p, const double* const* src6, const uint32_t* 
     if (last) ok = ok && ck(cudaMemcpyAsync(h.last[0], last, n * sizeof(uint32_t), cudaMemcpyDefault, st));
     else ok = ok && ck(cudaMemsetAsync(h.last[0], 0xFF, n * sizeof(uint32_t), st));
   }
-  ok = ok && ck(cudaMemsetAsync(h.cell_count, 0, ((size_t)zs.cell_cap + 1) * sizeof(uint32_t), st));
+  ok = ok && ck(cudaMemsetAsync(h.cell_count, 0, ((size_t)zs.cell_cap + 2) * sizeof(uint32_t), st));
   ok = ok && ck(cudaMemsetAsync(h.partner, 0xFF, n * sizeof(uint32_t), st));
   ok = ok && ck(cudaMemsetAsync(h.e_slot, 0xFF, (size_t)h.edge_cap * sizeof(uint2), st));
   if (zs.bins) ok = ok && ck(cudaMemsetAsync(h.prof_acc, 0, (size_t)zs.prof_cap * zs.bins * kProfQ * sizeof(long long), st));

@@ -86,6 +86,7 @@ struct Dyn {
                         // candidates; r + 1 is filled by round r)
   unsigned long long pair_tests;
   unsigned long long fast_tests;  // the part of pair_tests done by the fast-particle search
+  uint32_t n_absorbed;  // particles that left through absorbing walls this step
   uint32_t last_raw;    // n_raw of the last completed step (its pair buffer is kept)
   uint32_t have_counts; // split_cnt holds counts of the current state
   float split_thr[kSplitTrials];     // trial thresholds on |v|^2 (set with the grid)
@@ -102,6 +103,8 @@ struct SimDev {
   int32_t max_rounds, precision, profile_bins, profile_every, K, search_kernel;
   int32_t split_ok;     // 0: never split, 1: split when cheaper, 2: split whenever possible
   int32_t planar;       // 1: x-y dynamics (vz = 0), scatter directions in the plane
+  int32_t absorb;       // 1: some axis has absorbing walls (the sort keeps the particles
+                        // that left in one extra key after every cell: see graveyard_key)
   double split_min_occ; // smallest mean occupancy of the slow grid under a split
   double box[3];
   double piston_x0, piston_u, d0, dt, d0sq;
@@ -148,7 +151,7 @@ struct Batch {
   SimDev* const* sims;     // device table
   int nsims;
   const uint32_t* ptile;   // prefix of ceil(n / kTile) per simulation
-  const uint32_t* stile_c; // prefix of ceil((cell_cap + 1) / kScanTile)
+  const uint32_t* stile_c; // prefix of ceil((cell_cap + 2) / kScanTile)
   const uint32_t* prtile;  // prefix of ceil(n / kProfTile)
   uint32_t* tile_sums;      // scratch for the segmented scans
 };
@@ -164,6 +167,17 @@ __device__ __forceinline__ int find_sim(const uint32_t* prefix, int nsims, uint3
 
 __device__ __forceinline__ bool sim_active(const SimDev& s) {
   return s.d.status == 0 && s.d.steps_left > 0;
+}
+
+// Absorbing walls: the particles that have left sort into one extra key after every
+// cell key (and after the fast population's keys), so that they occupy the end of the
+// sorted order, [live, n), and no cell holds them.
+__device__ __forceinline__ uint32_t graveyard_key(const Grid& g) {
+  return g.nkeys * (g.split ? 2u : 1u);
+}
+// particles in the gas at the start of the step (after this step's sort)
+__device__ __forceinline__ uint32_t live_count(const SimDev& s) {
+  return s.absorb ? __ldg(s.cell_start + graveyard_key(s.d.grid)) : s.n;
 }
 
 // ---- exact binary64 arithmetic (never contracted into FMA) --------------- //

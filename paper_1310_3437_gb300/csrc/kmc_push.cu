@@ -73,25 +73,14 @@ __device__ __noinline__ XV reflect_walls(double x, double v, double X, double u)
   return {x, v};
 }
 
-__global__ void __launch_bounds__(kTile) k_push(Batch B) {
-  __shared__ double sX;                       // piston position at the end of the step
-  __shared__ uint32_t scnt[kSplitTrials];     // particles above each trial threshold
-  int k = find_sim(B.ptile, B.nsims, blockIdx.x);
-  SimDev& s = *B.sims[k];
-  if (!sim_active(s)) return;
-  const int cur = s.d.parity ^ 1;
-  const uint64_t step = s.d.step;
-  const double dt = s.dt;
-  if (threadIdx.x == 0)
-    sX = s.bc[0] == KMC_PERIODIC ? 0.0
-                                 : dsub(s.piston_x0, dmul(s.piston_u, dmul((double)(step + 1), dt)));
-  if (threadIdx.x < kSplitTrials) scnt[threadIdx.x] = 0;
-  __syncthreads();
-  uint32_t p = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
-  float vm = 0.0f;
-  if (p < s.n) {
-    uint32_t q = s.partner[p];
-    double vv[3];
+// Free streaming and walls of one particle (sorted position p); returns the binary32
+// upper bound of its |v|^2 (0 if it left).  ABS: the simulation has absorbing walls.
+template <bool ABS>
+__device__ __forceinline__ float push_particle(SimDev& s, int cur, uint32_t p, double dt, double sX,
+                                               bool& gone) {
+  const uint32_t q = s.partner[p];
+  double vv[3];
+  if (!ABS) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       double x = s.x[cur][a][p];
@@ -114,13 +103,80 @@ __global__ void __launch_bounds__(kTile) k_push(Batch B) {
       vv[a] = v;
     }
     if (q != kNone) s.last[cur][p] = s.id[cur][q];
-    vm = vmag2_up(vv[0], vv[1], vv[2]);
+    return vmag2_up(vv[0], vv[1], vv[2]);
+  }
+  double xs[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    xs[a] = s.x[cur][a][p];
+    vv[a] = s.v[cur][a][p];
+    if (q == kNone) xs[a] = dadd(xs[a], dmul(vv[a], dt));
+  }
+  // beyond an absorbing wall at the end of the step: the particle leaves the gas with
+  // this position and velocity (tested before any other axis' boundary)
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (s.bc[a] == KMC_ABSORB && (lt_zero(xs[a]) || xs[a] > s.box[a])) gone = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double x = xs[a];
+    double v = vv[a];
+    if (gone || s.bc[a] == KMC_ABSORB) {
+      // no wall acts (inside on this axis, or the particle has left)
+    } else if (s.bc[a] == KMC_PERIODIC) {
+      const double L = s.box[a];
+      if (dbits(x) >= dbits(L) || lt_zero(x)) x = wrap_periodic(x, L);
+    } else {
+      const double X = a == 0 ? sX : s.box[a];
+      const double u = a == 0 ? s.piston_u : 0.0;
+      if (lt_zero(x) || (dbits(X) > 0 ? dbits(x) > dbits(X) : x > X)) {
+        const XV r = reflect_walls(x, v, X, u);
+        x = r.x;
+        v = r.v;
+        s.v[cur][a][p] = v;
+      }
+    }
+    s.x[cur][a][p] = x;
+    vv[a] = v;
+  }
+  if (gone) s.last[cur][p] = KMC_ABSORBED;
+  else if (q != kNone) s.last[cur][p] = s.id[cur][q];
+  return gone ? 0.0f : vmag2_up(vv[0], vv[1], vv[2]);
+}
+
+__global__ void __launch_bounds__(kTile) k_push(Batch B) {
+  __shared__ double sX;                       // piston position at the end of the step
+  __shared__ uint32_t scnt[kSplitTrials];     // particles above each trial threshold
+  __shared__ uint32_t sgone;                  // particles absorbed in this block
+  int k = find_sim(B.ptile, B.nsims, blockIdx.x);
+  SimDev& s = *B.sims[k];
+  if (!sim_active(s)) return;
+  const int cur = s.d.parity ^ 1;
+  const uint64_t step = s.d.step;
+  const double dt = s.dt;
+  if (threadIdx.x == 0)
+    sX = s.bc[0] == KMC_PERIODIC ? 0.0
+                                 : dsub(s.piston_x0, dmul(s.piston_u, dmul((double)(step + 1), dt)));
+  if (threadIdx.x < kSplitTrials) scnt[threadIdx.x] = 0;
+  if (threadIdx.x == 0) sgone = 0;
+  __syncthreads();
+  uint32_t p = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
+  float vm = 0.0f;
+  // absorbing walls: particles that left earlier sit at the end of the order and stay
+  // as they are (live_count is this step's sort's count of the others)
+  const uint32_t n_in = live_count(s);
+  bool gone = false;
+  if (p < n_in) vm = s.absorb ? push_particle<true>(s, cur, p, dt, sX, gone)
+                              : push_particle<false>(s, cur, p, dt, sX, gone);
+  if (s.absorb) {
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, gone);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&sgone, (uint32_t)__popc(m));
   }
   if (s.split_ok) {
     // particles above each trial split threshold: warp ballots, shared counters, one
     // global atomic per block and trial; each particle keeps how many thresholds it
     // exceeds, which is all the next step's count needs to classify it
-    const bool valid = p < s.n;
+    const bool valid = p < n_in && !gone;
     uint32_t above = 0;
 #pragma unroll
     for (int t = 1; t < kSplitTrials; ++t) {
@@ -134,6 +190,7 @@ __global__ void __launch_bounds__(kTile) k_push(Batch B) {
   block_max_to(&s.d.vmax2_acc, vm);  // its block barrier also orders the shared counters
   if (s.split_ok && threadIdx.x > 0 && threadIdx.x < kSplitTrials && scnt[threadIdx.x])
     atomicAdd(&s.d.split_cnt[threadIdx.x], scnt[threadIdx.x]);
+  if (s.absorb && threadIdx.x == 0 && sgone) atomicAdd(&s.d.n_absorbed, sgone);
 }
 
 // ---- fixed-point digits for the profile sums ------------------------------- //
@@ -170,6 +227,7 @@ __global__ void __launch_bounds__(kTile) k_profile(Batch B) {
   for (uint32_t i = threadIdx.x; i < kProfTile; i += blockDim.x) {
     uint32_t p = base + i;
     if (p >= s.n) break;
+    if (s.absorb && s.last[cur][p] == KMC_ABSORBED) continue;  // out of the gas
     double x = s.x[cur][0][p];
     if (!(x >= 0.0)) continue;
     double f = dmul(x, scale);
@@ -203,6 +261,7 @@ __device__ void reset_step_counters(SimDev& s) {
   for (int r = 0; r < 5; ++r) s.d.wl_len[r] = 0;
   s.d.pair_tests = 0;
   s.d.fast_tests = 0;
+  s.d.n_absorbed = 0;
   s.d.vmax2_acc = 0;
 }
 
@@ -232,6 +291,8 @@ __global__ void k_finalize(Batch B) {
       rec.cells = s.d.grid.nkeys;
       rec.pair_tests = s.d.pair_tests;
       rec.fast_tests = s.d.fast_tests;
+      rec.absorbed = s.d.n_absorbed;
+      rec.live = live_count(s) - s.d.n_absorbed;  // this step's grid, before the next one
       s.hist[s.d.hist_count % s.hist_cap] = rec;
       s.d.hist_count += 1;
       if (s.d.prof_due) {
@@ -269,7 +330,8 @@ __global__ void __launch_bounds__(kTile) k_vmax(Batch B) {
   float vm = 0.0f;
   if (p < s.n) {
     int par = s.d.parity;
-    vm = vmag2_up(s.v[par][0][p], s.v[par][1][p], s.v[par][2][p]);
+    if (!(s.absorb && s.last[par][p] == KMC_ABSORBED))
+      vm = vmag2_up(s.v[par][0][p], s.v[par][1][p], s.v[par][2][p]);
   }
   block_max_to(&s.d.vmax2_acc, vm);
 }
@@ -393,11 +455,13 @@ __global__ void k_validate(SimDev* d, uint32_t* bad) {
   uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= s.n) return;
   bool out = false;
+  // a particle that already left through an absorbing wall may lie anywhere (finite)
+  const bool left = s.absorb && s.last[s.d.parity][p] == KMC_ABSORBED;
   for (int a = 0; a < 3; ++a) {
     double q = s.x[s.d.parity][a][p];
     double hi = (a == 0 && s.bc[0] == KMC_REFLECT) ? s.piston_x0 : s.box[a];
     bool periodic = s.bc[a] == KMC_PERIODIC;
-    if (!(q >= 0.0) || (periodic ? !(q < hi) : !(q <= hi))) out = true;
+    if (left ? !(fabs(q) < 1e300) : (!(q >= 0.0) || (periodic ? !(q < hi) : !(q <= hi)))) out = true;
     if (!(fabs(s.v[s.d.parity][a][p]) < 1e15)) out = true;
   }
   if (s.planar && s.v[s.d.parity][2][p] != 0.0) out = true;

@@ -101,8 +101,9 @@ __global__ void __launch_bounds__(kTile) k_search(Batch B) {
     unsigned long long tests = 0;
 
     uint32_t p = (tile - B.ptile[k]) * kTile + threadIdx.x;
-    // with the speed split only the slow population (keys below nkeys) is searched here
-    const uint32_t nslow = g.split ? __ldg(cs + g.nkeys) : n;
+    // with the speed split only the slow population (keys below nkeys) is searched here;
+    // particles that left through absorbing walls sit after every cell key
+    const uint32_t nslow = (g.split || s.absorb) ? __ldg(cs + g.nkeys) : n;
     if (p < nslow) {
       // the particle's cell, recomputed as the sort computed it
       const int cx = cell_coord(g, 0, s.x[cur][0][p]), cy = cell_coord(g, 1, s.x[cur][1][p]),
@@ -843,7 +844,7 @@ __global__ void __launch_bounds__(kTile, 4) k_search_rows32(Batch B) {
       kcur = k;
     }
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const uint32_t nslow = g.split ? __ldg(s.cell_start + g.nkeys) : s.n;
+    const uint32_t nslow = (g.split || s.absorb) ? __ldg(s.cell_start + g.nkeys) : s.n;
     const uint32_t p = (tile - B.ptile[k]) * kTile + threadIdx.x;
     if (p - lane >= nslow) continue;  // the whole warp is past the slow population
     uint2* pc = reinterpret_cast<uint2*>(rows_smem) + (size_t)warp * NP * 32;
@@ -1150,7 +1151,7 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4) k_search_fast(Batch B) {
     const Grid& g = s.d.grid;
     const uint32_t* __restrict__ cs = s.cell_start;
     const uint32_t nk = g.nkeys;
-    const uint32_t n = s.n;
+    const uint32_t n = s.absorb ? __ldg(cs + 2 * nk) : s.n;  // end of the fast keys
     const uint32_t nslow = __ldg(cs + nk);
     const uint32_t nfast = n - nslow;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;

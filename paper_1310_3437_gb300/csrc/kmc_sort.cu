@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kTile / 2) k_count(Batch B) {
   const int par = s.d.parity;
   double xs[2][3];
   uint32_t vb[2];
-  bool valid[2];
+  bool valid[2], gone[2];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     valid[h] = pp[h] < s.n;
@@ -62,12 +62,15 @@ __global__ void __launch_bounds__(kTile / 2) k_count(Batch B) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) xs[h][a] = s.x[par][a][q];
     vb[h] = g.split ? (uint32_t)s.vbucket[q] : 0u;
+    gone[h] = s.absorb && s.last[par][q] == KMC_ABSORBED;
   }
   const uint32_t lane = threadIdx.x & 31u;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     uint32_t key = 0;
-    if (valid[h]) {
+    if (valid[h] && gone[h]) {
+      key = graveyard_key(g);  // left through an absorbing wall: after every cell
+    } else if (valid[h]) {
       const int cx = cell_coord(g, 0, xs[h][0]);
       const int cy = cell_coord(g, 1, xs[h][1]);
       const int cz = cell_coord(g, 2, xs[h][2]);
@@ -98,7 +101,7 @@ struct ScanView {
 __device__ __forceinline__ ScanView scan_view(SimDev& s) {
   ScanView v;
   v.in = s.cell_count; v.out = s.cell_start; v.clear = s.cell_count;
-  v.len = s.d.grid.nkeys * (s.d.grid.split ? 2u : 1u);
+  v.len = graveyard_key(s.d.grid) + (s.absorb ? 1u : 0u);
   return v;
 }
 

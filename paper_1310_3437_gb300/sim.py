@@ -155,7 +155,8 @@ class Simulation:
         return [{"step": int(r.step), "collisions": int(r.collisions), "edges": int(r.edges),
                  "round_pairs": [int(x) for x in r.round_pairs], "survivors": int(r.survivors),
                  "cells": int(r.cells), "pair_tests": int(r.pair_tests),
-                 "fast_tests": int(r.fast_tests)} for r in arr[:cnt]]
+                 "fast_tests": int(r.fast_tests), "absorbed": int(r.absorbed),
+                 "live": int(r.live)} for r in arr[:cnt]]
 
     def profiles(self):
         bins = int(self.params.profile_bins)

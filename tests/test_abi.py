@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layouts_match_header():
     # sizes follow from the field lists in include/kmc.h
     assert C.sizeof(kmc.kmc_params) == 4 + 4 + 24 + 12 + 4 + 8 * 4 + 8 * 2 + 4 * 4 + 8 * 2 + 4 * 4 + 8
-    assert C.sizeof(kmc.kmc_step_counts) == 8 + 4 + 4 + 16 + 4 + 4 + 8 + 8
+    assert C.sizeof(kmc.kmc_step_counts) == 8 + 4 + 4 + 16 + 4 + 4 + 8 + 8 + 4 + 4
 
 
 def test_bytes_required_scales_with_n():

@@ -49,6 +49,7 @@ def assert_same_counts(gpu_counts, or_counts):
         assert g["step"] == o["step"]
         assert (g["collisions"], g["edges"], g["round_pairs"]) == \
                (o["collisions"], o["edges"], o["round_pairs"]), (g, o)
+        assert (g["absorbed"], g["live"]) == (o["absorbed"], o["live"]), (g, o)
 
 
 def run_both(setup, steps, precision=FP64, arrays=None, **kw):
@@ -369,3 +370,70 @@ def test_planar_rejects_out_of_plane_velocity():
     with pytest.raises(kmc.KmcError) as e:
         gpu_sim(s, arrays)
     assert e.value.code == kmc.KMC_EINVAL and "vz" in str(e.value)
+
+
+def _absorbing_setup(n=6000, seed=71, bc=(ki.ABSORB, ki.REFLECT, ki.PERIODIC), dt=0.01):
+    s = ki.equilibrium_setup(n=n, seed=seed, d0=0.02, dt=dt)
+    return s.with_(bc=bc, piston_x0=1.0, piston_u=0.0)
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
+def test_absorbing_walls_bit_exact(precision, kernel):
+    """Absorptive walls (Sec. 2): the particles that leave are the oracle's, step by
+    step, and keep the oracle's exit positions and velocities."""
+    s = _absorbing_setup()
+    sim, st, oc, _ = run_both(s, 60, precision, search_kernel=kernel)
+    assert_same_counts(sim.counts(), oc)
+    assert_same_state(sim, st)
+    assert oc[-1]["live"] < 0.8 * s.n
+    assert int((st.last == oracle.ABSORBED).sum()) == s.n - oc[-1]["live"]
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_absorbing_pair_lists_forced_split_and_resume(precision):
+    s = _absorbing_setup(n=8000, seed=72, bc=(ki.ABSORB, ki.ABSORB, ki.ABSORB))
+    arrays = ki.initial_state(s)
+    st = oracle.State(arrays)
+    sim = gpu_sim(s, arrays, precision=precision, flags=kmc.KMC_FLAG_FORCE_SPLIT)
+    for step in range(10):
+        pi, pj, _, _ = oracle.candidate_pairs(s, st)
+        counts, partner, _ = oracle.step(s, st, step)
+        sim.step(1).sync()
+        assert np.array_equal(sim.edges(), np.stack([pi, pj], axis=1)), f"step {step}"
+        assert np.array_equal(sim.partners(), partner), f"step {step}"
+    assert_same_state(sim, st)
+    # resume from the observed state (absorbed particles flagged in last)
+    mid, last = sim.state()
+    assert np.any(last == kmc.KMC_ABSORBED)
+    rest = gpu_sim(s, mid, precision, last=last, step0=10, flags=kmc.KMC_FLAG_FORCE_SPLIT)
+    rest.step(15).sync()
+    oc, _ = oracle.run(s, st, 10, 15)
+    assert_same_counts(rest.counts(), oc)
+    assert_same_state(rest, st)
+
+
+def test_absorbing_box_empties_and_groups_mix():
+    """Every particle leaves (live reaches 0, the steps after that are empty), and a
+    group mixing absorbing and periodic runs equals each run alone."""
+    s = _absorbing_setup(n=3000, seed=73, bc=(ki.ABSORB,) * 3, dt=0.05)
+    sim, st, oc, _ = run_both(s, 130, FP32)  # the last particle leaves at step 106
+    assert_same_counts(sim.counts(), oc)
+    assert_same_state(sim, st)
+    assert oc[-1]["live"] == 0 and np.all(st.last == oracle.ABSORBED)
+    setups = [_absorbing_setup(n=2000 + 500 * k, seed=80 + k,
+                               bc=(ki.ABSORB, ki.PERIODIC, ki.PERIODIC) if k % 2 else (ki.PERIODIC,) * 3)
+              for k in range(4)]
+    arrays = [ki.initial_state(q) for q in setups]
+    sims = [gpu_sim(q, a, FP32) for q, a in zip(setups, arrays)]
+    g = kmc.Group(sims)
+    for x in sims:
+        g.budget(x, 30)
+    g.step(30)
+    g.sync()
+    for q, a, x in zip(setups, arrays, sims):
+        st = oracle.State(a)
+        oc, _ = oracle.run(q, st, 0, 30)
+        assert_same_counts(x.counts(), oc)
+        assert_same_state(x, st)
+    g.close()
