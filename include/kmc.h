@@ -172,6 +172,22 @@ int sim_create(const kmc_params* p, const double* x, const double* y, const doub
                const double* vx, const double* vy, const double* vz, const uint32_t* last,
                void* stream, kmc_sim** out);
 
+/* Create a mixture (Sec. 2: every particle carries a mass and an effective radius).
+ * As sim_create, plus: species, n uint8 indices by particle id (host or device);
+ * mass and radius, nspecies (1..256) binary64 values each in HOST memory.  A pair
+ * (i, j) is in contact at radius[s_i] + radius[s_j]; p->d0 is the search reach and
+ * must be at least 2 max(radius).  A collision keeps the centre-of-mass velocity
+ * V = (m_a v_a + m_b v_b)/M and turns the relative velocity isotropically:
+ * v_a' = V + (m_b/M) |g| n, v_b' = V - (m_a/M) |g| n (M = m_a + m_b, a the smaller
+ * id; for equal power-of-two masses this is the single-species update bit for bit).
+ * Profiles stay unweighted (counts and velocity sums over all species).
+ * Errors: as sim_create, and KMC_EINVAL for a bad table, d0 < 2 max(radius) or a
+ * species index >= nspecies. */
+int sim_create_mixture(const kmc_params* p, const double* x, const double* y, const double* z,
+                       const double* vx, const double* vy, const double* vz, const uint32_t* last,
+                       const uint8_t* species, uint32_t nspecies, const double* mass,
+                       const double* radius, void* stream, kmc_sim** out);
+
 /* ---- device-side initial states (sim_create_init) ------------------------ */
 #define KMC_INIT_MAXWELL 1     /* positions uniform in the box, velocity components
                                   i.i.d. N(0, sigma^2) (the equilibrium box and the

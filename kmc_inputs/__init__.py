@@ -52,6 +52,9 @@ class Setup:
     steps: int = 1
     name: str = ""
     planar: bool = False  # two-dimensional dynamics in the x-y plane
+    species: object = None  # mixture: uint8 species index per particle id
+    masses: tuple = ()      # mixture: mass of each species
+    radii: tuple = ()       # mixture: effective radius of each species (contact r_i + r_j)
     extra: dict = field(default_factory=dict)
 
     def with_(self, **kw) -> "Setup":
@@ -190,8 +193,37 @@ def init_spec(setup: Setup) -> dict:
     return {"kind": 1, "sigma": 1.0}
 
 
+def mixture_setup(n: int = 6000, seed: int = 5, L: float = 1.0, frac_b: float = 0.3,
+                  mass_b: float = 4.0, d_a: float = 0.016, d_b: float = 0.032,
+                  kT_a: float = 1.0, kT_b: float = 1.0, dt: float = 0.004,
+                  steps: int = 100) -> Setup:
+    """Binary hard-sphere mixture in a periodic cube (Sec. 2: each particle carries a
+    mass and an effective radius): species A (m = 1, diameter d_a) and B (m = mass_b,
+    diameter d_b), the first round(frac_b n) ids are B; velocity components of each
+    species N(0, kT/m).  d0 (the search reach) is the largest contact distance d_b."""
+    n_b = int(round(frac_b * n))
+    sp = np.zeros(n, dtype=np.uint8)
+    sp[:n_b] = 1
+    return Setup(n=n, box=(L, L, L), bc=(PERIODIC,) * 3, d0=max(d_a, d_b), dt=dt, seed=seed,
+                 steps=steps, name=f"mixture_n{n}", species=sp, masses=(1.0, mass_b),
+                 radii=(0.5 * d_a, 0.5 * d_b), extra={"kT": (kT_a, kT_b)})
+
+
+def mixture_state(setup: Setup):
+    rng = np.random.default_rng(setup.seed)
+    n = setup.n
+    pos = [_uniform(rng, n, float(setup.box[k])) for k in range(3)]
+    kT = np.asarray(setup.extra.get("kT", (1.0,) * len(setup.masses)), dtype=np.float64)
+    m = np.asarray(setup.masses, dtype=np.float64)
+    sig = np.sqrt(kT / m)[setup.species]
+    vel = [rng.standard_normal(n) * sig for _ in range(3)]
+    return pos + vel
+
+
 def initial_state(setup: Setup):
     """Six float64 arrays (x, y, z, vx, vy, vz) in particle-id order."""
+    if setup.name.startswith("mixture"):
+        return mixture_state(setup)
     if setup.name.startswith("equal_speed"):
         return equal_speed_state(setup.n, setup.seed, setup.box, setup.extra.get("speed", 1.0),
                                  setup.planar)

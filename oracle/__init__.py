@@ -38,7 +38,9 @@ class Params(C.Structure):
         ("profile_bins", C.c_int32), ("profile_every", C.c_int32),
         ("profile_range", C.c_double),
         ("search", C.c_int32), ("threads", C.c_int32),
-        ("planar", C.c_int32), ("pad1", C.c_int32),
+        ("planar", C.c_int32), ("nspecies", C.c_int32),
+        ("species", C.POINTER(C.c_uint8)), ("mass", C.POINTER(C.c_double)),
+        ("radius", C.POINTER(C.c_double)),
     ]
 
 
@@ -132,6 +134,16 @@ def params_from(setup, search: int = 1, threads: int = 0) -> Params:
     p.search = int(search)
     p.threads = int(threads)
     p.planar = 1 if getattr(setup, "planar", False) else 0
+    sp = getattr(setup, "species", None)
+    if sp is not None:
+        # mixture: keep the arrays alive with the struct
+        p._keep = (np.ascontiguousarray(sp, dtype=np.uint8),
+                   np.ascontiguousarray(setup.masses, dtype=np.float64),
+                   np.ascontiguousarray(setup.radii, dtype=np.float64))
+        p.nspecies = len(p._keep[1])
+        p.species = p._keep[0].ctypes.data_as(C.POINTER(C.c_uint8))
+        p.mass = _dp(p._keep[1])
+        p.radius = _dp(p._keep[2])
     return p
 
 

@@ -60,7 +60,13 @@ typedef struct or_params {
   int32_t threads; /* 0: library default */
   int32_t planar;  /* 1: two-dimensional dynamics in the x-y plane (z and vz constant,
                       vz = 0); scatter directions isotropic in the plane */
-  int32_t pad1;
+  int32_t nspecies; /* 0: one species (m = 1, contact distance d0); else a mixture */
+  /* Mixture (Sec. 2: every particle carries its mass and effective radius): species[i]
+   * indexes mass[] and radius[]; a pair (i, j) is in contact at r_i + r_j; d0 must be
+   * at least the largest contact distance (it sets the search reach). */
+  const uint8_t* species;
+  const double* mass;
+  const double* radius;
 } or_params;
 
 /* Per-step record: collisions (matched pairs), candidate pairs, and the pairs
@@ -177,6 +183,8 @@ typedef struct geo {
   double L[3], halfL[3];
   int periodic[3];
   double dt, d0sq;
+  const uint8_t* species; /* mixture: contact distance radius[s_i] + radius[s_j] */
+  const double* radius;
 } geo;
 
 static void make_geo(const or_params* p, geo* g) {
@@ -187,6 +195,8 @@ static void make_geo(const or_params* p, geo* g) {
   }
   g->dt = p->dt;
   g->d0sq = p->d0 * p->d0;
+  g->species = p->nspecies > 0 ? p->species : NULL;
+  g->radius = p->radius;
 }
 
 /* Returns 1 and fills (d2, t) if (i, j) is a candidate pair. */
@@ -208,7 +218,12 @@ static int pair_test(const geo* g, const double* const st[6], const uint32_t* la
   double wy = r[2] * v[0] - r[0] * v[2];
   double wz = r[0] * v[1] - r[1] * v[0];
   double d2 = ((wx * wx + wy * wy) + wz * wz) / vv;
-  if (t >= 0.0 && t < g->dt && d2 < g->d0sq) {
+  double c2 = g->d0sq;
+  if (g->species) {
+    double c = g->radius[g->species[i]] + g->radius[g->species[j]];
+    c2 = c * c;
+  }
+  if (t >= 0.0 && t < g->dt && d2 < c2) {
     *d2_out = d2;
     *t_out = t;
     return 1;
@@ -590,17 +605,28 @@ int or_step(const or_params* p, double* const st[6], uint32_t* last, uint64_t st
       continue;
     }
     double g[3], V[3];
+    /* centre-of-mass velocity and the shares of the relative speed: equal masses
+     * V = (v_a + v_b)/2, both shares G/2; a mixture V = (m_a v_a + m_b v_b)/M,
+     * v_a' = V + (m_b/M) G n, v_b' = V - (m_a/M) G n (M = m_a + m_b), which is the
+     * equal-mass update, bit for bit, when m_a = m_b */
+    double ma = 1.0, mb = 1.0;
+    if (p->nspecies > 0) {
+      ma = p->mass[p->species[ia]];
+      mb = p->mass[p->species[ib]];
+    }
+    double M = ma + mb;
     for (int k = 0; k < 3; ++k) {
       g[k] = st[3 + k][ia] - st[3 + k][ib];
-      V[k] = (st[3 + k][ia] + st[3 + k][ib]) * 0.5;
+      if (p->nspecies > 0) V[k] = (ma * st[3 + k][ia] + mb * st[3 + k][ib]) / M;
+      else V[k] = (st[3 + k][ia] + st[3 + k][ib]) * 0.5;
     }
     double G = sqrt((g[0] * g[0] + g[1] * g[1]) + g[2] * g[2]);
-    double hG = 0.5 * G;
+    double hGa = (p->nspecies > 0 ? mb / M : 0.5) * G;
+    double hGb = (p->nspecies > 0 ? ma / M : 0.5) * G;
     double rest = p->dt - t;
     for (int k = 0; k < 3; ++k) {
-      double pk = hG * nv[k];
-      double va = V[k] + pk;
-      double vb = V[k] - pk;
+      double va = V[k] + hGa * nv[k];
+      double vb = V[k] - hGb * nv[k];
       double xa = st[k][ia], xb = st[k][ib];
       double oa = st[3 + k][ia], ob = st[3 + k][ib];
       st[k][ia] = (xa + oa * t) + va * rest;

@@ -114,6 +114,9 @@ def lib():
             L.sim_create.argtypes = [C.POINTER(kmc_params), _P, _P, _P, _P, _P, _P, _P, _P,
                                      C.POINTER(_P)]
             L.sim_create.restype = C.c_int
+            L.sim_create_mixture.argtypes = [C.POINTER(kmc_params), _P, _P, _P, _P, _P, _P, _P,
+                                             _P, C.c_uint32, _P, _P, _P, C.POINTER(_P)]
+            L.sim_create_mixture.restype = C.c_int
             L.sim_create_init.argtypes = [C.POINTER(kmc_params), C.POINTER(kmc_init), _P,
                                           C.POINTER(_P)]
             L.sim_create_init.restype = C.c_int
@@ -166,6 +169,15 @@ def _check(rc, handle=None):
 def sim_create(params: kmc_params, x, y, z, vx, vy, vz, last=None, stream=None):
     out = _P()
     rc = lib().sim_create(C.byref(params), x, y, z, vx, vy, vz, last, stream, C.byref(out))
+    _check(rc, None)
+    return out.value
+
+
+def sim_create_mixture(params: kmc_params, x, y, z, vx, vy, vz, last, species, nspecies: int,
+                       mass, radius, stream=None):
+    out = _P()
+    rc = lib().sim_create_mixture(C.byref(params), x, y, z, vx, vy, vz, last, species,
+                                  int(nspecies), mass, radius, stream, C.byref(out))
     _check(rc, None)
     return out.value
 

@@ -131,6 +131,7 @@ size_t bytes_for(const Sizes& z) {
   b += 2 * 6 * n * sizeof(double) + 2 * 2 * n * sizeof(uint32_t);  // state, double-buffered
   if (z.fp32) b += n * (sizeof(float4) + sizeof(float2));
   b += 3 * n * sizeof(uint32_t) + n;                                  // key, rank, src, speed class
+  b += n + 4096;                                                      // mixture species (if any)
   b += 2 * ((size_t)z.cell_cap + 2) * sizeof(uint32_t);               // cell count / start
   b += n * sizeof(uint32_t) + (n + 1) * sizeof(uint32_t);             // deg, list starts
   b += 4 * n * sizeof(uint32_t);                                      // best, best_e, partner, medge
@@ -494,14 +495,36 @@ int validate_init(const kmc_params* p, const kmc_init* in, std::string& err) {
   return KMC_OK;
 }
 
-// shared body of sim_create (src: six state arrays) and sim_create_init (init)
+struct Mixture {
+  const uint8_t* species;
+  uint32_t nspecies;
+  const double* mass;
+  const double* radius;
+};
+
+int validate_mixture(const kmc_params* p, const Mixture* m, std::string& err) {
+  if (!m->species || !m->mass || !m->radius) { err = "NULL mixture array"; return KMC_EINVAL; }
+  if (m->nspecies < 1 || m->nspecies > 256) { err = "nspecies must be in 1..256"; return KMC_EINVAL; }
+  double rmax = 0.0;
+  for (uint32_t k = 0; k < m->nspecies; ++k) {
+    if (!(m->mass[k] > 0.0) || !std::isfinite(m->mass[k])) { err = "masses must be finite and > 0"; return KMC_EINVAL; }
+    if (!(m->radius[k] > 0.0) || !std::isfinite(m->radius[k])) { err = "radii must be finite and > 0"; return KMC_EINVAL; }
+    rmax = std::max(rmax, m->radius[k]);
+  }
+  if (!(rmax + rmax <= p->d0)) { err = "d0 must be at least the largest contact distance 2 max(radius)"; return KMC_EINVAL; }
+  return KMC_OK;
+}
+
+// shared body of sim_create (src: six state arrays), sim_create_init (init) and
+// sim_create_mixture (mix)
 int create_impl(const kmc_params* p, const double* const* src6, const uint32_t* last,
-                const kmc_init* init, void* stream, kmc_sim** out) {
+                const kmc_init* init, const Mixture* mix, void* stream, kmc_sim** out) {
   if (out) *out = nullptr;
   g_create_error.clear();
   int rc = validate(p, g_create_error);
   if (rc) return rc;
   if (init && (rc = validate_init(p, init, g_create_error))) return rc;
+  if (mix && (rc = validate_mixture(p, mix, g_create_error))) return rc;
   if (!out || (!init && (!src6[0] || !src6[1] || !src6[2] || !src6[3] || !src6[4] || !src6[5]))) {
     g_create_error = "NULL array or output pointer";
     return KMC_EINVAL;
@@ -532,6 +555,8 @@ int create_impl(const kmc_params* p, const double* const* src6, const uint32_t* 
   h.split_ok = (p->flags & KMC_FLAG_NO_SPLIT) ? 0 : ((p->flags & KMC_FLAG_FORCE_SPLIT) ? 2 : 1);
   h.planar = (p->flags & KMC_FLAG_PLANAR) ? 1 : 0;
   h.absorb = (p->bc[0] == KMC_ABSORB || p->bc[1] == KMC_ABSORB || p->bc[2] == KMC_ABSORB) ? 1 : 0;
+  h.mix = mix ? 1 : 0;
+  h.mix_n = mix ? (int32_t)mix->nspecies : 0;
   h.split_min_occ = p->split_min_occ;
   h.piston_x0 = p->bc[0] == KMC_REFLECT ? p->piston_x0 : p->box[0];
   h.piston_u = p->bc[0] == KMC_REFLECT ? p->piston_u : 0.0;
@@ -567,6 +592,11 @@ int create_impl(const kmc_params* p, const double* const* src6, const uint32_t* 
     if ((rc = dalloc(s, &h.mir_a, n))) return fail(rc);
     if ((rc = dalloc(s, &h.mir_b, n))) return fail(rc);
   }
+  if (mix) {
+    if ((rc = dalloc(s, &h.species, n))) return fail(rc);
+    if ((rc = dalloc(s, &h.sp_mass, mix->nspecies))) return fail(rc);
+    if ((rc = dalloc(s, &h.sp_radius, mix->nspecies))) return fail(rc);
+  }
   if ((rc = dalloc(s, &h.key, n))) return fail(rc);
   if ((rc = dalloc(s, &h.rank, n))) return fail(rc);
   if ((rc = dalloc(s, &h.src, n))) return fail(rc);
@@ -600,6 +630,11 @@ int create_impl(const kmc_params* p, const double* const* src6, const uint32_t* 
   uint32_t* bad = nullptr;
   if ((rc = dalloc(s, &bad, 2))) return fail(rc);
   ok = ck(cudaMemsetAsync(bad, 0, 2 * sizeof(uint32_t), st));
+  if (mix) {
+    ok = ok && ck(cudaMemcpyAsync(h.species, mix->species, n, cudaMemcpyDefault, st)) &&
+         ck(cudaMemcpyAsync(h.sp_mass, mix->mass, mix->nspecies * sizeof(double), cudaMemcpyDefault, st)) &&
+         ck(cudaMemcpyAsync(h.sp_radius, mix->radius, mix->nspecies * sizeof(double), cudaMemcpyDefault, st));
+  }
   if (init) {
     InitLaunch L;
     std::memset(&L, 0, sizeof(L));
@@ -659,7 +694,8 @@ int create_impl(const kmc_params* p, const double* const* src6, const uint32_t* 
   }
   if (nbad[0]) {
     s->err = std::to_string(nbad[0]) + " particle(s) outside the box or with non-finite velocity" +
-             std::string(h.planar ? " (or, planar, with vz != 0)" : "");
+             std::string(h.planar ? " (or, planar, with vz != 0)" : "") +
+             std::string(mix ? " (or with a species index >= nspecies)" : "");
     return fail(KMC_EINVAL);
   }
   if ((rc = ensure_solo(s))) return fail(rc);
@@ -677,7 +713,16 @@ int sim_create(const kmc_params* p, const double* x, const double* y, const doub
                const double* vx, const double* vy, const double* vz, const uint32_t* last,
                void* stream, kmc_sim** out) {
   const double* src[6] = {x, y, z, vx, vy, vz};
-  return create_impl(p, src, last, nullptr, stream, out);
+  return create_impl(p, src, last, nullptr, nullptr, stream, out);
+}
+
+int sim_create_mixture(const kmc_params* p, const double* x, const double* y, const double* z,
+                       const double* vx, const double* vy, const double* vz, const uint32_t* last,
+                       const uint8_t* species, uint32_t nspecies, const double* mass,
+                       const double* radius, void* stream, kmc_sim** out) {
+  const double* src[6] = {x, y, z, vx, vy, vz};
+  Mixture m{species, nspecies, mass, radius};
+  return create_impl(p, src, last, nullptr, &m, stream, out);
 }
 
 int sim_create_init(const kmc_params* p, const kmc_init* init, void* stream, kmc_sim** out) {
@@ -686,7 +731,7 @@ int sim_create_init(const kmc_params* p, const kmc_init* init, void* stream, kmc
     g_create_error = "init descriptor is NULL";
     return KMC_EINVAL;
   }
-  return create_impl(p, nullptr, nullptr, init, stream, out);
+  return create_impl(p, nullptr, nullptr, init, nullptr, stream, out);
 }
 
 int sim_step(kmc_sim* s, uint32_t nsteps) {

@@ -103,6 +103,8 @@ struct SimDev {
   int32_t max_rounds, precision, profile_bins, profile_every, K, search_kernel;
   int32_t split_ok;     // 0: never split, 1: split when cheaper, 2: split whenever possible
   int32_t planar;       // 1: x-y dynamics (vz = 0), scatter directions in the plane
+  int32_t mix;          // 1: a mixture (per-particle species: mass and effective radius)
+  int32_t mix_n;        // number of species
   int32_t absorb;       // 1: some axis has absorbing walls (the sort keeps the particles
                         // that left in one extra key after every cell: see graveyard_key)
   double split_min_occ; // smallest mean occupancy of the slow grid under a split
@@ -116,6 +118,10 @@ struct SimDev {
   double* v[2][3];
   uint32_t* id[2];
   uint32_t* last[2];
+  // ---- mixture (mix == 1): species by particle id, mass and radius by species ----
+  uint8_t* species;
+  double* sp_mass;
+  double* sp_radius;
   // ---- per-step work arrays ----
   float4* mir_a;        // (ox, oy, oz, vx): binary32 offsets from the cell corner
   float2* mir_b;        // (vy, vz)

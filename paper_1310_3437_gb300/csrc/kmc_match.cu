@@ -141,6 +141,13 @@ __global__ void __launch_bounds__(kEdgeBlock) k_refine(Batch B) {
       bool cand = false;
       double d2 = 0.0, t = 0.0;
       uint32_t idi = s.id[cur][i], idj = s.id[cur][j];
+      // contact distance: d0, or in a mixture the sum of the two effective radii (the
+      // search tested against d0, at least every such sum)
+      double c2 = s.d0sq;
+      if (s.mix) {
+        const double c = dadd(s.sp_radius[s.species[idi]], s.sp_radius[s.species[idj]]);
+        c2 = dmul(c, c);
+      }
       if (!(s.last[cur][i] == idj && s.last[cur][j] == idi)) {
         double r[3], v[3];
 #pragma unroll
@@ -157,7 +164,7 @@ __global__ void __launch_bounds__(kEdgeBlock) k_refine(Batch B) {
           double wy = dsub(dmul(r[2], v[0]), dmul(r[0], v[2]));
           double wz = dsub(dmul(r[0], v[1]), dmul(r[1], v[0]));
           d2 = ddiv(dadd(dadd(dmul(wx, wx), dmul(wy, wy)), dmul(wz, wz)), vv);
-          cand = t >= 0.0 && t < s.dt && d2 < s.d0sq;
+          cand = t >= 0.0 && t < s.dt && d2 < c2;
         }
       }
       if (cand) {
@@ -320,22 +327,30 @@ __global__ void __launch_bounds__(kEdgeBlock) k_collide(Batch B) {
         atomicOr(&s.d.status, ST_RANDOM);
         continue;
       }
+      // equal masses: V = (v_a + v_b)/2 and both get half the relative speed; a mixture:
+      // V = (m_a v_a + m_b v_b)/M, v_a' = V + (m_b/M) G n, v_b' = V - (m_a/M) G n
+      double ma = 1.0, mb = 1.0;
+      if (s.mix) {
+        ma = s.sp_mass[s.species[ida]];
+        mb = s.sp_mass[s.species[s.id[cur][j]]];
+      }
+      const double M = dadd(ma, mb);
       double va[3], vb[3], g[3], V[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         va[c] = s.v[cur][c][i];
         vb[c] = s.v[cur][c][j];
         g[c] = dsub(va[c], vb[c]);
-        V[c] = dmul(dadd(va[c], vb[c]), 0.5);
+        V[c] = s.mix ? ddiv(dadd(dmul(ma, va[c]), dmul(mb, vb[c])), M) : dmul(dadd(va[c], vb[c]), 0.5);
       }
       double G = dsqrt(dadd(dadd(dmul(g[0], g[0]), dmul(g[1], g[1])), dmul(g[2], g[2])));
-      double hG = dmul(0.5, G);
+      const double hGa = dmul(s.mix ? ddiv(mb, M) : 0.5, G);
+      const double hGb = dmul(s.mix ? ddiv(ma, M) : 0.5, G);
       double rest = dsub(s.dt, t);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        double pc = dmul(hG, nv[c]);
-        double na = dadd(V[c], pc);
-        double nb = dsub(V[c], pc);
+        double na = dadd(V[c], dmul(hGa, nv[c]));
+        double nb = dsub(V[c], dmul(hGb, nv[c]));
         double xa = s.x[cur][c][i], xb = s.x[cur][c][j];
         s.x[cur][c][i] = dadd(dadd(xa, dmul(va[c], t)), dmul(na, rest));
         s.x[cur][c][j] = dadd(dadd(xb, dmul(vb[c], t)), dmul(nb, rest));

@@ -465,6 +465,7 @@ __global__ void k_validate(SimDev* d, uint32_t* bad) {
     if (!(fabs(s.v[s.d.parity][a][p]) < 1e15)) out = true;
   }
   if (s.planar && s.v[s.d.parity][2][p] != 0.0) out = true;
+  if (s.mix && s.species[s.id[s.d.parity][p]] >= (uint32_t)s.mix_n) out = true;
   if (out) atomicAdd(bad, 1u);
 }
 

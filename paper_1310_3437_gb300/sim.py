@@ -12,7 +12,8 @@ import numpy as np
 from . import (KMC_FP64, KMC_GUARDED_FP32, KMC_NONE, KMC_OBS_COUNTS, KMC_OBS_EDGES,
                KMC_OBS_LAUNCHES, KMC_OBS_PARTNERS, KMC_OBS_PHASE_MS, KMC_OBS_PROFILES,
                KMC_OBS_STATE, KMC_OBS_STEP, kmc_params, sim_set_timing,
-               kmc_step_counts, sim_create, sim_create_init, init_from_spec, sim_destroy, sim_group_add, sim_group_budget,
+               kmc_step_counts, sim_create, sim_create_init, sim_create_mixture,
+               init_from_spec, sim_destroy, sim_group_add, sim_group_budget,
                sim_group_create, sim_group_destroy, sim_group_remove, sim_group_step,
                sim_group_steps_left, sim_group_sync, sim_observe, sim_step, sim_sync)
 
@@ -74,10 +75,11 @@ def _torch_stream():
 class Simulation:
     """One simulation: state on the device, stepped by the library's kernels."""
 
-    def __init__(self, params: kmc_params, arrays=None, last=None, stream=None, init=None):
+    def __init__(self, params: kmc_params, arrays=None, last=None, stream=None, init=None,
+                 mixture=None):
         """From host or device arrays (x, y, z, vx, vy, vz) and optional last partners,
         or, with ``init`` (a dict with kmc_init's fields), from a state drawn on the
-        device."""
+        device.  ``mixture``: (species per id, masses, radii) for a mixture."""
         self.params = params
         self.n = int(params.n)
         self.group = None
@@ -101,7 +103,16 @@ class Simulation:
             self._keep.append(k)
         if stream is None:
             stream = _torch_stream()
-        self.handle = sim_create(params, *ptrs, lp, stream)
+        if mixture is not None:
+            sp, ms, rs = mixture
+            sp, k1 = _ptr(sp if hasattr(sp, "data_ptr") else np.ascontiguousarray(sp, np.uint8))
+            ms = np.ascontiguousarray(ms, dtype=np.float64)
+            rs = np.ascontiguousarray(rs, dtype=np.float64)
+            self._keep += [k1, ms, rs]
+            self.handle = sim_create_mixture(params, *ptrs, lp, sp, len(ms), ms.ctypes.data,
+                                             rs.ctypes.data, stream)
+        else:
+            self.handle = sim_create(params, *ptrs, lp, stream)
         self._keep = None
         self.group = None
 

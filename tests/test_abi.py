@@ -106,3 +106,24 @@ def test_init_descriptor_layout_and_host_checks():
     out = C.c_void_p()
     assert kmc.lib().sim_create_init(C.byref(kmc.params_from_setup(s)), None, None,
                                      C.byref(out)) == kmc.KMC_EINVAL
+
+
+def test_mixture_tables_are_checked_on_the_host():
+    import numpy as np
+    from kmc_inputs import mixture_setup
+    s = mixture_setup(n=100)
+    dummy = C.c_void_p(1)
+    sp = np.zeros(100, np.uint8)
+    for masses, radii, nsp, d0 in [((1.0, 0.0), (0.01, 0.01), 2, 0.1), ((1.0, 2.0), (0.01, -1.0), 2, 0.1),
+                                   ((1.0,), (0.01,), 0, 0.1), ((1.0, 2.0), (0.01, 0.06), 2, 0.1),
+                                   ((1.0, float("inf")), (0.01, 0.01), 2, 0.1)]:
+        p = kmc.params_from_setup(s)
+        p.d0 = d0
+        m = np.asarray(masses + (1.0,) * 4, np.float64)
+        r = np.asarray(radii + (0.01,) * 4, np.float64)
+        out = C.c_void_p()
+        rc = kmc.lib().sim_create_mixture(C.byref(p), dummy, dummy, dummy, dummy, dummy, dummy,
+                                          None, sp.ctypes.data, nsp, m.ctypes.data, r.ctypes.data,
+                                          None, C.byref(out))
+        assert rc == kmc.KMC_EINVAL, (masses, radii, nsp)
+        assert out.value is None

@@ -29,7 +29,10 @@ def gpu_sim(setup, arrays, precision=FP64, stencil=1, cell_scale=1.0, last=None,
     p = kmc.params_from_setup(setup, precision=precision, stencil=stencil, cell_scale=cell_scale,
                               step0=step0, edge_cap=edge_cap, search_kernel=search_kernel)
     p.flags |= flags
-    return kmc.Simulation(p, arrays, last=last)
+    mixture = None
+    if getattr(setup, "species", None) is not None:
+        mixture = (setup.species, setup.masses, setup.radii)
+    return kmc.Simulation(p, arrays, last=last, mixture=mixture)
 
 
 def assert_same_state(sim, st: oracle.State):
@@ -437,3 +440,41 @@ def test_absorbing_box_empties_and_groups_mix():
         assert_same_counts(x.counts(), oc)
         assert_same_state(x, st)
     g.close()
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
+def test_mixture_bit_exact(precision, kernel):
+    """Binary mixture (Sec. 2: per-particle mass and effective radius): contact at
+    r_i + r_j, mass-weighted scatter, bit-identical to the oracle."""
+    s = ki.mixture_setup(n=6000, seed=91, mass_b=4.0, kT_b=2.0)
+    sim, st, oc, _ = run_both(s, 60, precision, search_kernel=kernel)
+    assert_same_counts(sim.counts(), oc)
+    assert_same_state(sim, st)
+    assert sum(c["collisions"] for c in oc) > 5000
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_mixture_pair_lists_split_and_absorbing_walls(precision):
+    s = ki.mixture_setup(n=8000, seed=92, mass_b=9.0, d_a=0.01, d_b=0.03)
+    s = s.with_(bc=(ki.ABSORB, ki.PERIODIC, ki.REFLECT), piston_x0=1.0, piston_u=0.0)
+    arrays = ki.initial_state(s)
+    st = oracle.State(arrays)
+    sim = gpu_sim(s, arrays, precision=precision, flags=kmc.KMC_FLAG_FORCE_SPLIT)
+    for step in range(12):
+        pi, pj, _, _ = oracle.candidate_pairs(s, st)
+        counts, partner, _ = oracle.step(s, st, step)
+        sim.step(1).sync()
+        assert np.array_equal(sim.edges(), np.stack([pi, pj], axis=1)), f"step {step}"
+        assert np.array_equal(sim.partners(), partner), f"step {step}"
+    assert_same_state(sim, st)
+
+
+def test_mixture_rejects_bad_species_index():
+    s = ki.mixture_setup(n=1000, seed=93)
+    arrays = ki.initial_state(s)
+    sp = s.species.copy()
+    sp[500] = 2  # two species: 0 and 1
+    with pytest.raises(kmc.KmcError) as e:
+        kmc.Simulation(kmc.params_from_setup(s), arrays, mixture=(sp, s.masses, s.radii))
+    assert e.value.code == kmc.KMC_EINVAL and "species" in str(e.value)
