@@ -248,6 +248,8 @@ int build_plan(Plan& P, const std::vector<kmc_sim*>& sims, cudaStream_t st, std:
     pr[k + 1] = pr[k] + ceil_div(h.n, kProfTile);
     P.max_rounds = std::max(P.max_rounds, h.max_rounds);
     if (h.profile_bins > 0) P.has_profiles = true;
+    if (h.absorb) P.L.absorb = true;
+    if (h.mix) P.L.mix = true;
   }
   size_t scratch = (size_t)sc[m] + 1;
   size_t words = 3 * (size_t)(m + 1) + scratch;

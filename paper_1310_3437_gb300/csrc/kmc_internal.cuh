@@ -86,7 +86,6 @@ struct Dyn {
                         // candidates; r + 1 is filled by round r)
   unsigned long long pair_tests;
   unsigned long long fast_tests;  // the part of pair_tests done by the fast-particle search
-  uint32_t n_absorbed;  // particles that left through absorbing walls this step
   uint32_t last_raw;    // n_raw of the last completed step (its pair buffer is kept)
   uint32_t have_counts; // split_cnt holds counts of the current state
   float split_thr[kSplitTrials];     // trial thresholds on |v|^2 (set with the grid)
@@ -94,6 +93,7 @@ struct Dyn {
   uint32_t prof_due;    // the step being run ends with a profile
   uint32_t prof_count;  // snapshots written
   uint64_t hist_count;  // step records written
+  uint32_t n_absorbed;  // particles that left through absorbing walls this step
 };
 
 struct SimDev {
@@ -103,10 +103,6 @@ struct SimDev {
   int32_t max_rounds, precision, profile_bins, profile_every, K, search_kernel;
   int32_t split_ok;     // 0: never split, 1: split when cheaper, 2: split whenever possible
   int32_t planar;       // 1: x-y dynamics (vz = 0), scatter directions in the plane
-  int32_t mix;          // 1: a mixture (per-particle species: mass and effective radius)
-  int32_t mix_n;        // number of species
-  int32_t absorb;       // 1: some axis has absorbing walls (the sort keeps the particles
-                        // that left in one extra key after every cell: see graveyard_key)
   double split_min_occ; // smallest mean occupancy of the slow grid under a split
   double box[3];
   double piston_x0, piston_u, d0, dt, d0sq;
@@ -118,10 +114,6 @@ struct SimDev {
   double* v[2][3];
   uint32_t* id[2];
   uint32_t* last[2];
-  // ---- mixture (mix == 1): species by particle id, mass and radius by species ----
-  uint8_t* species;
-  double* sp_mass;
-  double* sp_radius;
   // ---- per-step work arrays ----
   float4* mir_a;        // (ox, oy, oz, vx): binary32 offsets from the cell corner
   float2* mir_b;        // (vy, vz)
@@ -150,6 +142,15 @@ struct SimDev {
   long long* prof_acc;  // prof_cap x bins x kProfQ fixed-point counters
   uint64_t* prof_step;
   Dyn d;
+  // ---- variants (after the fields every step reads, which keep their offsets) ----
+  int32_t absorb;       // 1: some axis has absorbing walls (the sort keeps the particles
+                        // that left in one extra key after every cell: see graveyard_key)
+  int32_t mix;          // 1: a mixture (per-particle species: mass and effective radius)
+  int32_t mix_n;        // number of species
+  // mixture: species by particle id, mass and radius by species
+  uint8_t* species;
+  double* sp_mass;
+  double* sp_radius;
 };
 
 // ---- batch mapping ------------------------------------------------------- //
@@ -181,9 +182,10 @@ __device__ __forceinline__ bool sim_active(const SimDev& s) {
 __device__ __forceinline__ uint32_t graveyard_key(const Grid& g) {
   return g.nkeys * (g.split ? 2u : 1u);
 }
-// particles in the gas at the start of the step (after this step's sort)
+// particles in the gas at the start of the step (after this step's sort); without
+// absorbing walls the scan's total at that key is n
 __device__ __forceinline__ uint32_t live_count(const SimDev& s) {
-  return s.absorb ? __ldg(s.cell_start + graveyard_key(s.d.grid)) : s.n;
+  return __ldg(s.cell_start + graveyard_key(s.d.grid));
 }
 
 // ---- exact binary64 arithmetic (never contracted into FMA) --------------- //
@@ -310,6 +312,10 @@ struct LaunchPlan {
   int row_blocks;     // row search, no periodic x axis
   int row_blocks_px;  // row search, periodic x axis
   int fast_blocks;
+  // some simulation of the plan has absorbing walls / is a mixture: the kernels that
+  // handle either are launched in their general form only then
+  bool absorb = false;
+  bool mix = false;
 };
 
 // each returns the number of kernels it launched

@@ -128,6 +128,8 @@ __device__ __forceinline__ uint32_t block_append(uint32_t* counter, uint32_t wan
 }
 
 // ---- k_refine ------------------------------------------------------------ //
+// MIX: the plan has a mixture (per-pair contact distance, mass-weighted scatter)
+template <bool MIX>
 __global__ void __launch_bounds__(kEdgeBlock) k_refine(Batch B) {
   for (int k = 0; k < B.nsims; ++k) {
     SimDev& s = *B.sims[k];
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(kEdgeBlock) k_refine(Batch B) {
       // contact distance: d0, or in a mixture the sum of the two effective radii (the
       // search tested against d0, at least every such sum)
       double c2 = s.d0sq;
-      if (s.mix) {
+      if (MIX && s.mix) {
         const double c = dadd(s.sp_radius[s.species[idi]], s.sp_radius[s.species[idj]]);
         c2 = dmul(c, c);
       }
@@ -310,6 +312,7 @@ __global__ void __launch_bounds__(kEdgeBlock) k_mutual(Batch B, int round) {
 // For the pair (a, b) with a the smaller id: stream both to t*, scatter
 //   g = v_a - v_b, V = (v_a + v_b) * 0.5, G = |g|,  v_a' = V + (G/2) n,  v_b' = V - (G/2) n,
 // then stream the rest of the step:  x' = (x + v t*) + v' (dt - t*).
+template <bool MIX>
 __global__ void __launch_bounds__(kEdgeBlock) k_collide(Batch B) {
   for (int k = 0; k < B.nsims; ++k) {
     SimDev& s = *B.sims[k];
@@ -329,23 +332,33 @@ __global__ void __launch_bounds__(kEdgeBlock) k_collide(Batch B) {
       }
       // equal masses: V = (v_a + v_b)/2 and both get half the relative speed; a mixture:
       // V = (m_a v_a + m_b v_b)/M, v_a' = V + (m_b/M) G n, v_b' = V - (m_a/M) G n
+      const bool mixed = MIX && s.mix;
       double ma = 1.0, mb = 1.0;
-      if (s.mix) {
+      if (mixed) {
         ma = s.sp_mass[s.species[ida]];
         mb = s.sp_mass[s.species[s.id[cur][j]]];
       }
-      const double M = dadd(ma, mb);
       double va[3], vb[3], g[3], V[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         va[c] = s.v[cur][c][i];
         vb[c] = s.v[cur][c][j];
         g[c] = dsub(va[c], vb[c]);
-        V[c] = s.mix ? ddiv(dadd(dmul(ma, va[c]), dmul(mb, vb[c])), M) : dmul(dadd(va[c], vb[c]), 0.5);
+      }
+      double fa = 0.5, fb = 0.5;
+      if (mixed) {
+        const double M = dadd(ma, mb);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) V[c] = ddiv(dadd(dmul(ma, va[c]), dmul(mb, vb[c])), M);
+        fa = ddiv(mb, M);
+        fb = ddiv(ma, M);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) V[c] = dmul(dadd(va[c], vb[c]), 0.5);
       }
       double G = dsqrt(dadd(dadd(dmul(g[0], g[0]), dmul(g[1], g[1])), dmul(g[2], g[2])));
-      const double hGa = dmul(s.mix ? ddiv(mb, M) : 0.5, G);
-      const double hGb = dmul(s.mix ? ddiv(ma, M) : 0.5, G);
+      const double hGa = dmul(fa, G);
+      const double hGb = dmul(fb, G);
       double rest = dsub(s.dt, t);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -363,7 +376,8 @@ __global__ void __launch_bounds__(kEdgeBlock) k_collide(Batch B) {
 
 int launch_match(const LaunchPlan& L, int max_rounds, cudaStream_t st) {
   int nb = L.edge_blocks;
-  k_refine<<<nb, kEdgeBlock, 0, st>>>(L.b);
+  if (L.mix) k_refine<true><<<nb, kEdgeBlock, 0, st>>>(L.b);
+  else k_refine<false><<<nb, kEdgeBlock, 0, st>>>(L.b);
   k_alloc<<<nb, kEdgeBlock, 0, st>>>(L.b);
   k_fill<<<nb, kEdgeBlock, 0, st>>>(L.b);
   for (int r = 0; r < max_rounds; ++r) {
@@ -373,7 +387,8 @@ int launch_match(const LaunchPlan& L, int max_rounds, cudaStream_t st) {
     k_best<<<nr, kEdgeBlock, 0, st>>>(L.b, r);
     k_mutual<<<nr, kEdgeBlock, 0, st>>>(L.b, r);
   }
-  k_collide<<<nb, kEdgeBlock, 0, st>>>(L.b);
+  if (L.mix) k_collide<true><<<nb, kEdgeBlock, 0, st>>>(L.b);
+  else k_collide<false><<<nb, kEdgeBlock, 0, st>>>(L.b);
   return 4 + 2 * max_rounds;
 }
 

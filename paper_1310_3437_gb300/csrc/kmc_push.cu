@@ -144,6 +144,7 @@ __device__ __forceinline__ float push_particle(SimDev& s, int cur, uint32_t p, d
   return gone ? 0.0f : vmag2_up(vv[0], vv[1], vv[2]);
 }
 
+template <bool ABS>
 __global__ void __launch_bounds__(kTile) k_push(Batch B) {
   __shared__ double sX;                       // piston position at the end of the step
   __shared__ uint32_t scnt[kSplitTrials];     // particles above each trial threshold
@@ -158,17 +159,17 @@ __global__ void __launch_bounds__(kTile) k_push(Batch B) {
     sX = s.bc[0] == KMC_PERIODIC ? 0.0
                                  : dsub(s.piston_x0, dmul(s.piston_u, dmul((double)(step + 1), dt)));
   if (threadIdx.x < kSplitTrials) scnt[threadIdx.x] = 0;
-  if (threadIdx.x == 0) sgone = 0;
+  if (ABS && threadIdx.x == 0) sgone = 0;
   __syncthreads();
   uint32_t p = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
   float vm = 0.0f;
   // absorbing walls: particles that left earlier sit at the end of the order and stay
   // as they are (live_count is this step's sort's count of the others)
-  const uint32_t n_in = live_count(s);
+  const uint32_t n_in = ABS ? live_count(s) : s.n;
   bool gone = false;
-  if (p < n_in) vm = s.absorb ? push_particle<true>(s, cur, p, dt, sX, gone)
-                              : push_particle<false>(s, cur, p, dt, sX, gone);
-  if (s.absorb) {
+  if (p < n_in) vm = (ABS && s.absorb) ? push_particle<true>(s, cur, p, dt, sX, gone)
+                                       : push_particle<false>(s, cur, p, dt, sX, gone);
+  if (ABS && s.absorb) {
     const unsigned m = __ballot_sync(0xFFFFFFFFu, gone);
     if ((threadIdx.x & 31) == 0 && m) atomicAdd(&sgone, (uint32_t)__popc(m));
   }
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(kTile) k_push(Batch B) {
   block_max_to(&s.d.vmax2_acc, vm);  // its block barrier also orders the shared counters
   if (s.split_ok && threadIdx.x > 0 && threadIdx.x < kSplitTrials && scnt[threadIdx.x])
     atomicAdd(&s.d.split_cnt[threadIdx.x], scnt[threadIdx.x]);
-  if (s.absorb && threadIdx.x == 0 && sgone) atomicAdd(&s.d.n_absorbed, sgone);
+  if (ABS && s.absorb && threadIdx.x == 0 && sgone) atomicAdd(&s.d.n_absorbed, sgone);
 }
 
 // ---- fixed-point digits for the profile sums ------------------------------- //
@@ -213,6 +214,7 @@ __device__ __forceinline__ void fx_digits(double q, long long d[3]) {
   d[0] = d0; d[1] = d1; d[2] = d2;
 }
 
+template <bool ABS>
 __global__ void __launch_bounds__(kTile) k_profile(Batch B) {
   extern __shared__ long long acc[];
   int k = find_sim(B.prtile, B.nsims, blockIdx.x);
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(kTile) k_profile(Batch B) {
   for (uint32_t i = threadIdx.x; i < kProfTile; i += blockDim.x) {
     uint32_t p = base + i;
     if (p >= s.n) break;
-    if (s.absorb && s.last[cur][p] == KMC_ABSORBED) continue;  // out of the gas
+    if (ABS && s.absorb && s.last[cur][p] == KMC_ABSORBED) continue;  // out of the gas
     double x = s.x[cur][0][p];
     if (!(x >= 0.0)) continue;
     double f = dmul(x, scale);
@@ -323,6 +325,7 @@ __global__ void k_finalize(Batch B) {
 }
 
 // ---- initial grid (creation, resume, after an error is cleared) ------------ //
+template <bool ABS>
 __global__ void __launch_bounds__(kTile) k_vmax(Batch B) {
   int k = find_sim(B.ptile, B.nsims, blockIdx.x);
   SimDev& s = *B.sims[k];
@@ -330,7 +333,7 @@ __global__ void __launch_bounds__(kTile) k_vmax(Batch B) {
   float vm = 0.0f;
   if (p < s.n) {
     int par = s.d.parity;
-    if (!(s.absorb && s.last[par][p] == KMC_ABSORBED))
+    if (!(ABS && s.absorb && s.last[par][p] == KMC_ABSORBED))
       vm = vmag2_up(s.v[par][0][p], s.v[par][1][p], s.v[par][2][p]);
   }
   block_max_to(&s.d.vmax2_acc, vm);
@@ -368,14 +371,20 @@ __global__ void k_zero_vmax(Batch B) {
 
 int launch_init_grid(const LaunchPlan& L, cudaStream_t st) {
   k_zero_vmax<<<1, 256, 0, st>>>(L.b);
-  k_vmax<<<L.ptiles, kTile, 0, st>>>(L.b);
+  if (L.absorb) k_vmax<true><<<L.ptiles, kTile, 0, st>>>(L.b);
+  else k_vmax<false><<<L.ptiles, kTile, 0, st>>>(L.b);
   k_init_grid<<<(L.b.nsims + 7) / 8, 256, 0, st>>>(L.b);
   return 3;
 }
 
 int launch_push(const LaunchPlan& L, cudaStream_t st) {
-  k_push<<<L.ptiles, kTile, 0, st>>>(L.b);
-  k_profile<<<L.prtiles, kTile, 256 * kProfQ * sizeof(long long), st>>>(L.b);
+  if (L.absorb) {
+    k_push<true><<<L.ptiles, kTile, 0, st>>>(L.b);
+    k_profile<true><<<L.prtiles, kTile, 256 * kProfQ * sizeof(long long), st>>>(L.b);
+  } else {
+    k_push<false><<<L.ptiles, kTile, 0, st>>>(L.b);
+    k_profile<false><<<L.prtiles, kTile, 256 * kProfQ * sizeof(long long), st>>>(L.b);
+  }
   k_finalize<<<(L.b.nsims + 7) / 8, 256, 0, st>>>(L.b);
   return 3;
 }

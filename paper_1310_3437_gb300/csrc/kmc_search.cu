@@ -1151,7 +1151,7 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4) k_search_fast(Batch B) {
     const Grid& g = s.d.grid;
     const uint32_t* __restrict__ cs = s.cell_start;
     const uint32_t nk = g.nkeys;
-    const uint32_t n = s.absorb ? __ldg(cs + 2 * nk) : s.n;  // end of the fast keys
+    const uint32_t n = __ldg(cs + 2 * nk);  // end of the fast keys (n without absorption)
     const uint32_t nslow = __ldg(cs + nk);
     const uint32_t nfast = n - nslow;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;

@@ -44,6 +44,9 @@ __device__ __forceinline__ uint32_t run_rank(uint32_t* counts, uint32_t key, boo
 
 // two particles per thread, half a tile apart: both sets of loads are in flight
 // before either key is needed (the kernel is bound by memory latency)
+// ABS: the plan has a simulation with absorbing walls (their absorbed particles take
+// the key after every cell)
+template <bool ABS>
 __global__ void __launch_bounds__(kTile / 2) k_count(Batch B) {
   int k = find_sim(B.ptile, B.nsims, blockIdx.x);
   SimDev& s = *B.sims[k];
@@ -62,7 +65,7 @@ __global__ void __launch_bounds__(kTile / 2) k_count(Batch B) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) xs[h][a] = s.x[par][a][q];
     vb[h] = g.split ? (uint32_t)s.vbucket[q] : 0u;
-    gone[h] = s.absorb && s.last[par][q] == KMC_ABSORBED;
+    gone[h] = ABS && s.absorb && s.last[par][q] == KMC_ABSORBED;
   }
   const uint32_t lane = threadIdx.x & 31u;
 #pragma unroll
@@ -288,7 +291,8 @@ int launch_cell_scan(const LaunchPlan& L, cudaStream_t st) {
 }
 
 int launch_sort(const LaunchPlan& L, cudaStream_t st) {
-  k_count<<<L.ptiles, kTile / 2, 0, st>>>(L.b);
+  if (L.absorb) k_count<true><<<L.ptiles, kTile / 2, 0, st>>>(L.b);
+  else k_count<false><<<L.ptiles, kTile / 2, 0, st>>>(L.b);
   int n = launch_cell_scan(L, st);
   k_scatter<<<L.ptiles, kTile, 0, st>>>(L.b);
   k_gather<<<L.ptiles, kTile, 0, st>>>(L.b);
