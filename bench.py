@@ -364,8 +364,8 @@ def run_gpu(args):
         knobs = {k: best[k] for k in knobs}
         tuning = {"chosen": best, "trials": next(iter(tuner.trials.values()))}
 
-    def timed_run(precision, warm, steps, sample_clocks=False):
-        params = kmc.params_from_setup(setup, precision=precision, **knobs)
+    def timed_run(precision, warm, steps, sample_clocks=False, kn=None):
+        params = kmc.params_from_setup(setup, precision=precision, **(knobs if kn is None else kn))
         sim = kmc.Simulation(params, dev_arrays, stream=stream.cuda_stream)
         sim.step(warm).sync()
         sim.counts()
@@ -414,7 +414,10 @@ def run_gpu(args):
     fp64 = None
     if not args.skip_fp64:
         k64 = max(1, min(args.steps, args.fp64_steps))
-        sim64, ms64, counts64, _, _ = timed_run(kmc.KMC_FP64, args.warmup, k64)
+        # the binary64 path with its own defaults (the tuner tunes the binary32 path; a
+        # binary32-only kernel choice would not carry over)
+        kn64 = {"search_kernel": 0, "stencil": 1, "cell_scale": 1.0, "split_min_occ": 0.0}
+        sim64, ms64, counts64, _, _ = timed_run(kmc.KMC_FP64, args.warmup, k64, kn=kn64)
         v64 = world * n * k64 / (ms64 / 1e3)
         same = [(c["collisions"], c["edges"]) for c in counts64] == \
                [(c["collisions"], c["edges"]) for c in counts32[:k64]]
