@@ -478,3 +478,34 @@ def test_mixture_rejects_bad_species_index():
     with pytest.raises(kmc.KmcError) as e:
         kmc.Simulation(kmc.params_from_setup(s), arrays, mixture=(sp, s.masses, s.radii))
     assert e.value.code == kmc.KMC_EINVAL and "species" in str(e.value)
+
+
+def test_group_mixing_every_variant_equals_each_alone():
+    """One group holding a plain gas, a mixture, an absorbing box, a planar gas and a
+    planar absorbing mixture: the plan launches the general forms of the kernels,
+    which must leave each member's results those of the oracle."""
+    plain = ki.equilibrium_setup(n=3000, seed=95)
+    mix = ki.mixture_setup(n=3500, seed=96, mass_b=3.0)
+    absorb = _absorbing_setup(n=2500, seed=97, bc=(ki.ABSORB, ki.REFLECT, ki.PERIODIC))
+    planar = ki.equal_speed_setup(n=4000, seed=98, d0=0.004, dt=0.01)
+    pmix = ki.equal_speed_setup(n=3000, seed=99, d0=0.006, dt=0.01)
+    n = pmix.n
+    pmix = pmix.with_(bc=(ki.ABSORB, ki.PERIODIC, ki.REFLECT), piston_x0=1.0,
+                      species=(np.arange(n) % 3).astype(np.uint8), masses=(1.0, 2.5, 0.5),
+                      radii=(0.003, 0.002, 0.001))
+    setups = [plain, mix, absorb, planar, pmix]
+    arrays = [ki.initial_state(q) for q in setups]
+    for prec in (FP64, FP32):
+        sims = [gpu_sim(q, a, prec) for q, a in zip(setups, arrays)]
+        g = kmc.Group(sims)
+        for x in sims:
+            g.budget(x, 25)
+        g.step(25)
+        g.sync()
+        for q, a, x in zip(setups, arrays, sims):
+            st = oracle.State(a)
+            oc, _ = oracle.run(q, st, 0, 25)
+            assert_same_counts(x.counts(), oc)
+            assert_same_state(x, st)
+            assert sum(c["collisions"] for c in oc) > 0
+        g.close()
