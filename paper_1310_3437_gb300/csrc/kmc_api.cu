@@ -74,6 +74,10 @@ struct kmc_sim {
   bool timing = false;       // per-phase CUDA-event timing (no graph)
   double phase_ms[5] = {0, 0, 0, 0, 0};  // sort, search, match, push; slow search kernels
   uint64_t timed_steps = 0;
+  // in a group: the step index at the group's last sync (or at joining) and the
+  // group's issued-step count then, so that a sync can tell how many of the group's
+  // steps this member missed after an overflow
+  uint64_t sync_step = 0, issued_base = 0;
   std::string err;
 };
 
@@ -83,6 +87,7 @@ struct kmc_group {
   bool own_stream = false;
   Plan plan;
   bool built = false;
+  uint64_t issued = 0;  // group steps enqueued since the last sync
   std::string err;
 };
 
@@ -935,6 +940,9 @@ int sim_group_create(kmc_sim* const* sims, uint32_t count, void* stream, kmc_gro
   }
   for (uint32_t i = 0; i < count; ++i) {
     cudaStreamSynchronize(sims[i]->stream);
+    Dyn dy;
+    if (read_dyn(sims[i], &dy, sims[i]->stream) == KMC_OK) sims[i]->sync_step = dy.step;
+    sims[i]->issued_base = 0;
     sims[i]->group = g;
     g->members.push_back(sims[i]);
   }
@@ -951,6 +959,11 @@ int sim_group_add(kmc_group* g, kmc_sim* s) {
     return KMC_EINVAL;
   }
   cudaStreamSynchronize(s->stream);
+  Dyn dy;
+  int rc = read_dyn(s, &dy, s->stream);
+  if (rc) return rc;
+  s->sync_step = dy.step;
+  s->issued_base = g->issued;
   s->group = g;
   g->members.push_back(s);
   g->built = false;
@@ -986,6 +999,7 @@ int sim_group_step(kmc_group* g, uint32_t nsteps) {
   uint64_t launched = 0;
   int rc = run_steps(g->plan, g->stream, nsteps, g->err, &launched);
   for (kmc_sim* s : g->members) s->launches += launched;
+  g->issued += nsteps;
   return rc;
 }
 
@@ -999,24 +1013,51 @@ int64_t sim_group_steps_left(kmc_group* g, kmc_sim* s) {
 
 int sim_group_sync(kmc_group* g) {
   if (!g) return KMC_EINVAL;
-  KCHECK(cudaStreamSynchronize(g->stream), g->err);
   int worst = KMC_OK;
-  for (kmc_sim* s : g->members) {
-    Dyn dy;
-    int rc = read_dyn(s, &dy, g->stream);
-    if (rc) return rc;
-    if (dy.status == 0) continue;
-    if (dy.status == ST_EDGE_OVERFLOW) {
-      rc = recover_overflow(s, dy, g->stream);
-    } else {
-      rc = status_code(dy.status, s->err);
+  for (int attempt = 0; attempt < 64; ++attempt) {
+    KCHECK(cudaStreamSynchronize(g->stream), g->err);
+    bool rerun = false;
+    worst = KMC_OK;
+    for (kmc_sim* s : g->members) {
+      Dyn dy;
+      int rc = read_dyn(s, &dy, g->stream);
+      if (rc) return rc;
+      if (dy.status == 0) {
+        s->sync_step = dy.step;
+        s->issued_base = 0;
+        continue;
+      }
+      if (dy.status == ST_EDGE_OVERFLOW) {
+        rc = recover_overflow(s, dy, g->stream);
+        if (rc == KMC_OK) {
+          // the group's steps after the overflow skipped this member: it runs the ones
+          // it missed since the last sync on its own (within its budget), so that a
+          // sync leaves every member where the group's steps should have taken it
+          const uint64_t window = g->issued - s->issued_base;
+          const uint64_t taken = dy.step - s->sync_step;
+          uint64_t lost = window > taken ? window - taken : 0;
+          if (lost > dy.steps_left) lost = dy.steps_left;
+          if (lost) {
+            rc = ensure_solo(s);
+            if (rc == KMC_OK) rc = run_steps(s->solo, g->stream, lost, s->err, &s->launches);
+            rerun = true;
+          }
+        }
+      } else {
+        rc = status_code(dy.status, s->err);
+      }
+      if (rc) {
+        g->err = s->err;
+        worst = rc;
+      }
     }
-    if (rc) {
-      g->err = s->err;
-      worst = rc;
+    if (!rerun) {
+      g->issued = 0;
+      return worst;
     }
   }
-  return worst;
+  g->err = "overflow recovery did not converge";
+  return KMC_EOVERFLOW;
 }
 
 int sim_group_destroy(kmc_group* g) {

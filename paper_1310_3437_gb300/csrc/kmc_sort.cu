@@ -241,43 +241,69 @@ __global__ void __launch_bounds__(kTile) k_scan_apply(Batch B) {
 // the new order, reads each particle from its old position (nearby reads share
 // sectors) and writes the permuted state, the mirror and the per-particle step
 // arrays with coalesced stores.
-__global__ void __launch_bounds__(kTile) k_scatter(Batch B) {
+// Both kernels take two particles per thread, half a tile apart, so that both
+// dependent load chains (key -> cell start; source -> state) are in flight at once.
+__global__ void __launch_bounds__(kTile / 2) k_scatter(Batch B) {
   int k = find_sim(B.ptile, B.nsims, blockIdx.x);
   SimDev& s = *B.sims[k];
   if (!sim_active(s)) return;
-  uint32_t p = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
-  if (p >= s.n) return;
-  s.src[s.cell_start[s.key[p]] + s.rank[p]] = p;
+  const uint32_t p0 = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
+  const uint32_t pp[2] = {p0, p0 + kTile / 2};
+  uint32_t key[2], rank[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const uint32_t q = pp[h] < s.n ? pp[h] : 0u;
+    key[h] = s.key[q];
+    rank[h] = s.rank[q];
+  }
+  uint32_t dst[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) dst[h] = s.cell_start[key[h]] + rank[h];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+    if (pp[h] < s.n) s.src[dst[h]] = pp[h];
 }
 
-__global__ void __launch_bounds__(kTile) k_gather(Batch B) {
+__global__ void __launch_bounds__(kTile / 2) k_gather(Batch B) {
   int k = find_sim(B.ptile, B.nsims, blockIdx.x);
   SimDev& s = *B.sims[k];
   if (!sim_active(s)) return;
-  uint32_t d = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
-  if (d >= s.n) return;
+  const uint32_t d0 = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
+  const uint32_t dd[2] = {d0, d0 + kTile / 2};
   const int from = s.d.parity, to = from ^ 1;
-  const uint32_t p = s.src[d];
-  double xs[3], vs[3];
+  uint32_t pp[2];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    xs[a] = s.x[from][a][p];
-    vs[a] = s.v[from][a][p];
-  }
-  const uint32_t id = s.id[from][p], last = s.last[from][p];
+  for (int h = 0; h < 2; ++h) pp[h] = s.src[dd[h] < s.n ? dd[h] : 0u];
+  double xs[2][3], vs[2][3];
+  uint32_t id[2], last[2];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    s.x[to][a][d] = xs[a];
-    s.v[to][a][d] = vs[a];
+  for (int h = 0; h < 2; ++h) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      xs[h][a] = s.x[from][a][pp[h]];
+      vs[h][a] = s.v[from][a][pp[h]];
+    }
+    id[h] = s.id[from][pp[h]];
+    last[h] = s.last[from][pp[h]];
   }
-  s.id[to][d] = id;
-  s.last[to][d] = last;
-  s.deg[d] = 0;
-  s.partner[d] = kNone;
-  if (s.precision == KMC_GUARDED_FP32) {
-    // box coordinates and velocity, each rounded once to binary32
-    s.mir_a[d] = make_float4(d2f_rn(xs[0]), d2f_rn(xs[1]), d2f_rn(xs[2]), d2f_rn(vs[0]));
-    s.mir_b[d] = make_float2(d2f_rn(vs[1]), d2f_rn(vs[2]));
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const uint32_t d = dd[h];
+    if (d >= s.n) continue;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      s.x[to][a][d] = xs[h][a];
+      s.v[to][a][d] = vs[h][a];
+    }
+    s.id[to][d] = id[h];
+    s.last[to][d] = last[h];
+    s.deg[d] = 0;
+    s.partner[d] = kNone;
+    if (s.precision == KMC_GUARDED_FP32) {
+      // box coordinates and velocity, each rounded once to binary32
+      s.mir_a[d] = make_float4(d2f_rn(xs[h][0]), d2f_rn(xs[h][1]), d2f_rn(xs[h][2]), d2f_rn(vs[h][0]));
+      s.mir_b[d] = make_float2(d2f_rn(vs[h][1]), d2f_rn(vs[h][2]));
+    }
   }
 }
 
@@ -294,8 +320,8 @@ int launch_sort(const LaunchPlan& L, cudaStream_t st) {
   if (L.absorb) k_count<true><<<L.ptiles, kTile / 2, 0, st>>>(L.b);
   else k_count<false><<<L.ptiles, kTile / 2, 0, st>>>(L.b);
   int n = launch_cell_scan(L, st);
-  k_scatter<<<L.ptiles, kTile, 0, st>>>(L.b);
-  k_gather<<<L.ptiles, kTile, 0, st>>>(L.b);
+  k_scatter<<<L.ptiles, kTile / 2, 0, st>>>(L.b);
+  k_gather<<<L.ptiles, kTile / 2, 0, st>>>(L.b);
   return n + 3;
 }
 

@@ -509,3 +509,28 @@ def test_group_mixing_every_variant_equals_each_alone():
             assert_same_state(x, st)
             assert sum(c["collisions"] for c in oc) > 0
         g.close()
+
+
+def test_group_member_whose_pair_buffer_overflows_catches_up_at_sync():
+    """A member whose candidate-pair buffer overflows in a group step is skipped by the
+    group's later steps; the group's sync grows its buffer and runs the steps it
+    missed, so after the sync every member is where its budget says."""
+    setups = [ki.equilibrium_setup(n=3000 + 700 * k, seed=110 + k) for k in range(3)]
+    arrays = [ki.initial_state(q) for q in setups]
+    sims = [gpu_sim(q, a, FP32, edge_cap=(8 if k == 1 else 0))
+            for k, (q, a) in enumerate(zip(setups, arrays))]
+    g = kmc.Group(sims)
+    budgets = [30, 30, 12]
+    for x, b in zip(sims, budgets):
+        g.budget(x, b)
+    g.step(10)
+    g.sync()
+    g.step(20)
+    g.sync()
+    for q, a, x, b in zip(setups, arrays, sims, budgets):
+        assert g.steps_left(x) == 0
+        st = oracle.State(a)
+        oc, _ = oracle.run(q, st, 0, b)
+        assert_same_counts(x.counts(), oc)
+        assert_same_state(x, st)
+    g.close()
