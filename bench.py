@@ -244,6 +244,44 @@ def run_serving(args, stream, dev):
     }
 
 
+def run_paper_workloads(args, stream, dev):
+    """The paper's own timing workloads at their stated sizes (Fig. 1: 10^8 particles,
+    3D; Fig. 3: 4 x 10^7 particles, 2D), equal speeds in random directions, each state
+    drawn on the device; guarded FP32, CUDA-event timing of K steps after warm-up."""
+    import torch
+
+    import paper_1310_3437_gb300 as kmc
+
+    out = {}
+    for fig, name in ((1, "fig1_3d_equal_speed_n1e8"), (3, "fig3_2d_equal_speed_n4e7")):
+        setup = ki.paper_timing_setup(fig)
+        params = kmc.params_from_setup(setup, precision=kmc.KMC_GUARDED_FP32)
+        sim = kmc.Simulation(params, init=ki.init_spec(setup), stream=stream.cuda_stream)
+        sim.step(3).sync()
+        sim.counts()
+        k = args.paper_steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(k)
+        e1.record(stream)
+        e1.synchronize()
+        sim.sync()
+        ms = e0.elapsed_time(e1)
+        counts = sim.counts()
+        cells = counts[-1]["cells"] if counts else 0
+        out[name] = {
+            "n": setup.n, "steps": k, "ms_per_step": ms / k,
+            "particle_steps_per_s": setup.n * k / (ms / 1e3),
+            "collisions_per_step": sum(c["collisions"] for c in counts) / max(1, len(counts)),
+            "particles_per_cell": setup.n / cells if cells else None,
+            "d0": setup.d0, "dt": setup.dt, "planar": setup.planar,
+        }
+        sim.close()
+        torch.cuda.synchronize(dev)
+    return out
+
+
 def run_ensemble(args, stream):
     """Batched ensemble: 256 independent runs of uneven size (N log-uniform in
     [2^12, 2^18], equilibrium boxes and piston tubes) stepped as one group: one launch
@@ -474,6 +512,9 @@ def run_gpu(args):
     ensemble = None
     if not args.skip_ensemble and rank == 0:
         ensemble = run_ensemble(args, stream)
+    paper = None
+    if not args.skip_paper and rank == 0:
+        paper = run_paper_workloads(args, stream, dev)
 
     if rank != 0:
         if world > 1:
@@ -540,6 +581,7 @@ def run_gpu(args):
         "e2e_device_init": e2e_dinit,
         "serve": serve,
         "ensemble": ensemble,
+        "paper_workloads": paper,
         "tuning": tuning,
         "gpu_launches": int(launches32),
         "clocks": clocks,
@@ -569,6 +611,9 @@ def main():
     ap.add_argument("--serve-host-init", action="store_true",
                     help="serving requests carry host arrays instead of a device-init descriptor")
     ap.add_argument("--skip-ensemble", action="store_true")
+    ap.add_argument("--skip-paper", action="store_true",
+                    help="skip the paper's timing workloads (10^8 3D, 4e7 2D particles)")
+    ap.add_argument("--paper-steps", type=int, default=10)
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--ensemble-steps", type=int, default=100)
     ap.add_argument("--serve-requests", type=int, default=200,

@@ -193,6 +193,27 @@ def init_spec(setup: Setup) -> dict:
     return {"kind": 1, "sigma": 1.0}
 
 
+def paper_timing_setup(figure: int, seed: int = 17, steps: int = 20) -> Setup:
+    """The paper's timing workloads at their stated sizes (Sec. 3, Fig. 1: 10^8
+    particles in three dimensions; Sec. 4, Fig. 3: 4 x 10^7 particles in two), with
+    one common speed s = 1, random directions and positions, reflecting walls, in a
+    unit box.  The paper states neither d0 nor the mean free path; here lambda =
+    0.01 (3D: lambda = 1/(sqrt(2) n pi d0^2)) and lambda = 0.001 (2D hard disks:
+    lambda = 1/(2 sqrt(2) n d0)), both well below the box (the paper asks for a
+    fluid-like gas), and dt = 0.1 lambda / s."""
+    if figure == 1:
+        n, lam = 10 ** 8, 0.01
+        d0 = math.sqrt(1.0 / (math.sqrt(2.0) * math.pi * n * lam))
+        return equal_speed_setup(n=n, seed=seed, L=1.0, d0=d0, dt=0.1 * lam, speed=1.0,
+                                 planar=False, steps=steps)
+    if figure == 3:
+        n, lam = 4 * 10 ** 7, 0.001
+        d0 = 1.0 / (2.0 * math.sqrt(2.0) * n * lam)
+        return equal_speed_setup(n=n, seed=seed, L=1.0, d0=d0, dt=0.1 * lam, speed=1.0,
+                                 planar=True, steps=steps)
+    raise ValueError("figure must be 1 or 3")
+
+
 def mixture_setup(n: int = 6000, seed: int = 5, L: float = 1.0, frac_b: float = 0.3,
                   mass_b: float = 4.0, d_a: float = 0.016, d_b: float = 0.032,
                   kT_a: float = 1.0, kT_b: float = 1.0, dt: float = 0.004,
