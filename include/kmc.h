@@ -232,7 +232,8 @@ int sim_step(kmc_sim* s, uint32_t nsteps);
 
 /* Wait for the enqueued steps.  If a candidate-pair buffer overflowed, it is grown
  * and the unfinished steps are re-run from the last completed step (results do not
- * change).  Errors: KMC_ERANDOM, KMC_EOVERFLOW, KMC_ENOMEM, KMC_ECUDA. */
+ * change).  For a member of a group this is sim_group_sync of its group.
+ * Errors: KMC_ERANDOM, KMC_EOVERFLOW, KMC_ENOMEM, KMC_ECUDA. */
 int sim_sync(kmc_sim* s);
 
 /* Copy an observable (KMC_OBS_*) into dst (host or device, dst_bytes long).  The
@@ -294,6 +295,11 @@ int sim_group_budget(kmc_group* g, kmc_sim* s, uint32_t nsteps);
 int sim_group_step(kmc_group* g, uint32_t nsteps);
 /* Steps left in member s's budget (waits for the group's stream). */
 int64_t sim_group_steps_left(kmc_group* g, kmc_sim* s);
+/* Wait for the group's steps.  A member whose candidate-pair buffer overflowed was
+ * skipped by the group's later steps: its buffer is grown and the steps it missed
+ * since the previous sync run for it alone (within its budget), so that afterwards
+ * every member stands where the group's steps took the others (results do not
+ * change).  Errors: as sim_sync, for the worst member. */
 int sim_group_sync(kmc_group* g);
 int sim_group_destroy(kmc_group* g);
 

@@ -761,6 +761,12 @@ int sim_set_timing(kmc_sim* s, int enable) {
 
 int sim_sync(kmc_sim* s) {
   if (!s) return KMC_EINVAL;
+  if (s->group) {
+    // the group's sync knows how many group steps a recovering member missed
+    const int rc = sim_group_sync(s->group);
+    if (rc) s->err = s->group->err;
+    return rc;
+  }
   cudaStream_t st = sim_work_stream(s);
   for (int attempt = 0; attempt < 64; ++attempt) {
     KCHECK(cudaStreamSynchronize(st), s->err);
@@ -770,7 +776,6 @@ int sim_sync(kmc_sim* s) {
     if (dy.status == 0) return KMC_OK;
     if (dy.status == ST_EDGE_OVERFLOW) {
       if ((rc = recover_overflow(s, dy, st))) return rc;
-      if (s->group) return KMC_OK;  // the group's next steps run the rest of the budget
       if (dy.steps_left) {
         if ((rc = run_steps(s->solo, st, dy.steps_left, s->err, &s->launches))) return rc;
       }
