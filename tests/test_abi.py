@@ -127,3 +127,18 @@ def test_mixture_tables_are_checked_on_the_host():
                                           None, C.byref(out))
         assert rc == kmc.KMC_EINVAL, (masses, radii, nsp)
         assert out.value is None
+
+
+def test_binding_constants_match_the_header():
+    """Every integer #define of include/kmc.h has the same value in the binding."""
+    text = open(HEADER).read()
+    defs = re.findall(r"^#define\s+(KMC_[A-Z0-9_]+)\s+\(?(-?(?:0x[0-9A-Fa-f]+|\d+))u?\)?", text, flags=re.M)
+    assert len(defs) > 20
+    missing = []
+    for name, val in defs:
+        want = int(val, 16) if val.lower().startswith("0x") or val.lower().startswith("-0x") else int(val)
+        if not hasattr(kmc, name):
+            missing.append(name)
+            continue
+        assert getattr(kmc, name) == want, name
+    assert not missing, missing
