@@ -550,6 +550,16 @@ def run_gpu(args):
         "frac": sort_gbs / pk["hbm_gbs"], "peak_source": f"{pk_kind} hbm_gbs",
         "bytes_per_particle": SORT_BYTES_PER_PARTICLE, "launch_ms": sort_ms,
     }
+    # the counting sort's key space: every key's count is read, its start written and
+    # the count cleared (12 B per key; the fast population, when split, has a second
+    # copy of the keys) -- reported beside the per-particle figure, not folded into it
+    if counts32 and sort_ms > 0:
+        keys = float(np.mean([c["cells"] * (2 if c["fast_tests"] else 1) for c in counts32]))
+        kb = SORT_BYTES_PER_PARTICLE * n + 12.0 * keys
+        roofline_sort["key_space"] = {
+            "keys": keys, "bytes_per_key": 12,
+            "achieved_incl_keys": kb / (sort_ms / 1e3) / 1e9,
+            "frac_incl_keys": kb / (sort_ms / 1e3) / 1e9 / pk["hbm_gbs"]}
 
     cpu = None
     if not args.skip_cpu and world >= 1:
