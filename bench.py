@@ -230,7 +230,17 @@ def run_serving(args, stream, dev):
                     stream=stream.cuda_stream)
     done, wall = server.run(reqs)
     sm = summarize(done, wall)
+    tests = sum(c["pair_tests"] for r in done for c in r.counts)
+    recs = sum(len(r.counts) for r in done)
+    if recs != sum(int(r.steps) for r in done):
+        raise RuntimeError(f"serving: {recs} step records for {sum(int(r.steps) for r in done)} steps")
+    achieved = tests * FLOPS_PER_PAIR_TEST / wall / 1e12
     return {
+        "pair_tests_per_s": tests / wall,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_FP32_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / ALU_FP32_PEAK_TFLOPS,
+                     "note": "pair tests of all requests over the stream's wall time "
+                             "(idle gaps between arrivals included)"},
         "p50_latency_ms": sm["p50_latency_s"] * 1e3, "p99_latency_ms": sm["p99_latency_s"] * 1e3,
         "mean_latency_ms": sm["mean_latency_s"] * 1e3,
         "particle_steps_per_s": sm["particle_steps_per_s"], "requests": sm["requests"],
@@ -238,7 +248,8 @@ def run_serving(args, stream, dev):
         "calibration_particle_steps_per_s": S, "budget_gb": args.serve_budget_gb,
         "mix": f"equilibrium boxes and piston tubes, N log-uniform [{n_lo}, {n_hi}], steps "
                f"U[{st_lo}, {st_hi}], guarded FP32, SplitMix64 seeds from master seed 7",
-        "latency": "arrival -> final state and step counts on the host",
+        "latency": "arrival -> final state and step counts on the host; bursts of at most "
+                   "16 group steps end when the live request closest to its end is done",
         "init": ("NumPy arrays generated on the host at admission" if args.serve_host_init
                  else "state drawn on the device at admission (sim_create_init)"),
     }
@@ -285,13 +296,17 @@ def run_paper_workloads(args, stream, dev):
 def run_ensemble(args, stream):
     """Batched ensemble: 256 independent runs of uneven size (N log-uniform in
     [2^12, 2^18], equilibrium boxes and piston tubes) stepped as one group: one launch
-    per kernel per step for all runs, the step captured in a CUDA graph."""
+    per kernel per step for all runs, the step captured in a CUDA graph.  Reports the
+    pair tests beside the particle-steps: the equilibrium boxes keep n sigma of the
+    4096-particle box, so their cells hold up to ~360 particles and a particle-step
+    costs up to ~10^4 pair tests there, against ~20 in the tube."""
     import torch
 
     import paper_1310_3437_gb300 as kmc
 
     setups = ki.ensemble_setups(count=256, steps=args.ensemble_steps)
-    sims = [kmc.Simulation(kmc.params_from_setup(q, precision=kmc.KMC_GUARDED_FP32),
+    sims = [kmc.Simulation(kmc.params_from_setup(q, precision=kmc.KMC_GUARDED_FP32,
+                                                 history_cap=args.ensemble_steps + 64),
                            ki.initial_state(q), stream=stream.cuda_stream) for q in setups]
     g = kmc.Group(sims, stream=stream.cuda_stream)
     warm = 3
@@ -299,6 +314,8 @@ def run_ensemble(args, stream):
         g.budget(q, warm + args.ensemble_steps)
     g.step(warm)
     g.sync()
+    for q in sims:
+        q.counts()
     l0 = sims[0].launches()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -310,15 +327,81 @@ def run_ensemble(args, stream):
     ms = e0.elapsed_time(e1)
     launches = sims[0].launches() - l0
     total_n = sum(q.n for q in setups)
+    tests = {"box": 0, "tube": 0}
+    psteps = {"box": 0, "tube": 0}
+    for q, sim in zip(setups, sims):
+        recs = sim.counts()
+        if len(recs) != args.ensemble_steps:
+            raise RuntimeError(f"ensemble member {q.name}: {len(recs)} step records, "
+                               f"expected {args.ensemble_steps}")
+        kind = "box" if q.name.startswith("equilibrium") else "tube"
+        tests[kind] += sum(c["pair_tests"] for c in recs)
+        psteps[kind] += q.n * len(recs)
+    secs = ms / 1e3
+    all_tests = tests["box"] + tests["tube"]
+    achieved = all_tests * FLOPS_PER_PAIR_TEST / secs / 1e12
     out = {"runs": len(setups), "particles": total_n, "steps": args.ensemble_steps,
-           "particle_steps_per_s": total_n * args.ensemble_steps / (ms / 1e3),
+           "particle_steps_per_s": total_n * args.ensemble_steps / secs,
            "ms_per_group_step": ms / args.ensemble_steps,
            "kernel_launches_per_group_step": launches / args.ensemble_steps,
+           "pair_tests_per_s": all_tests / secs,
+           "pair_tests_per_particle_step": {k: tests[k] / max(1, psteps[k]) for k in tests},
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_FP32_PEAK_TFLOPS,
+                        "unit": "TFLOP/s", "frac": achieved / ALU_FP32_PEAK_TFLOPS,
+                        "flops_per_pair_test": FLOPS_PER_PAIR_TEST,
+                        "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz"},
            "mix": "seeds 1000-1255, N log-uniform [2^12, 2^18], even: equilibrium box, "
                   "odd: piston tube with u_p in [1, 3]; guarded FP32; one CUDA graph per step"}
     g.close()
     for q in sims:
         q.close()
+    return out
+
+
+def run_blast(args, stream, dev):
+    """The spherical blast at full size (2^27 particles; hot ball of radius 0.1 at 8x
+    the background density and 100x its temperature, background lambda 0.005), state
+    drawn on the device: guarded binary32 for K steps after one, binary64 for one step
+    after one (binary64 runs at about 1/64 of the binary32 rate here), both with pair
+    tests, cells and the speed split's fast-particle share."""
+    import torch
+
+    import paper_1310_3437_gb300 as kmc
+
+    setup = ki.blast_setup(n=args.blast_n, seed=3)
+    out = {"n": setup.n, "d0": setup.d0, "dt": setup.dt, "n_hot": setup.extra["n_hot"]}
+    for prec, name, k in ((kmc.KMC_GUARDED_FP32, "fp32", args.blast_steps),
+                          (kmc.KMC_FP64, "fp64", args.blast_fp64_steps)):
+        if k <= 0:
+            continue
+        params = kmc.params_from_setup(setup, precision=prec)
+        sim = kmc.Simulation(params, init=ki.init_spec(setup), stream=stream.cuda_stream)
+        sim.step(1).sync()  # grows the pair buffer if the first step needs more
+        sim.counts()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(k)
+        e1.record(stream)
+        e1.synchronize()
+        l1 = sim.launches()
+        sim.sync()
+        recs = sim.counts()
+        if len(recs) != k or sim.launches() != l1:
+            raise RuntimeError(f"blast {name}: {len(recs)} step records for {k} steps")
+        ms = e0.elapsed_time(e1)
+        out[name] = {
+            "steps": k, "ms_per_step": ms / k, "particle_steps_per_s": setup.n * k / (ms / 1e3),
+            "pair_tests_per_step": float(np.mean([c["pair_tests"] for c in recs])),
+            "fast_pair_tests_per_step": float(np.mean([c["fast_tests"] for c in recs])),
+            "cells": recs[-1]["cells"],
+            "candidate_pairs_per_step": float(np.mean([c["edges"] for c in recs])),
+            "collisions_per_step": float(np.mean([c["collisions"] for c in recs]))}
+        sim.close()
+        torch.cuda.synchronize(dev)
+    if "fp32" in out and "fp64" in out:
+        out["speedup_fp32_over_fp64"] = out["fp32"]["particle_steps_per_s"] / \
+            out["fp64"]["particle_steps_per_s"]
     return out
 
 
@@ -402,34 +485,99 @@ def run_gpu(args):
         knobs = {k: best[k] for k in knobs}
         tuning = {"chosen": best, "trials": next(iter(tuner.trials.values()))}
 
-    def timed_run(precision, warm, steps, sample_clocks=False, kn=None):
+    def check_window(sim, first_step, steps, launches_before_sync):
+        """The timed steps ran: one step record per step, consecutive from first_step,
+        and nothing left for sim_sync to re-run (an overflowing pair buffer skips the
+        remaining steps on the device and would move their work out of the window)."""
+        recs = sim.counts()
+        got = [c["step"] for c in recs]
+        if got != list(range(first_step, first_step + steps)):
+            raise RuntimeError(f"timed window did not run its {steps} steps: step records "
+                               f"{got[:3]}..{got[-3:]} ({len(got)} records)")
+        sim.sync()
+        if sim.launches() != launches_before_sync:
+            raise RuntimeError("sim_sync re-ran steps of the timed window (pair-buffer overflow)")
+        return recs
+
+    def timed_run(precision, warm, steps, sample_clocks=False, kn=None, min_ms=0.0,
+                  max_windows=1):
+        """warm untimed steps, then windows of exactly `steps` steps, each bracketed by
+        a barrier and a device synchronisation and timed with CUDA events on the
+        simulation's stream; windows repeat until min_ms of timed work (the same
+        number of windows on every rank).  Returns per-window ms (max over ranks)."""
         params = kmc.params_from_setup(setup, precision=precision, **(knobs if kn is None else kn))
         sim = kmc.Simulation(params, dev_arrays, stream=stream.cuda_stream)
         sim.step(warm).sync()
         sim.counts()
-        l0 = sim.launches()
+        step_next = sim.step_index()
         sampler = ClockSampler(dev.index or 0) if sample_clocks else None
         barrier()
         if sampler:
             sampler.start()
             sampler.wait_first_sample()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sim.step(steps)
-        e1.record(stream)
-        e1.synchronize()
-        barrier()
+        windows, counts, launches = [], [], 0
+        nwin = 1
+        while len(windows) < nwin:
+            l0 = sim.launches()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(steps)
+            e1.record(stream)
+            e1.synchronize()
+            barrier()
+            windows.append(max_over_ranks(e0.elapsed_time(e1)))
+            l1 = sim.launches()
+            launches += l1 - l0
+            counts += check_window(sim, step_next, steps, l1)
+            step_next += steps
+            if len(windows) == 1:
+                # the same on every rank: derived from the max-over-ranks time
+                nwin = max(1, min(max_windows, math.ceil(min_ms / max(windows[0], 1e-3))))
         clocks = sampler.stop() if sampler else None
-        ms = max_over_ranks(e0.elapsed_time(e1))
-        sim.sync()
-        launches = sim.launches() - l0
-        counts = sim.counts()
-        return sim, ms, counts, launches, clocks
+        return sim, windows, counts, launches, clocks
+
+    def precision_check(steps):
+        """Guarded binary32 (the timed knobs) and binary64 from the same state, one step
+        at a time: sorted candidate-pair lists, partners and step counts compared in
+        every step, the whole state after the last (Sec. 2: the criteria and the
+        closest partner fix the list, so the pre-test precision must not change it)."""
+        a = kmc.Simulation(kmc.params_from_setup(setup, precision=kmc.KMC_GUARDED_FP32, **knobs),
+                           dev_arrays, stream=stream.cuda_stream)
+        b = kmc.Simulation(kmc.params_from_setup(setup, precision=kmc.KMC_FP64), dev_arrays,
+                           stream=stream.cuda_stream)
+        res = {"steps": steps, "edges_identical": True, "partners_identical": True,
+               "counts_identical": True, "edge_sha256_16": []}
+        for _ in range(steps):
+            a.step(1).sync()
+            b.step(1).sync()
+            ea, eb = a.edges(), b.edges()
+            ha = hashlib.sha256(np.ascontiguousarray(ea).tobytes()).hexdigest()[:16]
+            hb = hashlib.sha256(np.ascontiguousarray(eb).tobytes()).hexdigest()[:16]
+            res["edge_sha256_16"].append(ha)
+            res["edges_identical"] &= ha == hb and ea.shape == eb.shape
+            res["partners_identical"] &= bool(np.array_equal(a.partners(), b.partners()))
+            ca, cb = a.counts(), b.counts()
+            res["counts_identical"] &= [(c["collisions"], c["edges"], c["round_pairs"]) for c in ca] == \
+                [(c["collisions"], c["edges"], c["round_pairs"]) for c in cb]
+        ba = torch.empty(52 * n, dtype=torch.uint8, device=dev)
+        bb = torch.empty_like(ba)
+        a.state_device(ba)
+        b.state_device(bb)
+        torch.cuda.synchronize(dev)
+        res["state_identical"] = bool(torch.equal(ba, bb))
+        res["candidate_pairs_per_step"] = float(eb.shape[0])
+        a.close()
+        b.close()
+        del ba, bb
+        return res
 
     # ---- guarded binary32 (headline) ----
-    sim32, ms32, counts32, launches32, clocks = timed_run(kmc.KMC_GUARDED_FP32, args.warmup,
-                                                          args.steps, sample_clocks=True)
+    sim32, windows32, counts32, launches32, clocks = timed_run(
+        kmc.KMC_GUARDED_FP32, args.warmup, args.steps, sample_clocks=True,
+        min_ms=args.min_timed_s * 1e3, max_windows=args.max_windows)
+    ms32 = float(np.median(windows32))
     value = aggregate_rate(n * args.steps, world, ms32)
     # per-phase times of the next steps, CUDA events on the simulation's stream
     tsteps = max(3, min(args.steps, 10))
@@ -450,18 +598,17 @@ def run_gpu(args):
 
     # ---- binary64 path on the same workload (fewer steps: ~70x slower arithmetic) ----
     fp64 = None
+    check = None
     if not args.skip_fp64:
         k64 = max(1, min(args.steps, args.fp64_steps))
         # the binary64 path with its own defaults (the tuner tunes the binary32 path; a
         # binary32-only kernel choice would not carry over)
         kn64 = {"search_kernel": 0, "stencil": 1, "cell_scale": 1.0, "split_min_occ": 0.0}
-        sim64, ms64, counts64, _, _ = timed_run(kmc.KMC_FP64, args.warmup, k64, kn=kn64)
-        v64 = world * n * k64 / (ms64 / 1e3)
-        same = [(c["collisions"], c["edges"]) for c in counts64] == \
-               [(c["collisions"], c["edges"]) for c in counts32[:k64]]
-        fp64 = {"value": v64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
-                "same_counts_as_fp32": bool(same)}
+        sim64, win64, counts64, _, _ = timed_run(kmc.KMC_FP64, args.warmup, k64, kn=kn64)
+        v64 = world * n * k64 / (win64[0] / 1e3)
+        fp64 = {"value": v64, "unit": UNIT, "steps": k64, "ms_per_step": win64[0] / k64}
         sim64.close()
+        check = precision_check(args.check_steps)
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -515,6 +662,9 @@ def run_gpu(args):
     paper = None
     if not args.skip_paper and rank == 0:
         paper = run_paper_workloads(args, stream, dev)
+    blast = None
+    if not args.skip_blast and rank == 0:
+        blast = run_blast(args, stream, dev)
 
     if rank != 0:
         if world > 1:
@@ -580,8 +730,16 @@ def run_gpu(args):
                    "lambda": 0.02, "d0": setup.d0, "dt": setup.dt, "u_p": setup.piston_u,
                    "precision": "guarded-fp32", "l2": "inputs larger than L2 (state ~1.9 GB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
+        "timed_windows": {"windows": len(windows32), "steps_per_window": args.steps,
+                          "ms_per_window": windows32, "reported": "median window",
+                          "checked": "each window left exactly its steps' records, "
+                                     "consecutive, with no re-run at sync"},
         "fp64": fp64,
         "speedup_fp32_over_fp64": (value / fp64["value"]) if fp64 else None,
+        "fp32_fp64_edges_identical": (bool(check["edges_identical"] and check["partners_identical"]
+                                           and check["counts_identical"] and check["state_identical"])
+                                      if check else None),
+        "precision_check": check,
         "roofline": roofline,
         "roofline_sort": roofline_sort,
         "phase_ms_per_step": {k: ph[k] / max(1, ph["steps"]) for k in ("sort", "search", "match", "push")},
@@ -594,6 +752,7 @@ def run_gpu(args):
         "serve": serve,
         "ensemble": ensemble,
         "paper_workloads": paper,
+        "blast": blast,
         "tuning": tuning,
         "gpu_launches": int(launches32),
         "clocks": clocks,
@@ -602,6 +761,8 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    if check is not None and not line["fp32_fp64_edges_identical"]:
+        raise SystemExit("guarded binary32 and binary64 runs differ (precision_check)")
 
 
 def main():
@@ -615,6 +776,11 @@ def main():
                     help="tube: the 2^24 piston tube; sample: its 8x0.25x0.25 cross-section "
                          "(2^20 particles, same density), for profiling")
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--check-steps", type=int, default=8,
+                    help="steps of the binary32 vs binary64 pair-list comparison")
+    ap.add_argument("--min-timed-s", type=float, default=2.0,
+                    help="repeat the K-step timed window until this much timed work")
+    ap.add_argument("--max-windows", type=int, default=40)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
@@ -627,14 +793,17 @@ def main():
                     help="skip the paper's timing workloads (10^8 3D, 4e7 2D particles)")
     ap.add_argument("--paper-steps", type=int, default=10)
     ap.add_argument("--no-tune", action="store_true")
-    ap.add_argument("--ensemble-steps", type=int, default=100)
-    ap.add_argument("--serve-requests", type=int, default=200,
+    ap.add_argument("--ensemble-steps", type=int, default=500)
+    ap.add_argument("--skip-blast", action="store_true",
+                    help="skip the full-size spherical blast (2^27 particles)")
+    ap.add_argument("--blast-n", type=int, default=1 << 27)
+    ap.add_argument("--blast-steps", type=int, default=5)
+    ap.add_argument("--blast-fp64-steps", type=int, default=1)
+    ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests of the serving stream (the full stream is 10000)")
-    ap.add_argument("--serve-n-hi", type=int, default=1 << 18,
-                    help="largest request size (the full stream uses 2^22)")
-    ap.add_argument("--serve-steps-lo", type=int, default=20)
-    ap.add_argument("--serve-steps-hi", type=int, default=200,
-                    help="the full stream uses steps in [100, 2000]")
+    ap.add_argument("--serve-n-hi", type=int, default=1 << 22)
+    ap.add_argument("--serve-steps-lo", type=int, default=100)
+    ap.add_argument("--serve-steps-hi", type=int, default=2000)
     ap.add_argument("--serve-budget-gb", type=float, default=160.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -42,7 +42,9 @@ extern "C" {
 #define KMC_EINVAL (-1)    /* bad argument or parameter */
 #define KMC_ENOMEM (-2)    /* device allocation failed */
 #define KMC_ECUDA (-3)     /* a CUDA runtime call failed */
-#define KMC_ETIMEOUT (-4)  /* a bounded device-side wait ran out */
+#define KMC_ETIMEOUT (-4)  /* a bounded device-side wait ran out: a tile of the cell
+                              scan waited about a second for its predecessor's sum (the
+                              step's results are void; sim_sync reports it) */
 #define KMC_EOVERFLOW (-5) /* a buffer capacity was exceeded and could not grow */
 #define KMC_ESTATE (-6)    /* call not allowed in the current state */
 #define KMC_ERANDOM (-7)   /* 128 rejected sphere-point draws (probability ~1e-43) */
@@ -61,7 +63,12 @@ extern "C" {
 #define KMC_GUARDED_FP32 1  /* binary32 pre-tests with proven guard bands, binary64
                                re-check of the survivors: identical pair lists */
 
-/* ---- observables (sim_observe) ------------------------------------------ */
+/* ---- observables (sim_observe) ------------------------------------------
+ * The paper writes its output after the particles are sorted into their bins
+ * (Sec. 2, "Initial Simulation Setup") and only at a fixed interval of simulated
+ * time, kept by a time-step counter (Sec. 3, "Algorithm Optimization"): here the
+ * state, partners and candidate pairs describe the last completed step, per-step
+ * counts are kept for every step, and the profiles every profile_every steps. */
 #define KMC_OBS_STATE 1    /* 6 x n binary64 (x,y,z,vx,vy,vz) then n uint32 last
                               partner id (KMC_NONE if none): 52 n bytes */
 #define KMC_OBS_PARTNERS 2 /* n uint32: partner id of each particle in the last
@@ -69,7 +76,12 @@ extern "C" {
 #define KMC_OBS_COUNTS 3   /* kmc_step_counts records of the steps completed since
                               the previous COUNTS call (oldest first) */
 #define KMC_OBS_PROFILES 4 /* profile snapshots taken since the previous PROFILES
-                              call: per snapshot, profile_bins x 7 binary64 */
+                              call: per snapshot, profile_bins x 7 binary64 (count,
+                              sum vx, vy, vz, sum vx^2, vy^2, vz^2 over the particles in
+                              the gas with x in the bin).  The sums are exact fixed-point
+                              sums rounded once; a bin holding a velocity component with
+                              |v| >= 46341 (a square >= 2^31, beyond the fixed point's
+                              range) has NaN for its six sums, its count stays exact */
 #define KMC_OBS_EDGES 5    /* candidate pairs of the last completed step as uint32
                               (id_lo, id_hi) pairs, unordered list */
 #define KMC_OBS_STEP 6     /* one uint64: absolute index of the next step */
@@ -81,6 +93,15 @@ extern "C" {
                               of timed steps, then the milliseconds of the main search
                               kernel alone (the one that searches the slow population:
                               row, cell or particle search), part of the search phase */
+#define KMC_OBS_VMAX 9     /* one binary64: the largest particle speed of the current
+                              state, sqrt(max ((vx*vx + vy*vy) + vz*vz)) over the particles
+                              in the gas, each operation correctly rounded (0 for an
+                              empty gas).  Sec. 2 derives the time step from the maximum
+                              speed and Sec. 4 reduces it over all domains; here it sizes
+                              the cells (d0 + 2 v_max dt) and the speed split */
+#define KMC_OBS_DOMAINS 10 /* a decomposition (sim_create_domains): 2 x ndomains uint32,
+                              the particles each domain owned in the last step, then
+                              the ghosts it held (Sec. 4: the first phase's counts) */
 
 #define KMC_NONE 0xFFFFFFFFu
 #define KMC_ABSORBED 0xFFFFFFFEu /* last-partner value of a particle that has left
@@ -100,6 +121,9 @@ extern "C" {
                                   z axis an extent below 3 cells (one cell: a 9-cell
                                   stencil) and reflecting walls.  sim_create fails with
                                   KMC_EINVAL if a vz is not 0. */
+#define KMC_FLAG_SCAN_WAIT_TEST 8u /* test of the failure path only: the cell scan's tiles
+                                  wait for a status word that is never written, run into
+                                  their bounded wait and sim_sync returns KMC_ETIMEOUT */
 
 /* ---- search kernels (kmc_params.search_kernel) ----------------------------- */
 #define KMC_SEARCH_AUTO 0      /* per step: warp-per-cell search when cells are well
@@ -226,6 +250,28 @@ typedef struct kmc_init {
  * 1e-20 per particle), KMC_ENOMEM, KMC_ECUDA.  On error *out is NULL. */
 int sim_create_init(const kmc_params* p, const kmc_init* init, void* stream, kmc_sim** out);
 
+/* Create a simulation decomposed into ndomains (1..64) equal slabs along x, the
+ * domain decomposition of Sec. 4 ("Hybrid Simulations"), run on this GPU.  Domain k
+ * owns the particles with X_k <= x < X_(k+1), X_k = k X / ndomains (X the box length,
+ * or the larger of it and piston_x0 on a reflecting x axis), and holds as ghosts the
+ * particles within the reach d0 + 2 v_max dt of its slab.  Every step runs the
+ * paper's four communication phases between the domains: ghosts (with their counts),
+ * the global v_max, the collision partners of ghosts in every matching round, and the
+ * migration of particles that crossed a cut.  Results -- state, partners, candidate
+ * pairs, step counts -- are bit for bit those of sim_create on the same input; the
+ * decomposition changes the work, never a result.  sim_step, sim_sync, sim_observe
+ * (STATE, PARTNERS, EDGES, COUNTS, STEP, VMAX, LAUNCHES, DOMAINS) and sim_destroy
+ * apply; it cannot join a group and keeps no profiles.  The exchanges go through
+ * id-indexed device buffers on this GPU (no inter-GPU transport).  Arguments as
+ * sim_create.  Errors: KMC_EINVAL (as sim_create, and: ndomains outside 1..64, an
+ * absorbing axis, profile_bins != 0), KMC_ENOMEM, KMC_ECUDA; sim_sync returns
+ * KMC_EOVERFLOW if a domain's candidate-pair buffer overflowed (no regrowth: each
+ * domain's buffer holds edge_cap pairs, by default one per particle).  Device memory: about ndomains times that of
+ * sim_create, plus 4 ndomains + 70 bytes per particle. */
+int sim_create_domains(const kmc_params* p, uint32_t ndomains, const double* x, const double* y,
+                       const double* z, const double* vx, const double* vy, const double* vz,
+                       const uint32_t* last, void* stream, kmc_sim** out);
+
 /* Enqueue nsteps time steps (Sec. 2: sort, detect, collide, stream, boundaries).
  * Errors: KMC_ESTATE if the simulation belongs to a group, KMC_ECUDA. */
 int sim_step(kmc_sim* s, uint32_t nsteps);
@@ -236,10 +282,12 @@ int sim_step(kmc_sim* s, uint32_t nsteps);
  * Errors: KMC_ERANDOM, KMC_EOVERFLOW, KMC_ENOMEM, KMC_ECUDA. */
 int sim_sync(kmc_sim* s);
 
-/* Copy an observable (KMC_OBS_*) into dst (host or device, dst_bytes long).  The
- * copy is ordered after the enqueued steps; for a host dst the call waits.
- * Returns the number of items written (records, snapshots, pairs, or 1) or a
- * negative status: KMC_EINVAL (unknown observable, dst too small). */
+/* Copy an observable (KMC_OBS_*) into dst (host or device, dst_bytes long): the
+ * paper's output (Sec. 2: after the sort; Sec. 3: at a fixed interval of simulated
+ * time).  The copy is ordered after the enqueued steps; for a host dst the call
+ * waits.  Returns the number of items written (records, snapshots, pairs, or 1) or
+ * a negative status: KMC_EINVAL (unknown observable, dst too small), KMC_ENOMEM
+ * (a staging buffer for a host dst), KMC_ECUDA. */
 int64_t sim_observe(kmc_sim* s, int what, void* dst, size_t dst_bytes);
 
 /* Diagnostics: with enable != 0, later sim_step calls launch the kernels one by one
@@ -266,20 +314,27 @@ size_t sim_bytes_required(const kmc_params* p);
  * binary64 values as KMC_OBS_PROFILES -- per x bin over [0, range): count, sum vx,
  * sum vy, sum vz, sum vx^2, sum vy^2, sum vz^2 -- for the n particles in the caller's
  * device arrays x, vx, vy, vz (any order), into the caller's device array out.
- * Scratch: a fixed array of 256 x 19 int64 counters (38,912 bytes) compiled into
- * the library; every GPU that loads the library holds it until the process exits.
- * bins above 256 (or below 1), range <= 0, NULL or host pointers: KMC_EINVAL, with a
- * line on stderr.  The first call on a device, with that device current, looks up
- * the array's device address; make that first call before any stream capture.
- * Calls share the array and it keeps the last call's contents (each call clears the
- * counters it uses first); calls that overlap on the GPU race and return wrong
- * sums, so order them on one stream.  Enqueued on stream; out is valid after the
- * stream synchronises.  Calls no cudaMalloc, cudaFree or allocating library routine. */
+ * Limits: n < 2^31 (the fixed-point digit sums are int64); a bin holding a velocity
+ * component with |v| >= 46341 (a square >= 2^31) gets NaN for its six sums, as in
+ * KMC_OBS_PROFILES.  Scratch: a fixed array of 256 x 20 int64 counters (40,960
+ * bytes) compiled into the library; every GPU that loads the library holds it until
+ * the process exits.  bins above 256 (or below 1), range <= 0, n >= 2^31, NULL or
+ * host pointers, memory of another device, or a stream of another device:
+ * KMC_EINVAL, with a line on stderr.  The first call on a device, with that device
+ * current, looks up the array's device address; make that first call before any
+ * stream capture.  Calls share the array and it keeps the last call's contents
+ * (each call clears the counters it uses first); calls that overlap on the GPU race
+ * and return wrong sums, so order them on one stream.  Enqueued on stream; out is
+ * valid after the stream synchronises.  Calls no cudaMalloc, cudaFree or
+ * allocating library routine. */
 int sim_profile_static(const double* x, const double* vx, const double* vy, const double* vz,
                        uint32_t n, int32_t bins, double range, double* out, void* stream);
 
 /* ---- batching ------------------------------------------------------------ */
-/* A group steps many simulations of uneven size with one launch per kernel for
+/* The paper runs one simulation per job, split over nodes (Sec. 4); a group is the
+ * GPU's form of many independent jobs at once (no exchange between members, so
+ * each member's results equal its run alone).
+ * A group steps many simulations of uneven size with one launch per kernel for
  * all of them; the per-step launch sequence is captured in a CUDA graph.  All
  * members must share precision and stencil.  Members keep their own state and can
  * still be observed; sim_step on a member returns KMC_ESTATE.

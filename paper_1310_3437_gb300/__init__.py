@@ -41,6 +41,8 @@ KMC_OBS_EDGES = 5
 KMC_OBS_STEP = 6
 KMC_OBS_LAUNCHES = 7
 KMC_OBS_PHASE_MS = 8
+KMC_OBS_VMAX = 9
+KMC_OBS_DOMAINS = 10
 
 KMC_NONE = 0xFFFFFFFF
 KMC_ABSORBED = 0xFFFFFFFE
@@ -48,6 +50,7 @@ KMC_ABSORBED = 0xFFFFFFFE
 KMC_FLAG_NO_SPLIT = 1
 KMC_FLAG_FORCE_SPLIT = 2
 KMC_FLAG_PLANAR = 4
+KMC_FLAG_SCAN_WAIT_TEST = 8
 
 KMC_INIT_MAXWELL = 1
 KMC_INIT_EQUAL_SPEED = 2
@@ -120,6 +123,9 @@ def lib():
             L.sim_create_init.argtypes = [C.POINTER(kmc_params), C.POINTER(kmc_init), _P,
                                           C.POINTER(_P)]
             L.sim_create_init.restype = C.c_int
+            L.sim_create_domains.argtypes = [C.POINTER(kmc_params), C.c_uint32, _P, _P, _P, _P,
+                                             _P, _P, _P, _P, C.POINTER(_P)]
+            L.sim_create_domains.restype = C.c_int
             L.sim_step.argtypes = [_P, C.c_uint32]
             L.sim_step.restype = C.c_int
             L.sim_sync.argtypes = [_P]
@@ -150,6 +156,9 @@ def lib():
             L.sim_group_sync.restype = C.c_int
             L.sim_group_destroy.argtypes = [_P]
             L.sim_group_destroy.restype = C.c_int
+            L.sim_profile_static.argtypes = [_P, _P, _P, _P, C.c_uint32, C.c_int32, C.c_double,
+                                             _P, _P]
+            L.sim_profile_static.restype = C.c_int
             _lib = L
     return _lib
 
@@ -185,6 +194,15 @@ def sim_create_mixture(params: kmc_params, x, y, z, vx, vy, vz, last, species, n
 def sim_create_init(params: kmc_params, init: kmc_init, stream=None):
     out = _P()
     rc = lib().sim_create_init(C.byref(params), C.byref(init), stream, C.byref(out))
+    _check(rc, None)
+    return out.value
+
+
+def sim_create_domains(params: kmc_params, ndomains: int, x, y, z, vx, vy, vz, last=None,
+                       stream=None):
+    out = _P()
+    rc = lib().sim_create_domains(C.byref(params), int(ndomains), x, y, z, vx, vy, vz, last,
+                                  stream, C.byref(out))
     _check(rc, None)
     return out.value
 
@@ -265,6 +283,14 @@ def sim_group_sync(group):
 
 def sim_group_destroy(group):
     return lib().sim_group_destroy(group)
+
+
+def sim_profile_static(x, vx, vy, vz, n: int, bins: int, range_: float, out, stream=None):
+    """Allocation-free x-profile of caller-owned device arrays (pointers)."""
+    rc = lib().sim_profile_static(x, vx, vy, vz, int(n), int(bins), float(range_), out, stream)
+    if rc < 0:
+        raise KmcError(int(rc), "sim_profile_static rejected its arguments (see stderr)")
+    return rc
 
 
 from .sim import Simulation, Group, params_from_setup  # noqa: E402,F401

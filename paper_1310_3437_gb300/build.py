@@ -30,6 +30,7 @@ SOURCES = {
     "kmc_api.cu": ["-fmad=false"],
     "kmc_noalloc.cu": ["-fmad=false"],
     "kmc_init.cu": ["-fmad=false"],
+    "kmc_domain.cu": ["-fmad=false"],
 }
 
 

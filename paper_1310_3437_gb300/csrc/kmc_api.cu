@@ -78,7 +78,24 @@ struct kmc_sim {
   // group's issued-step count then, so that a sync can tell how many of the group's
   // steps this member missed after an overflow
   uint64_t sync_step = 0, issued_base = 0;
+  // a decomposition into x slabs (sim_create_domains): the steps run on its domains
+  struct Domains* dom = nullptr;
   std::string err;
+};
+
+// Domain decomposition (Sec. 4): the member simulations are the domains, stepped as
+// one batch; the exchange buffers live in DomainDev (kmc_domain.cu).
+struct Domains {
+  std::vector<kmc_sim*> members;
+  Plan plan;
+  DomainDev h{};
+  DomainDev* d = nullptr;
+  void* state = nullptr;  // id-order state, 52 n bytes (the layout of KMC_OBS_STATE)
+  std::vector<void*> allocs;
+  cudaGraphExec_t graph = nullptr;
+  bool graph_tried = false;
+  int launches_per_step = 0;
+  uint64_t hist_read = 0;
 };
 
 struct kmc_group {
@@ -151,7 +168,11 @@ size_t bytes_for(const Sizes& z) {
 int validate(const kmc_params* p, std::string& err) {
   if (!p) { err = "params is NULL"; return KMC_EINVAL; }
   if (p->n == 0) { err = "n must be >= 1"; return KMC_EINVAL; }
-  if (p->flags & ~(uint32_t)(KMC_FLAG_NO_SPLIT | KMC_FLAG_FORCE_SPLIT | KMC_FLAG_PLANAR)) { err = "unknown flags"; return KMC_EINVAL; }
+  if (p->flags & ~(uint32_t)(KMC_FLAG_NO_SPLIT | KMC_FLAG_FORCE_SPLIT | KMC_FLAG_PLANAR |
+                             KMC_FLAG_SCAN_WAIT_TEST)) {
+    err = "unknown flags";
+    return KMC_EINVAL;
+  }
   if ((p->flags & KMC_FLAG_NO_SPLIT) && (p->flags & KMC_FLAG_FORCE_SPLIT)) { err = "conflicting split flags"; return KMC_EINVAL; }
   for (int a = 0; a < 3; ++a) {
     if (!(p->box[a] > 0.0)) { err = "box extents must be > 0"; return KMC_EINVAL; }
@@ -169,7 +190,8 @@ int validate(const kmc_params* p, std::string& err) {
   if (p->profile_bins > 0 && !(p->profile_range > 0.0)) { err = "profile_range must be > 0"; return KMC_EINVAL; }
   if (p->cell_scale != 0.0 && !(p->cell_scale >= 1.0)) { err = "cell_scale must be 0 or >= 1"; return KMC_EINVAL; }
   if (p->bc[0] == KMC_REFLECT && !(p->piston_x0 > 0.0)) { err = "reflecting x axis needs piston_x0 > 0"; return KMC_EINVAL; }
-  if (p->n > 0x7FFFFFFFu) { err = "n too large"; return KMC_EINVAL; }
+  // the cell tables hold 2 n + 4096 keys in uint32 indices
+  if (p->n > 0x7FFFF000u) { err = "n too large (at most 2^31 - 4096)"; return KMC_EINVAL; }
   if (p->search_kernel < 0 || p->search_kernel > 3) { err = "bad search_kernel"; return KMC_EINVAL; }
   if (p->split_min_occ < 0.0) { err = "split_min_occ must be >= 0"; return KMC_EINVAL; }
   return KMC_OK;
@@ -256,8 +278,10 @@ int build_plan(Plan& P, const std::vector<kmc_sim*>& sims, cudaStream_t st, std:
     if (h.absorb) P.L.absorb = true;
     if (h.mix) P.L.mix = true;
   }
-  size_t scratch = (size_t)sc[m] + 1;
-  size_t words = 3 * (size_t)(m + 1) + scratch;
+  // prefixes (3 (m + 1) words, padded to an even count), the scan's two control
+  // words, then one 64-bit status word per scan tile
+  const size_t head = (3 * (size_t)(m + 1) + 1) & ~(size_t)1;
+  size_t words = head + 2 + 2 * ((size_t)sc[m] + 1);
   if (cudaMalloc(&P.d_table, sizeof(SimDev*) * m) != cudaSuccess ||
       cudaMalloc(&P.d_pre, words * sizeof(uint32_t)) != cudaSuccess) {
     cudaGetLastError();
@@ -270,6 +294,7 @@ int build_plan(Plan& P, const std::vector<kmc_sim*>& sims, cudaStream_t st, std:
   std::copy(sc.begin(), sc.end(), host.begin() + (m + 1));
   std::copy(pr.begin(), pr.end(), host.begin() + 2 * (m + 1));
   KCHECK(cudaMemcpyAsync(P.d_table, table.data(), sizeof(SimDev*) * m, cudaMemcpyHostToDevice, st), err);
+  KCHECK(cudaMemsetAsync(P.d_pre, 0, words * sizeof(uint32_t), st), err);
   KCHECK(cudaMemcpyAsync(P.d_pre, host.data(), host.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st), err);
   KCHECK(cudaStreamSynchronize(st), err);
   LaunchPlan& L = P.L;
@@ -278,7 +303,8 @@ int build_plan(Plan& P, const std::vector<kmc_sim*>& sims, cudaStream_t st, std:
   L.b.ptile = P.d_pre;
   L.b.stile_c = P.d_pre + (m + 1);
   L.b.prtile = P.d_pre + 2 * (m + 1);
-  L.b.tile_sums = P.d_pre + 3 * (m + 1);
+  L.b.scan_ctl = P.d_pre + head;
+  L.b.tile_status = reinterpret_cast<unsigned long long*>(P.d_pre + head + 2);
   L.ptiles = pt[m];
   L.stiles_c = sc[m];
   L.prtiles = pr[m];
@@ -414,6 +440,7 @@ int recover_overflow(kmc_sim* s, Dyn& dy, cudaStream_t st) {
 int status_code(uint32_t status, std::string& err) {
   if (status & ST_RANDOM) { err = "128 rejected sphere-point draws"; return KMC_ERANDOM; }
   if (status & ST_CELL_OVERFLOW) { err = "cell grid exceeds capacity"; return KMC_EOVERFLOW; }
+  if (status & ST_SCAN_WAIT) { err = "a scan tile's wait for its predecessor ran out"; return KMC_ETIMEOUT; }
   if (status & ST_EDGE_OVERFLOW) { err = "candidate-pair buffer overflow"; return KMC_EOVERFLOW; }
   return KMC_OK;
 }
@@ -456,6 +483,15 @@ int sim_destroy(kmc_sim* s) {
   if (!s) return KMC_OK;
   if (s->group) sim_group_remove(s->group, s);
   cudaStreamSynchronize(s->stream);
+  if (s->dom) {
+    Domains* D = s->dom;
+    for (kmc_sim* m : D->members) sim_destroy(m);
+    if (D->graph) cudaGraphExecDestroy(D->graph);
+    free_plan(D->plan);
+    for (void* q : D->allocs) cudaFree(q);  // the device descriptor D->d is one of them
+    delete D;
+    s->dom = nullptr;
+  }
   free_plan(s->solo);
   for (void* q : s->allocs) cudaFree(q);
   s->allocs.clear();
@@ -561,6 +597,7 @@ int create_impl(const kmc_params* p, const double* const* src6, const uint32_t* 
   h.search_kernel = p->search_kernel;
   h.split_ok = (p->flags & KMC_FLAG_NO_SPLIT) ? 0 : ((p->flags & KMC_FLAG_FORCE_SPLIT) ? 2 : 1);
   h.planar = (p->flags & KMC_FLAG_PLANAR) ? 1 : 0;
+  h.scan_wait_test = (p->flags & KMC_FLAG_SCAN_WAIT_TEST) ? 1 : 0;
   h.absorb = (p->bc[0] == KMC_ABSORB || p->bc[1] == KMC_ABSORB || p->bc[2] == KMC_ABSORB) ? 1 : 0;
   h.mix = mix ? 1 : 0;
   h.mix_n = mix ? (int32_t)mix->nspecies : 0;
@@ -712,6 +749,282 @@ int create_impl(const kmc_params* p, const double* const* src6, const uint32_t* 
   return KMC_OK;
 }
 
+// ---- domain decomposition (Sec. 4) ------------------------------------------ //
+template <typename T>
+int dom_alloc(Domains* D, T** out, size_t count, std::string& err) {
+  void* ptr = nullptr;
+  const cudaError_t e = cudaMalloc(&ptr, std::max<size_t>(count * sizeof(T), 16));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    err = std::string("cudaMalloc failed: ") + cudaGetErrorString(e);
+    return KMC_ENOMEM;
+  }
+  D->allocs.push_back(ptr);
+  *out = (T*)ptr;
+  return KMC_OK;
+}
+
+int dom_create(const kmc_params* p, uint32_t ndom, const double* const* src6, const uint32_t* last,
+               void* stream, kmc_sim** out) {
+  if (out) *out = nullptr;
+  g_create_error.clear();
+  int rc = validate(p, g_create_error);
+  if (rc) return rc;
+  if (ndom < 1 || ndom > (uint32_t)kMaxDomains) { g_create_error = "ndomains must be in 1..64"; return KMC_EINVAL; }
+  for (int a = 0; a < 3; ++a)
+    if (p->bc[a] == KMC_ABSORB) { g_create_error = "a decomposition has no absorbing walls"; return KMC_EINVAL; }
+  if (p->profile_bins != 0) { g_create_error = "a decomposition keeps no profiles (profile_bins must be 0)"; return KMC_EINVAL; }
+  if (!out || !src6[0] || !src6[1] || !src6[2] || !src6[3] || !src6[4] || !src6[5]) {
+    g_create_error = "NULL array or output pointer";
+    return KMC_EINVAL;
+  }
+  kmc_sim* s = new (std::nothrow) kmc_sim();
+  if (!s) { g_create_error = "out of host memory"; return KMC_ENOMEM; }
+  Domains* D = new (std::nothrow) Domains();
+  if (!D) { delete s; g_create_error = "out of host memory"; return KMC_ENOMEM; }
+  s->dom = D;
+  s->p = *p;
+  s->h.n = p->n;
+  s->h.precision = p->precision;
+  s->h.hist_cap = p->history_cap ? p->history_cap : 4096u;
+  if (stream) {
+    s->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete D;
+      delete s;
+      g_create_error = "cudaStreamCreate failed";
+      return KMC_ECUDA;
+    }
+    s->own_stream = true;
+  }
+  auto fail = [&](int code) {
+    g_create_error = s->err.empty() ? g_create_error : s->err;
+    sim_destroy(s);
+    return code;
+  };
+  const size_t n = p->n;
+  cudaStream_t st = s->stream;
+  DomainDev& h = D->h;
+  char* state = nullptr;
+  if ((rc = dom_alloc(D, &state, 52 * n, s->err))) return fail(rc);
+  D->state = state;
+  for (int a = 0; a < 3; ++a) {
+    h.x[a] = (double*)state + (size_t)a * n;
+    h.v[a] = (double*)state + (size_t)(3 + a) * n;
+  }
+  h.last = (uint32_t*)((double*)state + 6 * n);
+  bool ok = true;
+  for (int a = 0; a < 3 && ok; ++a) {
+    ok = cudaMemcpyAsync(h.x[a], src6[a], n * sizeof(double), cudaMemcpyDefault, st) == cudaSuccess &&
+         cudaMemcpyAsync(h.v[a], src6[3 + a], n * sizeof(double), cudaMemcpyDefault, st) == cudaSuccess;
+  }
+  if (ok && last) ok = cudaMemcpyAsync(h.last, last, n * sizeof(uint32_t), cudaMemcpyDefault, st) == cudaSuccess;
+  if (ok && !last) ok = cudaMemsetAsync(h.last, 0xFF, n * sizeof(uint32_t), st) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    s->err = "copying the initial state failed";
+    return fail(KMC_ECUDA);
+  }
+  // the domains: simulations of the whole box over every particle slot (ids 0..n-1),
+  // slots outside the domain absent (the absorbed-particle marker); no speed split
+  // (each step's grid is built afresh from the particles a domain holds)
+  kmc_params q = *p;
+  q.flags = (q.flags & ~(uint32_t)KMC_FLAG_FORCE_SPLIT) | KMC_FLAG_NO_SPLIT;
+  // a domain cannot regrow its candidate-pair buffer mid-run (the others have moved
+  // on): start it at one pair per particle slot unless the caller chose a size
+  if (q.edge_cap == 0) q.edge_cap = std::max<uint32_t>(4096u, p->n);
+  const double* mem6[6] = {h.x[0], h.x[1], h.x[2], h.v[0], h.v[1], h.v[2]};
+  for (uint32_t k = 0; k < ndom; ++k) {
+    kmc_sim* m = nullptr;
+    rc = create_impl(&q, mem6, h.last, nullptr, nullptr, st, &m);
+    if (rc) {
+      s->err = g_create_error;
+      return fail(rc);
+    }
+    D->members.push_back(m);
+    m->h.absorb = 1;
+    const int32_t one = 1;
+    if (cudaMemcpyAsync(&m->d->absorb, &one, sizeof(one), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      cudaGetLastError();
+      s->err = "descriptor update failed";
+      return fail(KMC_ECUDA);
+    }
+  }
+  if ((rc = build_plan(D->plan, D->members, st, s->err))) return fail(rc);
+  h.n = p->n;
+  h.P = (int32_t)ndom;
+  h.periodic_x = p->bc[0] == KMC_PERIODIC ? 1 : 0;
+  h.Lx = p->box[0];
+  const double xmax = p->bc[0] == KMC_REFLECT ? std::max(p->box[0], p->piston_x0) : p->box[0];
+  for (uint32_t k = 0; k <= ndom; ++k) h.X[k] = xmax * (double)k / (double)ndom;
+  h.d0 = p->d0;
+  h.dt = p->dt;
+  h.hist_cap = s->h.hist_cap;
+  if ((rc = dom_alloc(D, &h.owner, n, s->err)) || (rc = dom_alloc(D, &h.bestG, n, s->err)) ||
+      (rc = dom_alloc(D, &h.partnerG, n, s->err)) || (rc = dom_alloc(D, &h.partner_out, n, s->err)) ||
+      (rc = dom_alloc(D, &h.loc, (size_t)ndom * n, s->err)) ||
+      (rc = dom_alloc(D, &h.hist, h.hist_cap, s->err)) || (rc = dom_alloc(D, &D->d, 1, s->err)))
+    return fail(rc);
+  ok = cudaMemsetAsync(h.partner_out, 0xFF, n * sizeof(uint32_t), st) == cudaSuccess &&
+       cudaMemsetAsync(h.bestG, 0xFF, n * sizeof(uint32_t), st) == cudaSuccess &&
+       cudaMemsetAsync(h.partnerG, 0xFF, n * sizeof(uint32_t), st) == cudaSuccess &&
+       cudaMemcpyAsync(D->d, &h, sizeof(DomainDev), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+       cudaStreamSynchronize(st) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    s->err = "initialising the exchange buffers failed";
+    return fail(KMC_ECUDA);
+  }
+  *out = s;
+  return KMC_OK;
+}
+
+int dom_enqueue(Domains* D, cudaStream_t st) {
+  const Plan& P = D->plan;
+  return launch_domain_step(P.L, D->d, D->h.n, P.precision, P.K, P.max_rounds, st);
+}
+
+int dom_step(kmc_sim* s, uint32_t nsteps) {
+  Domains* D = s->dom;
+  cudaStream_t st = s->stream;
+  for (kmc_sim* m : D->members) launch_add_steps(m->d, nsteps, st);
+  s->launches += D->members.size();
+  if (!D->graph_tried) {
+    D->graph_tried = true;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      D->launches_per_step = dom_enqueue(D, st);
+      const cudaError_t e = cudaStreamEndCapture(st, &graph);
+      if (e == cudaSuccess && graph) {
+        if (cudaGraphInstantiate(&D->graph, graph, 0) != cudaSuccess) D->graph = nullptr;
+        cudaGraphDestroy(graph);
+      }
+    }
+    cudaGetLastError();
+  }
+  for (uint32_t i = 0; i < nsteps; ++i) {
+    if (D->graph) {
+      KCHECK(cudaGraphLaunch(D->graph, st), s->err);
+      s->launches += D->launches_per_step;
+    } else {
+      s->launches += dom_enqueue(D, st);
+    }
+  }
+  KCHECK(cudaGetLastError(), s->err);
+  return KMC_OK;
+}
+
+int dom_sync(kmc_sim* s) {
+  KCHECK(cudaStreamSynchronize(s->stream), s->err);
+  for (kmc_sim* m : s->dom->members) {
+    Dyn dy;
+    int rc = read_dyn(m, &dy, s->stream);
+    if (rc) { s->err = m->err; return rc; }
+    if (dy.status) {
+      rc = status_code(dy.status, s->err);
+      if (dy.status & ST_EDGE_OVERFLOW)
+        s->err = "candidate-pair buffer of a domain overflowed: create it with a larger edge_cap";
+      return rc;
+    }
+  }
+  return KMC_OK;
+}
+
+int64_t dom_observe(kmc_sim* s, int what, void* dst, size_t dst_bytes) {
+  Domains* D = s->dom;
+  cudaStream_t st = s->stream;
+  const uint32_t n = D->h.n;
+  int rc;
+  switch (what) {
+    case KMC_OBS_STATE: {
+      const size_t need = (size_t)n * 52;
+      if (dst_bytes < need) { s->err = "dst too small for STATE"; return KMC_EINVAL; }
+      KCHECK(cudaMemcpyAsync(dst, D->state, need, cudaMemcpyDefault, st), s->err);
+      KCHECK(cudaStreamSynchronize(st), s->err);
+      return 1;
+    }
+    case KMC_OBS_PARTNERS: {
+      const size_t need = (size_t)n * sizeof(uint32_t);
+      if (dst_bytes < need) { s->err = "dst too small for PARTNERS"; return KMC_EINVAL; }
+      KCHECK(cudaMemcpyAsync(dst, D->h.partner_out, need, cudaMemcpyDefault, st), s->err);
+      KCHECK(cudaStreamSynchronize(st), s->err);
+      return n;
+    }
+    case KMC_OBS_EDGES: {
+      const uint32_t cap = (uint32_t)std::min<size_t>(dst_bytes / sizeof(uint2), 0xFFFFFFFFu);
+      if ((rc = stage_reserve(s, (size_t)cap * sizeof(uint2) + 16))) return rc;
+      uint32_t* cnt = (uint32_t*)s->stage;
+      uint2* buf = (uint2*)((char*)s->stage + 16);
+      KCHECK(cudaMemsetAsync(cnt, 0, sizeof(uint32_t), st), s->err);
+      launch_domain_edges(D->plan.L, D->d, cap, buf, cnt, st);
+      KCHECK(cudaGetLastError(), s->err);
+      uint32_t count = 0;
+      KCHECK(cudaMemcpyAsync(&count, cnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), s->err);
+      KCHECK(cudaStreamSynchronize(st), s->err);
+      if (count > cap) { s->err = "dst too small for EDGES"; return KMC_EINVAL; }
+      KCHECK(cudaMemcpyAsync(dst, buf, (size_t)count * sizeof(uint2), cudaMemcpyDefault, st), s->err);
+      KCHECK(cudaStreamSynchronize(st), s->err);
+      return count;
+    }
+    case KMC_OBS_COUNTS: {
+      uint64_t hc = 0;
+      KCHECK(cudaMemcpyAsync(&hc, &D->d->hist_count, sizeof(hc), cudaMemcpyDeviceToHost, st), s->err);
+      KCHECK(cudaStreamSynchronize(st), s->err);
+      uint64_t avail = hc - D->hist_read, first = D->hist_read;
+      if (avail > D->h.hist_cap) {
+        first = hc - D->h.hist_cap;
+        avail = D->h.hist_cap;
+      }
+      if (avail > dst_bytes / sizeof(kmc_step_counts)) { s->err = "dst too small for COUNTS"; return KMC_EINVAL; }
+      kmc_step_counts* o = (kmc_step_counts*)dst;
+      for (uint64_t i = 0; i < avail;) {
+        const uint64_t slot = (first + i) % D->h.hist_cap;
+        const uint64_t run = std::min<uint64_t>(avail - i, D->h.hist_cap - slot);
+        KCHECK(cudaMemcpyAsync(o + i, D->h.hist + slot, run * sizeof(kmc_step_counts), cudaMemcpyDefault, st), s->err);
+        i += run;
+      }
+      KCHECK(cudaStreamSynchronize(st), s->err);
+      D->hist_read = hc;
+      return (int64_t)avail;
+    }
+    case KMC_OBS_DOMAINS: {
+      const size_t need = (size_t)2 * D->h.P * sizeof(uint32_t);
+      if (dst_bytes < need) { s->err = "dst too small for DOMAINS"; return KMC_EINVAL; }
+      std::vector<uint32_t> v(2 * D->h.P);
+      KCHECK(cudaMemcpyAsync(v.data(), D->d->owned, D->h.P * sizeof(uint32_t), cudaMemcpyDeviceToHost, st), s->err);
+      KCHECK(cudaMemcpyAsync(v.data() + D->h.P, D->d->ghosts, D->h.P * sizeof(uint32_t), cudaMemcpyDeviceToHost, st), s->err);
+      KCHECK(cudaStreamSynchronize(st), s->err);
+      KCHECK(cudaMemcpy(dst, v.data(), need, cudaMemcpyDefault), s->err);
+      return 2 * D->h.P;
+    }
+    case KMC_OBS_VMAX: {
+      if (dst_bytes < sizeof(double)) { s->err = "dst too small for VMAX"; return KMC_EINVAL; }
+      if ((rc = stage_reserve(s, 16))) return rc;
+      unsigned long long* acc = (unsigned long long*)s->stage;
+      double* val = (double*)((char*)s->stage + 8);
+      launch_domain_vmax(D->d, acc, val, st);
+      KCHECK(cudaGetLastError(), s->err);
+      KCHECK(cudaMemcpyAsync(dst, val, sizeof(double), cudaMemcpyDefault, st), s->err);
+      KCHECK(cudaStreamSynchronize(st), s->err);
+      return 1;
+    }
+    case KMC_OBS_STEP:
+      return sim_observe(D->members[0], what, dst, dst_bytes);
+    case KMC_OBS_LAUNCHES: {
+      if (dst_bytes < sizeof(uint64_t)) { s->err = "dst too small for LAUNCHES"; return KMC_EINVAL; }
+      KCHECK(cudaMemcpy(dst, &s->launches, sizeof(uint64_t), cudaMemcpyDefault), s->err);
+      return 1;
+    }
+    case KMC_OBS_PROFILES:
+      return 0;
+    default:
+      s->err = "observable not available for a decomposition";
+      return KMC_EINVAL;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -732,6 +1045,13 @@ int sim_create_mixture(const kmc_params* p, const double* x, const double* y, co
   return create_impl(p, src, last, nullptr, &m, stream, out);
 }
 
+int sim_create_domains(const kmc_params* p, uint32_t ndomains, const double* x, const double* y,
+                       const double* z, const double* vx, const double* vy, const double* vz,
+                       const uint32_t* last, void* stream, kmc_sim** out) {
+  const double* src6[6] = {x, y, z, vx, vy, vz};
+  return dom_create(p, ndomains, src6, last, stream, out);
+}
+
 int sim_create_init(const kmc_params* p, const kmc_init* init, void* stream, kmc_sim** out) {
   if (out) *out = nullptr;
   if (!init) {
@@ -745,6 +1065,7 @@ int sim_step(kmc_sim* s, uint32_t nsteps) {
   if (!s) return KMC_EINVAL;
   if (s->group) { s->err = "simulation belongs to a group"; return KMC_ESTATE; }
   if (nsteps == 0) return KMC_OK;
+  if (s->dom) return dom_step(s, nsteps);
   int rc = ensure_solo(s);
   if (rc) return rc;
   launch_add_steps(s->d, nsteps, s->stream);
@@ -761,6 +1082,7 @@ int sim_set_timing(kmc_sim* s, int enable) {
 
 int sim_sync(kmc_sim* s) {
   if (!s) return KMC_EINVAL;
+  if (s->dom) return dom_sync(s);
   if (s->group) {
     // the group's sync knows how many group steps a recovering member missed
     const int rc = sim_group_sync(s->group);
@@ -790,6 +1112,7 @@ int sim_sync(kmc_sim* s) {
 int64_t sim_observe(kmc_sim* s, int what, void* dst, size_t dst_bytes) {
   if (!s) return KMC_EINVAL;
   if (!dst) { s->err = "dst is NULL"; return KMC_EINVAL; }
+  if (s->dom) return dom_observe(s, what, dst, dst_bytes);
   cudaStream_t st = sim_work_stream(s);
   uint32_t n = s->h.n;
   bool dev = is_device_ptr(dst);
@@ -901,6 +1224,19 @@ int64_t sim_observe(kmc_sim* s, int what, void* dst, size_t dst_bytes) {
       KCHECK(cudaMemcpy(dst, v, m * sizeof(double), cudaMemcpyDefault), s->err);
       return (int64_t)m;
     }
+    case KMC_OBS_VMAX: {
+      if (dst_bytes < sizeof(double)) { s->err = "dst too small for VMAX"; return KMC_EINVAL; }
+      if ((rc = stage_reserve(s, 16))) return rc;
+      unsigned long long* acc = (unsigned long long*)s->stage;
+      double* val = (double*)((char*)s->stage + 8);
+      launch_vmax_exact(s->d, acc, dev ? (double*)dst : val, st);
+      KCHECK(cudaGetLastError(), s->err);
+      if (!dev) {
+        KCHECK(cudaMemcpyAsync(dst, val, sizeof(double), cudaMemcpyDeviceToHost, st), s->err);
+        KCHECK(cudaStreamSynchronize(st), s->err);
+      }
+      return 1;
+    }
     case KMC_OBS_STEP: {
       if (dst_bytes < sizeof(uint64_t)) { s->err = "dst too small for STEP"; return KMC_EINVAL; }
       Dyn dy;
@@ -924,6 +1260,7 @@ int sim_group_create(kmc_sim* const* sims, uint32_t count, void* stream, kmc_gro
   }
   for (uint32_t i = 0; i < count; ++i) {
     if (!sims[i] || sims[i]->group) { g_create_error = "member NULL or already grouped"; return KMC_EINVAL; }
+    if (sims[i]->dom) { g_create_error = "a decomposition cannot join a group"; return KMC_EINVAL; }
     if (sims[i]->h.precision != sims[0]->h.precision || sims[i]->h.K != sims[0]->h.K) {
       g_create_error = "members must share precision and stencil";
       return KMC_EINVAL;
@@ -958,6 +1295,7 @@ int sim_group_create(kmc_sim* const* sims, uint32_t count, void* stream, kmc_gro
 int sim_group_add(kmc_group* g, kmc_sim* s) {
   if (!g || !s) return KMC_EINVAL;
   if (s->group) { g->err = "simulation already grouped"; return KMC_EINVAL; }
+  if (s->dom) { g->err = "a decomposition cannot join a group"; return KMC_EINVAL; }
   if (g->members.size() >= (size_t)kMaxGroup) { g->err = "group full"; return KMC_EINVAL; }
   if (!g->members.empty() && (s->h.precision != g->members[0]->h.precision || s->h.K != g->members[0]->h.K)) {
     g->err = "members must share precision and stencil";
@@ -1038,7 +1376,7 @@ int sim_group_sync(kmc_group* g) {
           // the group's steps after the overflow skipped this member: it runs the ones
           // it missed since the last sync on its own (within its budget), so that a
           // sync leaves every member where the group's steps should have taken it
-          const uint64_t window = g->issued - s->issued_base;
+          const uint64_t window = g->issued > s->issued_base ? g->issued - s->issued_base : 0;
           const uint64_t taken = dy.step - s->sync_step;
           uint64_t lost = window > taken ? window - taken : 0;
           if (lost > dy.steps_left) lost = dy.steps_left;
@@ -1057,7 +1395,14 @@ int sim_group_sync(kmc_group* g) {
       }
     }
     if (!rerun) {
+      // the next sync counts the group's steps from here for every member, including
+      // one whose recovery failed (its issued_base must not stay above the new count)
       g->issued = 0;
+      for (kmc_sim* s : g->members) {
+        Dyn dy;
+        if (s->issued_base != 0 && read_dyn(s, &dy, g->stream) == KMC_OK) s->sync_step = dy.step;
+        s->issued_base = 0;
+      }
       return worst;
     }
   }

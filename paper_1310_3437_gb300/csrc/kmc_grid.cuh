@@ -107,6 +107,17 @@ __device__ inline double fast_cost(double nfast, double rho, double rf_cells, do
   return nfast * (2.0 * tests + 15.0 * ncol);
 }
 
+// Trial thresholds of the speed split, fractions of the bound V of max |v| (squares
+// rounded down), with their particle counts cleared for the next count.
+__device__ inline void set_split_thresholds(SimDev& s, float vmax2_bound) {
+  const double V = sqrt((double)vmax2_bound) * (1.0 + 0x1p-20);
+  for (int t = 0; t < kSplitTrials; ++t) {
+    const double f = (double)split_frac(t);
+    s.d.split_thr[t] = __double2float_rd(f * V * f * V);
+    s.d.split_cnt[t] = 0;
+  }
+}
+
 // Called by all 32 lanes of a warp: lane t < kSplitTrials estimates the cost of
 // trial threshold t, lane 0 chooses and writes the grid (the others only read).
 __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step, uint32_t lane) {
@@ -208,11 +219,7 @@ __device__ inline void compute_grid(SimDev& s, float vmax2_bound, uint64_t step,
   g.split_t = best;
   g.s1sq = s1sq;
   // trial thresholds for the next step (counted by the push of this step)
-  for (int t = 0; t < kSplitTrials; ++t) {
-    const double f = (double)split_frac(t);
-    s.d.split_thr[t] = __double2float_rd(f * V * f * V);
-    s.d.split_cnt[t] = 0;
-  }
+  set_split_thresholds(s, vmax2_bound);
 
   CellPlan p = plan_cells(ext, (s.d0 + 2.0 * S1 * s.dt) * scale, K,
                           (uint64_t)s.cell_cap / (split ? 2 : 1));

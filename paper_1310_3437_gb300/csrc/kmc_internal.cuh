@@ -20,7 +20,7 @@ constexpr int kProfTile = 8192;     // particles per block in the profile kernel
 constexpr int kEdgeBlock = 256;     // threads per block in edge / adjacency kernels
 constexpr int kSearchBuf = 512;     // per-block shared-memory staging of emitted pairs
 constexpr uint32_t kNone = 0xFFFFFFFFu;
-constexpr int kProfQ = 19;          // int64 counters per profile bin (see kmc_push.cu)
+constexpr int kProfQ = 20;          // int64 counters per profile bin (see profile_add below)
 constexpr int kMaxGroup = 4096;     // simulations per batch
 constexpr int kSplitTrials = 7;     // trial thresholds of the speed split (index 0: none)
 
@@ -34,6 +34,7 @@ enum : uint32_t {
   ST_EDGE_OVERFLOW = 1u << 0,  // candidate-pair buffer too small (host grows it)
   ST_RANDOM = 1u << 1,         // 128 rejected sphere-point draws
   ST_CELL_OVERFLOW = 1u << 2,  // grid key space above capacity (cannot happen: coarsened)
+  ST_SCAN_WAIT = 1u << 3,      // a scan tile waited too long for its predecessor's sum
 };
 
 // Search grid of the current step.  Cells are keyed column-major along x inside a
@@ -151,6 +152,7 @@ struct SimDev {
   uint8_t* species;
   double* sp_mass;
   double* sp_radius;
+  int32_t scan_wait_test;  // KMC_FLAG_SCAN_WAIT_TEST: the scan waits for a word never written
 };
 
 // ---- batch mapping ------------------------------------------------------- //
@@ -160,7 +162,10 @@ struct Batch {
   const uint32_t* ptile;   // prefix of ceil(n / kTile) per simulation
   const uint32_t* stile_c; // prefix of ceil((cell_cap + 2) / kScanTile)
   const uint32_t* prtile;  // prefix of ceil(n / kProfTile)
-  uint32_t* tile_sums;      // scratch for the segmented scans
+  // single-pass segmented scan: per tile a status word (epoch << 34 | state << 32 |
+  // value), and the control words [0] next tile to hand out, [1] current epoch
+  unsigned long long* tile_status;
+  uint32_t* scan_ctl;
 };
 
 __device__ __forceinline__ int find_sim(const uint32_t* prefix, int nsims, uint32_t tile) {
@@ -194,6 +199,108 @@ __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a,
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
 __device__ __forceinline__ double dsqrt(double a) { return __dsqrt_rn(a); }
+
+// ---- fixed-point profile counters ----------------------------------------- //
+// A profile bin keeps kProfQ int64 counters: [0] the particle count, [1 + 3a + c]
+// digit c of sum v_a, [10 + 3a + c] digit c of sum v_a^2, [19] the terms that were
+// out of range.  A term q is |q| 2^64 truncated, split into three 32-bit digits with
+// the sign of q; the digits are summed exactly in int64 (below 2^31 terms per bin),
+// so the sums do not depend on the order of the atomic additions.  A term with
+// |q| >= 2^31 (|v_a| >= 46341 for the squares) does not fit the three digits: it is
+// counted in [19] instead, and the bin's six velocity sums convert to NaN.
+__device__ __forceinline__ bool fx_digits(double q, long long d[3]) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(q);
+  const bool neg = (bits >> 63) != 0;
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  d[0] = d[1] = d[2] = 0;
+  if (ex == 0) return true;      // zero or subnormal: below 2^-64
+  const int sh = ex - 1075 + 64; // |q| 2^64 = man 2^sh
+  if (sh > 42) return false;     // |q| >= 2^31, infinity or NaN
+  const unsigned long long man = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+  unsigned __int128 f;
+  if (sh >= 0) f = (unsigned __int128)man << sh;
+  else if (sh > -64) f = (unsigned __int128)(man >> (-sh));
+  else f = 0;
+  long long d0 = (long long)(uint32_t)f, d1 = (long long)(uint32_t)(f >> 32),
+            d2 = (long long)(uint32_t)(f >> 64);
+  if (neg) { d0 = -d0; d1 = -d1; d2 = -d2; }
+  d[0] = d0; d[1] = d1; d[2] = d2;
+  return true;
+}
+
+// add one particle (velocity v) to the counters q of its bin (shared or global memory)
+__device__ __forceinline__ void profile_add(long long* q, const double v[3]) {
+  atomicAdd((unsigned long long*)&q[0], 1ull);
+  unsigned long long bad = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    long long d[3];
+    if (fx_digits(v[a], d)) {
+      for (int c = 0; c < 3; ++c) atomicAdd((unsigned long long*)&q[1 + 3 * a + c], (unsigned long long)d[c]);
+    } else {
+      ++bad;
+    }
+    if (fx_digits(__dmul_rn(v[a], v[a]), d)) {
+      for (int c = 0; c < 3; ++c) atomicAdd((unsigned long long*)&q[10 + 3 * a + c], (unsigned long long)d[c]);
+    } else {
+      ++bad;
+    }
+  }
+  if (bad) atomicAdd((unsigned long long*)&q[19], bad);
+}
+
+// value k (0: count, 1..3: sum v_a, 4..6: sum v_a^2) of a bin's counters, in binary64:
+// (d2 2^64 + d1 2^32 + d0) 2^-64 from a signed 128-bit total, rounded once; NaN for a
+// velocity sum of a bin with out-of-range terms
+__device__ __forceinline__ double profile_value(const long long* src, int k) {
+  if (k == 0) return (double)src[0];
+  if (src[19] != 0) return __longlong_as_double(0x7FF8000000000000ll);
+  const long long* dg = src + 1 + 3 * (k - 1);
+  const __int128 tot = ((__int128)dg[2] << 64) + ((__int128)dg[1] << 32) + (__int128)dg[0];
+  const bool neg = tot < 0;
+  const unsigned __int128 mag = neg ? (unsigned __int128)(-tot) : (unsigned __int128)tot;
+  const double hi = (double)(unsigned long long)(mag >> 64);
+  const double lo = (double)(unsigned long long)mag;
+  const double val = __dadd_rn(__dmul_rn(hi, 1.0), __dmul_rn(lo, 0x1p-64));
+  return neg ? -val : val;
+}
+
+// Block-aggregated append: one atomic per block on the shared counter (a counter that
+// every warp of the grid hits is a hot spot: its atomics serialise in L2).  Every
+// thread of the block must call it; *also, if given, is advanced by the same total.
+// Returns this thread's first index in the buffer behind *counter.
+__device__ __forceinline__ uint32_t block_append(uint32_t* counter, uint32_t want,
+                                                 uint32_t* also = nullptr) {
+  constexpr int kW = kEdgeBlock / 32;  // blocks of kEdgeBlock threads
+  __shared__ uint32_t wsum[kW], wbase[kW], bbase;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint32_t incl = want;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= (uint32_t)o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t v = lane < (uint32_t)kW ? wsum[lane] : 0u;
+    uint32_t vi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, vi, o);
+      if (lane >= (uint32_t)o) vi += y;
+    }
+    if (lane < (uint32_t)kW) wbase[lane] = vi - v;
+    if (lane == (uint32_t)kW - 1) {
+      bbase = vi ? atomicAdd(counter, vi) : 0u;
+      if (also && vi) atomicAdd(also, vi);
+    }
+  }
+  __syncthreads();
+  const uint32_t r = bbase + wbase[warp] + incl - want;
+  __syncthreads();  // the slots are free for the next call
+  return r;
+}
 
 // ---- Morton column code --------------------------------------------------- //
 __device__ __forceinline__ uint32_t dilate16(uint32_t x) {
@@ -302,6 +409,36 @@ __device__ __forceinline__ int cell_coord(const Grid& g, int k, double x) {
   return cell_coord_f(g, k, d2f_rn(x));
 }
 
+// ---- domain decomposition (kmc_domain.cu) ---------------------------------- //
+constexpr int kMaxDomains = 64;
+constexpr uint32_t kElsewhere = 0xFFFFFFFDu;  // partner of a ghost matched to a particle
+                                              // that its domain does not hold
+
+struct DomainDev {
+  uint32_t n;                   // particles (global ids 0..n-1)
+  int32_t P;                    // domains: x slabs
+  int32_t periodic_x;
+  double Lx;                    // box length along x
+  double X[kMaxDomains + 1];    // domain k owns X[k] <= x < X[k+1] (the last one all above)
+  double d0, dt;
+  // id-order exchange buffers: the state (52 n bytes: x, y, z, vx, vy, vz, last)
+  double* x[3];
+  double* v[3];
+  uint32_t* last;
+  uint8_t* owner;               // domain owning each particle during the current step
+  uint32_t* bestG;              // round's best partner (global id) of each owned particle
+  uint32_t* partnerG;           // round's match (global id) of each owned particle
+  uint32_t* partner_out;        // partner (global id) in the last step, KMC_NONE if none
+  uint32_t* loc;                // P x n: position of each id in each domain (kNone: absent)
+  unsigned long long vmax2_bits;
+  double reach;                 // ghost reach of the step (d0 + 2 v_max dt, widened)
+  uint32_t owned[kMaxDomains], ghosts[kMaxDomains];
+  uint32_t acc_edges, acc_round[4];
+  kmc_step_counts* hist;
+  uint32_t hist_cap;
+  uint64_t hist_count;
+};
+
 // ---- launch helpers (host) ----------------------------------------------- //
 struct LaunchPlan {
   Batch b;
@@ -327,9 +464,19 @@ int launch_search(const LaunchPlan& L, int precision, int K, cudaStream_t st,
 // attribute); called when a launch plan is built, before any capture
 void search_grids(int precision, int K, int num_sms, uint32_t ptiles, LaunchPlan& L);
 int launch_match(const LaunchPlan& L, int max_rounds, cudaStream_t st);
+// the parts of launch_match around the rounds: exact test and candidate lists; collision
+int launch_match_lists(const LaunchPlan& L, cudaStream_t st);
+int launch_collide(const LaunchPlan& L, cudaStream_t st);
 int launch_push(const LaunchPlan& L, cudaStream_t st);
 int launch_init_grid(const LaunchPlan& L, cudaStream_t st);
 int launch_cell_scan(const LaunchPlan& L, cudaStream_t st);
+
+// one step of a domain decomposition (the members of L are its domains, in order)
+int launch_domain_step(const LaunchPlan& L, DomainDev* D, uint32_t n, int precision, int K,
+                       int max_rounds, cudaStream_t st);
+void launch_domain_edges(const LaunchPlan& L, DomainDev* D, uint32_t cap, uint2* out,
+                         uint32_t* count, cudaStream_t st);
+void launch_domain_vmax(const DomainDev* D, unsigned long long* acc, double* out, cudaStream_t st);
 
 // observe helpers
 void launch_gather_state(SimDev* d, uint32_t n, void* out, cudaStream_t st);
@@ -339,6 +486,8 @@ void launch_profile_convert(SimDev* d, uint32_t first, uint32_t count, uint32_t 
                             double* out, cudaStream_t st);
 void launch_add_steps(SimDev* d, uint64_t nsteps, cudaStream_t st);
 void launch_validate(SimDev* d, uint32_t n, uint32_t* bad, cudaStream_t st);
+// KMC_OBS_VMAX: acc is 8 bytes of device scratch, out one binary64 (device)
+void launch_vmax_exact(SimDev* d, unsigned long long* acc, double* out, cudaStream_t st);
 
 // device-side initial state (kmc_init.cu): writes buffer 0 of the state in id order,
 // the ids and last = kNone; counts particles whose rejection loops ran out in *fails

@@ -90,43 +90,6 @@ __device__ __forceinline__ double min_image(double r, double L) {
   return r;
 }
 
-// Block-aggregated append: one atomic per block on the shared counter (a counter that
-// every warp of the grid hits is a hot spot: its atomics serialise in L2).  Every
-// thread of the block must call it; *also, if given, is advanced by the same total.
-// Returns this thread's first index in the buffer behind *counter.
-__device__ __forceinline__ uint32_t block_append(uint32_t* counter, uint32_t want,
-                                                 uint32_t* also = nullptr) {
-  constexpr int kW = kEdgeBlock / 32;
-  __shared__ uint32_t wsum[kW], wbase[kW], bbase;
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  uint32_t incl = want;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= (uint32_t)o) incl += y;
-  }
-  if (lane == 31) wsum[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    const uint32_t v = lane < (uint32_t)kW ? wsum[lane] : 0u;
-    uint32_t vi = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, vi, o);
-      if (lane >= (uint32_t)o) vi += y;
-    }
-    if (lane < (uint32_t)kW) wbase[lane] = vi - v;
-    if (lane == (uint32_t)kW - 1) {
-      bbase = vi ? atomicAdd(counter, vi) : 0u;
-      if (also && vi) atomicAdd(also, vi);
-    }
-  }
-  __syncthreads();
-  const uint32_t r = bbase + wbase[warp] + incl - want;
-  __syncthreads();  // the slots are free for the next call
-  return r;
-}
-
 // ---- k_refine ------------------------------------------------------------ //
 // MIX: the plan has a mixture (per-pair contact distance, mass-weighted scatter)
 template <bool MIX>
@@ -374,22 +337,34 @@ __global__ void __launch_bounds__(kEdgeBlock) k_collide(Batch B) {
   }
 }
 
-int launch_match(const LaunchPlan& L, int max_rounds, cudaStream_t st) {
-  int nb = L.edge_blocks;
+int launch_match_lists(const LaunchPlan& L, cudaStream_t st) {
+  const int nb = L.edge_blocks;
   if (L.mix) k_refine<true><<<nb, kEdgeBlock, 0, st>>>(L.b);
   else k_refine<false><<<nb, kEdgeBlock, 0, st>>>(L.b);
   k_alloc<<<nb, kEdgeBlock, 0, st>>>(L.b);
   k_fill<<<nb, kEdgeBlock, 0, st>>>(L.b);
+  return 3;
+}
+
+int launch_collide(const LaunchPlan& L, cudaStream_t st) {
+  const int nb = L.edge_blocks;
+  if (L.mix) k_collide<true><<<nb, kEdgeBlock, 0, st>>>(L.b);
+  else k_collide<false><<<nb, kEdgeBlock, 0, st>>>(L.b);
+  return 1;
+}
+
+int launch_match(const LaunchPlan& L, int max_rounds, cudaStream_t st) {
+  const int nb = L.edge_blocks;
+  int n = launch_match_lists(L, st);
   for (int r = 0; r < max_rounds; ++r) {
     // the later rounds' work lists hold a few percent of the first round's: a grid of
     // one block per SM covers them (grid-stride) without launching idle blocks
     const int nr = r == 0 ? nb : std::max(1, nb / 8);
     k_best<<<nr, kEdgeBlock, 0, st>>>(L.b, r);
     k_mutual<<<nr, kEdgeBlock, 0, st>>>(L.b, r);
+    n += 2;
   }
-  if (L.mix) k_collide<true><<<nb, kEdgeBlock, 0, st>>>(L.b);
-  else k_collide<false><<<nb, kEdgeBlock, 0, st>>>(L.b);
-  return 4 + 2 * max_rounds;
+  return n + launch_collide(L, st);
 }
 
 }  // namespace kmc

@@ -10,12 +10,15 @@
 // its only scratch is the fixed-size array below, which lives in the library's
 // device image.
 //
-// The scratch array holds kStaticBins x 19 int64 fixed-point counters (38,912
-// bytes).  Every GPU that loads the library keeps its own copy until the process
-// exits.  All calls on a device share it and it keeps the last call's contents;
-// each call clears the counters it uses before accumulating.  Two calls whose work
-// overlaps on the GPU (different streams, no ordering between them) race on the
-// counters and give wrong sums: order such calls on one stream or with events.
+// The scratch array holds kStaticBins x 20 int64 fixed-point counters (40,960
+// bytes): per bin the count, three 32-bit digits of each velocity sum and of each
+// sum of squares, and the number of terms out of the digits' range (profile_add in
+// kmc_internal.cuh; the profile kernel of the simulations uses the same helpers).
+// Every GPU that loads the library keeps its own copy until the process exits.
+// All calls on a device share it and it keeps the last call's contents; each call
+// clears the counters it uses before accumulating.  Two calls whose work overlaps
+// on the GPU (different streams, no ordering between them) race on the counters
+// and give wrong sums: order such calls on one stream or with events.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -26,34 +29,15 @@
 namespace {
 
 constexpr int kStaticBins = 256;  // largest supported number of bins
-constexpr int kQ = 19;            // counters per bin: count, 3 x 3 digits of sum v, of sum v^2
+constexpr int kQ = kmc::kProfQ;   // counters per bin (see profile_add)
 constexpr int kMaxDevices = 64;
 
 }  // namespace
 
-// fixed-point profile counters (see the file comment): 256 x 19 x 8 = 38,912 bytes
+// fixed-point profile counters (see the file comment): 256 x 20 x 8 = 40,960 bytes
 static __device__ __align__(256) long long kmc_profile_scratch[kStaticBins * kQ];
 
 namespace {
-
-// |q| * 2^64 truncated, as three 32-bit digits with the sign of q (|q| < 2^31)
-__device__ __forceinline__ void digits3(double q, long long d[3]) {
-  unsigned long long bits = (unsigned long long)__double_as_longlong(q);
-  bool neg = (bits >> 63) != 0;
-  int ex = (int)((bits >> 52) & 0x7FF);
-  d[0] = d[1] = d[2] = 0;
-  if (ex == 0) return;
-  unsigned long long man = (bits & ((1ull << 52) - 1)) | (1ull << 52);
-  int sh = ex - 1075 + 64;
-  unsigned __int128 f;
-  if (sh >= 0) f = (unsigned __int128)man << (sh > 42 ? 42 : sh);
-  else if (sh > -64) f = (unsigned __int128)(man >> (-sh));
-  else f = 0;
-  long long d0 = (long long)(uint32_t)f, d1 = (long long)(uint32_t)(f >> 32),
-            d2 = (long long)(uint32_t)(f >> 64);
-  if (neg) { d0 = -d0; d1 = -d1; d2 = -d2; }
-  d[0] = d0; d[1] = d1; d[2] = d2;
-}
 
 __global__ void k_static_clear(long long* acc, int count) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) acc[i] = 0;
@@ -69,22 +53,13 @@ __global__ void __launch_bounds__(256) k_static_profile(const double* __restrict
   for (int i = threadIdx.x; i < nb * kQ; i += blockDim.x) sh[i] = 0;
   __syncthreads();
   const double scale = kmc::ddiv((double)nb, range);
-  const double* vel[3] = {vx, vy, vz};
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     double xp = x[p];
     if (!(xp >= 0.0)) continue;
     double f = kmc::dmul(xp, scale);
     if (f >= (double)nb) continue;
-    long long* q = sh + (int)f * kQ;
-    atomicAdd((unsigned long long*)&q[0], 1ull);
-    for (int a = 0; a < 3; ++a) {
-      double v = vel[a][p];
-      long long d[3];
-      digits3(v, d);
-      for (int c = 0; c < 3; ++c) atomicAdd((unsigned long long*)&q[1 + 3 * a + c], (unsigned long long)d[c]);
-      digits3(kmc::dmul(v, v), d);
-      for (int c = 0; c < 3; ++c) atomicAdd((unsigned long long*)&q[10 + 3 * a + c], (unsigned long long)d[c]);
-    }
+    const double v[3] = {vx[p], vy[p], vz[p]};
+    kmc::profile_add(sh + (int)f * kQ, v);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nb * kQ; i += blockDim.x)
@@ -93,37 +68,24 @@ __global__ void __launch_bounds__(256) k_static_profile(const double* __restrict
 
 // counters -> binary64: count, sum vx, sum vy, sum vz, sum vx^2, sum vy^2, sum vz^2
 __global__ void k_static_convert(const long long* acc, int nb, double* out) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb * 7; i += gridDim.x * blockDim.x) {
-    int b = i / 7, q = i % 7;
-    const long long* src = acc + b * kQ;
-    double val;
-    if (q == 0) {
-      val = (double)src[0];
-    } else {
-      const long long* dg = src + 1 + 3 * (q - 1);
-      __int128 tot = ((__int128)dg[2] << 64) + ((__int128)dg[1] << 32) + (__int128)dg[0];
-      bool neg = tot < 0;
-      unsigned __int128 mag = neg ? (unsigned __int128)(-tot) : (unsigned __int128)tot;
-      double hi = (double)(unsigned long long)(mag >> 64);
-      double lo = (double)(unsigned long long)mag;
-      val = kmc::dadd(kmc::dmul(hi, 1.0), kmc::dmul(lo, 0x1p-64));
-      val = neg ? -val : val;
-    }
-    out[i] = val;
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb * 7; i += gridDim.x * blockDim.x)
+    out[i] = kmc::profile_value(acc + (i / 7) * kQ, i % 7);
 }
 
 std::mutex g_setup_mutex;
 long long* g_scratch_addr[kMaxDevices] = {nullptr};
 int g_num_sms[kMaxDevices] = {0};
 
-bool on_device(const void* ptr) {
+// device memory of the current device dev (or managed memory): a pointer to another
+// GPU's memory would be dereferenced without a peer mapping
+bool on_device(const void* ptr, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 int reject(const char* why) {
@@ -140,12 +102,22 @@ extern "C" int sim_profile_static(const double* x, const double* vx, const doubl
   if (!(range > 0.0)) return reject("range must be > 0");
   if (!out) return reject("out is NULL");
   if (n > 0 && (!x || !vx || !vy || !vz)) return reject("a particle array is NULL");
-  if (!on_device(out) || (n > 0 && (!on_device(x) || !on_device(vx) || !on_device(vy) || !on_device(vz))))
-    return reject("all arrays must be device memory");
+  if (n >= 0x80000000u) return reject("n must be below 2^31 (int64 digit sums)");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
     return KMC_ECUDA;
+  }
+  if (!on_device(out, dev) ||
+      (n > 0 && (!on_device(x, dev) || !on_device(vx, dev) || !on_device(vy, dev) || !on_device(vz, dev))))
+    return reject("all arrays must be device memory of the current device");
+  if (stream) {
+    int sdev = -1;
+    if (cudaStreamGetDevice((cudaStream_t)stream, &sdev) != cudaSuccess) {
+      cudaGetLastError();
+      return reject("stream is not a valid CUDA stream");
+    }
+    if (sdev != dev) return reject("stream belongs to another device");
   }
   long long* acc = nullptr;
   int sms = 0;

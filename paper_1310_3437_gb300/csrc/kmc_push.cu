@@ -194,26 +194,6 @@ __global__ void __launch_bounds__(kTile) k_push(Batch B) {
   if (ABS && s.absorb && threadIdx.x == 0 && sgone) atomicAdd(&s.d.n_absorbed, sgone);
 }
 
-// ---- fixed-point digits for the profile sums ------------------------------- //
-// |q| * 2^64, truncated, split into three 32-bit digits (q must satisfy |q| < 2^31).
-__device__ __forceinline__ void fx_digits(double q, long long d[3]) {
-  unsigned long long bits = (unsigned long long)__double_as_longlong(q);
-  bool neg = (bits >> 63) != 0;
-  int ex = (int)((bits >> 52) & 0x7FF);
-  d[0] = d[1] = d[2] = 0;
-  if (ex == 0) return;  // zero or subnormal: below 2^-64
-  unsigned long long man = (bits & ((1ull << 52) - 1)) | (1ull << 52);
-  int sh = ex - 1075 + 64;
-  unsigned __int128 f;
-  if (sh >= 0) f = (unsigned __int128)man << (sh > 42 ? 42 : sh);
-  else if (sh > -64) f = (unsigned __int128)(man >> (-sh));
-  else f = 0;
-  long long d0 = (long long)(uint32_t)f, d1 = (long long)(uint32_t)(f >> 32),
-            d2 = (long long)(uint32_t)(f >> 64);
-  if (neg) { d0 = -d0; d1 = -d1; d2 = -d2; }
-  d[0] = d0; d[1] = d1; d[2] = d2;
-}
-
 template <bool ABS>
 __global__ void __launch_bounds__(kTile) k_profile(Batch B) {
   extern __shared__ long long acc[];
@@ -235,17 +215,8 @@ __global__ void __launch_bounds__(kTile) k_profile(Batch B) {
     double f = dmul(x, scale);
     if (f >= (double)nb) continue;
     int b = (int)f;
-    long long* q = acc + b * kProfQ;
-    atomicAdd((unsigned long long*)&q[0], 1ull);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      double v = s.v[cur][a][p];
-      long long d[3];
-      fx_digits(v, d);
-      for (int c = 0; c < 3; ++c) atomicAdd((unsigned long long*)&q[1 + 3 * a + c], (unsigned long long)d[c]);
-      fx_digits(dmul(v, v), d);
-      for (int c = 0; c < 3; ++c) atomicAdd((unsigned long long*)&q[10 + 3 * a + c], (unsigned long long)d[c]);
-    }
+    const double v[3] = {s.v[cur][0][p], s.v[cur][1][p], s.v[cur][2][p]};
+    profile_add(acc + b * kProfQ, v);
   }
   __syncthreads();
   long long* out = s.prof_acc + (size_t)(s.d.prof_count % s.prof_cap) * nb * kProfQ;
@@ -339,16 +310,50 @@ __global__ void __launch_bounds__(kTile) k_vmax(Batch B) {
   block_max_to(&s.d.vmax2_acc, vm);
 }
 
+// the trial thresholds of the speed split from the state's bound of max |v|^2
+__global__ void k_init_thresholds(Batch B) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < B.nsims; k += gridDim.x * blockDim.x) {
+    SimDev& s = *B.sims[k];
+    s.d.vmax2 = __uint_as_float(s.d.vmax2_acc);
+    set_split_thresholds(s, s.d.vmax2);
+  }
+}
+
+// particles above each trial threshold, and each particle's speed class, as the push
+// counts them at the end of a step: the first step can split the fast particles off
+template <bool ABS>
+__global__ void __launch_bounds__(kTile) k_split_count(Batch B) {
+  __shared__ uint32_t scnt[kSplitTrials];
+  const int k = find_sim(B.ptile, B.nsims, blockIdx.x);
+  SimDev& s = *B.sims[k];
+  if (!s.split_ok) return;
+  if (threadIdx.x < kSplitTrials) scnt[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t p = (blockIdx.x - B.ptile[k]) * kTile + threadIdx.x;
+  const int par = s.d.parity;
+  const bool valid = p < s.n && !(ABS && s.absorb && s.last[par][p] == KMC_ABSORBED);
+  const float vm = valid ? vmag2_up(s.v[par][0][p], s.v[par][1][p], s.v[par][2][p]) : 0.0f;
+  uint32_t above = 0;
+#pragma unroll
+  for (int t = 1; t < kSplitTrials; ++t) {
+    const bool hi = valid && vm > s.d.split_thr[t];
+    above += hi ? 1u : 0u;
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, hi);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&scnt[t], (uint32_t)__popc(m));
+  }
+  if (valid) s.vbucket[p] = (uint8_t)above;
+  __syncthreads();
+  if (threadIdx.x > 0 && threadIdx.x < kSplitTrials && scnt[threadIdx.x])
+    atomicAdd(&s.d.split_cnt[threadIdx.x], scnt[threadIdx.x]);
+}
+
 // one warp per simulation, as k_finalize
 __global__ void k_init_grid(Batch B) {
   const uint32_t lane = threadIdx.x & 31u;
   const int nwarps = (int)(gridDim.x * blockDim.x / 32u);
   for (int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) / 32u); k < B.nsims; k += nwarps) {
     SimDev& s = *B.sims[k];
-    if (lane == 0) {
-      s.d.vmax2 = __uint_as_float(s.d.vmax2_acc);
-      s.d.have_counts = 0;
-    }
+    if (lane == 0) s.d.have_counts = s.split_ok ? 1u : 0u;  // k_split_count's
     __syncwarp();
     compute_grid(s, s.d.vmax2, s.d.step, lane);
     __syncwarp();
@@ -373,8 +378,11 @@ int launch_init_grid(const LaunchPlan& L, cudaStream_t st) {
   k_zero_vmax<<<1, 256, 0, st>>>(L.b);
   if (L.absorb) k_vmax<true><<<L.ptiles, kTile, 0, st>>>(L.b);
   else k_vmax<false><<<L.ptiles, kTile, 0, st>>>(L.b);
+  k_init_thresholds<<<(L.b.nsims + 255) / 256, 256, 0, st>>>(L.b);
+  if (L.absorb) k_split_count<true><<<L.ptiles, kTile, 0, st>>>(L.b);
+  else k_split_count<false><<<L.ptiles, kTile, 0, st>>>(L.b);
   k_init_grid<<<(L.b.nsims + 7) / 8, 256, 0, st>>>(L.b);
-  return 3;
+  return 5;
 }
 
 int launch_push(const LaunchPlan& L, cudaStream_t st) {
@@ -440,22 +448,39 @@ __global__ void k_profile_convert(SimDev* d, uint32_t first, uint32_t count, uin
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     uint32_t snap = i / (bins * 7), rem = i % (bins * 7), b = rem / 7, q = rem % 7;
     const long long* src = s.prof_acc + ((size_t)((first + snap) % s.prof_cap) * bins + b) * kProfQ;
-    double val;
-    if (q == 0) {
-      val = (double)src[0];
-    } else {
-      const long long* dg = src + 1 + 3 * (q - 1);
-      // value = (d2 * 2^64 + d1 * 2^32 + d0) * 2^-64 with signed 128-bit accumulation
-      __int128 tot = ((__int128)dg[2] << 64) + ((__int128)dg[1] << 32) + (__int128)dg[0];
-      bool neg = tot < 0;
-      unsigned __int128 mag = neg ? (unsigned __int128)(-tot) : (unsigned __int128)tot;
-      double hi = (double)(unsigned long long)(mag >> 64);
-      double lo = (double)(unsigned long long)mag;
-      val = dadd(dmul(hi, 1.0), dmul(lo, 0x1p-64));
-      val = neg ? -val : val;
-    }
-    out[i] = val;
+    out[i] = profile_value(src, (int)q);
   }
+}
+
+// KMC_OBS_VMAX: max over the particles in the gas of (vx*vx + vy*vy) + vz*vz, each
+// operation correctly rounded; the squares are non-negative, so their bit patterns
+// order as their values and one 64-bit atomicMax per warp reduces them exactly
+__global__ void k_vmax_exact(SimDev* d, unsigned long long* acc) {
+  SimDev& s = *d;
+  const int par = s.d.parity;
+  unsigned long long m = 0ull;
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < s.n; p += gridDim.x * blockDim.x) {
+    if (s.absorb && s.last[par][p] == KMC_ABSORBED) continue;
+    const double vx = s.v[par][0][p], vy = s.v[par][1][p], vz = s.v[par][2][p];
+    const double q = dadd(dadd(dmul(vx, vx), dmul(vy, vy)), dmul(vz, vz));
+    const unsigned long long b = (unsigned long long)__double_as_longlong(q);
+    m = b > m ? b : m;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, m, off);
+    m = o > m ? o : m;
+  }
+  if ((threadIdx.x & 31u) == 0 && m) atomicMax(acc, m);
+}
+
+__global__ void k_vmax_sqrt(const unsigned long long* acc, double* out) {
+  out[0] = dsqrt(__longlong_as_double((long long)*acc));
+}
+
+void launch_vmax_exact(SimDev* d, unsigned long long* acc, double* out, cudaStream_t st) {
+  cudaMemsetAsync(acc, 0, sizeof(unsigned long long), st);
+  k_vmax_exact<<<304, 256, 0, st>>>(d, acc);
+  k_vmax_sqrt<<<1, 1, 0, st>>>(acc, out);
 }
 
 // particles outside the box at creation: count them (host reports KMC_EINVAL)

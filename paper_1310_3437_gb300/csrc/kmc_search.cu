@@ -71,6 +71,18 @@ __device__ __forceinline__ bool batch_uses(const Batch& B, int mode) {
   return __syncthreads_or(any) != 0;
 }
 
+// Conservative binary64 approach and time pre-tests on a sphere survivor.  The search
+// computes r = x_j - x_i, v = v_j - v_i, |v|^2 and r.v with the same operations as the
+// exact test (k_refine), so rv is its value bit for bit; the exact test needs
+// t* = fl(-rv / vv) >= 0 and < dt.  Dropped here only when that provably fails:
+//   rv > vv 2^-1000: -rv / vv <= -2^-1000 (too large to round to -0.0, which would
+//     count as >= 0), so t* < 0;
+//   -rv >= fl(fl(dt vv)(1 + 2^-48)) >= dt vv (1 + 2^-50): fl(-rv / vv) >= dt.
+// (vv >= 2^-900 here; rounding of the two thresholds only makes the drops rarer.)
+__device__ __forceinline__ bool f64_cannot_approach(double rv, double vv, double dt) {
+  return rv > dmul(vv, 0x1p-1000) || -rv >= dmul(dmul(dt, vv), 1.0 + 0x1p-48);
+}
+
 template <int PREC, int K>
 __global__ void __launch_bounds__(kTile) k_search(Batch B) {
   __shared__ uint2 sbuf[kSearchBuf];
@@ -185,6 +197,9 @@ __global__ void __launch_bounds__(kTile) k_search(Batch B) {
                 double R = dadd(dadd(dmul(r0, r0), dmul(r1, r1)), dmul(r2, r2));
                 double Bv = dadd(dadd(dmul(g0, g0), dmul(g1, g1)), dmul(g2, g2));
                 if (Bv >= 0x1p-900 && R > dadd(g.c0, dmul(g.c1, Bv))) continue;
+                if (Bv >= 0x1p-900 &&
+                    f64_cannot_approach(dadd(dadd(dmul(r0, g0), dmul(r1, g1)), dmul(r2, g2)), Bv, s.dt))
+                  continue;
                 uint32_t pos = atomicAdd(&scnt, 1u);
                 if (pos < (uint32_t)kSearchBuf) {
                   sbuf[pos] = make_uint2(p, j);
@@ -438,6 +453,9 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_cell(Batch B) {
                     double R = dadd(dadd(dmul(r0, r0), dmul(r1, r1)), dmul(r2, r2));
                     double Bv = dadd(dadd(dmul(g0, g0), dmul(g1, g1)), dmul(g2, g2));
                     bool emit = valid && !(Bv >= 0x1p-900 && R > dadd(C0, dmul(C1, Bv)));
+                    if (emit && Bv >= 0x1p-900 &&
+                        f64_cannot_approach(dadd(dadd(dmul(r0, g0), dmul(r1, g1)), dmul(r2, g2)), Bv, s.dt))
+                      emit = false;
                     warp_emit(we_, s, lane, emit, i, j);
                   }
                 } else {
@@ -1341,6 +1359,9 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4) k_search_fast(Batch B) {
               const double R = dadd(dadd(dmul(r0, r0), dmul(r1, r1)), dmul(r2, r2));
               const double Bv = dadd(dadd(dmul(g0, g0), dmul(g1, g1)), dmul(g2, g2));
               emit = !(Bv >= 0x1p-900 && R > dadd(g.c0, dmul(g.c1, Bv)));
+              if (emit && Bv >= 0x1p-900 &&
+                  f64_cannot_approach(dadd(dadd(dmul(r0, g0), dmul(r1, g1)), dmul(r2, g2)), Bv, s.dt))
+                emit = false;
             } else {
               // own coordinates moved by the image shift (j seen at x_j + w L)
               const float wxf = (float)((int)(d & 1u) - (int)((d >> 1) & 1u));

@@ -48,6 +48,11 @@ __device__ __forceinline__ uint32_t run_rank(uint32_t* counts, uint32_t key, boo
 // the key after every cell)
 template <bool ABS>
 __global__ void __launch_bounds__(kTile / 2) k_count(Batch B) {
+  // the scan that follows hands out its tiles from 0 and starts a new epoch
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    B.scan_ctl[0] = 0u;
+    B.scan_ctl[1] += 1u;
+  }
   int k = find_sim(B.ptile, B.nsims, blockIdx.x);
   SimDev& s = *B.sims[k];
   if (!sim_active(s)) return;
@@ -135,102 +140,88 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* t
   return r;
 }
 
-__global__ void __launch_bounds__(kTile) k_scan_reduce(Batch B) {
-  const uint32_t* pre = B.stile_c;
-  int k = find_sim(pre, B.nsims, blockIdx.x);
-  SimDev& s = *B.sims[k];
-  uint32_t sum = 0;
-  if (sim_active(s)) {
-    ScanView v = scan_view(s);
-    uint32_t base = (blockIdx.x - pre[k]) * kScanTile;
-    for (int i = threadIdx.x; i < kScanTile; i += kTile) {
-      uint32_t e = base + i;
-      if (e < v.len) sum += v.in[e];
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
-  __shared__ uint32_t ws[kTile / 32];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = sum;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t t = 0;
-    for (int w = 0; w < kTile / 32; ++w) t += ws[w];
-    B.tile_sums[blockIdx.x] = t;
-  }
+// Single-pass segmented scan with decoupled look-back (Merrill and Garland, "Single-
+// pass Parallel Prefix Scan with Decoupled Look-back", NVIDIA technical report, 2016).
+// Tiles are handed out in launch order by an atomic counter, so every tile a block
+// waits for belongs to a block that is already running.  Each tile publishes its own
+// sum at once, then its inclusive prefix once it knows it; a tile's exclusive prefix
+// is the sum of its predecessors' published values back to the first inclusive prefix
+// (or to the start of its simulation's segment, which starts at zero).  Status words
+// carry the epoch of the scan, so the words of the previous step read as not ready.
+// The wait for a predecessor is bounded: if it runs out the simulation gets the
+// ST_SCAN_WAIT status (sim_sync reports KMC_ETIMEOUT) instead of the block spinning on.
+constexpr unsigned long long kStAgg = 1ull, kStIncl = 2ull;
+constexpr int kScanWaitLimit = 1 << 22;
+
+__device__ __forceinline__ unsigned long long scan_word(uint32_t epoch, unsigned long long state,
+                                                        uint32_t value) {
+  return ((unsigned long long)epoch << 34) | (state << 32) | (unsigned long long)value;
 }
 
-// one block: exclusive scan of the tile sums inside each simulation's segment
-__global__ void __launch_bounds__(1024) k_scan_tiles(Batch B, uint32_t ntiles) {
-  const uint32_t* pre = B.stile_c;
-  __shared__ uint32_t warp_sums[32];
-  __shared__ uint32_t carry;
-  if (threadIdx.x == 0) carry = 0;
+__global__ void __launch_bounds__(kTile) k_scan_onepass(Batch B, uint32_t ntiles) {
+  __shared__ uint32_t s_tile, s_excl;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&B.scan_ctl[0], 1u);
   __syncthreads();
-  unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-  for (uint32_t base = 0; base < ntiles; base += 1024) {
-    uint32_t i = base + threadIdx.x;
-    uint32_t x = i < ntiles ? B.tile_sums[i] : 0;
-    uint32_t incl = x;
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (lane >= (unsigned)o) incl += y;
-    }
-    if (lane == 31) warp_sums[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-      uint32_t w = warp_sums[lane];
-      uint32_t wi = w;
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
-        if (lane >= (unsigned)o) wi += y;
-      }
-      warp_sums[lane] = wi - w;
-    }
-    __syncthreads();
-    uint32_t excl = carry + warp_sums[wid] + incl - x;
-    __syncthreads();
-    if (i < ntiles) B.tile_sums[i] = excl;
-    if (threadIdx.x == 1023) carry = excl + x;
-    __syncthreads();
-  }
-  // make each segment start at zero
-  __shared__ uint32_t seg_base[kMaxGroup];
-  for (int k = threadIdx.x; k < B.nsims; k += 1024) {
-    uint32_t t0 = pre[k];
-    seg_base[k] = t0 < ntiles ? B.tile_sums[t0] : 0;
-  }
-  __syncthreads();
-  for (uint32_t i = threadIdx.x; i < ntiles; i += 1024) {
-    int k = find_sim(pre, B.nsims, i);
-    B.tile_sums[i] -= seg_base[k];
-  }
-}
-
-__global__ void __launch_bounds__(kTile) k_scan_apply(Batch B) {
+  const uint32_t tile = s_tile;
+  if (tile >= ntiles) return;
   const uint32_t* pre = B.stile_c;
-  int k = find_sim(pre, B.nsims, blockIdx.x);
+  const int k = find_sim(pre, B.nsims, tile);
   SimDev& s = *B.sims[k];
   if (!sim_active(s)) return;
-  ScanView v = scan_view(s);
-  uint32_t base = (blockIdx.x - pre[k]) * kScanTile;
-  if (base > v.len) return;
+  const ScanView v = scan_view(s);
+  const uint32_t first = pre[k];
+  const uint32_t base = (tile - first) * kScanTile;
+  if (base > v.len) return;  // past the key space: no later tile of this segment waits
+  const uint32_t epoch = *(volatile uint32_t*)&B.scan_ctl[1] & 0x3FFFFFFFu;
+  volatile unsigned long long* status = B.tile_status;
   constexpr int PER = kScanTile / kTile;
   uint32_t vals[PER];
-  uint32_t e0 = base + threadIdx.x * PER;
+  const uint32_t e0 = base + threadIdx.x * PER;
   uint32_t local = 0;
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
-    uint32_t e = e0 + i;
-    vals[i] = e < v.len ? v.in[e] : 0;
+    const uint32_t e = e0 + i;
+    vals[i] = e < v.len ? v.in[e] : 0u;
     local += vals[i];
   }
-  uint32_t off = block_exclusive_scan(local, nullptr) + B.tile_sums[blockIdx.x];
+  uint32_t agg = 0;
+  const uint32_t off = block_exclusive_scan(local, &agg);
+  if (threadIdx.x == 0) {
+    if (tile == first) {
+      status[tile] = scan_word(epoch, kStIncl, agg);
+      s_excl = 0;
+    } else {
+      status[tile] = scan_word(epoch, kStAgg, agg);
+      uint32_t excl = 0;
+      bool timed_out = false;
+      // the failure-path test waits for an epoch that no tile writes
+      const uint32_t want = s.scan_wait_test ? ((epoch + 1u) & 0x3FFFFFFFu) : epoch;
+      for (uint32_t p = tile - 1;; --p) {
+        unsigned long long w = status[p];
+        int spins = 0;
+        while ((uint32_t)(w >> 34) != want || ((w >> 32) & 3ull) == 0ull) {
+          if (++spins > kScanWaitLimit) { timed_out = true; break; }
+          if (spins > 32) __nanosleep(64);
+          w = status[p];
+        }
+        if (timed_out) break;
+        excl += (uint32_t)w;
+        if (((w >> 32) & 3ull) == kStIncl || p == first) break;
+      }
+      if (timed_out) atomicOr(&s.d.status, ST_SCAN_WAIT);
+      __threadfence();
+      status[tile] = scan_word(epoch, kStIncl, excl + agg);
+      s_excl = excl;
+    }
+  }
+  __syncthreads();
+  uint32_t o = s_excl + off;
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
-    uint32_t e = e0 + i;
-    if (e <= v.len) v.out[e] = off;
+    const uint32_t e = e0 + i;
+    if (e <= v.len) v.out[e] = o;
     if (v.clear && e < v.len && vals[i]) v.clear[e] = 0;
-    off += vals[i];
+    o += vals[i];
   }
 }
 
@@ -310,10 +301,8 @@ __global__ void __launch_bounds__(kTile / 2) k_gather(Batch B) {
 // --------------------------------------------------------------------------- //
 int launch_cell_scan(const LaunchPlan& L, cudaStream_t st) {
   const uint32_t nt = L.stiles_c;
-  k_scan_reduce<<<nt, kTile, 0, st>>>(L.b);
-  k_scan_tiles<<<1, 1024, 0, st>>>(L.b, nt);
-  k_scan_apply<<<nt, kTile, 0, st>>>(L.b);
-  return 3;
+  k_scan_onepass<<<nt, kTile, 0, st>>>(L.b, nt);
+  return 1;
 }
 
 int launch_sort(const LaunchPlan& L, cudaStream_t st) {

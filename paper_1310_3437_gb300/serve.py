@@ -6,6 +6,8 @@ footprint (``sim_bytes_required``) fits the HBM budget, adds each admitted
 simulation to one group with a step budget equal to its requested steps, and
 advances the group in short bursts: one launch per kernel per step covers every
 live simulation (members whose budget is spent are skipped on the device).  A
+burst is at most ``burst_steps`` long and ends when the live request closest to its
+end has run its steps, so no request waits for a burst to run past its end.  A
 request is complete when its budget is spent and its final state and per-step
 counts have been copied to the host; it then leaves the group and its memory is
 freed, so queued requests can be admitted.  Latency is measured from arrival to
@@ -37,6 +39,7 @@ class Request:
     state: object = None
     counts: list = field(default_factory=list)
     bytes: int = 0
+    remaining: int = 0         # steps of the budget not yet issued to the group
 
     @property
     def latency(self):
@@ -73,6 +76,7 @@ class Server:
         else:
             self.group.add(sim)
         self.group.budget(sim, int(req.steps))
+        req.remaining = int(req.steps)
         req.admitted = now
         self.live[sim] = req
         self.in_use += req.bytes
@@ -119,12 +123,19 @@ class Server:
                     if wait > 0:
                         time.sleep(min(wait, 0.05))
                 continue
-            # one burst of group steps; never past the smallest remaining budget by
-            # more than the burst (finished members are skipped on the device)
-            self.group.step(self.burst)
+            # one burst of group steps, ending when the live request closest to its end
+            # has run its budget (members whose budget is spent are skipped on the
+            # device; the group's sync leaves every member where its budget says)
+            burst = max(1, min(self.burst, min(r.remaining for r in self.live.values())))
+            self.group.step(burst)
             self.group.sync()
             for sim, req in list(self.live.items()):
-                if self.group.steps_left(sim) == 0:
+                req.remaining = max(0, req.remaining - burst)
+                if req.remaining == 0:
+                    left = self.group.steps_left(sim)
+                    if left != 0:
+                        raise RuntimeError(f"request {req.rid}: {left} steps left on the "
+                                           f"device, none on the host")
                     self._retire(sim, req, clock)
                     done.append(req)
         wall = clock()

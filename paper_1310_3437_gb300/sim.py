@@ -11,8 +11,8 @@ import numpy as np
 
 from . import (KMC_FP64, KMC_GUARDED_FP32, KMC_NONE, KMC_OBS_COUNTS, KMC_OBS_EDGES,
                KMC_OBS_LAUNCHES, KMC_OBS_PARTNERS, KMC_OBS_PHASE_MS, KMC_OBS_PROFILES,
-               KMC_OBS_STATE, KMC_OBS_STEP, kmc_params, sim_set_timing,
-               kmc_step_counts, sim_create, sim_create_init, sim_create_mixture,
+               KMC_OBS_STATE, KMC_OBS_STEP, KMC_OBS_VMAX, KMC_OBS_DOMAINS, kmc_params, sim_set_timing,
+               kmc_step_counts, sim_create, sim_create_init, sim_create_mixture, sim_create_domains,
                init_from_spec, sim_destroy, sim_group_add, sim_group_budget,
                sim_group_create, sim_group_destroy, sim_group_remove, sim_group_step,
                sim_group_steps_left, sim_group_sync, sim_observe, sim_step, sim_sync)
@@ -76,10 +76,11 @@ class Simulation:
     """One simulation: state on the device, stepped by the library's kernels."""
 
     def __init__(self, params: kmc_params, arrays=None, last=None, stream=None, init=None,
-                 mixture=None):
+                 mixture=None, domains=None):
         """From host or device arrays (x, y, z, vx, vy, vz) and optional last partners,
         or, with ``init`` (a dict with kmc_init's fields), from a state drawn on the
-        device.  ``mixture``: (species per id, masses, radii) for a mixture."""
+        device.  ``mixture``: (species per id, masses, radii) for a mixture.
+        ``domains``: decompose into that many x slabs (sim_create_domains)."""
         self.params = params
         self.n = int(params.n)
         self.group = None
@@ -103,7 +104,11 @@ class Simulation:
             self._keep.append(k)
         if stream is None:
             stream = _torch_stream()
-        if mixture is not None:
+        if domains is not None:
+            if mixture is not None:
+                raise ValueError("a decomposition of a mixture is not supported")
+            self.handle = sim_create_domains(params, int(domains), *ptrs, lp, stream)
+        elif mixture is not None:
             sp, ms, rs = mixture
             sp, k1 = _ptr(sp if hasattr(sp, "data_ptr") else np.ascontiguousarray(sp, np.uint8))
             ms = np.ascontiguousarray(ms, dtype=np.float64)
@@ -194,6 +199,19 @@ class Simulation:
         sim_observe(self.handle, KMC_OBS_PHASE_MS, out.ctypes.data, out.nbytes)
         return {"sort": out[0], "search": out[1], "match": out[2], "push": out[3],
                 "steps": int(out[4]), "search_slow": out[5]}
+
+    def vmax(self) -> float:
+        """Largest particle speed of the current state (binary64, correctly rounded)."""
+        out = np.zeros(1)
+        sim_observe(self.handle, KMC_OBS_VMAX, out.ctypes.data, out.nbytes)
+        return float(out[0])
+
+    def domains(self):
+        """(owned, ghosts) per domain in the last step of a decomposition."""
+        cap = 2 * 64
+        out = np.zeros(cap, dtype=np.uint32)
+        cnt = sim_observe(self.handle, KMC_OBS_DOMAINS, out.ctypes.data, out.nbytes)
+        return out[: cnt // 2].copy(), out[cnt // 2: cnt].copy()
 
     def step_index(self) -> int:
         out = np.zeros(1, dtype=np.uint64)

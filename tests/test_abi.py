@@ -54,7 +54,8 @@ def test_bytes_required_scales_with_n():
 
 @pytest.mark.parametrize("field,value", [
     ("n", 0), ("d0", 0.0), ("dt", -1.0), ("max_rounds", 5), ("precision", 7), ("stencil", 3),
-    ("profile_bins", 300), ("cell_scale", 0.5), ("flags", 8), ("flags", 3), ("search_kernel", 4),
+    ("profile_bins", 300), ("cell_scale", 0.5), ("flags", 16), ("flags", 3), ("search_kernel", 4),
+    ("n", 0x7FFFF001),
 ])
 def test_invalid_parameters_are_rejected_on_the_host(field, value):
     p = kmc.params_from_setup(piston_setup(n=1000))

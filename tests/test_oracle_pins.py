@@ -252,3 +252,29 @@ def test_threads_do_not_change_results():
     for x, y in zip(a.a, b.a):
         assert np.array_equal(x, y)
     assert np.array_equal(a.last, b.last)
+
+
+def test_vmax2_is_the_largest_squared_speed():
+    """The oracle's largest squared speed (the maximum speed that Sec. 2 derives the
+    time step from) against exact rational arithmetic: every square and sum computed
+    exactly, the maximum taken exactly, then compared within the three roundings of
+    (vx*vx + vy*vy) + vz*vz.  A (3, 4, 12) particle has |v|^2 = 169 exactly."""
+    from fractions import Fraction
+
+    rng = np.random.default_rng(71)
+    for n in (1, 2, 7, 1000):
+        v = [rng.normal(0, 1, n) * 3 for _ in range(3)]
+        want = max(sum(Fraction(float(c[i])) ** 2 for c in v) for i in range(n))
+        st = oracle.State([np.zeros(n)] * 3 + v)
+        got = oracle.vmax2(st)
+        assert abs(Fraction(got) - want) <= want * Fraction(3 * U)
+    v = [np.array([0.5, 3.0, -1.0]), np.array([0.5, -4.0, 2.0]), np.array([0.5, 12.0, 2.0])]
+    st = oracle.State([np.zeros(3)] * 3 + v)
+    assert oracle.vmax2(st) == 169.0
+    # the largest particle wins wherever it sits, whichever component carries it
+    for pos in range(3):
+        for comp in range(3):
+            v = [np.full(4, 0.25) for _ in range(3)]
+            v[comp][pos] = -7.0
+            st = oracle.State([np.zeros(4)] * 3 + v)
+            assert oracle.vmax2(st) == 49.0 + 2 * 0.0625
