@@ -358,6 +358,35 @@ def run_ensemble(args, stream):
     return out
 
 
+def run_launch_overhead(stream):
+    """Per-step cost of the launch sequence itself: a 4096-particle box (launch-bound)
+    replays its step graph 200 times; us per step and per kernel launch bound what a
+    single persistent kernel could save over the graph of per-phase kernels."""
+    import torch
+
+    import paper_1310_3437_gb300 as kmc
+
+    setup = ki.equilibrium_setup(n=4096, seed=1)
+    sim = kmc.Simulation(kmc.params_from_setup(setup, precision=kmc.KMC_GUARDED_FP32),
+                         ki.initial_state(setup), stream=stream.cuda_stream)
+    sim.step(5).sync()
+    l0 = sim.launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    steps = 200
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    sim.sync()
+    per_step = (sim.launches() - l0 - 1) / steps
+    us = e0.elapsed_time(e1) * 1e3 / steps
+    sim.close()
+    return {"n": setup.n, "steps": steps, "us_per_step": us, "launches_per_step": per_step,
+            "us_per_launch": us / per_step if per_step else None,
+            "note": "graph replay of one step's kernels on a launch-bound 4096-particle box"}
+
+
 def run_blast(args, stream, dev):
     """The spherical blast at full size (2^27 particles; hot ball of radius 0.1 at 8x
     the background density and 100x its temperature, background lambda 0.005), state
@@ -503,13 +532,36 @@ def run_gpu(args):
                   max_windows=1):
         """warm untimed steps, then windows of exactly `steps` steps, each bracketed by
         a barrier and a device synchronisation and timed with CUDA events on the
-        simulation's stream; windows repeat until min_ms of timed work (the same
-        number of windows on every rank).  Returns per-window ms (max over ranks)."""
-        params = kmc.params_from_setup(setup, precision=precision, **(knobs if kn is None else kn))
+        simulation's stream.  With more than one window, every window restarts from
+        the same state (the one after the warm-up, one more untimed step to capture
+        the step's graph), so the windows time the same steps of the same run and the
+        median is not shifted by the shock's growth; windows repeat until min_ms of
+        timed work (the same number on every rank).  Returns per-window ms (max over
+        ranks) and the last window's simulation."""
+        kn = knobs if kn is None else kn
+        params = kmc.params_from_setup(setup, precision=precision, **kn)
         sim = kmc.Simulation(params, dev_arrays, stream=stream.cuda_stream)
         sim.step(warm).sync()
         sim.counts()
-        step_next = sim.step_index()
+        snap = None
+        if max_windows > 1:
+            snap = torch.empty(52 * n, dtype=torch.uint8, device=dev)
+            sim.state_device(snap)
+            torch.cuda.synchronize(dev)
+            sim.close()
+            f = snap[: 48 * n].view(torch.float64).view(6, n)
+            cols = [f[k] for k in range(6)]
+            last = snap[48 * n:].view(torch.int32)
+
+        def window_sim():
+            if snap is None:
+                return sim
+            q = kmc.Simulation(kmc.params_from_setup(setup, precision=precision, step0=warm, **kn),
+                               cols, last=last, stream=stream.cuda_stream)
+            q.step(1).sync()
+            q.counts()
+            return q
+
         sampler = ClockSampler(dev.index or 0) if sample_clocks else None
         barrier()
         if sampler:
@@ -517,26 +569,30 @@ def run_gpu(args):
             sampler.wait_first_sample()
         windows, counts, launches = [], [], 0
         nwin = 1
+        cur = None
         while len(windows) < nwin:
-            l0 = sim.launches()
+            if cur is not None and cur is not sim:
+                cur.close()
+            cur = window_sim()
+            step_next = cur.step_index()
+            l0 = cur.launches()
             barrier()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            sim.step(steps)
+            cur.step(steps)
             e1.record(stream)
             e1.synchronize()
             barrier()
             windows.append(max_over_ranks(e0.elapsed_time(e1)))
-            l1 = sim.launches()
+            l1 = cur.launches()
             launches += l1 - l0
-            counts += check_window(sim, step_next, steps, l1)
-            step_next += steps
+            counts += check_window(cur, step_next, steps, l1)
             if len(windows) == 1:
                 # the same on every rank: derived from the max-over-ranks time
                 nwin = max(1, min(max_windows, math.ceil(min_ms / max(windows[0], 1e-3))))
         clocks = sampler.stop() if sampler else None
-        return sim, windows, counts, launches, clocks
+        return cur, windows, counts, launches, clocks
 
     def precision_check(steps):
         """Guarded binary32 (the timed knobs) and binary64 from the same state, one step
@@ -665,6 +721,7 @@ def run_gpu(args):
     blast = None
     if not args.skip_blast and rank == 0:
         blast = run_blast(args, stream, dev)
+    launch_overhead = run_launch_overhead(stream) if rank == 0 else None
 
     if rank != 0:
         if world > 1:
@@ -731,7 +788,10 @@ def run_gpu(args):
                    "precision": "guarded-fp32", "l2": "inputs larger than L2 (state ~1.9 GB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "timed_windows": {"windows": len(windows32), "steps_per_window": args.steps,
+                          "first_step": args.warmup + 1 if len(windows32) > 1 else args.warmup,
                           "ms_per_window": windows32, "reported": "median window",
+                          "restart": "every window restarts from the state after the warm-up "
+                                     "(and one untimed step): the same steps of the same run",
                           "checked": "each window left exactly its steps' records, "
                                      "consecutive, with no re-run at sync"},
         "fp64": fp64,
@@ -753,8 +813,10 @@ def run_gpu(args):
         "ensemble": ensemble,
         "paper_workloads": paper,
         "blast": blast,
+        "launch_overhead": launch_overhead,
         "tuning": tuning,
         "gpu_launches": int(launches32),
+        "gpu_launches_per_window": int(launches32) // max(1, len(windows32)),
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

@@ -186,32 +186,49 @@ __global__ void __launch_bounds__(kTile) k_scan_onepass(Batch B, uint32_t ntiles
   }
   uint32_t agg = 0;
   const uint32_t off = block_exclusive_scan(local, &agg);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    // warp 0: publish the tile's sum, then look back 32 predecessors at a time
+    const uint32_t lane = threadIdx.x;
     if (tile == first) {
-      status[tile] = scan_word(epoch, kStIncl, agg);
-      s_excl = 0;
+      if (lane == 0) {
+        status[tile] = scan_word(epoch, kStIncl, agg);
+        s_excl = 0;
+      }
     } else {
-      status[tile] = scan_word(epoch, kStAgg, agg);
-      uint32_t excl = 0;
-      bool timed_out = false;
+      if (lane == 0) status[tile] = scan_word(epoch, kStAgg, agg);
       // the failure-path test waits for an epoch that no tile writes
       const uint32_t want = s.scan_wait_test ? ((epoch + 1u) & 0x3FFFFFFFu) : epoch;
-      for (uint32_t p = tile - 1;; --p) {
-        unsigned long long w = status[p];
+      uint32_t excl = 0;
+      bool timed_out = false;
+      long long top = (long long)tile - 1;  // lane l reads tile top - l
+      for (;;) {
+        const long long p = top - (long long)lane;
+        const bool in_seg = p >= (long long)first;
+        unsigned long long w = 0ull;
         int spins = 0;
-        while ((uint32_t)(w >> 34) != want || ((w >> 32) & 3ull) == 0ull) {
+        for (;;) {
+          w = in_seg ? status[p] : 0ull;
+          const bool ready = !in_seg || ((uint32_t)(w >> 34) == want && ((w >> 32) & 3ull) != 0ull);
+          if (__all_sync(0xFFFFFFFFu, ready)) break;
           if (++spins > kScanWaitLimit) { timed_out = true; break; }
-          if (spins > 32) __nanosleep(64);
-          w = status[p];
+          if (spins > 16) __nanosleep(100);
         }
         if (timed_out) break;
-        excl += (uint32_t)w;
-        if (((w >> 32) & 3ull) == kStIncl || p == first) break;
+        // the nearest inclusive prefix ends the look-back; the segment's first tile
+        // always publishes one, so some window finds it
+        const unsigned incl = __ballot_sync(0xFFFFFFFFu, in_seg && ((w >> 32) & 3ull) == kStIncl);
+        const int stop = incl ? __ffs((int)incl) - 1 : 31;
+        uint32_t val = (in_seg && (int)lane <= stop) ? (uint32_t)w : 0u;
+        for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xFFFFFFFFu, val, o);
+        excl += val;
+        if (incl || top - 31 <= (long long)first) break;
+        top -= 32;
       }
-      if (timed_out) atomicOr(&s.d.status, ST_SCAN_WAIT);
-      __threadfence();
-      status[tile] = scan_word(epoch, kStIncl, excl + agg);
-      s_excl = excl;
+      if (lane == 0) {
+        if (timed_out) atomicOr(&s.d.status, ST_SCAN_WAIT);
+        status[tile] = scan_word(epoch, kStIncl, excl + agg);
+        s_excl = excl;
+      }
     }
   }
   __syncthreads();

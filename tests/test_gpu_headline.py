@@ -12,6 +12,7 @@
   100 steps, past the formation of the shock: trajectory, counts and profiles.
 * The batched ensemble: 32 runs with N log-spaced over [2^12, 2^18] (equilibrium
   boxes and piston tubes), stepped as one group, each equal to the oracle.
+* The spherical blast at 2^17 particles for 100 steps (its expansion).
 """
 import math
 
@@ -191,3 +192,24 @@ def test_ensemble_32_runs_spanning_2e12_to_2e18_as_one_group():
         g.close()
         for sim in sims:
             sim.close()
+
+
+def test_spherical_blast_2e17_for_100_steps_bit_exact():
+    """The spherical blast (hot ball at 8x density and 100x temperature, background mean
+    free path 0.005) at 2^17 particles for 100 steps: the hot ball's particles travel
+    about four ball radii, so the run covers the blast's expansion and the speed split
+    changes its threshold as the fast tail thins out.  The full size (2^27) is out of
+    the oracle's reach (its cells are sized for the fastest particle: ~10^13 pair tests
+    per step); the GPU runs it in the benchmark."""
+    s = ki.blast_setup(n=1 << 17, seed=3, steps=100)
+    arrays = ki.initial_state(s)
+    st = oracle.State(arrays)
+    oc, _ = oracle.run(s, st, 0, 100)
+    assert sum(c["collisions"] for c in oc) > 500000
+    for prec in (FP32, FP64):
+        sim = _sim(s, arrays, prec).step(100).sync()
+        got = sim.counts()
+        _assert_counts_equal(got, oc, f"blast, precision {prec}")
+        assert sum(c["fast_tests"] for c in got) > 0, "the speed split ran"
+        _assert_state_equals_oracle(sim, st, f"blast, precision {prec}")
+        sim.close()
