@@ -744,7 +744,7 @@ def run_gpu(args):
         "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz",
         "traffic": (traffic["dram_bytes_per_particle"] * n) if traffic else None,
         # what bounds it: the share of issue slots used (ncu, same kernel source)
-        "issue_active_pct": traffic.get("issue_active_pct_2e22") if traffic else None,
+        "issue_active_pct": traffic.get("issue_active_pct") if traffic else None,
         "flops_per_pair_test": FLOPS_PER_PAIR_TEST,
         "pair_tests_per_launch": float(slow_tests),
         "launch_ms": slow_ms,

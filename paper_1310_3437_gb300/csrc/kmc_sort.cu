@@ -151,7 +151,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* t
 // The wait for a predecessor is bounded: if it runs out the simulation gets the
 // ST_SCAN_WAIT status (sim_sync reports KMC_ETIMEOUT) instead of the block spinning on.
 constexpr unsigned long long kStAgg = 1ull, kStIncl = 2ull;
-constexpr int kScanWaitLimit = 1 << 22;
+constexpr int kScanWaitLimit = 1 << 20;  // spins of at least 0.1 us: about a second
 
 __device__ __forceinline__ unsigned long long scan_word(uint32_t epoch, unsigned long long state,
                                                         uint32_t value) {
@@ -186,49 +186,63 @@ __global__ void __launch_bounds__(kTile) k_scan_onepass(Batch B, uint32_t ntiles
   }
   uint32_t agg = 0;
   const uint32_t off = block_exclusive_scan(local, &agg);
-  if (threadIdx.x < 32) {
-    // warp 0: publish the tile's sum, then look back 32 predecessors at a time
-    const uint32_t lane = threadIdx.x;
-    if (tile == first) {
-      if (lane == 0) {
-        status[tile] = scan_word(epoch, kStIncl, agg);
-        s_excl = 0;
-      }
-    } else {
-      if (lane == 0) status[tile] = scan_word(epoch, kStAgg, agg);
-      // the failure-path test waits for an epoch that no tile writes
-      const uint32_t want = s.scan_wait_test ? ((epoch + 1u) & 0x3FFFFFFFu) : epoch;
-      uint32_t excl = 0;
-      bool timed_out = false;
-      long long top = (long long)tile - 1;  // lane l reads tile top - l
+  // publish the tile's sum, then look back with the whole block, kTile predecessors
+  // per read (all tiles start at about the same time, so the nearest inclusive prefix
+  // can be far back: a tile reads about t / kTile windows)
+  __shared__ uint32_t s_stop, s_val[kTile / 32];
+  __shared__ int s_done;
+  if (tile == first) {
+    if (threadIdx.x == 0) {
+      status[tile] = scan_word(epoch, kStIncl, agg);
+      s_excl = 0;
+    }
+  } else {
+    if (threadIdx.x == 0) status[tile] = scan_word(epoch, kStAgg, agg);
+    // the failure-path test waits for an epoch that no tile writes
+    const uint32_t want = s.scan_wait_test ? ((epoch + 1u) & 0x3FFFFFFFu) : epoch;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t excl = 0;
+    bool timed_out = false;
+    long long top = (long long)tile - 1;  // thread t reads tile top - t
+    for (;;) {
+      const long long p = top - (long long)threadIdx.x;
+      const bool in_seg = p >= (long long)first;
+      unsigned long long w = 0ull;
+      int spins = 0;
       for (;;) {
-        const long long p = top - (long long)lane;
-        const bool in_seg = p >= (long long)first;
-        unsigned long long w = 0ull;
-        int spins = 0;
-        for (;;) {
-          w = in_seg ? status[p] : 0ull;
-          const bool ready = !in_seg || ((uint32_t)(w >> 34) == want && ((w >> 32) & 3ull) != 0ull);
-          if (__all_sync(0xFFFFFFFFu, ready)) break;
-          if (++spins > kScanWaitLimit) { timed_out = true; break; }
-          if (spins > 16) __nanosleep(100);
-        }
-        if (timed_out) break;
-        // the nearest inclusive prefix ends the look-back; the segment's first tile
-        // always publishes one, so some window finds it
-        const unsigned incl = __ballot_sync(0xFFFFFFFFu, in_seg && ((w >> 32) & 3ull) == kStIncl);
-        const int stop = incl ? __ffs((int)incl) - 1 : 31;
-        uint32_t val = (in_seg && (int)lane <= stop) ? (uint32_t)w : 0u;
-        for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xFFFFFFFFu, val, o);
-        excl += val;
-        if (incl || top - 31 <= (long long)first) break;
-        top -= 32;
+        w = in_seg ? status[p] : 0ull;
+        const bool ready = !in_seg || ((uint32_t)(w >> 34) == want && ((w >> 32) & 3ull) != 0ull);
+        if (__syncthreads_and(ready)) break;
+        if (++spins > kScanWaitLimit) { timed_out = true; break; }
+        if (spins > 16) __nanosleep(100);
       }
-      if (lane == 0) {
-        if (timed_out) atomicOr(&s.d.status, ST_SCAN_WAIT);
-        status[tile] = scan_word(epoch, kStIncl, excl + agg);
-        s_excl = excl;
+      if (timed_out) break;
+      // the nearest inclusive prefix (lowest thread index) ends the look-back; the
+      // segment's first tile always publishes one, so some window finds it
+      if (threadIdx.x == 0) s_stop = 0xFFFFFFFFu;
+      __syncthreads();
+      const bool incl = in_seg && ((w >> 32) & 3ull) == kStIncl;
+      if (incl) atomicMin(&s_stop, threadIdx.x);
+      __syncthreads();
+      const uint32_t stop = s_stop;
+      uint32_t val = (in_seg && threadIdx.x <= stop) ? (uint32_t)w : 0u;
+      for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xFFFFFFFFu, val, o);
+      if (lane == 0) s_val[warp] = val;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int i = 0; i < kTile / 32; ++i) t += s_val[i];
+        excl += t;
+        s_done = (stop != 0xFFFFFFFFu || top - (kTile - 1) <= (long long)first) ? 1 : 0;
       }
+      __syncthreads();
+      if (s_done) break;
+      top -= kTile;
+    }
+    if (threadIdx.x == 0) {
+      if (timed_out) atomicOr(&s.d.status, ST_SCAN_WAIT);
+      status[tile] = scan_word(epoch, kStIncl, excl + agg);
+      s_excl = excl;
     }
   }
   __syncthreads();
