@@ -151,7 +151,7 @@ size_t bytes_for(const Sizes& z) {
   size_t n = z.n;
   size_t b = 0;
   b += 2 * 6 * n * sizeof(double) + 2 * 2 * n * sizeof(uint32_t);  // state, double-buffered
-  if (z.fp32) b += n * (sizeof(float4) + sizeof(float2));
+  if (z.fp32) b += (n + 1) / 2 * 3 * sizeof(float4);               // binary32 mirror
   b += 3 * n * sizeof(uint32_t) + n;                                  // key, rank, src, speed class
   b += n + 4096;                                                      // mixture species (if any)
   b += 2 * ((size_t)z.cell_cap + 2) * sizeof(uint32_t);               // cell count / start
@@ -633,8 +633,7 @@ int create_impl(const kmc_params* p, const double* const* src6, const uint32_t* 
     if ((rc = dalloc(s, &h.last[b], n))) return fail(rc);
   }
   if (zs.fp32) {
-    if ((rc = dalloc(s, &h.mir_a, n))) return fail(rc);
-    if ((rc = dalloc(s, &h.mir_b, n))) return fail(rc);
+    if ((rc = dalloc(s, &h.mir, 3 * ((n + 1) / 2)))) return fail(rc);
   }
   if (mix) {
     if ((rc = dalloc(s, &h.species, n))) return fail(rc);

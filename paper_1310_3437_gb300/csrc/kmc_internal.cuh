@@ -116,8 +116,8 @@ struct SimDev {
   uint32_t* id[2];
   uint32_t* last[2];
   // ---- per-step work arrays ----
-  float4* mir_a;        // (ox, oy, oz, vx): binary32 offsets from the cell corner
-  float2* mir_b;        // (vy, vz)
+  float4* mir;          // binary32 mirror in pair records (mirror_load / mirror_store)
+  void* mir_spare;      // unused: keeps the offsets of the fields below
   uint32_t* key;        // cell key per particle (pre-sort order)
   uint32_t* rank;       // rank inside the cell (pre-sort order)
   uint8_t* vbucket;     // per particle: how many of the trial split thresholds its
@@ -300,6 +300,29 @@ __device__ __forceinline__ uint32_t block_append(uint32_t* counter, uint32_t wan
   const uint32_t r = bbase + wbase[warp] + incl - want;
   __syncthreads();  // the slots are free for the next call
   return r;
+}
+
+// ---- guarded-binary32 mirror ------------------------------------------------ //
+// Box coordinates and velocity of every particle (sorted order), each rounded once to
+// binary32, in pair records: particles 2k and 2k + 1 share three float4,
+//   (x0, x1, y0, y1), (z0, z1, vx0, vx1), (vy0, vy1, vz0, vz1),
+// so that a 16-byte load gives one component of two consecutive partners already
+// paired for the packed f32x2 arithmetic of the row search.
+__device__ __forceinline__ void mirror_load(const float4* __restrict__ M, uint32_t j, float4& a,
+                                            float2& b) {
+  const float* r = reinterpret_cast<const float*>(M + 3 * (size_t)(j >> 1)) + (j & 1u);
+  a = make_float4(__ldg(r), __ldg(r + 2), __ldg(r + 4), __ldg(r + 6));
+  b = make_float2(__ldg(r + 8), __ldg(r + 10));
+}
+__device__ __forceinline__ void mirror_store(float4* M, uint32_t j, float x, float y, float z,
+                                             float vx, float vy, float vz) {
+  float* r = reinterpret_cast<float*>(M + 3 * (size_t)(j >> 1)) + (j & 1u);
+  r[0] = x;
+  r[2] = y;
+  r[4] = z;
+  r[6] = vx;
+  r[8] = vy;
+  r[10] = vz;
 }
 
 // ---- Morton column code --------------------------------------------------- //

@@ -130,14 +130,14 @@ __global__ void __launch_bounds__(kTile) k_search(Batch B) {
       const double* __restrict__ V0 = s.v[cur][0];
       const double* __restrict__ V1 = s.v[cur][1];
       const double* __restrict__ V2 = s.v[cur][2];
-      const float4* __restrict__ MA = s.mir_a;
-      const float2* __restrict__ MB = s.mir_b;
+      const float4* __restrict__ MM = s.mir;
       if (PREC == KMC_FP64) {
         xo[0] = X0[p]; xo[1] = X1[p]; xo[2] = X2[p];
         vo[0] = V0[p]; vo[1] = V1[p]; vo[2] = V2[p];
       } else {
-        float4 a = MA[p];
-        float2 b = MB[p];
+        float4 a;
+        float2 b;
+        mirror_load(MM, p, a, b);
         o32 = {a.x, a.y, a.z, a.w, b.x, b.y};
       }
       // one-cell periodic axes need the minimum image explicitly
@@ -215,8 +215,9 @@ __global__ void __launch_bounds__(kTile) k_search(Batch B) {
               const float sy = o32.oy - (float)wy * g.Lf[1];
               const float sz = o32.oz - (float)wz * g.Lf[2];
               for (uint32_t j = beg; j < end; ++j) {
-                const float4 a = __ldg(MA + j);
-                const float2 b = __ldg(MB + j);
+                float4 a;
+                float2 b;
+                mirror_load(MM, j, a, b);
                 float rx = a.x - sx, ry = a.y - sy, rz = a.z - sz;
                 bool keep = false;
                 if (any_cp) {
@@ -346,8 +347,7 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_cell(Batch B) {
     const float d0up = G.d0up, brel = G.b_rel, babs = G.b_abs, we = G.w_e, wrel = G.w_rel;
     const double C0 = G.c0, C1 = G.c1;
     const double L0 = s.box[0], L1 = s.box[1], L2 = s.box[2];
-    const float4* __restrict__ MA = s.mir_a;
-    const float2* __restrict__ MB = s.mir_b;
+    const float4* __restrict__ MM = s.mir;
     const double* __restrict__ X0 = s.x[cur][0];
     const double* __restrict__ X1 = s.x[cur][1];
     const double* __restrict__ X2 = s.x[cur][2];
@@ -370,8 +370,11 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_cell(Batch B) {
             sd[warp][0][t] = X0[i0 + t]; sd[warp][1][t] = X1[i0 + t]; sd[warp][2][t] = X2[i0 + t];
             sd[warp][3][t] = V0[i0 + t]; sd[warp][4][t] = V1[i0 + t]; sd[warp][5][t] = V2[i0 + t];
           } else {
-            sa[warp][t] = MA[i0 + t];
-            sb[warp][t] = MB[i0 + t];
+            float4 a;
+            float2 b;
+            mirror_load(MM, i0 + t, a, b);
+            sa[warp][t] = a;
+            sb[warp][t] = b;
           }
         }
         __syncwarp();
@@ -461,8 +464,9 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_cell(Batch B) {
                 } else {
                   float jx = 0.f, jy = 0.f, jz = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
                   if (jv) {
-                    float4 a = __ldg(MA + j);
-                    float2 b = __ldg(MB + j);
+                    float4 a;
+                    float2 b;
+                    mirror_load(MM, j, a, b);
                     int t = 0;
 #pragma unroll
                     for (int q = 0; q < 2 * K; ++q) t += j >= bnd[q] ? 1 : 0;
@@ -664,8 +668,7 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_cell32(Batch B) {
     const uint32_t* __restrict__ cs = s.cell_start;
     const float Lx = G.Lf[0], Ly = G.Lf[1], Lz = G.Lf[2];
     const float c0 = G.s_c0, c1 = G.s_c1;
-    const float4* __restrict__ MA = s.mir_a;
-    const float2* __restrict__ MB = s.mir_b;
+    const float4* __restrict__ MM = s.mir;
     float* my = si[warp];
     uint2* buf = wbuf[warp];
     uint32_t* cnt = &wcount[warp];
@@ -682,8 +685,9 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_cell32(Batch B) {
         __syncwarp();
         for (uint32_t t = lane; t < nI4; t += 32) {
           if (t < nI) {
-            const float4 a = MA[i0 + t];
-            const float2 b = MB[i0 + t];
+            float4 a;
+            float2 b;
+            mirror_load(MM, i0 + t, a, b);
             my[t] = a.x; my[ICAP + t] = a.y; my[2 * ICAP + t] = a.z;
             my[3 * ICAP + t] = a.w; my[4 * ICAP + t] = b.x; my[5 * ICAP + t] = b.y;
           } else {
@@ -747,8 +751,9 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_cell32(Batch B) {
                 const uint32_t j = cb + lane;
                 float jx = 1e30f, jy = 0.f, jz = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
                 if (j < jend) {
-                  const float4 a = __ldg(MA + j);
-                  const float2 b = __ldg(MB + j);
+                  float4 a;
+                  float2 b;
+                  mirror_load(MM, j, a, b);
                   jx = a.x + shx;
                   jy = a.y + shy;
                   jz = a.z + shz;
@@ -880,8 +885,7 @@ __global__ void __launch_bounds__(kTile, 4) k_search_rows32(Batch B) {
     const bool cp0 = nx == 1 && px, cp1 = ny == 1 && py, cp2 = nz == 1 && pz;
     const bool any_cp = cp0 || cp1 || cp2;
     const uint32_t* __restrict__ cs = s.cell_start;
-    const float4* __restrict__ MA = s.mir_a;
-    const float2* __restrict__ MB = s.mir_b;
+    const float4* __restrict__ MM = s.mir;
 
     // 1. the lane's non-empty pieces, column by column
     int np = 0;
@@ -889,8 +893,9 @@ __global__ void __launch_bounds__(kTile, 4) k_search_rows32(Batch B) {
     Own32 o = {0, 0, 0, 0, 0, 0};
     int cx = 0, cy = 0, cz = 0;
     if (valid) {
-      const float4 a = MA[p];
-      const float2 b = MB[p];
+      float4 a;
+      float2 b;
+      mirror_load(MM, p, a, b);
       o = {a.x, a.y, a.z, a.w, b.x, b.y};
       // the particle's cell, recomputed from the mirror as the sort computed it
       cx = cell_coord_f(g, 0, a.x);
@@ -1005,7 +1010,7 @@ __global__ void __launch_bounds__(kTile, 4) k_search_rows32(Batch B) {
             cd[np * 32 + lane] = (uint8_t)image_code(0, wy, wz);
             ++np;
             total += je - jb;
-            iters += (je - jb + 1u) >> 1;
+            iters += ((je + 1u) >> 1) - (jb >> 1);  // pair slots
           }
         }
         if (px && xa < 0) {  // cells [xa + nx, nx) seen through the image at -L
@@ -1015,7 +1020,7 @@ __global__ void __launch_bounds__(kTile, 4) k_search_rows32(Batch B) {
             cd[np * 32 + lane] = (uint8_t)image_code(-1, wy, wz);
             ++np;
             total += je - jb;
-            iters += (je - jb + 1u) >> 1;
+            iters += ((je + 1u) >> 1) - (jb >> 1);  // pair slots
           }
         }
         if (px && xb >= nx) {  // cells [0, xb - nx] seen through the image at +L
@@ -1025,14 +1030,14 @@ __global__ void __launch_bounds__(kTile, 4) k_search_rows32(Batch B) {
             cd[np * 32 + lane] = (uint8_t)image_code(1, wy, wz);
             ++np;
             total += je - jb;
-            iters += (je - jb + 1u) >> 1;
+            iters += ((je + 1u) >> 1) - (jb >> 1);  // pair slots
           }
         }
       }
     }
 
-    // 2. walk the pieces, two tests of one piece per iteration (one at a piece's odd
-    //    end), the binary32 pre-tests of both in packed f32x2 arithmetic
+    // 2. walk the pieces in pair slots of the mirror, two tests per iteration (a half
+    //    outside the piece masked), the binary32 pre-tests in packed f32x2 arithmetic
     const uint32_t T = __reduce_max_sync(0xFFFFFFFFu, any_cp ? total : iters);
     uint32_t j = 0, je = 0;
     int r = 0;
@@ -1051,8 +1056,9 @@ __global__ void __launch_bounds__(kTile, 4) k_search_rows32(Batch B) {
       // one-cell periodic axes (thin slabs): one test per iteration with the minimum image
       for (uint32_t t = 0; t < T; ++t) {
         if (j < je) {
-          const float4 a = __ldg(MA + j);
-          const float2 b = __ldg(MB + j);
+          float4 a;
+          float2 b;
+          mirror_load(MM, j, a, b);
           float rx = a.x - sx, ry = a.y - sy, rz = a.z - sz;
           bool keep = false;
           if (cp0) min_image_f(rx, g.halfLf[0], g.Lf[0], g.tief[0], keep);
@@ -1079,23 +1085,26 @@ __global__ void __launch_bounds__(kTile, 4) k_search_rows32(Batch B) {
       const f32x2 C0 = pack2(c0, c0), C1 = pack2(c1, c1);
       const f32x2 VX = pack2(o.vx, o.vx), VY = pack2(o.vy, o.vy), VZ = pack2(o.vz, o.vz);
       f32x2 SX = pack2(sx, sx), SY = pack2(sy, sy), SZ = pack2(sz, sz);
+      // the piece [j, je) in pair slots: slot k holds particles 2k and 2k + 1, three
+      // 16-byte loads give each component of both already paired; a half outside the
+      // piece (its first slot's lower, its last slot's upper half) is masked
+      const ulonglong2* __restrict__ MP = reinterpret_cast<const ulonglong2*>(MM);
+      uint32_t k = j >> 1, ke = (je + 1u) >> 1;
       for (uint32_t t = 0; t < T; ++t) {
-        if (j < je) {
-          const bool two = j + 1u < je;
-          const uint32_t j1 = two ? j + 1u : j;  // without a second test the first is repeated
-          const float4 a0 = __ldg(MA + j), a1 = __ldg(MA + j1);
-          const float2 b0 = __ldg(MB + j), b1 = __ldg(MB + j1);
-          const f32x2 rx = sub2(pack2(a0.x, a1.x), SX), ry = sub2(pack2(a0.y, a1.y), SY),
-                      rz = sub2(pack2(a0.z, a1.z), SZ);
-          const f32x2 gx = sub2(pack2(a0.w, a1.w), VX), gy = sub2(pack2(b0.x, b1.x), VY),
-                      gz = sub2(pack2(b0.y, b1.y), VZ);
+        if (k < ke) {
+          const ulonglong2* rec = MP + 3 * (size_t)k;
+          const ulonglong2 Q0 = __ldg(rec), Q1 = __ldg(rec + 1), Q2 = __ldg(rec + 2);
+          const f32x2 rx = sub2(Q0.x, SX), ry = sub2(Q0.y, SY), rz = sub2(Q1.x, SZ);
+          const f32x2 gx = sub2(Q1.y, VX), gy = sub2(Q2.x, VY), gz = sub2(Q2.y, VZ);
           const f32x2 R = fma2(rz, rz, fma2(ry, ry, mul2(rx, rx)));
           const f32x2 Bv = fma2(gz, gz, fma2(gy, gy, mul2(gx, gx)));
           const f32x2 bound = fma2(C1, Bv, C0);
           float R0, R1, T0, T1;
           unpack2(R, R0, R1);
           unpack2(bound, T0, T1);
-          if (R0 <= T0 || (two && R1 <= T1)) {  // rare: a sphere survivor
+          const uint32_t j0 = 2u * k;
+          const bool s0 = j0 >= j && R0 <= T0, s1 = j0 + 1u < je && R1 <= T1;
+          if (s0 || s1) {  // rare: a sphere survivor
             float rx0, rx1, ry0, ry1, rz0, rz1, gx0, gx1, gy0, gy1, gz0, gz1, B0, B1;
             unpack2(rx, rx0, rx1);
             unpack2(ry, ry0, ry1);
@@ -1104,18 +1113,19 @@ __global__ void __launch_bounds__(kTile, 4) k_search_rows32(Batch B) {
             unpack2(gy, gy0, gy1);
             unpack2(gz, gz0, gz1);
             unpack2(Bv, B0, B1);
-            if (R0 <= T0 && full_test32_call(sq, rx0, ry0, rz0, gx0, gy0, gz0, B0))
-              emit_lane(buf, cnt, s, p, j);
-            if (two && R1 <= T1 && full_test32_call(sq, rx1, ry1, rz1, gx1, gy1, gz1, B1))
-              emit_lane(buf, cnt, s, p, j + 1u);
+            if (s0 && full_test32_call(sq, rx0, ry0, rz0, gx0, gy0, gz0, B0))
+              emit_lane(buf, cnt, s, p, j0);
+            if (s1 && full_test32_call(sq, rx1, ry1, rz1, gx1, gy1, gz1, B1))
+              emit_lane(buf, cnt, s, p, j0 + 1u);
           }
-          j += two ? 2u : 1u;
-          if (j == je && r + 1 < np) {
+          if (++k == ke && r + 1 < np) {
             ++r;
             const uint2 q = pc[r * 32 + lane];
             const float4 sh = shift_tab[cd[r * 32 + lane]];
             j = q.x;
             je = q.y;
+            k = j >> 1;
+            ke = (je + 1u) >> 1;
             SX = pack2(o.ox - sh.x, o.ox - sh.x);
             SY = pack2(o.oy - sh.y, o.oy - sh.y);
             SZ = pack2(o.oz - sh.z, o.oz - sh.z);
@@ -1193,8 +1203,7 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4) k_search_fast(Batch B) {
     const double* __restrict__ V0 = s.v[cur][0];
     const double* __restrict__ V1 = s.v[cur][1];
     const double* __restrict__ V2 = s.v[cur][2];
-    const float4* __restrict__ MA = s.mir_a;
-    const float2* __restrict__ MB = s.mir_b;
+    const float4* __restrict__ MM = s.mir;
     const double L0 = s.box[0], L1 = s.box[1], L2 = s.box[2];
     Guard32 q;
     q.c0 = g.s_c0; q.c1 = g.s_c1; q.ag = g.a_g; q.tg = g.t_g; q.dtf = g.dtf;
@@ -1215,8 +1224,9 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4) k_search_fast(Batch B) {
         o32 = {d2f_rn(xo[0]), d2f_rn(xo[1]), d2f_rn(xo[2]), d2f_rn(vo[0]), d2f_rn(vo[1]),
                d2f_rn(vo[2])};
       } else {
-        const float4 a = MA[p];
-        const float2 b = MB[p];
+        float4 a;
+        float2 b;
+        mirror_load(MM, p, a, b);
         o32 = {a.x, a.y, a.z, a.w, b.x, b.y};
       }
       // cell trimming: a pair (p, j) has |r| < d0 + (|v_p| + |v_j|) dt <= d0 + (|v_p| + V) dt,
@@ -1370,8 +1380,9 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4) k_search_fast(Batch B) {
               const float sx = o32.ox - wxf * Lf0;
               const float sy = o32.oy - wyf * Lf1;
               const float sz = o32.oz - wzf * Lf2;
-              const float4 a = __ldg(MA + j);
-              const float2 b = __ldg(MB + j);
+              float4 a;
+              float2 b;
+              mirror_load(MM, j, a, b);
               const float rx = a.x - sx, ry = a.y - sy, rz = a.z - sz;
               const float gx = a.w - o32.vx, gy = b.x - o32.vy, gz = b.y - o32.vz;
               const float R = fmaf(rz, rz, fmaf(ry, ry, rx * rx));

@@ -323,8 +323,8 @@ __global__ void __launch_bounds__(kTile / 2) k_gather(Batch B) {
     s.partner[d] = kNone;
     if (s.precision == KMC_GUARDED_FP32) {
       // box coordinates and velocity, each rounded once to binary32
-      s.mir_a[d] = make_float4(d2f_rn(xs[h][0]), d2f_rn(xs[h][1]), d2f_rn(xs[h][2]), d2f_rn(vs[h][0]));
-      s.mir_b[d] = make_float2(d2f_rn(vs[h][1]), d2f_rn(vs[h][2]));
+      mirror_store(s.mir, d, d2f_rn(xs[h][0]), d2f_rn(xs[h][1]), d2f_rn(xs[h][2]),
+                   d2f_rn(vs[h][0]), d2f_rn(vs[h][1]), d2f_rn(vs[h][2]));
     }
   }
 }
