@@ -50,11 +50,13 @@ def headline_setup(n: int):
     return ki.piston_setup(n=n, seed=2, profile_bins=256, profile_every=100)
 
 
-def sample_setup():
-    """Cross-section sample of the headline tube: same density, 1/16 of the particles."""
+def sample_setup(box_yz: float = 0.25):
+    """Cross-section sample of the headline tube: same density, box_yz^2 of the
+    particles (1/16 at 0.25)."""
     n_full = 1 << 24
     full = headline_setup(n_full)
-    s = ki.piston_setup(n=n_full // 16, seed=2, box=(8.0, 0.25, 0.25), profile_bins=0,
+    n = int(round(n_full * box_yz * box_yz))
+    s = ki.piston_setup(n=n, seed=2, box=(8.0, box_yz, box_yz), profile_bins=0,
                         profile_every=0)
     return s.with_(d0=full.d0, dt=full.dt, name="piston_tube_cross_section")
 
@@ -176,23 +178,25 @@ def ncu_traffic(kernel_file: str):
 
 
 # --------------------------------------------------------------------------- #
-def oracle_sample_rate(max_seconds: float, warmup: int = 0, steps_cap: int = 50):
-    """Time the oracle on the cross-section sample; returns (rate, steps, seconds, threads)."""
+def oracle_sample_rate(max_seconds: float, warmup: int = 0, steps_cap: int = 50,
+                       threads: int = 0, box_yz: float = 0.25):
+    """Time the oracle on a cross-section sample; returns (rate, steps, seconds,
+    threads, setup).  threads = 0: all host threads."""
     import oracle
 
-    s = sample_setup()
+    s = sample_setup(box_yz)
     st = oracle.State(ki.initial_state(s))
     for k in range(warmup):
-        oracle.step(s, st, k)
+        oracle.step(s, st, k, threads=threads)
     t0 = time.perf_counter()
     done = 0
     while done < steps_cap:
-        oracle.step(s, st, warmup + done)
+        oracle.step(s, st, warmup + done, threads=threads)
         done += 1
         if time.perf_counter() - t0 >= max_seconds:
             break
     dt = time.perf_counter() - t0
-    return s.n * done / dt, done, dt, oracle.max_threads(), s
+    return s.n * done / dt, done, dt, (threads or oracle.max_threads()), s
 
 
 def run_serving(args, stream, dev):
@@ -355,6 +359,46 @@ def run_ensemble(args, stream):
     g.close()
     for q in sims:
         q.close()
+    return out
+
+
+def run_domains(args, stream):
+    """The paper's domain decomposition (Sec. 4) on one GPU: the 2^22-particle piston
+    tube (the 2^20 tube's density in an 8 x 2 x 2 box) as 1 and as 4 x slabs, guarded
+    binary32, the same steps; the decomposition changes the work, never the result
+    (the states are compared)."""
+    import torch
+
+    import paper_1310_3437_gb300 as kmc
+
+    n = args.domains_n
+    setup = ki.piston_setup(n=n, seed=2, box=(8.0, 2.0, 2.0), profile_bins=0, profile_every=0)
+    arrays = ki.initial_state(setup)
+    out = {"n": n, "box": list(setup.box), "steps": args.domains_steps}
+    states = {}
+    for P in (1, 4):
+        params = kmc.params_from_setup(setup, precision=kmc.KMC_GUARDED_FP32)
+        sim = kmc.Simulation(params, arrays, stream=stream.cuda_stream, domains=P)
+        sim.step(2).sync()
+        sim.counts()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(args.domains_steps)
+        e1.record(stream)
+        e1.synchronize()
+        sim.sync()
+        ms = e0.elapsed_time(e1) / args.domains_steps
+        owned, ghosts = sim.domains()
+        out[f"p{P}"] = {"ms_per_step": ms, "particle_steps_per_s": n / (ms / 1e3),
+                        "owned": owned.tolist(), "ghosts": ghosts.tolist()}
+        st, last = sim.state()
+        states[P] = [a.copy() for a in st] + [last.copy()]
+        sim.close()
+    out["identical_states"] = all(np.array_equal(a.view(np.uint8), b.view(np.uint8))
+                                  for a, b in zip(states[1], states[4]))
+    if not out["identical_states"]:
+        raise RuntimeError("domain decomposition: 4 slabs differ from 1")
     return out
 
 
@@ -722,6 +766,7 @@ def run_gpu(args):
     if not args.skip_blast and rank == 0:
         blast = run_blast(args, stream, dev)
     launch_overhead = run_launch_overhead(stream) if rank == 0 else None
+    domains = run_domains(args, stream) if (rank == 0 and not args.skip_domains) else None
 
     if rank != 0:
         if world > 1:
@@ -771,11 +816,18 @@ def run_gpu(args):
             "frac_incl_keys": kb / (sort_ms / 1e3) / 1e9 / pk["hbm_gbs"]}
 
     cpu = None
+    cpu1 = None
     if not args.skip_cpu and world >= 1:
         rate, done, secs, threads, s = oracle_sample_rate(args.cpu_seconds, warmup=0)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{s.n} particles (8x0.25x0.25 cross-section of the tube, same "
                          f"density), {done} oracle steps from t=0, {secs:.1f} s"}
+        rate1, done1, secs1, _, s1 = oracle_sample_rate(args.cpu_seconds / 2, warmup=0,
+                                                        threads=1, box_yz=0.125)
+        cpu1 = {"value": rate1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"{s1.n} particles (8x0.125x0.125 cross-section of the tube, same "
+                          f"density), {done1} oracle steps from t=0 on one thread, "
+                          f"{secs1:.1f} s"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -807,6 +859,7 @@ def run_gpu(args):
         "search_phase": search_phase,
         "candidate_pairs_per_step": edges_mean, "collisions_per_step": coll_mean,
         "cpu_baseline": cpu,
+        "cpu_baseline_1core": cpu1,
         "e2e": e2e,
         "e2e_device_init": e2e_dinit,
         "serve": serve,
@@ -814,6 +867,7 @@ def run_gpu(args):
         "paper_workloads": paper,
         "blast": blast,
         "launch_overhead": launch_overhead,
+        "domains": domains,
         "tuning": tuning,
         "gpu_launches": int(launches32),
         "gpu_launches_per_window": int(launches32) // max(1, len(windows32)),
@@ -859,6 +913,10 @@ def main():
     ap.add_argument("--skip-blast", action="store_true",
                     help="skip the full-size spherical blast (2^27 particles)")
     ap.add_argument("--blast-n", type=int, default=1 << 27)
+    ap.add_argument("--skip-domains", action="store_true",
+                    help="skip the domain decomposition leg (2^22 tube as 1 and 4 slabs)")
+    ap.add_argument("--domains-n", type=int, default=1 << 22)
+    ap.add_argument("--domains-steps", type=int, default=10)
     ap.add_argument("--blast-steps", type=int, default=5)
     ap.add_argument("--blast-fp64-steps", type=int, default=1)
     ap.add_argument("--serve-requests", type=int, default=300,

@@ -826,10 +826,9 @@ int dom_create(const kmc_params* p, uint32_t ndom, const double* const* src6, co
     return fail(KMC_ECUDA);
   }
   // the domains: simulations of the whole box over every particle slot (ids 0..n-1),
-  // slots outside the domain absent (the absorbed-particle marker); no speed split
-  // (each step's grid is built afresh from the particles a domain holds)
+  // slots outside the domain absent (the absorbed-particle marker); each step's grid,
+  // speed split included, is built afresh from the particles a domain holds
   kmc_params q = *p;
-  q.flags = (q.flags & ~(uint32_t)KMC_FLAG_FORCE_SPLIT) | KMC_FLAG_NO_SPLIT;
   // a domain cannot regrow its candidate-pair buffer mid-run (the others have moved
   // on): start it at one pair per particle slot unless the caller chose a size
   if (q.edge_cap == 0) q.edge_cap = std::max<uint32_t>(4096u, p->n);
