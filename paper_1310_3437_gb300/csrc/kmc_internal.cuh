@@ -302,6 +302,22 @@ __device__ __forceinline__ uint32_t block_append(uint32_t* counter, uint32_t wan
   return r;
 }
 
+// A batch launch deals the work items of its simulations to the blocks as one
+// sequence: simulation k's items start at the block after the one where simulation
+// k - 1's ended, so a batch of small simulations spreads over the whole grid instead of
+// piling onto its first blocks.  Every block walks the simulations in the same order
+// with the same item counts, so all agree on *base (the block where the next
+// simulation starts) and the blocks still cover each simulation's items exactly once.
+// Returns this thread's first item; the stride is gridDim.x * blockDim.x, and every
+// thread of a block makes the same number of trips over a span rounded up to a
+// multiple of the stride.
+__device__ __forceinline__ uint32_t dealt_first(uint32_t* base, uint32_t items) {
+  const uint32_t nb = gridDim.x;
+  const uint32_t b = (blockIdx.x + nb - *base) % nb;
+  *base = (*base + (items + blockDim.x - 1) / blockDim.x) % nb;
+  return b * blockDim.x + threadIdx.x;
+}
+
 // ---- guarded-binary32 mirror ------------------------------------------------ //
 // Box coordinates and velocity of every particle (sorted order), each rounded once to
 // binary32, in pair records: particles 2k and 2k + 1 share three float4,

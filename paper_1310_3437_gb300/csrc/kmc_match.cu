@@ -94,13 +94,14 @@ __device__ __forceinline__ double min_image(double r, double L) {
 // MIX: the plan has a mixture (per-pair contact distance, mass-weighted scatter)
 template <bool MIX>
 __global__ void __launch_bounds__(kEdgeBlock) k_refine(Batch B) {
+  uint32_t base = 0;
   for (int k = 0; k < B.nsims; ++k) {
     SimDev& s = *B.sims[k];
     if (!sim_active(s)) continue;
     const int cur = s.d.parity ^ 1;
     uint32_t nraw = s.d.n_raw < s.edge_cap ? s.d.n_raw : s.edge_cap;
     uint32_t found = 0;
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nraw; e += gridDim.x * blockDim.x) {
+    for (uint32_t e = dealt_first(&base, nraw); e < nraw; e += gridDim.x * blockDim.x) {
       uint2 pr = s.edge[e];
       uint32_t i = pr.x, j = pr.y;
       bool cand = false;
@@ -151,6 +152,7 @@ __global__ void __launch_bounds__(kEdgeBlock) k_refine(Batch B) {
 
 // the pair whose slot is 0 at an endpoint opens that endpoint's list
 __global__ void __launch_bounds__(kEdgeBlock) k_alloc(Batch B) {
+  uint32_t base = 0;
   for (int k = 0; k < B.nsims; ++k) {
     SimDev& s = *B.sims[k];
     if (!sim_active(s)) continue;
@@ -158,7 +160,7 @@ __global__ void __launch_bounds__(kEdgeBlock) k_alloc(Batch B) {
     const uint32_t stride = gridDim.x * blockDim.x;
     // uniform trip count: the appends are block-wide
     const uint32_t span = ((nraw + stride - 1) / stride) * stride;
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < span; e += stride) {
+    for (uint32_t e = dealt_first(&base, nraw); e < span; e += stride) {
       uint32_t i = kNone, j = kNone, di = 0, dj = 0;
       if (e < nraw) {
         const uint2 sl = s.e_slot[e];
@@ -177,11 +179,12 @@ __global__ void __launch_bounds__(kEdgeBlock) k_alloc(Batch B) {
 }
 
 __global__ void __launch_bounds__(kEdgeBlock) k_fill(Batch B) {
+  uint32_t base = 0;
   for (int k = 0; k < B.nsims; ++k) {
     SimDev& s = *B.sims[k];
     if (!sim_active(s)) continue;
     uint32_t nraw = s.d.n_raw < s.edge_cap ? s.d.n_raw : s.edge_cap;
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nraw; e += gridDim.x * blockDim.x) {
+    for (uint32_t e = dealt_first(&base, nraw); e < nraw; e += gridDim.x * blockDim.x) {
       uint2 sl = s.e_slot[e];
       if (sl.x == kNone) continue;
       uint2 pr = s.edge[e];
@@ -207,13 +210,14 @@ __device__ __forceinline__ bool key_less(double d2a, double ta, uint32_t ja, dou
 // pick nor be picked: the rounds over the lists match exactly the pairs that rounds
 // over all particles would.
 __global__ void __launch_bounds__(kEdgeBlock) k_best(Batch B, int round) {
+  uint32_t base = 0;
   for (int k = 0; k < B.nsims; ++k) {
     SimDev& s = *B.sims[k];
     if (!sim_active(s) || round >= s.max_rounds) continue;
     const int cur = s.d.parity ^ 1;
     const uint32_t len = s.d.wl_len[round];
     const uint32_t* __restrict__ list = s.wl[round & 1];
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < len; t += gridDim.x * blockDim.x) {
+    for (uint32_t t = dealt_first(&base, len); t < len; t += gridDim.x * blockDim.x) {
       const uint32_t i = list[t];
       const uint32_t q0 = s.off[i], q1 = q0 + s.deg[i];
       uint32_t bj = kNone, be = kNone, bid = kNone;
@@ -235,6 +239,7 @@ __global__ void __launch_bounds__(kEdgeBlock) k_best(Batch B, int round) {
 }
 
 __global__ void __launch_bounds__(kEdgeBlock) k_mutual(Batch B, int round) {
+  uint32_t base = 0;
   for (int k = 0; k < B.nsims; ++k) {
     SimDev& s = *B.sims[k];
     if (!sim_active(s) || round >= s.max_rounds) continue;
@@ -245,7 +250,7 @@ __global__ void __launch_bounds__(kEdgeBlock) k_mutual(Batch B, int round) {
     const uint32_t stride = gridDim.x * blockDim.x;
     // uniform trip count: the appends are block-wide
     const uint32_t span = ((len + stride - 1) / stride) * stride;
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < span; t += stride) {
+    for (uint32_t t = dealt_first(&base, len); t < span; t += stride) {
       bool pair = false, again = false;
       uint32_t i = kNone;
       if (t < len) {
@@ -277,12 +282,13 @@ __global__ void __launch_bounds__(kEdgeBlock) k_mutual(Batch B, int round) {
 // then stream the rest of the step:  x' = (x + v t*) + v' (dt - t*).
 template <bool MIX>
 __global__ void __launch_bounds__(kEdgeBlock) k_collide(Batch B) {
+  uint32_t base = 0;
   for (int k = 0; k < B.nsims; ++k) {
     SimDev& s = *B.sims[k];
     if (!sim_active(s)) continue;
     const int cur = s.d.parity ^ 1;
     const uint32_t total = s.d.n_pairs;
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+    for (uint32_t q = dealt_first(&base, total); q < total; q += gridDim.x * blockDim.x) {
       // the pair list holds each colliding pair once, by its smaller-id member
       const uint32_t i = s.pairs[q];
       const uint32_t j = s.partner[i];

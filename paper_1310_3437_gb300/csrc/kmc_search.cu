@@ -331,6 +331,12 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_cell(Batch B) {
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const uint32_t gwarp = blockIdx.x * kCellWarps + warp, nwarps = gridDim.x * kCellWarps;
 
+  // The cells of the batch's simulations are dealt to the warps as one sequence: a
+  // simulation's cells start at the warp after the previous simulation's last (every
+  // block walks the simulations in the same order, so all agree on the running base);
+  // dealt from warp 0 each time, the small simulations of a batch all landed on the
+  // same few blocks.
+  uint32_t base = 0;
   for (int k = 0; k < B.nsims; ++k) {
     SimDev& s = *B.sims[k];
     if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_CELL) continue;
@@ -357,7 +363,9 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_cell(Batch B) {
     WarpEmit we_ = {wbuf[warp], 0u};
     unsigned long long tests = 0;
 
-    for (uint32_t key = gwarp; key < nkeys; key += nwarps) {
+    const uint32_t first = (gwarp + nwarps - base % nwarps) % nwarps;
+    base += nkeys;
+    for (uint32_t key = first; key < nkeys; key += nwarps) {
       const uint32_t startA = __ldg(cs + key), endA = __ldg(cs + key + 1);
       if (startA == endA) continue;
       int cx, cy, cz;
@@ -648,6 +656,12 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_cell32(Batch B) {
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const uint32_t gwarp = blockIdx.x * kCellWarps + warp, nwarps = gridDim.x * kCellWarps;
 
+  // The cells of the batch's simulations are dealt to the warps as one sequence: a
+  // simulation's cells start at the warp after the previous simulation's last (every
+  // block walks the simulations in the same order, so all agree on the running base);
+  // dealt from warp 0 each time, the small simulations of a batch all landed on the
+  // same few blocks.
+  uint32_t base = 0;
   for (int k = 0; k < B.nsims; ++k) {
     SimDev& s = *B.sims[k];
     if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_CELL) continue;
@@ -674,7 +688,9 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_cell32(Batch B) {
     uint32_t* cnt = &wcount[warp];
     unsigned long long tests = 0;
 
-    for (uint32_t key = gwarp; key < nkeys; key += nwarps) {
+    const uint32_t first = (gwarp + nwarps - base % nwarps) % nwarps;
+    base += nkeys;
+    for (uint32_t key = first; key < nkeys; key += nwarps) {
       const uint32_t startA = __ldg(cs + key), endA = __ldg(cs + key + 1);
       if (startA == endA) continue;
       int cx, cy, cz;
