@@ -181,6 +181,14 @@ __device__ __forceinline__ bool sim_active(const SimDev& s) {
   return s.d.status == 0 && s.d.steps_left > 0;
 }
 
+// A member that runs this step.  Unlike the status word, which the searches, the scan
+// and the collision set while they run, steps_left changes only between kernels (the
+// step's last one counts it down), so every thread and block of a launch reads the
+// same value.  Control flow that reaches a barrier, or that blocks must agree on
+// (dealing a batch's items), decides on this and the launch-fixed grid fields; the
+// status word only gates the work, read once per block or per warp.
+__device__ __forceinline__ bool sim_scheduled(const SimDev& s) { return s.d.steps_left > 0; }
+
 // Absorbing walls: the particles that have left sort into one extra key after every
 // cell key (and after the fast population's keys), so that they occupy the end of the
 // sorted order, [live, n), and no cell holds them.
@@ -300,22 +308,6 @@ __device__ __forceinline__ uint32_t block_append(uint32_t* counter, uint32_t wan
   const uint32_t r = bbase + wbase[warp] + incl - want;
   __syncthreads();  // the slots are free for the next call
   return r;
-}
-
-// A batch launch deals the work items of its simulations to the blocks as one
-// sequence: simulation k's items start at the block after the one where simulation
-// k - 1's ended, so a batch of small simulations spreads over the whole grid instead of
-// piling onto its first blocks.  Every block walks the simulations in the same order
-// with the same item counts, so all agree on *base (the block where the next
-// simulation starts) and the blocks still cover each simulation's items exactly once.
-// Returns this thread's first item; the stride is gridDim.x * blockDim.x, and every
-// thread of a block makes the same number of trips over a span rounded up to a
-// multiple of the stride.
-__device__ __forceinline__ uint32_t dealt_first(uint32_t* base, uint32_t items) {
-  const uint32_t nb = gridDim.x;
-  const uint32_t b = (blockIdx.x + nb - *base) % nb;
-  *base = (*base + (items + blockDim.x - 1) / blockDim.x) % nb;
-  return b * blockDim.x + threadIdx.x;
 }
 
 // ---- guarded-binary32 mirror ------------------------------------------------ //

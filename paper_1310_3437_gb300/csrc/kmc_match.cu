@@ -90,18 +90,83 @@ __device__ __forceinline__ double min_image(double r, double L) {
   return r;
 }
 
+// ---- dealing a batch's items to the blocks ---------------------------------- //
+// The items of all members (candidate pairs, work-list entries, colliding pairs) form
+// one sequence dealt to the blocks: member k's first item goes to the block after the
+// one that took member k - 1's last, so a batch of many small members spreads over the
+// whole grid instead of piling onto the grid's first blocks.  A block reads the counts
+// of up to kEdgeBlock members at once, one thread each (walked one member after
+// another, the counts were a chain of dependent loads of about a microsecond per
+// member and kernel), places the members by a block-wide scan of the blocks each one
+// spans, and visits only the members it holds items of.  count(s) gives member s's
+// items from fields that stay fixed during the launch, so every block deals alike; the
+// status word is read once per member and block.  body(s, first, trips) does the
+// block's share: items first, first + stride, ..., trips of them per thread, the same
+// trips for every thread of the block (the last may lie past the end), so body may use
+// block-wide appends.  Blocks of kEdgeBlock threads.
+template <class Count, class Body>
+__device__ __forceinline__ void for_dealt(const Batch& B, Count count, Body body) {
+  __shared__ uint32_t s_first[kEdgeBlock], s_trips[kEdgeBlock], s_wsum[kEdgeBlock / 32];
+  const uint32_t nb = gridDim.x, stride = nb * (uint32_t)kEdgeBlock;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint32_t base = 0;  // the block where the chunk's first member starts
+  for (int k0 = 0; k0 < B.nsims; k0 += kEdgeBlock) {
+    const int k = k0 + (int)threadIdx.x;
+    uint32_t c = 0;
+    bool live = false;
+    if (k < B.nsims) {
+      const SimDev& s = *B.sims[k];
+      c = count(s);
+      live = s.d.status == 0;
+    }
+    // blocks the member spans, modulo the grid
+    const uint32_t span = (uint32_t)((((uint64_t)c + kEdgeBlock - 1) / kEdgeBlock) % nb);
+    uint32_t incl = span;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= (uint32_t)o) incl += y;
+    }
+    if (lane == 31) s_wsum[warp] = incl;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kEdgeBlock / 32; ++w) {
+      const uint32_t v = s_wsum[w];
+      if (w < (int)warp) before += v;
+      total += v;
+    }
+    const uint32_t start = (base + before + incl - span) % nb;
+    const uint32_t at = ((blockIdx.x + nb - start) % nb) * (uint32_t)kEdgeBlock;
+    s_first[threadIdx.x] = at;
+    s_trips[threadIdx.x] =
+        (live && c > at) ? (uint32_t)(((uint64_t)(c - at) + stride - 1) / stride) : 0u;
+    base = (base + total) % nb;
+    __syncthreads();
+    const int kn = B.nsims - k0 < kEdgeBlock ? B.nsims - k0 : kEdgeBlock;
+    for (int j = 0; j < kn; ++j) {
+      const uint32_t trips = s_trips[j];
+      if (trips) body(*B.sims[k0 + j], s_first[j] + threadIdx.x, trips);
+    }
+    __syncthreads();  // the tables are rewritten for the next chunk
+  }
+}
+
+// candidate pairs the search stored (a member whose buffer overflowed is not live)
+__device__ __forceinline__ uint32_t raw_pairs(const SimDev& s) {
+  return s.d.n_raw < s.edge_cap ? s.d.n_raw : s.edge_cap;
+}
+
 // ---- k_refine ------------------------------------------------------------ //
 // MIX: the plan has a mixture (per-pair contact distance, mass-weighted scatter)
 template <bool MIX>
 __global__ void __launch_bounds__(kEdgeBlock) k_refine(Batch B) {
-  uint32_t base = 0;
-  for (int k = 0; k < B.nsims; ++k) {
-    SimDev& s = *B.sims[k];
-    if (!sim_active(s)) continue;
+  for_dealt(B, [](const SimDev& s) { return sim_scheduled(s) ? raw_pairs(s) : 0u; },
+            [](SimDev& s, uint32_t first, uint32_t) {
     const int cur = s.d.parity ^ 1;
-    uint32_t nraw = s.d.n_raw < s.edge_cap ? s.d.n_raw : s.edge_cap;
+    const uint32_t nraw = raw_pairs(s);
     uint32_t found = 0;
-    for (uint32_t e = dealt_first(&base, nraw); e < nraw; e += gridDim.x * blockDim.x) {
+    for (uint32_t e = first; e < nraw; e += gridDim.x * kEdgeBlock) {
       uint2 pr = s.edge[e];
       uint32_t i = pr.x, j = pr.y;
       bool cand = false;
@@ -145,22 +210,20 @@ __global__ void __launch_bounds__(kEdgeBlock) k_refine(Batch B) {
       }
     }
     block_append(&s.d.n_edges, found);  // one atomic per block
-  }
+  });
 }
 
 // ---- candidate lists -------------------------------------------------------- //
 
 // the pair whose slot is 0 at an endpoint opens that endpoint's list
 __global__ void __launch_bounds__(kEdgeBlock) k_alloc(Batch B) {
-  uint32_t base = 0;
-  for (int k = 0; k < B.nsims; ++k) {
-    SimDev& s = *B.sims[k];
-    if (!sim_active(s)) continue;
-    const uint32_t nraw = s.d.n_raw < s.edge_cap ? s.d.n_raw : s.edge_cap;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    // uniform trip count: the appends are block-wide
-    const uint32_t span = ((nraw + stride - 1) / stride) * stride;
-    for (uint32_t e = dealt_first(&base, nraw); e < span; e += stride) {
+  for_dealt(B, [](const SimDev& s) { return sim_scheduled(s) ? raw_pairs(s) : 0u; },
+            [](SimDev& s, uint32_t first, uint32_t trips) {
+    const uint32_t nraw = raw_pairs(s);
+    const uint32_t stride = gridDim.x * kEdgeBlock;
+    // the block's trip count, the same for all its threads: the appends are block-wide
+    uint32_t e = first;
+    for (uint32_t t = 0; t < trips; ++t, e += stride) {
       uint32_t i = kNone, j = kNone, di = 0, dj = 0;
       if (e < nraw) {
         const uint2 sl = s.e_slot[e];
@@ -175,23 +238,21 @@ __global__ void __launch_bounds__(kEdgeBlock) k_alloc(Batch B) {
       if (i != kNone) { s.off[i] = at; s.wl[0][wa] = i; }
       if (j != kNone) { s.off[j] = at + di; s.wl[0][wa + (i != kNone ? 1u : 0u)] = j; }
     }
-  }
+  });
 }
 
 __global__ void __launch_bounds__(kEdgeBlock) k_fill(Batch B) {
-  uint32_t base = 0;
-  for (int k = 0; k < B.nsims; ++k) {
-    SimDev& s = *B.sims[k];
-    if (!sim_active(s)) continue;
-    uint32_t nraw = s.d.n_raw < s.edge_cap ? s.d.n_raw : s.edge_cap;
-    for (uint32_t e = dealt_first(&base, nraw); e < nraw; e += gridDim.x * blockDim.x) {
+  for_dealt(B, [](const SimDev& s) { return sim_scheduled(s) ? raw_pairs(s) : 0u; },
+            [](SimDev& s, uint32_t first, uint32_t) {
+    const uint32_t nraw = raw_pairs(s);
+    for (uint32_t e = first; e < nraw; e += gridDim.x * kEdgeBlock) {
       uint2 sl = s.e_slot[e];
       if (sl.x == kNone) continue;
       uint2 pr = s.edge[e];
       s.adj[s.off[pr.x] + sl.x] = make_uint2(pr.y, e);
       s.adj[s.off[pr.y] + sl.y] = make_uint2(pr.x, e);
     }
-  }
+  });
 }
 
 // ---- matching rounds ------------------------------------------------------ //
@@ -209,15 +270,17 @@ __device__ __forceinline__ bool key_less(double d2a, double ta, uint32_t ja, dou
 // candidate).  A particle left off it has no unmatched candidate, so it can neither
 // pick nor be picked: the rounds over the lists match exactly the pairs that rounds
 // over all particles would.
+__device__ __forceinline__ uint32_t round_list(const SimDev& s, int round) {
+  return sim_scheduled(s) && round < s.max_rounds ? s.d.wl_len[round] : 0u;
+}
+
 __global__ void __launch_bounds__(kEdgeBlock) k_best(Batch B, int round) {
-  uint32_t base = 0;
-  for (int k = 0; k < B.nsims; ++k) {
-    SimDev& s = *B.sims[k];
-    if (!sim_active(s) || round >= s.max_rounds) continue;
+  for_dealt(B, [round](const SimDev& s) { return round_list(s, round); },
+            [round](SimDev& s, uint32_t first, uint32_t) {
     const int cur = s.d.parity ^ 1;
     const uint32_t len = s.d.wl_len[round];
     const uint32_t* __restrict__ list = s.wl[round & 1];
-    for (uint32_t t = dealt_first(&base, len); t < len; t += gridDim.x * blockDim.x) {
+    for (uint32_t t = first; t < len; t += gridDim.x * kEdgeBlock) {
       const uint32_t i = list[t];
       const uint32_t q0 = s.off[i], q1 = q0 + s.deg[i];
       uint32_t bj = kNone, be = kNone, bid = kNone;
@@ -235,22 +298,20 @@ __global__ void __launch_bounds__(kEdgeBlock) k_best(Batch B, int round) {
       s.best[i] = bj;
       s.best_e[i] = be;
     }
-  }
+  });
 }
 
 __global__ void __launch_bounds__(kEdgeBlock) k_mutual(Batch B, int round) {
-  uint32_t base = 0;
-  for (int k = 0; k < B.nsims; ++k) {
-    SimDev& s = *B.sims[k];
-    if (!sim_active(s) || round >= s.max_rounds) continue;
+  for_dealt(B, [round](const SimDev& s) { return round_list(s, round); },
+            [round](SimDev& s, uint32_t first, uint32_t trips) {
     const int cur = s.d.parity ^ 1;
     const uint32_t len = s.d.wl_len[round];
     const uint32_t* __restrict__ list = s.wl[round & 1];
     uint32_t* __restrict__ next = s.wl[(round + 1) & 1];
-    const uint32_t stride = gridDim.x * blockDim.x;
-    // uniform trip count: the appends are block-wide
-    const uint32_t span = ((len + stride - 1) / stride) * stride;
-    for (uint32_t t = dealt_first(&base, len); t < span; t += stride) {
+    const uint32_t stride = gridDim.x * kEdgeBlock;
+    // the block's trip count, the same for all its threads: the appends are block-wide
+    uint32_t t = first;
+    for (uint32_t q = 0; q < trips; ++q, t += stride) {
       bool pair = false, again = false;
       uint32_t i = kNone;
       if (t < len) {
@@ -273,7 +334,7 @@ __global__ void __launch_bounds__(kEdgeBlock) k_mutual(Batch B, int round) {
         if (again) next[w] = i;
       }
     }
-  }
+  });
 }
 
 // ---- collision update ------------------------------------------------------ //
@@ -282,13 +343,11 @@ __global__ void __launch_bounds__(kEdgeBlock) k_mutual(Batch B, int round) {
 // then stream the rest of the step:  x' = (x + v t*) + v' (dt - t*).
 template <bool MIX>
 __global__ void __launch_bounds__(kEdgeBlock) k_collide(Batch B) {
-  uint32_t base = 0;
-  for (int k = 0; k < B.nsims; ++k) {
-    SimDev& s = *B.sims[k];
-    if (!sim_active(s)) continue;
+  for_dealt(B, [](const SimDev& s) { return sim_scheduled(s) ? s.d.n_pairs : 0u; },
+            [](SimDev& s, uint32_t first, uint32_t) {
     const int cur = s.d.parity ^ 1;
     const uint32_t total = s.d.n_pairs;
-    for (uint32_t q = dealt_first(&base, total); q < total; q += gridDim.x * blockDim.x) {
+    for (uint32_t q = first; q < total; q += gridDim.x * kEdgeBlock) {
       // the pair list holds each colliding pair once, by its smaller-id member
       const uint32_t i = s.pairs[q];
       const uint32_t j = s.partner[i];
@@ -340,7 +399,7 @@ __global__ void __launch_bounds__(kEdgeBlock) k_collide(Batch B) {
         s.v[cur][c][j] = nb;
       }
     }
-  }
+  });
 }
 
 int launch_match_lists(const LaunchPlan& L, cudaStream_t st) {

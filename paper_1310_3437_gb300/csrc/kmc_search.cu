@@ -95,8 +95,10 @@ __global__ void __launch_bounds__(kTile) k_search(Batch B) {
   for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     int k = find_sim(B.ptile, B.nsims, tile);
     SimDev& s = *B.sims[k];
-    if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_PARTICLE) continue;
-    __syncthreads();  // the previous tile's flush has read the staging buffer
+    if (s.d.grid.mode != KMC_SEARCH_PARTICLE) continue;
+    // the previous tile's flush has read the staging buffer; the status word can change
+    // while the search runs (a full pair buffer), so the block takes one answer
+    if (!__syncthreads_and(sim_active(s))) continue;
     if (threadIdx.x == 0) { scnt = 0; stests = 0; }
     __syncthreads();
 
@@ -332,14 +334,18 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_cell(Batch B) {
   const uint32_t gwarp = blockIdx.x * kCellWarps + warp, nwarps = gridDim.x * kCellWarps;
 
   // The cells of the batch's simulations are dealt to the warps as one sequence: a
-  // simulation's cells start at the warp after the previous simulation's last (every
-  // block walks the simulations in the same order, so all agree on the running base);
-  // dealt from warp 0 each time, the small simulations of a batch all landed on the
-  // same few blocks.
+  // simulation's cells start at the warp after the previous simulation's last.  Every
+  // warp walks the simulations in the same order and decides on fields that stay fixed
+  // during the launch, so all agree on the running base; the status word, which the
+  // search itself can set (a full pair buffer), only gates the work.  Dealt from warp 0
+  // each time, the small simulations of a batch all landed on the same few blocks.
   uint32_t base = 0;
   for (int k = 0; k < B.nsims; ++k) {
     SimDev& s = *B.sims[k];
-    if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_CELL) continue;
+    if (!sim_scheduled(s) || s.d.grid.mode != KMC_SEARCH_CELL) continue;
+    const uint32_t first = (gwarp + nwarps - base % nwarps) % nwarps;
+    base += s.d.grid.nkeys;
+    if (!__all_sync(0xFFFFFFFFu, sim_active(s))) continue;
     const Grid& G = s.d.grid;
     const int nx = G.nc[0], ny = G.nc[1], nz = G.nc[2];
     const int Kx = nx == 1 ? 0 : K, Ky = ny == 1 ? 0 : K, Kz = nz == 1 ? 0 : K;
@@ -363,8 +369,6 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_cell(Batch B) {
     WarpEmit we_ = {wbuf[warp], 0u};
     unsigned long long tests = 0;
 
-    const uint32_t first = (gwarp + nwarps - base % nwarps) % nwarps;
-    base += nkeys;
     for (uint32_t key = first; key < nkeys; key += nwarps) {
       const uint32_t startA = __ldg(cs + key), endA = __ldg(cs + key + 1);
       if (startA == endA) continue;
@@ -656,16 +660,17 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_cell32(Batch B) {
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const uint32_t gwarp = blockIdx.x * kCellWarps + warp, nwarps = gridDim.x * kCellWarps;
 
-  // The cells of the batch's simulations are dealt to the warps as one sequence: a
-  // simulation's cells start at the warp after the previous simulation's last (every
-  // block walks the simulations in the same order, so all agree on the running base);
-  // dealt from warp 0 each time, the small simulations of a batch all landed on the
-  // same few blocks.
+  // The cells of the batch's simulations are dealt to the warps as one sequence (see
+  // k_search_cell: the dealing decides on launch-fixed fields only).
   uint32_t base = 0;
   for (int k = 0; k < B.nsims; ++k) {
     SimDev& s = *B.sims[k];
-    if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_CELL) continue;
-    __syncthreads();
+    if (!sim_scheduled(s) || s.d.grid.mode != KMC_SEARCH_CELL) continue;
+    const uint32_t first = (gwarp + nwarps - base % nwarps) % nwarps;
+    base += s.d.grid.nkeys;
+    // every warp is done with the previous simulation's constants; the status word can
+    // change while the search runs, so the block takes one answer
+    if (!__syncthreads_and(sim_active(s))) continue;
     if (threadIdx.x == 0) {
       const Grid& G0 = s.d.grid;
       sq.c0 = G0.s_c0; sq.c1 = G0.s_c1; sq.ag = G0.a_g; sq.tg = G0.t_g; sq.dtf = G0.dtf;
@@ -688,8 +693,6 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_cell32(Batch B) {
     uint32_t* cnt = &wcount[warp];
     unsigned long long tests = 0;
 
-    const uint32_t first = (gwarp + nwarps - base % nwarps) % nwarps;
-    base += nkeys;
     for (uint32_t key = first; key < nkeys; key += nwarps) {
       const uint32_t startA = __ldg(cs + key), endA = __ldg(cs + key + 1);
       if (startA == endA) continue;
@@ -830,6 +833,7 @@ __global__ void __launch_bounds__(kTile, 4) k_search_rows32(Batch B) {
   __shared__ uint32_t wcount[RL::kWarps];
   __shared__ Guard32 sq;
   __shared__ float4 shift_tab[64];  // image shift (x, y, z) of each image code
+  __shared__ int s_live;            // the current simulation runs this step
   // grid-stride over tiles of kTile particles: the kernel is launched every step on an
   // occupancy-sized grid and exits at once when the step runs another search
   if (!batch_uses(B, KMC_SEARCH_ROW)) return;
@@ -859,7 +863,8 @@ __global__ void __launch_bounds__(kTile, 4) k_search_rows32(Batch B) {
   for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int k = find_sim(B.ptile, B.nsims, tile);
     SimDev& s = *B.sims[k];
-    if (!sim_active(s) || s.d.grid.mode != KMC_SEARCH_ROW || (s.bc[0] == KMC_PERIODIC) != PX)
+    // launch-fixed fields only: the barriers below depend on it
+    if (!sim_scheduled(s) || s.d.grid.mode != KMC_SEARCH_ROW || (s.bc[0] == KMC_PERIODIC) != PX)
       continue;
     const Grid& g = s.d.grid;
     // The shared constants change only with the simulation (block-uniform: every warp
@@ -871,6 +876,9 @@ __global__ void __launch_bounds__(kTile, 4) k_search_rows32(Batch B) {
       if (threadIdx.x == 0) {
         sq.c0 = g.s_c0; sq.c1 = g.s_c1; sq.ag = g.a_g; sq.tg = g.t_g; sq.dtf = g.dtf;
         sq.d0up = g.d0up; sq.brel = g.b_rel; sq.babs = g.b_abs; sq.we = g.w_e; sq.wrel = g.w_rel;
+        // the status word, read once per simulation and block (the search itself can set
+        // it: a full pair buffer only stops the stores, which are bounds-checked)
+        s_live = sim_active(s) ? 1 : 0;
       }
       if (threadIdx.x < 64) {
         const uint32_t c = threadIdx.x;
@@ -882,6 +890,7 @@ __global__ void __launch_bounds__(kTile, 4) k_search_rows32(Batch B) {
       __syncthreads();
       kcur = k;
     }
+    if (!s_live) continue;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t nslow = (g.split || s.absorb) ? __ldg(s.cell_start + g.nkeys) : s.n;
     const uint32_t p = (tile - B.ptile[k]) * kTile + threadIdx.x;
@@ -1191,7 +1200,10 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4) k_search_fast(Batch B) {
   for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int k = find_sim(B.ptile, B.nsims, tile);
     SimDev& s = *B.sims[k];
-    if (!sim_active(s) || !s.d.grid.split) continue;
+    // launch-fixed fields first; the status word (the search itself can set it) as one
+    // answer per warp
+    if (!sim_scheduled(s) || !s.d.grid.split) continue;
+    if (!__all_sync(0xFFFFFFFFu, sim_active(s))) continue;
     const Grid& g = s.d.grid;
     const uint32_t* __restrict__ cs = s.cell_start;
     const uint32_t nk = g.nkeys;

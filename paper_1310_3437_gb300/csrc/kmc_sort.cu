@@ -167,7 +167,9 @@ __global__ void __launch_bounds__(kTile) k_scan_onepass(Batch B, uint32_t ntiles
   const uint32_t* pre = B.stile_c;
   const int k = find_sim(pre, B.nsims, tile);
   SimDev& s = *B.sims[k];
-  if (!sim_active(s)) return;
+  // a tile that waited too long sets the status word while the scan runs: the block
+  // takes one answer (every thread reaches the barriers below or none does)
+  if (!__syncthreads_and(sim_active(s))) return;
   const ScanView v = scan_view(s);
   const uint32_t first = pre[k];
   const uint32_t base = (tile - first) * kScanTile;
