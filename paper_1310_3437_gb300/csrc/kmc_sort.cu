@@ -5,8 +5,8 @@
 //   k_count   cell key per particle; rank inside the cell by a warp-aggregated
 //             atomic increment (a run of equal keys in neighbouring lanes shares one
 //             atomic).
-//   scan      segmented exclusive scan of the counts -> cell_start (three launches,
-//             no inter-block waiting); clears the counts for the next step.
+//   scan      segmented exclusive scan of the counts -> cell_start (one launch,
+//             decoupled look-back); clears the counts for the next step.
 //   k_scatter records the source of every position of the new order;
 //   k_gather  permutes the binary64 state into the other buffer, writes the
 //             binary32 mirror (box coordinates and velocity) for the guarded
@@ -113,33 +113,6 @@ __device__ __forceinline__ ScanView scan_view(SimDev& s) {
   return v;
 }
 
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* total) {
-  __shared__ uint32_t warp_sums[kTile / 32 + 1];
-  unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-  uint32_t incl = x;
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= (unsigned)o) incl += y;
-  }
-  if (lane == 31) warp_sums[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    uint32_t w = lane < kTile / 32 ? warp_sums[lane] : 0;
-    uint32_t wi = w;
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
-      if (lane >= (unsigned)o) wi += y;
-    }
-    if (lane < kTile / 32) warp_sums[lane] = wi - w;  // exclusive
-    if (lane == kTile / 32 - 1) warp_sums[kTile / 32] = wi;
-  }
-  __syncthreads();
-  uint32_t r = warp_sums[wid] + incl - x;
-  if (total) *total = warp_sums[kTile / 32];
-  __syncthreads();
-  return r;
-}
-
 // Single-pass segmented scan with decoupled look-back (Merrill and Garland, "Single-
 // pass Parallel Prefix Scan with Decoupled Look-back", NVIDIA technical report, 2016).
 // Tiles are handed out in launch order by an atomic counter, so every tile a block
@@ -176,18 +149,60 @@ __global__ void __launch_bounds__(kTile) k_scan_onepass(Batch B, uint32_t ntiles
   if (base > v.len) return;  // past the key space: no later tile of this segment waits
   const uint32_t epoch = *(volatile uint32_t*)&B.scan_ctl[1] & 0x3FFFFFFFu;
   volatile unsigned long long* status = B.tile_status;
-  constexpr int PER = kScanTile / kTile;
-  uint32_t vals[PER];
-  const uint32_t e0 = base + threadIdx.x * PER;
-  uint32_t local = 0;
+  // The tile in the warps' layout: warp w holds keys [512 w, 512 w + 512) of the tile
+  // and lane l the four 16-byte groups 512 w + 128 q + 4 l (q = 0..3), so every load
+  // and store instruction of a warp covers 512 contiguous bytes.  Groups that reach
+  // past the key space are read and written element by element.
+  constexpr int kGroups = kScanTile / kTile / 4;
+  constexpr uint32_t kWarpKeys = kScanTile / (kTile / 32);
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t eb = base + warp * kWarpKeys + lane * 4u;  // this lane's group q = 0
+  uint4 val[kGroups];
+  uint32_t gsum[kGroups], goff[kGroups];
 #pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const uint32_t e = e0 + i;
-    vals[i] = e < v.len ? v.in[e] : 0u;
-    local += vals[i];
+  for (int q = 0; q < kGroups; ++q) {
+    const uint32_t e = eb + 128u * q;
+    if (e + 3u < v.len) {
+      val[q] = *reinterpret_cast<const uint4*>(v.in + e);
+    } else {
+      val[q].x = e < v.len ? v.in[e] : 0u;
+      val[q].y = e + 1u < v.len ? v.in[e + 1u] : 0u;
+      val[q].z = e + 2u < v.len ? v.in[e + 2u] : 0u;
+      val[q].w = 0u;
+    }
+    gsum[q] = val[q].x + val[q].y + val[q].z + val[q].w;
   }
-  uint32_t agg = 0;
-  const uint32_t off = block_exclusive_scan(local, &agg);
+  // exclusive prefix of each group within the warp, groups in (q, lane) order
+  uint32_t wrun = 0;
+#pragma unroll
+  for (int q = 0; q < kGroups; ++q) {
+    uint32_t incl = gsum[q];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= (uint32_t)o) incl += y;
+    }
+    goff[q] = wrun + incl - gsum[q];
+    wrun += __shfl_sync(0xFFFFFFFFu, incl, 31);
+  }
+  // the warps' totals -> each warp's offset in the tile, and the tile's sum
+  __shared__ uint32_t s_w[kTile / 32 + 1];
+  if (lane == 0) s_w[warp] = wrun;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = lane < kTile / 32 ? s_w[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+      if (lane >= (uint32_t)o) wi += y;
+    }
+    if (lane < kTile / 32) s_w[lane] = wi - w;
+    if (lane == kTile / 32 - 1) s_w[kTile / 32] = wi;
+  }
+  __syncthreads();
+  const uint32_t woff = s_w[warp];
+  const uint32_t agg = s_w[kTile / 32];
   // publish the tile's sum, then look back with the whole block, kTile predecessors
   // per read (all tiles start at about the same time, so the nearest inclusive prefix
   // can be far back: a tile reads about t / kTile windows)
@@ -202,7 +217,6 @@ __global__ void __launch_bounds__(kTile) k_scan_onepass(Batch B, uint32_t ntiles
     if (threadIdx.x == 0) status[tile] = scan_word(epoch, kStAgg, agg);
     // the failure-path test waits for an epoch that no tile writes
     const uint32_t want = s.scan_wait_test ? ((epoch + 1u) & 0x3FFFFFFFu) : epoch;
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     uint32_t excl = 0;
     bool timed_out = false;
     long long top = (long long)tile - 1;  // thread t reads tile top - t
@@ -248,13 +262,32 @@ __global__ void __launch_bounds__(kTile) k_scan_onepass(Batch B, uint32_t ntiles
     }
   }
   __syncthreads();
-  uint32_t o = s_excl + off;
+  const uint32_t tb = s_excl + woff;
 #pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const uint32_t e = e0 + i;
-    if (e <= v.len) v.out[e] = o;
-    if (v.clear && e < v.len && vals[i]) v.clear[e] = 0;
-    o += vals[i];
+  for (int q = 0; q < kGroups; ++q) {
+    const uint32_t e = eb + 128u * q;
+    uint4 st;
+    st.x = tb + goff[q];
+    st.y = st.x + val[q].x;
+    st.z = st.y + val[q].y;
+    st.w = st.z + val[q].z;
+    // element len (a virtual zero) receives the total
+    if (e + 3u <= v.len) {
+      *reinterpret_cast<uint4*>(v.out + e) = st;
+    } else {
+      if (e <= v.len) v.out[e] = st.x;
+      if (e + 1u <= v.len) v.out[e + 1u] = st.y;
+      if (e + 2u <= v.len) v.out[e + 2u] = st.z;
+    }
+    if (v.clear && gsum[q]) {  // the counts are cleared for the next step
+      if (e + 3u < v.len) {
+        *reinterpret_cast<uint4*>(v.clear + e) = make_uint4(0u, 0u, 0u, 0u);
+      } else {
+        if (e < v.len) v.clear[e] = 0u;
+        if (e + 1u < v.len) v.clear[e + 1u] = 0u;
+        if (e + 2u < v.len) v.clear[e + 2u] = 0u;
+      }
+    }
   }
 }
 
