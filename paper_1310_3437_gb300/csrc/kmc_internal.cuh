@@ -15,7 +15,7 @@
 namespace kmc {
 
 constexpr int kTile = 256;          // particles per block in particle kernels
-constexpr int kScanTile = 4096;     // keys per tile of the cell scan
+constexpr int kScanTile = 8192;     // keys per tile of the cell scan
 constexpr int kProfTile = 8192;     // particles per block in the profile kernel
 constexpr int kEdgeBlock = 256;     // threads per block in edge / adjacency kernels
 constexpr int kSearchBuf = 512;     // per-block shared-memory staging of emitted pairs
