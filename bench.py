@@ -765,7 +765,7 @@ def run_gpu(args):
     blast = None
     if not args.skip_blast and rank == 0:
         blast = run_blast(args, stream, dev)
-    launch_overhead = run_launch_overhead(stream) if rank == 0 else None
+    launch_overhead = run_launch_overhead(stream) if rank == 0 and not args.skip_launch_probe else None
     domains = run_domains(args, stream) if (rank == 0 and not args.skip_domains) else None
 
     if rank != 0:
@@ -905,6 +905,8 @@ def main():
     ap.add_argument("--serve-host-init", action="store_true",
                     help="serving requests carry host arrays instead of a device-init descriptor")
     ap.add_argument("--skip-ensemble", action="store_true")
+    ap.add_argument("--skip-launch-probe", action="store_true",
+                    help="skip the launch-overhead probe (200 graph replays of a 4096-particle box)")
     ap.add_argument("--skip-paper", action="store_true",
                     help="skip the paper's timing workloads (10^8 3D, 4e7 2D particles)")
     ap.add_argument("--paper-steps", type=int, default=10)

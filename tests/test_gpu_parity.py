@@ -511,6 +511,31 @@ def test_group_mixing_every_variant_equals_each_alone():
         g.close()
 
 
+@pytest.mark.parametrize("search", [kmc.KMC_SEARCH_CELL, kmc.KMC_SEARCH_ROW])
+def test_group_members_overflowing_mid_search_leave_the_others_exact(search):
+    """Batch kernels deal the members' cells and pairs to the grid as one sequence.  A
+    member whose pair buffer fills sets its status while the search runs; blocks that
+    look at it earlier or later must still agree on where every other member's work
+    falls, so no cell of another member is searched twice or missed.  Members 0 and 3
+    overflow in every step here; all six end where the oracle says."""
+    setups = [ki.equilibrium_setup(n=2000 + 500 * k, seed=140 + k) for k in range(6)]
+    arrays = [ki.initial_state(q) for q in setups]
+    sims = [gpu_sim(q, a, FP32, edge_cap=(8 if k in (0, 3) else 0), search_kernel=search)
+            for k, (q, a) in enumerate(zip(setups, arrays))]
+    g = kmc.Group(sims)
+    for x in sims:
+        g.budget(x, 6)
+    g.step(6)
+    g.sync()
+    for q, a, x in zip(setups, arrays, sims):
+        assert g.steps_left(x) == 0
+        st = oracle.State(a)
+        oc, _ = oracle.run(q, st, 0, 6)
+        assert_same_counts(x.counts(), oc)
+        assert_same_state(x, st)
+    g.close()
+
+
 def test_group_member_whose_pair_buffer_overflows_catches_up_at_sync():
     """A member whose candidate-pair buffer overflows in a group step is skipped by the
     group's later steps; the group's sync grows its buffer and runs the steps it
