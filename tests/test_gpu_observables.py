@@ -138,7 +138,8 @@ def test_bounded_scan_wait_reports_a_timeout_and_the_device_stays_usable():
     test flag makes them wait for a status word that is never written: each wait runs
     out after about a second, the step is abandoned with the timeout status, sim_sync
     returns KMC_ETIMEOUT, and the next simulation on the device runs as usual."""
-    s = ki.equilibrium_setup(n=20000, seed=55)
+    # a tube whose key space spans many scan tiles (8192 keys each), so that tiles wait
+    s = ki.piston_setup(n=1 << 17, seed=55, profile_bins=0, profile_every=0)
     arrays = ki.initial_state(s)
     p = kmc.params_from_setup(s, precision=kmc.KMC_FP64, flags=kmc.KMC_FLAG_SCAN_WAIT_TEST)
     sim = kmc.Simulation(p, arrays)
@@ -151,6 +152,7 @@ def test_bounded_scan_wait_reports_a_timeout_and_the_device_stays_usable():
     st = oracle.State(arrays)
     oracle.run(s, st, 0, 3)
     ok = kmc.Simulation(kmc.params_from_setup(s, precision=kmc.KMC_FP64), arrays).step(3).sync()
+    assert ok.counts()[0]["cells"] > 4 * 8192  # several scan tiles, so tiles did wait
     got, _ = ok.state()
     for k in range(6):
         assert np.array_equal(got[k], st.a[k])
