@@ -343,8 +343,8 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_search_cell(Batch B) {
   for (int k = 0; k < B.nsims; ++k) {
     SimDev& s = *B.sims[k];
     if (!sim_scheduled(s) || s.d.grid.mode != KMC_SEARCH_CELL) continue;
-    const uint32_t first = (gwarp + nwarps - base % nwarps) % nwarps;
-    base += s.d.grid.nkeys;
+    const uint32_t first = (gwarp + nwarps - base) % nwarps;
+    base = (base + s.d.grid.nkeys % nwarps) % nwarps;
     if (!__all_sync(0xFFFFFFFFu, sim_active(s))) continue;
     const Grid& G = s.d.grid;
     const int nx = G.nc[0], ny = G.nc[1], nz = G.nc[2];
@@ -666,8 +666,8 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) k_search_cell32(Batch B) {
   for (int k = 0; k < B.nsims; ++k) {
     SimDev& s = *B.sims[k];
     if (!sim_scheduled(s) || s.d.grid.mode != KMC_SEARCH_CELL) continue;
-    const uint32_t first = (gwarp + nwarps - base % nwarps) % nwarps;
-    base += s.d.grid.nkeys;
+    const uint32_t first = (gwarp + nwarps - base) % nwarps;
+    base = (base + s.d.grid.nkeys % nwarps) % nwarps;
     // every warp is done with the previous simulation's constants; the status word can
     // change while the search runs, so the block takes one answer
     if (!__syncthreads_and(sim_active(s))) continue;
