@@ -511,6 +511,34 @@ def test_group_mixing_every_variant_equals_each_alone():
         g.close()
 
 
+def test_group_of_more_members_than_a_block_has_threads_is_exact():
+    """The matching kernels read the members' item counts a block's width (256) at a
+    time and carry the dealing position from one chunk of members to the next; a group
+    of 300 small runs (boxes and tubes of uneven size) crosses that boundary.  Every
+    member ends where the oracle says."""
+    setups = []
+    for k in range(300):
+        if k % 2 == 0:
+            setups.append(ki.equilibrium_setup(n=300 + (k * 37) % 500, seed=2000 + k))
+        else:
+            setups.append(ki.piston_setup(n=2000 + (k * 37) % 2000, seed=2000 + k,
+                                          profile_bins=0, profile_every=0))
+    arrays = [ki.initial_state(q) for q in setups]
+    sims = [gpu_sim(q, a, FP32) for q, a in zip(setups, arrays)]
+    g = kmc.Group(sims)
+    for x in sims:
+        g.budget(x, 4)
+    g.step(4)
+    g.sync()
+    for q, a, x in zip(setups, arrays, sims):
+        assert g.steps_left(x) == 0
+        st = oracle.State(a)
+        oc, _ = oracle.run(q, st, 0, 4)
+        assert_same_counts(x.counts(), oc)
+        assert_same_state(x, st)
+    g.close()
+
+
 @pytest.mark.parametrize("search", [kmc.KMC_SEARCH_CELL, kmc.KMC_SEARCH_ROW])
 def test_group_members_overflowing_mid_search_leave_the_others_exact(search):
     """Batch kernels deal the members' cells and pairs to the grid as one sequence.  A
