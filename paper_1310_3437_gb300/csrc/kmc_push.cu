@@ -403,19 +403,34 @@ void launch_add_steps(SimDev* d, uint64_t nsteps, cudaStream_t st) {
 }
 
 // ---- observables ------------------------------------------------------------ //
+// The state in id order (x, y, z, vx, vy, vz as n binary64 each, then n last
+// partners).  Written as a gather: k_state_where scatters each particle's sorted
+// position into the last-partner section (one 4-byte store per particle), then
+// k_gather_state walks the ids in order, reads every field from that position and
+// writes all seven arrays with coalesced stores (the last partner replaces the
+// position it was read from).  Scattering the seven fields directly, 8-byte stores
+// to random addresses, made the memory system read back most sectors it wrote.
+__global__ void k_state_where(SimDev* d, void* out) {
+  SimDev& s = *d;
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= s.n) return;
+  uint32_t* ol = (uint32_t*)((double*)out + (size_t)6 * s.n);
+  ol[s.id[s.d.parity][p]] = p;
+}
+
 __global__ void k_gather_state(SimDev* d, void* out) {
   SimDev& s = *d;
-  uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= s.n) return;
-  int par = s.d.parity;
-  uint32_t id = s.id[par][p];
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  const int par = s.d.parity;
   double* o = (double*)out;
-  for (int a = 0; a < 3; ++a) {
-    o[(size_t)a * s.n + id] = s.x[par][a][p];
-    o[(size_t)(3 + a) * s.n + id] = s.v[par][a][p];
-  }
   uint32_t* ol = (uint32_t*)(o + (size_t)6 * s.n);
-  ol[id] = s.last[par][p];
+  const uint32_t p = ol[i];
+  for (int a = 0; a < 3; ++a) {
+    o[(size_t)a * s.n + i] = s.x[par][a][p];
+    o[(size_t)(3 + a) * s.n + i] = s.v[par][a][p];
+  }
+  ol[i] = s.last[par][p];
 }
 
 __global__ void k_gather_partners(SimDev* d, uint32_t* out) {
@@ -508,6 +523,8 @@ void launch_validate(SimDev* d, uint32_t n, uint32_t* bad, cudaStream_t st) {
 }
 
 void launch_gather_state(SimDev* d, uint32_t n, void* out, cudaStream_t st) {
+  if (n == 0) return;
+  k_state_where<<<(n + 255) / 256, 256, 0, st>>>(d, out);
   k_gather_state<<<(n + 255) / 256, 256, 0, st>>>(d, out);
 }
 void launch_gather_partners(SimDev* d, uint32_t n, uint32_t* out, cudaStream_t st) {
