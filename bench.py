@@ -44,6 +44,7 @@ FLOPS_PER_PAIR_TEST = 18
 # algorithmic bytes of the sort per particle: read the binary64 state and id/last
 # (56), write it permuted (56), write the cell-local binary32 mirror (24) and the key (4)
 SORT_BYTES_PER_PARTICLE = 140
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal (fractions against it beside the measured peak)
 
 
 def headline_setup(n: int):
@@ -788,6 +789,10 @@ def run_gpu(args):
         "frac": achieved_tflops / ALU_FP32_PEAK_TFLOPS,
         "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz",
         "traffic": (traffic["dram_bytes_per_particle"] * n) if traffic else None,
+        # the same kernel's HBM fraction beside the ALU one: its measured DRAM bytes per
+        # launch over the launch time, against the measured copy bandwidth
+        "hbm_frac": (traffic["dram_bytes_per_particle"] * n / (slow_ms / 1e3) / 1e9 / pk["hbm_gbs"])
+                    if traffic and slow_ms > 0 else None,
         # what bounds it: the share of issue slots used (ncu, same kernel source)
         "issue_active_pct": traffic.get("issue_active_pct") if traffic else None,
         "flops_per_pair_test": FLOPS_PER_PAIR_TEST,
@@ -802,6 +807,7 @@ def run_gpu(args):
         "kernel": "sort phase (k_count, scans, k_scatter, k_gather)",
         "bound": "hbm", "achieved": sort_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
         "frac": sort_gbs / pk["hbm_gbs"], "peak_source": f"{pk_kind} hbm_gbs",
+        "frac_of_nominal": sort_gbs / HBM_NOMINAL_GBS,
         "bytes_per_particle": SORT_BYTES_PER_PARTICLE, "launch_ms": sort_ms,
     }
     # the counting sort's key space: every key's count is read, its start written and
